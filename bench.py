@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the PPS silhouette hot path on B300.
+
+One step = one pass of the whole hot path over the resident synthetic workload
+"large" (n = 1,000,000, d = 32 FP32, k = 32 Gaussian mixture with Zipf(1.1)
+cluster sizes, per-cluster sigma ~ U[0.5, 3]; t = 256, m0 = 2 ln(5k/delta),
+delta = 0.01):
+  for each metric in (euclidean, cosine, manhattan, canberra on |x|+1 data):
+    Phase 1 (silh_sample_pps) -> Phase 2 (silh_estimate, all n rows) -> silh_global,
+    exact silhouette (silh_exact) of a seeded 100k-row sub-dataset -> silh_global.
+value = PPS silhouette points/s = 4 n / step time (exact leg included in the time).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU runs are independent replicas (one workload per rank, seeds differ),
+so scaling is weak; value sums the points of all ranks over the max-over-ranks
+time.  --impl reference times the FP64 CPU oracle on a bounded sample of the
+same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2607_01993_b300 import synth  # noqa: E402
+
+METRICS = ("euclidean", "cosine", "manhattan", "canberra")
+WORKLOAD = dict(name="large", n=1_000_000, d=32, k=32, t=256.0, delta=0.01, exact_rows=100_000)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def make_workload(seed: int, scale: float = 1.0):
+    w = dict(WORKLOAD)
+    n = int(w["n"] * scale)
+    X, lab, _ = synth.large(seed=seed, n=n, d=w["d"], k=w["k"])
+    rows = synth.seeded_rows(n, min(int(w["exact_rows"] * scale), n), seed=seed + 1000)
+    return X, lab, rows
+
+
+# --------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while it runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0])); mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def cpu_oracle_sample(X, lab, rows_exact, k, t, delta, budget_s=20.0):
+    """Time the FP64 oracle on a bounded sample of one step and extrapolate.
+
+    Per metric: full Phase 1 (all n), Phase 2 on m2 rows, exact on m3 rows of
+    the exact sub-dataset.  Returns (extrapolated step seconds, description).
+    """
+    import oracle
+    n = X.shape[0]
+    Xd = X.astype(np.float64)
+    Xc = synth.abs_shift(X).astype(np.float64)
+    Xs, ls = Xd[rows_exact], lab[rows_exact]
+    Xsc = Xc[rows_exact]
+    m2, m3 = 8192, 1024
+    r2 = synth.seeded_rows(n, m2, seed=7)
+    r3 = synth.seeded_rows(len(rows_exact), m3, seed=8)
+    total = 0.0
+    parts = []
+    for metric in METRICS:
+        Xm, Xsm = (Xc, Xsc) if metric == "canberra" else (Xd, Xs)
+        t0 = time.perf_counter()
+        smp = oracle.sample_pps(Xm, lab, k, metric, t=t, delta=delta, seed=0)
+        t1 = time.perf_counter()
+        oracle.estimate(Xm, lab, k, metric, smp.offsets, smp.idx, smp.ps, rows=r2)
+        t2 = time.perf_counter()
+        oracle.exact(Xsm, ls, k, metric, rows=r3)
+        t3 = time.perf_counter()
+        step = (t1 - t0) + (t2 - t1) * n / m2 + (t3 - t2) * len(rows_exact) / m3
+        total += step
+        parts.append(f"{metric}: phase1 {t1 - t0:.2f}s full, phase2 {m2} rows {t2 - t1:.2f}s, "
+                     f"exact {m3} rows {t3 - t2:.2f}s")
+    desc = (f"FP64 oracle (C, OpenMP) on n={n}: Phase 1 in full, Phase 2 on {m2} seeded rows, "
+            f"exact on {m3} of {len(rows_exact)} rows, per metric; Phase 2 and exact extrapolated "
+            f"linearly in rows to the full step. " + "; ".join(parts))
+    return total, desc
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2607_01993_b300 import silh
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    silh.load()
+    w = WORKLOAD
+    X, lab, rows_ex = make_workload(seed=1 + rank)
+    n, d, k = X.shape[0], X.shape[1], w["k"]
+    Xc = synth.abs_shift(X)
+    sizes = np.bincount(lab, minlength=k)
+    # host (pinned) copies for the end-to-end leg
+    h = {
+        "X": torch.from_numpy(X).pin_memory(), "Xc": torch.from_numpy(Xc).pin_memory(),
+        "lab": torch.from_numpy(lab).pin_memory(),
+        "Xs": torch.from_numpy(np.ascontiguousarray(X[rows_ex])).pin_memory(),
+        "Xsc": torch.from_numpy(np.ascontiguousarray(Xc[rows_ex])).pin_memory(),
+        "ls": torch.from_numpy(np.ascontiguousarray(lab[rows_ex])).pin_memory(),
+    }
+    g = {key: v.to(dev) for key, v in h.items()}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    est_ms = {m: [] for m in METRICS}
+    leg_ms = {m: {"phase1": [], "phase2": [], "exact": []} for m in METRICS}
+    outs = {}
+    info = {}
+
+    def step(bufs, seed, record):
+        results = {}
+        for mi, metric in enumerate(METRICS):
+            Xm = bufs["Xc"] if metric == "canberra" else bufs["X"]
+            Xsm = bufs["Xsc"] if metric == "canberra" else bufs["Xs"]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            smp = silh.silh_sample_pps(Xm, bufs["lab"], k, metric, t=w["t"], delta=w["delta"],
+                                       seed=seed, clustering_id=mi)
+            ev[1].record(stream)
+            s = silh.silh_estimate(Xm, bufs["lab"], k, smp, metric)
+            ev[2].record(stream)
+            gm = silh.silh_global(s)
+            se = silh.silh_exact(Xsm, bufs["ls"], k, metric)
+            ge = silh.silh_global(se)
+            ev[3].record(stream)
+            results[metric] = (s, gm, ge, smp.size)
+            if record:
+                info.setdefault("sample_size", {})[metric] = smp.size
+                leg_ms[metric]["_ev"] = leg_ms[metric].get("_ev", []) + [ev]
+        return results
+
+    # warm-up
+    for i in range(args.warmup):
+        step(g, seed=i, record=False)
+    torch.cuda.synchronize()
+
+    # timed region: device time per step with CUDA events, L2 flushed between steps
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = silh.kernel_launches()
+    step_ev = []
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs = step(g, seed=100 + i, record=True)
+            e1.record(stream)
+            step_ev.append((e0, e1))
+        torch.cuda.synchronize()
+    launches = silh.kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    for metric in METRICS:
+        for ev in leg_ms[metric].pop("_ev"):
+            leg_ms[metric]["phase1"].append(ev[0].elapsed_time(ev[1]))
+            leg_ms[metric]["phase2"].append(ev[1].elapsed_time(ev[2]))
+            leg_ms[metric]["exact"].append(ev[2].elapsed_time(ev[3]))
+    ms = float(np.sum(step_ms)) / args.steps
+
+    # end-to-end through the public API from pinned host buffers
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        bufs = {key: v.to(dev, non_blocking=True) for key, v in h.items()}
+        res = step(bufs, seed=200 + i, record=False)
+        host_out = [(r[0].cpu(), r[1].cpu(), r[2].cpu()) for r in res.values()]
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = sum(v.numel() * v.element_size() for v in h.values())
+    d2h = sum(o[0].numel() * 4 + 16 for o in host_out)
+    del host_out
+
+    times = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    ms_max, e2e_max = float(times[0]), float(times[1])
+    return dict(ms=ms_max, e2e_s=e2e_max, step_ms=step_ms, legs=leg_ms, info=info,
+                launches=int(launches), clocks=clk.summary(), h2d=h2d, d2h=d2h, n=n, d=d, k=k,
+                sizes=sizes, rows_ex=len(rows_ex), X=X, lab=lab, rows=rows_ex)
+
+
+def dist_evals(res, t_step_samples):
+    """Distance evaluations of one step: Phase 1 ~ n * m0 pairs (W) plus the
+    same pairs again for gamma, Phase 2 n |S|, exact m^2 (per metric)."""
+    n, k = res["n"], res["k"]
+    m0 = 2 * math.log(5 * k / WORKLOAD["delta"])
+    total = 0.0
+    for metric in METRICS:
+        S = res["info"]["sample_size"][metric]
+        total += n * m0 + n * S + res["rows_ex"] ** 2
+    return total
+
+
+def roofline(res, peaks, peak_kind):
+    """Dominant kernel: the Phase-2 sweep of the metric with the longest leg.
+
+    Algorithmic FP32-pipe work per pair (d = 32 coordinates): euclidean 2d
+    (sub, fma) + sqrt, cosine d (fma), manhattan 2d (sub, add), canberra 3.5d
+    FP32 + d/2 reciprocals; the reported unit is FP32 lane-operations.
+    """
+    d = res["d"]
+    per_pair = {"euclidean": 2 * d + 2, "cosine": d + 3, "manhattan": 2 * d + 1,
+                "canberra": 3.5 * d + 1}
+    mean_p2 = {m: float(np.mean(res["legs"][m]["phase2"])) for m in METRICS}
+    dom = max(mean_p2, key=mean_p2.get)
+    S = res["info"]["sample_size"][dom]
+    ops = res["n"] * S * per_pair[dom]
+    achieved = ops / (mean_p2[dom] * 1e-3) / 1e9          # Gop/s
+    clock = peaks.get("sm_max_mhz", 2032.0)
+    peak = 148 * 128 * clock * 1e6 / 1e9                   # FP32 lanes x clock
+    return dom, {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
+                 "unit": "Gop/s", "frac": round(achieved / peak, 4), "traffic": None,
+                 "kernel": f"k_sweep ({dom}, Phase 2)",
+                 "peak_source": f"148 SMs x 128 FP32 lanes x {clock:.0f} MHz ({peak_kind} clock)"}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="silh", choices=["silh", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    peaks, peak_kind = _peaks()
+    w = WORKLOAD
+    config = {"workload": f"large: n={w['n']}, d={w['d']} FP32, k={w['k']} Zipf(1.1) Gaussian "
+                          f"mixture; t={int(w['t'])}, delta={w['delta']}; 4 metrics; exact on "
+                          f"{w['exact_rows']}-row subset",
+              "n": w["n"], "d": w["d"], "k": w["k"], "t": w["t"],
+              "metrics": list(METRICS), "l2": "flushed (256 MB write) between timed steps",
+              "parallelism": f"replicas x{world}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        X, lab, rows = make_workload(seed=1)
+        import oracle
+        ts = []
+        desc = ""
+        for _ in range(args.steps):
+            t_step, desc = cpu_oracle_sample(X, lab, rows, w["k"], w["t"], w["delta"])
+            ts.append(t_step)
+        t_mean = float(np.mean(ts))
+        value = 4 * w["n"] / t_mean
+        line = {"impl": "reference", "metric": "PPS silhouette points/s", "value": value,
+                "unit": "points/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_mean * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.nthreads(),
+                                 "kind": "oracle", "sample": desc},
+                "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = run_gpu(args, rank, world, local_rank)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    pts = 4 * res["n"] * world
+    value = pts / (res["ms"] * 1e-3)
+    evals = dist_evals(res, None) * world
+    dom, roof = roofline(res, peaks, peak_kind)
+    legs = {m: {leg: round(float(np.mean(v)), 3) for leg, v in res["legs"][m].items()}
+            for m in METRICS}
+    line = {"metric": "PPS silhouette points/s", "value": round(value, 1), "unit": "points/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(res["ms"], 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+            "dist_evals_per_s": round(evals / (res["ms"] * 1e-3), 1),
+            "legs_ms": legs, "sample_size": res["info"]["sample_size"],
+            "roofline": roof,
+            "e2e": {"value": round(pts / res["e2e_s"], 1), "unit": "points/s",
+                    "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
+            "gpu_launches": res["launches"], "clocks": res["clocks"]}
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        t_cpu, desc = cpu_oracle_sample(res["X"], res["lab"], res["rows"], res["k"], WORKLOAD["t"],
+                                        WORKLOAD["delta"])
+        line["cpu_baseline"] = {"value": round(4 * res["n"] / t_cpu, 1), "unit": "points/s",
+                                "cores": oracle.nthreads(), "kind": "oracle", "sample": desc}
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,156 @@
+/*
+ * silh.h -- C ABI of the B300 PPS silhouette library (libsilh.so).
+ *
+ * Implements the silh-pps-all estimator of Altieri, Pietracaprina, Pucci and
+ * Vandin, "Scalable and Distributed Silhouette Approximation":
+ *   Problem 1 (Sec. 4.1):  estimate s(e) for every element e of V;
+ *   Problem 2 (Sec. 4.2):  estimate the silhouette s(C) of the clustering;
+ *   Algorithm 1:           Phase 1 = PPS sampling, Phase 2 = estimation;
+ *   Eq. 1-3:               exact silhouette of an element / of a clustering.
+ *
+ * Conventions shared by every entry point
+ *   - Data X: n rows of d coordinates, row-major with a leading dimension of
+ *     ld elements (ld >= d), in device memory, FP32 or BF16 (silh_dtype).
+ *     Rows and the base pointer must be 16-byte aligned (ld * element size a
+ *     multiple of 16 bytes).
+ *   - labels: int32 device array of n cluster ids in [0, k).  A clustering is a
+ *     partition of V into k >= 2 non-empty clusters (Sec. 2).
+ *   - Every pointer argument is device memory owned by the caller, unless the
+ *     comment says host.  The library allocates only temporary scratch
+ *     (stream-ordered, released before the call's work completes on stream) and
+ *     never frees caller memory.
+ *   - stream: a cudaStream_t passed as void*; NULL is the legacy default stream.
+ *     Work is enqueued on it; calls documented as synchronising wait for it.
+ *   - Errors come back as a silh_status; silh_last_error() describes the last
+ *     failure of the calling thread.  No entry point aborts or traps.
+ *   - n < 2^31 and k <= SILH_MAX_K.
+ */
+#ifndef SILH_H
+#define SILH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SILH_MAX_K 8192
+
+/* Distances of Sec. 5.1.1.  d_cos is read as 1 - <x,y>/(|x||y|) (the printed
+ * numerator is garbled); a zero-norm operand gives 1.  Canberra terms with
+ * |x_i| + |y_i| = 0 contribute 0. */
+typedef enum {
+    SILH_EUCLIDEAN = 0,
+    SILH_COSINE = 1,
+    SILH_MANHATTAN = 2,
+    SILH_CANBERRA = 3
+} silh_metric;
+
+/* Storage type of X. */
+typedef enum { SILH_F32 = 0, SILH_BF16 = 1 } silh_dtype;
+
+/* Arithmetic of the Phase-2 / exact distance evaluation.
+ *   SILH_PREC_FP32   FP32 on CUDA cores (reference precision, |ds| <= 1e-5);
+ *   SILH_PREC_TF32   Euclidean/cosine inner products on tensor cores (TF32);
+ *   SILH_PREC_3XTF32 split-TF32 (hi*hi + hi*lo + lo*hi) on tensor cores.
+ * Manhattan and Canberra always run on CUDA cores in FP32. */
+typedef enum {
+    SILH_PREC_FP32 = 0,
+    SILH_PREC_TF32 = 1,
+    SILH_PREC_3XTF32 = 2
+} silh_prec;
+
+typedef enum {
+    SILH_OK = 0,
+    SILH_EINVAL = -1,    /* bad argument or clustering */
+    SILH_ENOMEM = -2,    /* scratch allocation failed */
+    SILH_ECUDA = -3,     /* CUDA runtime error (see silh_last_error) */
+    SILH_ECAPACITY = -4, /* caller's sample buffers too small; size holds need */
+    SILH_ETIMEOUT = -5   /* a bounded device wait gave up */
+} silh_status;
+
+/* The sample set S = union of F_Cj (Algorithm 1, Phase 1), as per-cluster
+ * lists.  All arrays are device memory owned by the caller:
+ *   sizes[k]        |Cj| (written by silh_sample_pps)
+ *   offsets[k+1]    F_Cj occupies positions offsets[j] .. offsets[j+1]-1
+ *   idx[cap]        element ids (rows of X), ascending within each cluster
+ *   p[cap]          inclusion probability p_e of each sampled element (FP64)
+ * size is the number of sampled elements |S| (host field).  cap = n is always
+ * enough. */
+typedef struct silh_sample {
+    int32_t k;
+    int64_t *sizes;
+    int64_t *offsets;
+    int32_t *idx;
+    double *p;
+    int64_t cap;
+    int64_t size;
+} silh_sample;
+
+/* Phase 1 of Algorithm 1 (PPS sampling), for every cluster Cj:
+ *   if |Cj| <= t: F_Cj = Cj with p = 1;
+ *   else F0 = Poisson sample of Cj with probability min(1, m0/|Cj|);
+ *        W(e0) = sum_{e' in Cj} d(e0, e') for e0 in F0;
+ *        gamma_e = max(1/|Cj|, max_{e0 in F0} d(e, e0)/W(e0));
+ *        p_e = min(1, t gamma_e); F_Cj = Poisson sample with probabilities p_e.
+ * m0 <= 0 selects m0 = 2 ln(5k/delta) (Algorithm 1).  The uniforms are
+ * Philox4x64-10 with key (seed, 0) and counter (e, stream, clustering_id, 0),
+ * u = (word0 >> 11) 2^-53; stream 0 draws F0, stream 1 draws F.  Distances,
+ * W, gamma and p are evaluated in FP64.
+ * uniform != 0 runs the uniform-sampling variant of Sec. 4.1.3 instead:
+ * p_e = min(1, t/|Cj|) for clusters with |Cj| > t, no initial sample.
+ * Synchronising: returns after the sample is complete (reads |S| to out->size).
+ * Errors: SILH_EINVAL (k < 2, n < 2, d < 1, t <= 0, a label outside [0, k),
+ * an empty cluster, null pointers); SILH_ECAPACITY if out->cap < |S| (out->size
+ * then holds |S|; sizes are written, the lists are not). */
+silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                            const int32_t *labels, int32_t k, silh_metric metric, double t,
+                            double m0, double delta, uint64_t seed, uint32_t clustering_id,
+                            int32_t uniform, silh_sample *out, void *stream);
+
+/* Phase 2 of Algorithm 1 for the listed rows (rows == NULL: all n rows, in
+ * order; else nrows int64 device row ids):
+ *   W_hat_j(e) = sum_{e' in F_Cj} d(e, e') / p_e';
+ *   a_hat = W_hat_C(e)/(|C|-1), b_hat = min_{j != C} W_hat_j(e)/|Cj|,
+ *   s_hat = (b_hat - a_hat)/max(a_hat, b_hat)   (Eq. 8); singleton -> 0.
+ * Outputs are FP32 arrays of nrows entries; a_hat and b_hat may be NULL.
+ * Per-cluster sums are carried in FP64 across column tiles.
+ * S must describe a sample of this clustering (sizes, offsets, idx, p).
+ * Asynchronous.  Errors: SILH_EINVAL for bad sizes/pointers.  A label outside
+ * [0, k) in a listed row yields NaN for that row. */
+silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                          const int32_t *labels, int32_t k, silh_metric metric, silh_prec prec,
+                          const silh_sample *S, const int64_t *rows, int64_t nrows,
+                          float *s_hat, float *a_hat, float *b_hat, void *stream);
+
+/* Exact silhouette (Eq. 1-2) of the listed rows against all n elements:
+ * Phase 2 with F_Cj = Cj and p = 1.  Synchronising (validates labels).
+ * Errors: as silh_sample_pps. */
+silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                       const int32_t *labels, int32_t k, silh_metric metric, silh_prec prec,
+                       const int64_t *rows, int64_t nrows, float *s, float *a, float *b,
+                       void *stream);
+
+/* Mean of n FP32 values in FP64 with a fixed reduction tree (Eq. 3 for exact
+ * s, Eq. 6 for s_hat, Eq. 7 for a row subset).  out: one double, device memory.
+ * Asynchronous.  Errors: SILH_EINVAL if n < 1 or a pointer is NULL. */
+silh_status silh_global(const float *s, int64_t n, double *out, void *stream);
+
+/* Lemma 1: t = ceil((3c/eps^2) ln(5 n k / delta)) with c = 18.  Host-only. */
+double silh_t_from_eps(double eps, double delta, int64_t n, int32_t k);
+
+/* Description of the calling thread's last failure ("" if none). */
+const char *silh_last_error(void);
+
+/* Library version string. */
+const char *silh_version(void);
+
+/* Number of CUDA kernels this library has launched in the calling process
+ * (all threads, all devices) -- for launch accounting in benchmarks. */
+uint64_t silh_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SILH_H */

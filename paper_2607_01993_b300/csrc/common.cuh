@@ -1,0 +1,115 @@
+// Internal helpers of libsilh: status reporting, stream-ordered scratch,
+// the counter-based generator, element loads.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/silh.h"
+
+namespace silh {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const char *fmt, ...);
+silh_status fail(silh_status st, const char *fmt, ...);
+
+#define SILH_CK(call)                                                               \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            st = ::silh::fail(SILH_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, \
+                              cudaGetErrorString(e_));                              \
+            goto done;                                                              \
+        }                                                                           \
+    } while (0)
+
+#define SILH_REQ(cond, ...)                                   \
+    do {                                                      \
+        if (!(cond)) {                                        \
+            st = ::silh::fail(SILH_EINVAL, __VA_ARGS__);      \
+            goto done;                                        \
+        }                                                     \
+    } while (0)
+
+// --------------------------------------------------------------- scratch
+
+// Stream-ordered scratch.  Every block is released with cudaFreeAsync on the
+// same stream when the Scratch object goes out of scope, so the memory returns
+// to the pool only after the kernels that use it have run.
+struct Scratch {
+    cudaStream_t stream;
+    std::vector<void *> blocks;
+    explicit Scratch(cudaStream_t s) : stream(s) {}
+    ~Scratch() {
+        for (void *p : blocks) cudaFreeAsync(p, stream);
+    }
+    template <class T>
+    cudaError_t alloc(T **out, size_t count) {
+        void *p = nullptr;
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        bytes = (bytes + 255) & ~size_t(255);
+        cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+        if (e != cudaSuccess) return e;
+        blocks.push_back(p);
+        *out = static_cast<T *>(p);
+        return cudaSuccess;
+    }
+};
+
+// Keep freed scratch cached in the device's default pool between calls.
+void ensure_pool_retains(int device);
+
+// ----------------------------------------------------------- Philox4x64-10
+
+// Salmon et al., "Parallel random numbers: as easy as 1, 2, 3" (SC'11):
+// 4x64 variant, 10 rounds.  Round: products of words 0 and 2 with the two
+// multipliers; new words = (hi(w2*M1) ^ w1 ^ k0, lo(w2*M1), hi(w0*M0) ^ w3 ^ k1,
+// lo(w0*M0)); the key advances by two Weyl increments between rounds.
+__device__ __forceinline__ uint64_t philox_word0(uint64_t c0, uint64_t c1, uint64_t c2,
+                                                 uint64_t c3, uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
+        uint64_t lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
+        uint64_t n0 = hi1 ^ c1 ^ k0;
+        uint64_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += W0; k1 += W1;
+    }
+    return c0;
+}
+
+// U(seed, stream, cid, e) in [0, 1): key (seed, 0), counter (e, stream, cid, 0),
+// top 53 bits of the first output word.
+__device__ __forceinline__ double uniform01(uint64_t seed, uint64_t stream, uint64_t cid,
+                                            uint64_t e) {
+    uint64_t w = philox_word0(e, stream, cid, 0, seed, 0);
+    return (double)(w >> 11) * 0x1.0p-53;
+}
+
+// ----------------------------------------------------------------- loads
+
+template <class T>
+__device__ __forceinline__ float to_f32(T v);
+template <>
+__device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+
+inline int ceil_div_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Number of kernels this library has launched in the process (all threads).
+void count_launches(int nlaunch);
+
+}  // namespace silh

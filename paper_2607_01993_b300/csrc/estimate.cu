@@ -1,0 +1,438 @@
+// Phase 2 of Algorithm 1 (W_hat, a_hat, b_hat, s_hat), the exact silhouette
+// (Eq. 1-2, the same sweep with F_Cj = Cj and p = 1) and the FP64 global mean
+// (Eq. 3 / Eq. 6).
+//
+// Column operand: the sampled rows gathered into a dense cluster-major matrix
+// Y (m x D floats, D = d rounded up, zero padded) with per-column weights
+// wY = 1/p.  A CTA owns a tile of rows and streams the columns of one cluster
+// after another through shared memory, so the per-row state is constant:
+// the running FP32 sum of the current column chunk, the FP64 sum of the
+// current cluster, the own-cluster weight and the running minimum for b_hat.
+#include <cfloat>
+#include <cmath>
+
+#include "kernels.cuh"
+
+namespace silh {
+
+int padded_dim(int d) {
+    if (d <= 8) return 8;
+    if (d <= 16) return 16;
+    if (d <= 32) return 32;
+    if (d <= 64) return 64;
+    return 128;
+}
+
+namespace {
+
+// ------------------------------------------------------------- gather
+
+template <class T>
+__global__ void k_gather(const T *__restrict__ X, int d, int64_t ld, const int32_t *__restrict__ idx,
+                         const double *__restrict__ p, int64_t m, int D, int metric,
+                         float *__restrict__ Y, float *__restrict__ wY) {
+    int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x & 31;
+    if (i >= m) return;
+    int64_t e = idx ? idx[i] : i;
+    const T *x = X + e * ld;
+    float scale = 1.0f;
+    if (metric == SILH_COSINE) {
+        double s = 0.0;
+        for (int c = lane; c < d; c += 32) {
+            double v = (double)to_f32<T>(x[c]);
+            s += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        scale = s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.0f;
+    }
+    for (int c = lane; c < D; c += 32) Y[i * D + c] = (c < d) ? to_f32<T>(x[c]) * scale : 0.0f;
+    if (lane == 0) wY[i] = p ? (float)(1.0 / p[i]) : 1.0f;
+}
+
+// ------------------------------------------------------- pair kernels
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Distance of one row (registers) to one column (shared memory, float4).
+// Euclidean: sqrt(sum (x - y)^2).  Manhattan: sum |x - y|.  Cosine: rows and
+// columns are unit-normalised, d = clamp(1 - <x,y>, 0, 2).  Canberra: terms
+// |x - y| / (|x| + |y|) taken two at a time as (n1 d2 + n2 d1)/(d1 d2) so that
+// one reciprocal serves two coordinates; |x| carries +1e-30 so an all-zero
+// coordinate pair contributes 0 instead of 0/0.
+template <int METRIC, int D>
+__device__ __forceinline__ float pair_dist(const float (&x)[D], const float4 *__restrict__ y4) {
+    float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < D / 4; ++q) {
+        float4 y = y4[q];
+        float ys[4] = {y.x, y.y, y.z, y.w};
+        if (METRIC == SILH_EUCLIDEAN) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float t = x[4 * q + c] - ys[c];
+                if (c & 1) acc1 = fmaf(t, t, acc1); else acc0 = fmaf(t, t, acc0);
+            }
+        } else if (METRIC == SILH_MANHATTAN) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float t = fabsf(x[4 * q + c] - ys[c]);
+                if (c & 1) acc1 += t; else acc0 += t;
+            }
+        } else if (METRIC == SILH_COSINE) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c & 1) acc1 = fmaf(x[4 * q + c], ys[c], acc1);
+                else acc0 = fmaf(x[4 * q + c], ys[c], acc0);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; c += 2) {
+                float n1 = fabsf(x[4 * q + c] - ys[c]);
+                float n2 = fabsf(x[4 * q + c + 1] - ys[c + 1]);
+                float d1 = fabsf(x[4 * q + c]) + 1e-30f + fabsf(ys[c]);
+                float d2 = fabsf(x[4 * q + c + 1]) + 1e-30f + fabsf(ys[c + 1]);
+                float num = fmaf(n2, d1, n1 * d2);
+                float den = d1 * d2;
+                if (c == 0) acc0 = fmaf(num, rcp_approx(den), acc0);
+                else acc1 = fmaf(num, rcp_approx(den), acc1);
+            }
+        }
+    }
+    float a = acc0 + acc1;
+    if (METRIC == SILH_EUCLIDEAN) return sqrt_approx(a);
+    if (METRIC == SILH_COSINE) return fminf(fmaxf(1.0f - a, 0.0f), 2.0f);
+    return a;
+}
+
+constexpr int kThreads = 128;
+
+template <class T, int METRIC, int D, int RPT, int BN>
+__global__ void __launch_bounds__(kThreads)
+k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__restrict__ labels,
+        int k, const int64_t *__restrict__ sizes, const int64_t *__restrict__ offsets,
+        const float *__restrict__ Y, const float *__restrict__ wY, const int64_t *__restrict__ rows,
+        int64_t nrows, float *__restrict__ s_out, float *__restrict__ a_out,
+        float *__restrict__ b_out) {
+    __shared__ __align__(16) float sh_y[BN * D];
+    __shared__ float sh_w[BN];
+    constexpr int BM = kThreads * RPT;
+    float x[RPT][D];
+    int own[RPT];
+    double wown[RPT], bmin[RPT];
+    int64_t r0 = (int64_t)blockIdx.x * BM;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        int64_t rr = r0 + threadIdx.x + r * kThreads;
+        int64_t e = (rr < nrows) ? (rows ? rows[rr] : rr) : -1;
+        own[r] = -1;
+        if (e >= 0 && e < n) {
+            int l = labels[e];
+            own[r] = (l >= 0 && l < k) ? l : -2;
+        }
+        float sc = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            x[r][c] = (e >= 0 && e < n && c < d) ? to_f32<T>(X[e * ld + c]) : 0.f;
+            sc += x[r][c] * x[r][c];
+        }
+        if (METRIC == SILH_COSINE) {
+            float inv = sc > 0.f ? rsqrtf(sc) : 0.f;
+#pragma unroll
+            for (int c = 0; c < D; ++c) x[r][c] *= inv;
+        }
+        wown[r] = 0.0;
+        bmin[r] = INFINITY;
+    }
+    for (int j = 0; j < k; ++j) {
+        int64_t cs = offsets[j], ce = offsets[j + 1];
+        double accd[RPT];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) accd[r] = 0.0;
+        for (int64_t cb = cs; cb < ce; cb += BN) {
+            int nb = (int)min((int64_t)BN, ce - cb);
+            __syncthreads();
+            const float4 *src = reinterpret_cast<const float4 *>(Y + cb * D);
+            float4 *dst = reinterpret_cast<float4 *>(sh_y);
+            for (int q = threadIdx.x; q < nb * (D / 4); q += kThreads) dst[q] = src[q];
+            for (int q = threadIdx.x; q < BN; q += kThreads) sh_w[q] = (q < nb) ? wY[cb + q] : 0.f;
+            __syncthreads();
+            float accf[RPT];
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) accf[r] = 0.f;
+            for (int col = 0; col < nb; ++col) {
+                const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * D);
+                float w = sh_w[col];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) accf[r] = fmaf(w, pair_dist<METRIC, D>(x[r], y4), accf[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) accd[r] += (double)accf[r];
+        }
+        double csz = (double)sizes[j];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            if (j == own[r]) wown[r] = accd[r];
+            else bmin[r] = fmin(bmin[r], accd[r] / csz);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        int64_t rr = r0 + threadIdx.x + r * kThreads;
+        if (rr >= nrows) continue;
+        float sv, av, bv;
+        if (own[r] < 0) {
+            sv = av = bv = NAN;
+        } else {
+            int64_t nc = sizes[own[r]];
+            double a = (nc > 1) ? wown[r] / (double)(nc - 1) : 0.0;
+            double b = bmin[r];
+            double mx = fmax(a, b);
+            double s = (nc > 1 && mx > 0.0) ? (b - a) / mx : 0.0;
+            sv = (float)s; av = (float)a; bv = (float)b;
+        }
+        s_out[rr] = sv;
+        if (a_out) a_out[rr] = av;
+        if (b_out) b_out[rr] = bv;
+    }
+}
+
+template <class T, int METRIC, int D>
+void launch_sweep(cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
+                  const int32_t *labels, int k, const int64_t *sizes, const int64_t *offsets,
+                  const float *Y, const float *wY, const int64_t *rows, int64_t nrows, float *s,
+                  float *a, float *b) {
+    constexpr int RPT = (D <= 32) ? 2 : 1;
+    constexpr int BN = (D <= 32) ? 64 : 32;
+    int grid = (int)((nrows + kThreads * RPT - 1) / (kThreads * RPT));
+    k_sweep<T, METRIC, D, RPT, BN><<<grid, kThreads, 0, stream>>>(
+        X, d, ld, n, labels, k, sizes, offsets, Y, wY, rows, nrows, s, a, b); count_launches(1);
+}
+
+template <class T, int METRIC>
+void launch_sweep_d(int D, cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
+                    const int32_t *labels, int k, const int64_t *sizes, const int64_t *offsets,
+                    const float *Y, const float *wY, const int64_t *rows, int64_t nrows, float *s,
+                    float *a, float *b) {
+#define SILH_SWEEP_D(DD)                                                                  \
+    case DD:                                                                              \
+        launch_sweep<T, METRIC, DD>(stream, X, d, ld, n, labels, k, sizes, offsets, Y, wY, \
+                                    rows, nrows, s, a, b);                                \
+        break;
+    switch (D) {
+        SILH_SWEEP_D(8)
+        SILH_SWEEP_D(16)
+        SILH_SWEEP_D(32)
+        SILH_SWEEP_D(64)
+        SILH_SWEEP_D(128)
+        default: break;
+    }
+#undef SILH_SWEEP_D
+}
+
+template <class T>
+void launch_sweep_m(int metric, int D, cudaStream_t stream, const T *X, int d, int64_t ld,
+                    int64_t n, const int32_t *labels, int k, const int64_t *sizes,
+                    const int64_t *offsets, const float *Y, const float *wY, const int64_t *rows,
+                    int64_t nrows, float *s, float *a, float *b) {
+    switch (metric) {
+        case SILH_EUCLIDEAN:
+            launch_sweep_d<T, SILH_EUCLIDEAN>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
+                                              Y, wY, rows, nrows, s, a, b);
+            break;
+        case SILH_COSINE:
+            launch_sweep_d<T, SILH_COSINE>(D, stream, X, d, ld, n, labels, k, sizes, offsets, Y,
+                                           wY, rows, nrows, s, a, b);
+            break;
+        case SILH_MANHATTAN:
+            launch_sweep_d<T, SILH_MANHATTAN>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
+                                              Y, wY, rows, nrows, s, a, b);
+            break;
+        default:
+            launch_sweep_d<T, SILH_CANBERRA>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
+                                             Y, wY, rows, nrows, s, a, b);
+            break;
+    }
+}
+
+// ------------------------------------------------------------- global
+
+constexpr int kSumThreads = 256;
+
+__global__ void k_sum_partial(const float *__restrict__ s, int64_t n, double *__restrict__ part) {
+    __shared__ double sh[kSumThreads];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kSumThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kSumThreads)
+        acc += (double)s[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = kSumThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_final(const double *__restrict__ part, int np, int64_t n,
+                            double *__restrict__ out) {
+    __shared__ double sh[kSumThreads];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < np; i += kSumThreads) acc += part[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = kSumThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0] / (double)n;
+}
+
+}  // namespace
+
+silh_status gather_columns(const void *X, silh_dtype dtype, int32_t d, int64_t ld,
+                           const int32_t *idx, const double *p, int64_t m, int D, int metric,
+                           float *Y, float *wY, cudaStream_t stream) {
+    silh_status st = SILH_OK;
+    if (m > 0) {
+        int grid = ceil_div_i(m, 8);
+        if (dtype == SILH_F32)
+            k_gather<float><<<grid, 256, 0, stream>>>((const float *)X, d, ld, idx, p, m, D,
+                                                      metric, Y, wY);
+        else
+            k_gather<__nv_bfloat16><<<grid, 256, 0, stream>>>((const __nv_bfloat16 *)X, d, ld,
+                                                              idx, p, m, D, metric, Y, wY);
+        count_launches(1);
+    }
+    SILH_CK(cudaGetLastError());
+done:
+    return st;
+}
+
+silh_status phase2_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                         const int32_t *labels, int32_t k, int metric, int prec,
+                         const int64_t *sizes, const int64_t *offsets, const float *Y,
+                         const float *wY, int64_t m, int D, const int64_t *rows, int64_t nrows,
+                         float *s, float *a, float *b, cudaStream_t stream) {
+    silh_status st = SILH_OK;
+    (void)prec;
+    (void)m;
+    if (nrows > 0) {
+        if (dtype == SILH_F32)
+            launch_sweep_m<float>(metric, D, stream, (const float *)X, d, ld, n, labels, k, sizes,
+                                  offsets, Y, wY, rows, nrows, s, a, b);
+        else
+            launch_sweep_m<__nv_bfloat16>(metric, D, stream, (const __nv_bfloat16 *)X, d, ld, n,
+                                          labels, k, sizes, offsets, Y, wY, rows, nrows, s, a, b);
+    }
+    SILH_CK(cudaGetLastError());
+done:
+    return st;
+}
+
+}  // namespace silh
+
+using namespace silh;
+
+static silh_status check_data_args(const void *X, silh_dtype dtype, int64_t n, int32_t d,
+                                   int64_t ld, const int32_t *labels, int32_t k,
+                                   silh_metric metric, silh_prec prec) {
+    if (!X || !labels) return fail(SILH_EINVAL, "null pointer argument");
+    if (n < 2 || n >= (int64_t(1) << 31)) return fail(SILH_EINVAL, "n must be in [2, 2^31)");
+    if (d < 1 || d > 128 || ld < d) return fail(SILH_EINVAL, "need 1 <= d <= 128 and ld >= d");
+    if (k < 2 || k > SILH_MAX_K) return fail(SILH_EINVAL, "k must be in [2, %d]", SILH_MAX_K);
+    if (metric < SILH_EUCLIDEAN || metric > SILH_CANBERRA) return fail(SILH_EINVAL, "unknown metric");
+    if (dtype != SILH_F32 && dtype != SILH_BF16) return fail(SILH_EINVAL, "unknown dtype");
+    if (prec < SILH_PREC_FP32 || prec > SILH_PREC_3XTF32) return fail(SILH_EINVAL, "unknown precision");
+    return SILH_OK;
+}
+
+extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n, int32_t d,
+                                     int64_t ld, const int32_t *labels, int32_t k,
+                                     silh_metric metric, silh_prec prec, const silh_sample *S,
+                                     const int64_t *rows, int64_t nrows, float *s_hat,
+                                     float *a_hat, float *b_hat, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    silh_status st = check_data_args(X, dtype, n, d, ld, labels, k, metric, prec);
+    if (st != SILH_OK) return st;
+    int dev = 0;
+    int D = padded_dim(d);
+    Scratch sc(stream);
+    float *Y = nullptr, *wY = nullptr;
+    int64_t m = 0;
+    SILH_REQ(S && S->k == k && S->sizes && S->offsets, "sample missing or k mismatch");
+    m = S->size;
+    SILH_REQ(m >= 0 && m <= S->cap && (m == 0 || (S->idx && S->p)), "bad sample size");
+    SILH_REQ(s_hat, "s_hat is null");
+    if (rows == nullptr) nrows = n;
+    SILH_REQ(nrows >= 0, "nrows < 0");
+    SILH_CK(cudaGetDevice(&dev));
+    ensure_pool_retains(dev);
+    SILH_CK(sc.alloc(&Y, (size_t)m * D));
+    SILH_CK(sc.alloc(&wY, (size_t)m));
+    st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, Y, wY, stream);
+    if (st != SILH_OK) goto done;
+    st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, S->sizes, S->offsets, Y, wY, m,
+                      D, rows, nrows, s_hat, a_hat, b_hat, stream);
+done:
+    return st;
+}
+
+extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, int32_t d,
+                                  int64_t ld, const int32_t *labels, int32_t k, silh_metric metric,
+                                  silh_prec prec, const int64_t *rows, int64_t nrows, float *s,
+                                  float *a, float *b, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    silh_status st = check_data_args(X, dtype, n, d, ld, labels, k, metric, prec);
+    if (st != SILH_OK) return st;
+    int dev = 0;
+    int D = padded_dim(d);
+    Scratch sc(stream);
+    std::vector<int64_t> h_sizes, h_coff;
+    int64_t *sizes = nullptr, *coff = nullptr;
+    int32_t *order = nullptr;
+    float *Y = nullptr, *wY = nullptr;
+    SILH_REQ(s, "s is null");
+    if (rows == nullptr) nrows = n;
+    SILH_REQ(nrows >= 0, "nrows < 0");
+    SILH_CK(cudaGetDevice(&dev));
+    ensure_pool_retains(dev);
+    SILH_CK(sc.alloc(&sizes, (size_t)k));
+    st = cluster_sort(labels, n, k, sc, stream, sizes, &coff, &order, h_sizes, h_coff);
+    if (st != SILH_OK) goto done;
+    SILH_CK(sc.alloc(&Y, (size_t)n * D));
+    SILH_CK(sc.alloc(&wY, (size_t)n));
+    st = gather_columns(X, dtype, d, ld, order, nullptr, n, D, metric, Y, wY, stream);
+    if (st != SILH_OK) goto done;
+    st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, Y, wY, n, D, rows,
+                      nrows, s, a, b, stream);
+done:
+    return st;
+}
+
+extern "C" silh_status silh_global(const float *s, int64_t n, double *out, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    silh_status st = SILH_OK;
+    Scratch sc(stream);
+    double *part = nullptr;
+    int np = 0;
+    SILH_REQ(s && out, "null pointer argument");
+    SILH_REQ(n >= 1, "n must be >= 1");
+    np = (int)std::min<int64_t>(1024, (n + kSumThreads - 1) / kSumThreads);
+    SILH_CK(sc.alloc(&part, np));
+    k_sum_partial<<<np, kSumThreads, 0, stream>>>(s, n, part); count_launches(1);
+    k_sum_final<<<1, kSumThreads, 0, stream>>>(part, np, n, out); count_launches(1);
+    SILH_CK(cudaGetLastError());
+done:
+    return st;
+}

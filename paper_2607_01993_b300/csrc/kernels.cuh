@@ -1,0 +1,44 @@
+// Host-side helpers shared by the entry points of libsilh.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace silh {
+
+// Stable counting sort of the labels.  On success:
+//   d_sizes[k]   |Cj| (device, caller memory)
+//   *d_coff      exclusive prefix of the sizes, k+1 entries (scratch)
+//   *d_order     element ids grouped by cluster, ascending inside a cluster (scratch)
+//   h_sizes/h_coff  host copies.
+// Synchronises the stream once (validation of the clustering).
+silh_status cluster_sort(const int32_t *labels, int64_t n, int k, Scratch &sc,
+                         cudaStream_t stream, int64_t *d_sizes, int64_t **d_coff,
+                         int32_t **d_order, std::vector<int64_t> &h_sizes,
+                         std::vector<int64_t> &h_coff);
+
+// Exclusive prefix sum of n int32 flags (0/1) into out[n] (int64); the total is
+// written to *d_total (device).
+cudaError_t scan_flags(const int32_t *flags, int64_t n, int64_t *out, int64_t *d_total,
+                       Scratch &sc, cudaStream_t stream);
+
+// Rows of the Phase-2 column operand: Y[i, :] = X[idx[i], :] for i < m, padded
+// with zeros to D columns; cosine rows are scaled to unit norm.  wY[i] = 1/p[i]
+// (or 1 when p == nullptr).
+silh_status gather_columns(const void *X, silh_dtype dtype, int32_t d, int64_t ld,
+                           const int32_t *idx, const double *p, int64_t m, int D, int metric,
+                           float *Y, float *wY, cudaStream_t stream);
+
+// Phase-2 sweep: for every listed row, W_hat_j over the cluster-major column
+// operand (Y, wY, offsets) and the silhouette of Eq. 8.
+silh_status phase2_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                         const int32_t *labels, int32_t k, int metric, int prec,
+                         const int64_t *sizes, const int64_t *offsets, const float *Y,
+                         const float *wY, int64_t m, int D, const int64_t *rows, int64_t nrows,
+                         float *s, float *a, float *b, cudaStream_t stream);
+
+// Padded row width of the column operand for a given d.
+int padded_dim(int d);
+
+}  // namespace silh

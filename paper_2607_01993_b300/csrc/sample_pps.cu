@@ -1,0 +1,577 @@
+// Phase 1 of Algorithm 1 (PPS sampling) and the cluster bookkeeping it needs.
+//
+// Layout: every per-element array of Phase 1 is indexed by the element's
+// position in cluster-major order ("pos"): order[pos] is the element id,
+// coff[j] .. coff[j+1]-1 are the positions of cluster j, ascending element id
+// inside a cluster.  Distances from cluster members to the initial sample F0_j
+// are kept in an FP64 matrix D_j of |F0_j| x |Cj| (F0-major, so that the W sums
+// and the gamma sweep both read it coalesced).
+//
+// Precision: all of Phase 1 is IEEE FP64.  Each distance is evaluated in
+// ascending coordinate order with explicitly rounded operations (no fused
+// multiply-add) and correctly rounded sqrt/divide, so a pair's distance is the
+// same double the FP64 oracle computes; only the order of the W sums differs.
+#include <algorithm>
+#include <cmath>
+
+#include "kernels.cuh"
+
+namespace silh {
+
+namespace {
+
+constexpr int kHistWarps = 1;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Per-tile histograms: counts[j * ntiles + tile] (cluster-major).
+__global__ void k_tile_hist(const int32_t *__restrict__ labels, int64_t n, int k, int tile,
+                            int ntiles, int32_t *__restrict__ counts, int32_t *__restrict__ bad) {
+    extern __shared__ int32_t sh_cnt[];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) sh_cnt[j] = 0;
+    __syncwarp();
+    int64_t base = (int64_t)blockIdx.x * tile;
+    int64_t end = min(base + (int64_t)tile, n);
+    for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x) {
+        int32_t l = labels[i];
+        if (l < 0 || l >= k) {
+            atomicOr(bad, 1);
+            continue;
+        }
+        atomicAdd(&sh_cnt[l], 1);
+    }
+    __syncwarp();
+    for (int j = threadIdx.x; j < k; j += blockDim.x)
+        counts[(int64_t)j * ntiles + blockIdx.x] = sh_cnt[j];
+}
+
+// Block j: exclusive scan over tiles of cluster j's tile counts; sizes[j] = total.
+__global__ void k_cluster_scan(const int32_t *__restrict__ counts, int ntiles,
+                               int64_t *__restrict__ tile_base, int64_t *__restrict__ sizes) {
+    __shared__ int64_t sh[1024];
+    int j = blockIdx.x;
+    const int32_t *c = counts + (int64_t)j * ntiles;
+    int64_t *o = tile_base + (int64_t)j * ntiles;
+    int per = (ntiles + blockDim.x - 1) / blockDim.x;
+    int lo = threadIdx.x * per, hi = min(lo + per, ntiles);
+    int64_t s = 0;
+    for (int i = lo; i < hi; ++i) s += c[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    // Hillis-Steele inclusive scan of the per-thread sums.
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        int64_t v = (threadIdx.x >= (unsigned)off) ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = sh[threadIdx.x] - s;
+    for (int i = lo; i < hi; ++i) {
+        o[i] = run;
+        run += c[i];
+    }
+    if (threadIdx.x == blockDim.x - 1) sizes[j] = sh[threadIdx.x];
+}
+
+// Stable scatter: one warp walks its tile in element order; lanes with the same
+// label are ranked by lane id.
+__global__ void k_scatter(const int32_t *__restrict__ labels, int64_t n, int k, int tile,
+                          int ntiles, const int64_t *__restrict__ tile_base,
+                          const int64_t *__restrict__ coff, int32_t *__restrict__ order) {
+    extern __shared__ int32_t sh_cnt[];
+    for (int j = threadIdx.x; j < k; j += 32) sh_cnt[j] = 0;
+    __syncwarp();
+    int64_t base = (int64_t)blockIdx.x * tile;
+    int64_t end = min(base + (int64_t)tile, n);
+    unsigned lt = lanemask_lt();
+    for (int64_t i0 = base; i0 < end; i0 += 32) {
+        int64_t i = i0 + threadIdx.x;
+        int32_t l = (i < end) ? labels[i] : -1;
+        bool ok = (l >= 0 && l < k);
+        int key = ok ? l : -1;
+        unsigned peers = __match_any_sync(0xffffffffu, key);
+        int rank = __popc(peers & lt);
+        int cnt = ok ? sh_cnt[l] : 0;
+        __syncwarp();
+        if (ok) {
+            int64_t pos = coff[l] + tile_base[(int64_t)l * ntiles + blockIdx.x] + cnt + rank;
+            order[pos] = (int32_t)i;
+            if (rank == 0) sh_cnt[l] = cnt + __popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------- scan
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ int64_t block_excl_scan(int64_t v, int64_t *sh, int64_t *total) {
+    int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int off = 1; off < kScanThreads; off <<= 1) {
+        int64_t u = (t >= off) ? sh[t - off] : 0;
+        __syncthreads();
+        sh[t] += u;
+        __syncthreads();
+    }
+    int64_t incl = sh[t];
+    if (total) *total = sh[kScanThreads - 1];
+    __syncthreads();
+    return incl - v;
+}
+
+__global__ void k_scan_reduce(const int32_t *__restrict__ f, int64_t n, int64_t *__restrict__ bsum) {
+    __shared__ int64_t sh[kScanThreads];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) s += f[base + i];
+    int64_t tot;
+    block_excl_scan(s, sh, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(int64_t *__restrict__ bsum, int nb, int64_t *__restrict__ total) {
+    __shared__ int64_t sh[kScanThreads];
+    int per = (nb + kScanThreads - 1) / kScanThreads;
+    int lo = threadIdx.x * per, hi = min(lo + per, nb);
+    int64_t s = 0;
+    for (int i = lo; i < hi; ++i) s += bsum[i];
+    int64_t tot;
+    int64_t run = block_excl_scan(s, sh, &tot);
+    for (int i = lo; i < hi; ++i) {
+        int64_t v = bsum[i];
+        bsum[i] = run;
+        run += v;
+    }
+    if (threadIdx.x == 0) *total = tot;
+}
+
+__global__ void k_scan_down(const int32_t *__restrict__ f, int64_t n,
+                            const int64_t *__restrict__ bsum, int64_t *__restrict__ out) {
+    __shared__ int64_t sh[kScanThreads];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int32_t v[kScanItems];
+    int64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < n) ? f[base + i] : 0;
+        s += v[i];
+    }
+    int64_t run = block_excl_scan(s, sh, nullptr) + bsum[blockIdx.x];
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+}
+
+// ---------------------------------------------------------------- Phase 1
+
+// Initial Poisson sample F0 (stream 0) for clusters with |Cj| > t.
+__global__ void k_draw_f0(const int32_t *__restrict__ order, const int32_t *__restrict__ labels,
+                          const int64_t *__restrict__ sizes, int64_t n, double t, double m0,
+                          uint64_t seed, uint64_t cid, int32_t *__restrict__ flag0) {
+    int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= n) return;
+    int32_t e = order[pos];
+    int64_t nc = sizes[labels[e]];
+    int32_t f = 0;
+    if ((double)nc > t) {
+        double q = __ddiv_rn(m0, (double)nc);
+        if (q > 1.0) q = 1.0;
+        f = uniform01(seed, 0, cid, (uint64_t)e) < q ? 1 : 0;
+    }
+    flag0[pos] = f;
+}
+
+__global__ void k_compact(const int32_t *__restrict__ flag, const int64_t *__restrict__ pos_of,
+                          const int32_t *__restrict__ order, int64_t n, int32_t *__restrict__ ids,
+                          const double *__restrict__ pv, double *__restrict__ pout) {
+    int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= n || !flag[pos]) return;
+    int64_t o = pos_of[pos];
+    ids[o] = order[pos];
+    if (pout) pout[o] = pv[pos];
+}
+
+// off[j] = pos_of[coff[j]] (j < k), off[k] = total.
+__global__ void k_seg_offsets(const int64_t *__restrict__ pos_of, const int64_t *__restrict__ coff,
+                              int k, int64_t n, const int64_t *__restrict__ total,
+                              int64_t *__restrict__ off) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > k) return;
+    off[j] = (j == k || coff[j] >= n) ? *total : pos_of[coff[j]];
+}
+
+constexpr int kF0Group = 8;     // F0 rows staged in shared memory at a time
+constexpr int kDistThreads = 128;
+
+template <class T>
+__device__ __forceinline__ double ld64(const T *X, int64_t off) {
+    return (double)to_f32<T>(X[off]);
+}
+
+// D_j[f, i] = d(member i, F0_j[f]) in FP64, one thread per member, F0 rows in
+// shared memory.  Work item w covers members [chunk*128, chunk*128+128) of
+// cluster item_cluster[w].
+template <class T, int METRIC>
+__global__ void k_dist_f0(const T *__restrict__ X, int d, int64_t ld,
+                          const int32_t *__restrict__ order, const int64_t *__restrict__ coff,
+                          const int32_t *__restrict__ f0_elem, const int64_t *__restrict__ f0off,
+                          const int64_t *__restrict__ doff, const int32_t *__restrict__ item_cluster,
+                          const int32_t *__restrict__ item_chunk, double *__restrict__ D) {
+    extern __shared__ double sh_y[];            // kF0Group x d
+    __shared__ double sh_ny[kF0Group];
+    int j = item_cluster[blockIdx.x];
+    int64_t c0 = coff[j], nc = coff[j + 1] - c0;
+    int64_t i = (int64_t)item_chunk[blockIdx.x] * kDistThreads + threadIdx.x;
+    bool live = i < nc;
+    int64_t e = live ? order[c0 + i] : 0;
+    int64_t g0 = f0off[j], nf = f0off[j + 1] - g0;
+    double *Dj = D + doff[j];
+    for (int64_t gb = 0; gb < nf; gb += kF0Group) {
+        int gc = (int)min((int64_t)kF0Group, nf - gb);
+        __syncthreads();
+        for (int q = threadIdx.x; q < kF0Group * d; q += blockDim.x) {
+            int g = q / d, c = q % d;
+            sh_y[q] = (g < gc) ? ld64(X, (int64_t)f0_elem[g0 + gb + g] * ld + c) : 0.0;
+        }
+        __syncthreads();
+        if (METRIC == SILH_COSINE && threadIdx.x < kF0Group) {
+            double s = 0.0;
+            for (int c = 0; c < d; ++c)
+                s = __dadd_rn(s, __dmul_rn(sh_y[threadIdx.x * d + c], sh_y[threadIdx.x * d + c]));
+            sh_ny[threadIdx.x] = s;
+        }
+        __syncthreads();
+        if (!live) continue;
+        double acc[kF0Group];
+        double nx = 0.0;
+#pragma unroll
+        for (int g = 0; g < kF0Group; ++g) acc[g] = 0.0;
+        const T *xr = X + e * ld;
+        for (int c = 0; c < d; ++c) {
+            double xv = (double)to_f32<T>(xr[c]);
+            if (METRIC == SILH_COSINE) nx = __dadd_rn(nx, __dmul_rn(xv, xv));
+#pragma unroll
+            for (int g = 0; g < kF0Group; ++g) {
+                double yv = sh_y[g * d + c];
+                if (METRIC == SILH_EUCLIDEAN) {
+                    double t = __dsub_rn(xv, yv);
+                    acc[g] = __dadd_rn(acc[g], __dmul_rn(t, t));
+                } else if (METRIC == SILH_MANHATTAN) {
+                    acc[g] = __dadd_rn(acc[g], fabs(__dsub_rn(xv, yv)));
+                } else if (METRIC == SILH_CANBERRA) {
+                    double num = fabs(__dsub_rn(xv, yv));
+                    double den = __dadd_rn(fabs(xv), fabs(yv));
+                    if (den > 0.0) acc[g] = __dadd_rn(acc[g], __ddiv_rn(num, den));
+                } else {
+                    acc[g] = __dadd_rn(acc[g], __dmul_rn(xv, yv));
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < kF0Group; ++g) {
+            if (g >= gc) break;
+            double v = acc[g];
+            if (METRIC == SILH_EUCLIDEAN) {
+                v = __dsqrt_rn(v);
+            } else if (METRIC == SILH_COSINE) {
+                double ny = sh_ny[g];
+                if (nx == 0.0 || ny == 0.0) {
+                    v = 1.0;
+                } else {
+                    v = __dsub_rn(1.0, __ddiv_rn(v, __dmul_rn(__dsqrt_rn(nx), __dsqrt_rn(ny))));
+                    v = v < 0.0 ? 0.0 : (v > 2.0 ? 2.0 : v);
+                }
+            }
+            Dj[(gb + g) * nc + i] = v;
+        }
+    }
+}
+
+// W(e0) = sum over the members of column e0 of D_j, fixed reduction tree.
+__global__ void k_w0(const int32_t *__restrict__ f0_elem, const int32_t *__restrict__ labels,
+                     const int64_t *__restrict__ coff, const int64_t *__restrict__ f0off,
+                     const int64_t *__restrict__ doff, const double *__restrict__ D,
+                     double *__restrict__ W0) {
+    __shared__ double sh[256];
+    int64_t g = blockIdx.x;
+    int j = labels[f0_elem[g]];
+    int64_t nc = coff[j + 1] - coff[j];
+    int64_t f = g - f0off[j];
+    const double *col = D + doff[j] + f * nc;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < nc; i += 256) s += col[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) W0[g] = sh[0];
+}
+
+// gamma_e, p_e and the final Poisson draw (stream 1), one thread per position.
+__global__ void k_gamma_draw(const int32_t *__restrict__ order, const int32_t *__restrict__ labels,
+                             const int64_t *__restrict__ coff, const int64_t *__restrict__ sizes,
+                             const int64_t *__restrict__ f0off, const int64_t *__restrict__ doff,
+                             const double *__restrict__ D, const double *__restrict__ W0, int64_t n,
+                             double t, int uniform, uint64_t seed, uint64_t cid,
+                             double *__restrict__ pS, int32_t *__restrict__ flag1) {
+    int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= n) return;
+    int32_t e = order[pos];
+    int j = labels[e];
+    int64_t nc = sizes[j];
+    double p;
+    if ((double)nc <= t) {
+        p = 1.0;
+    } else if (uniform) {
+        p = __ddiv_rn(t, (double)nc);
+        if (p > 1.0) p = 1.0;
+    } else {
+        int64_t i = pos - coff[j];
+        int64_t g0 = f0off[j], nf = f0off[j + 1] - g0;
+        const double *Dj = D + doff[j];
+        double g2 = 0.0;
+        for (int64_t f = 0; f < nf; ++f) {
+            double W = W0[g0 + f];
+            double r = (W > 0.0) ? __ddiv_rn(Dj[f * nc + i], W) : 0.0;
+            if (r > g2) g2 = r;
+        }
+        double g1 = __ddiv_rn(1.0, (double)nc);
+        double g = g1 > g2 ? g1 : g2;
+        p = __dmul_rn(t, g);
+        if (!(p < 1.0)) p = 1.0;
+    }
+    pS[pos] = p;
+    flag1[pos] = (p >= 1.0 || uniform01(seed, 1, cid, (uint64_t)e) < p) ? 1 : 0;
+}
+
+template <class T>
+void launch_dist_f0(int metric, int nitems, size_t smem, cudaStream_t stream, const T *X, int d,
+                    int64_t ld, const int32_t *order, const int64_t *coff, const int32_t *f0_elem,
+                    const int64_t *f0off, const int64_t *doff, const int32_t *ic,
+                    const int32_t *ik, double *D) {
+    switch (metric) {
+        case SILH_EUCLIDEAN:
+            k_dist_f0<T, SILH_EUCLIDEAN><<<nitems, kDistThreads, smem, stream>>>(
+                X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
+            break;
+        case SILH_COSINE:
+            k_dist_f0<T, SILH_COSINE><<<nitems, kDistThreads, smem, stream>>>(
+                X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
+            break;
+        case SILH_MANHATTAN:
+            k_dist_f0<T, SILH_MANHATTAN><<<nitems, kDistThreads, smem, stream>>>(
+                X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
+            break;
+        default:
+            k_dist_f0<T, SILH_CANBERRA><<<nitems, kDistThreads, smem, stream>>>(
+                X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
+            break;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host helpers
+
+cudaError_t scan_flags(const int32_t *flags, int64_t n, int64_t *out, int64_t *d_total,
+                       Scratch &sc, cudaStream_t stream) {
+    int nb = (int)std::max<int64_t>(1, (n + kScanTile - 1) / kScanTile);
+    int64_t *bsum = nullptr;
+    cudaError_t e = sc.alloc(&bsum, nb);
+    if (e != cudaSuccess) return e;
+    k_scan_reduce<<<nb, kScanThreads, 0, stream>>>(flags, n, bsum); count_launches(1);
+    k_scan_top<<<1, kScanThreads, 0, stream>>>(bsum, nb, d_total); count_launches(1);
+    k_scan_down<<<nb, kScanThreads, 0, stream>>>(flags, n, bsum, out); count_launches(1);
+    return cudaGetLastError();
+}
+
+silh_status cluster_sort(const int32_t *labels, int64_t n, int k, Scratch &sc,
+                         cudaStream_t stream, int64_t *d_sizes, int64_t **d_coff,
+                         int32_t **d_order, std::vector<int64_t> &h_sizes,
+                         std::vector<int64_t> &h_coff) {
+    silh_status st = SILH_OK;
+    int tile = (k <= 512) ? 1024 : 8192;
+    int ntiles = (int)((n + tile - 1) / tile);
+    int32_t *counts = nullptr, *bad = nullptr;
+    int64_t *tile_base = nullptr;
+    int32_t h_bad = 0;
+    size_t smem = sizeof(int32_t) * (size_t)k;
+    SILH_CK(sc.alloc(&counts, (size_t)k * ntiles));
+    SILH_CK(sc.alloc(&tile_base, (size_t)k * ntiles));
+    SILH_CK(sc.alloc(&bad, 1));
+    SILH_CK(sc.alloc(d_coff, (size_t)k + 1));
+    SILH_CK(sc.alloc(d_order, (size_t)n));
+    SILH_CK(cudaMemsetAsync(bad, 0, sizeof(int32_t), stream));
+    if (smem > 48 * 1024) {
+        SILH_CK(cudaFuncSetAttribute(k_tile_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        SILH_CK(cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    }
+    k_tile_hist<<<ntiles, 32 * kHistWarps, smem, stream>>>(labels, n, k, tile, ntiles, counts, bad); count_launches(1);
+    k_cluster_scan<<<k, 256, 0, stream>>>(counts, ntiles, tile_base, d_sizes); count_launches(1);
+    SILH_CK(cudaGetLastError());
+    h_sizes.assign(k, 0);
+    SILH_CK(cudaMemcpyAsync(h_sizes.data(), d_sizes, sizeof(int64_t) * k, cudaMemcpyDeviceToHost,
+                            stream));
+    SILH_CK(cudaMemcpyAsync(&h_bad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    SILH_CK(cudaStreamSynchronize(stream));
+    SILH_REQ(h_bad == 0, "a label is outside [0, k)");
+    for (int j = 0; j < k; ++j) SILH_REQ(h_sizes[j] > 0, "cluster %d is empty", j);
+    h_coff.assign(k + 1, 0);
+    for (int j = 0; j < k; ++j) h_coff[j + 1] = h_coff[j] + h_sizes[j];
+    SILH_CK(cudaMemcpyAsync(*d_coff, h_coff.data(), sizeof(int64_t) * (k + 1),
+                            cudaMemcpyHostToDevice, stream));
+    k_scatter<<<ntiles, 32, smem, stream>>>(labels, n, k, tile, ntiles, tile_base, *d_coff,
+                                            *d_order); count_launches(1);
+    SILH_CK(cudaGetLastError());
+done:
+    return st;
+}
+
+}  // namespace silh
+
+using namespace silh;
+
+extern "C" silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t n, int32_t d,
+                                       int64_t ld, const int32_t *labels, int32_t k,
+                                       silh_metric metric, double t, double m0, double delta,
+                                       uint64_t seed, uint32_t clustering_id, int32_t uniform,
+                                       silh_sample *out, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    silh_status st = SILH_OK;
+    int dev = 0;
+    Scratch sc(stream);
+    std::vector<int64_t> h_sizes, h_coff, h_f0off, h_doff, h_off;
+    std::vector<int32_t> h_ic, h_ik;
+    int64_t *coff = nullptr, *pos0 = nullptr, *pos1 = nullptr, *tot = nullptr, *f0off = nullptr;
+    int64_t *doff = nullptr;
+    int32_t *order = nullptr, *flag0 = nullptr, *flag1 = nullptr, *f0_elem = nullptr;
+    int32_t *ic = nullptr, *ik = nullptr;
+    double *D = nullptr, *W0 = nullptr, *pS = nullptr;
+    int64_t nf0 = 0, dtot = 0, size = 0;
+    int nblk = 0;
+
+    SILH_REQ(X && labels && out, "null pointer argument");
+    SILH_REQ(n >= 2 && n < (int64_t(1) << 31), "n must be in [2, 2^31)");
+    SILH_REQ(d >= 1 && ld >= d, "need d >= 1 and ld >= d");
+    SILH_REQ(k >= 2 && k <= SILH_MAX_K, "k must be in [2, %d]", SILH_MAX_K);
+    SILH_REQ(out->k == k && out->sizes && out->offsets && out->idx && out->p,
+             "silh_sample buffers missing or k mismatch");
+    SILH_REQ(t > 0.0 && std::isfinite(t), "t must be positive");
+    SILH_REQ(metric >= SILH_EUCLIDEAN && metric <= SILH_CANBERRA, "unknown metric");
+    SILH_REQ(dtype == SILH_F32 || dtype == SILH_BF16, "unknown dtype");
+    if (!(m0 > 0.0)) {
+        SILH_REQ(delta > 0.0 && delta < 1.0, "delta must be in (0, 1)");
+        m0 = 2.0 * std::log(5.0 * (double)k / delta);
+    }
+    SILH_CK(cudaGetDevice(&dev));
+    ensure_pool_retains(dev);
+
+    st = cluster_sort(labels, n, k, sc, stream, out->sizes, &coff, &order, h_sizes, h_coff);
+    if (st != SILH_OK) goto done;
+    nblk = ceil_div_i(n, 256);
+    SILH_CK(sc.alloc(&flag0, n));
+    SILH_CK(sc.alloc(&flag1, n));
+    SILH_CK(sc.alloc(&pos0, n));
+    SILH_CK(sc.alloc(&pos1, n));
+    SILH_CK(sc.alloc(&tot, 2));
+    SILH_CK(sc.alloc(&f0off, (size_t)k + 1));
+    SILH_CK(sc.alloc(&pS, n));
+
+    h_f0off.assign(k + 1, 0);
+    if (!uniform) {
+        k_draw_f0<<<nblk, 256, 0, stream>>>(order, labels, out->sizes, n, t, m0, seed,
+                                            clustering_id, flag0); count_launches(1);
+        SILH_CK(scan_flags(flag0, n, pos0, tot, sc, stream));
+        k_seg_offsets<<<ceil_div_i(k + 1, 256), 256, 0, stream>>>(pos0, coff, k, n, tot, f0off); count_launches(1);
+        SILH_CK(cudaGetLastError());
+        SILH_CK(cudaMemcpyAsync(h_f0off.data(), f0off, sizeof(int64_t) * (k + 1),
+                                cudaMemcpyDeviceToHost, stream));
+        SILH_CK(cudaStreamSynchronize(stream));
+        nf0 = h_f0off[k];
+    } else {
+        SILH_CK(cudaMemsetAsync(f0off, 0, sizeof(int64_t) * (k + 1), stream));
+    }
+    // Plan the member x F0 distance matrices and the work items.
+    h_doff.assign(k + 1, 0);
+    for (int j = 0; j < k; ++j) {
+        int64_t nc = h_sizes[j], nf = h_f0off[j + 1] - h_f0off[j];
+        h_doff[j + 1] = h_doff[j] + nc * nf;
+        if (nf > 0)
+            for (int64_t c = 0; c * kDistThreads < nc; ++c) {
+                h_ic.push_back(j);
+                h_ik.push_back((int32_t)c);
+            }
+    }
+    dtot = h_doff[k];
+    SILH_CK(sc.alloc(&doff, (size_t)k + 1));
+    SILH_CK(cudaMemcpyAsync(doff, h_doff.data(), sizeof(int64_t) * (k + 1),
+                            cudaMemcpyHostToDevice, stream));
+    SILH_CK(sc.alloc(&D, (size_t)std::max<int64_t>(dtot, 1)));
+    SILH_CK(sc.alloc(&W0, (size_t)std::max<int64_t>(nf0, 1)));
+    SILH_CK(sc.alloc(&f0_elem, (size_t)std::max<int64_t>(nf0, 1)));
+    if (nf0 > 0) {
+        k_compact<<<nblk, 256, 0, stream>>>(flag0, pos0, order, n, f0_elem, nullptr, nullptr); count_launches(1);
+        int nitems = (int)h_ic.size();
+        SILH_CK(sc.alloc(&ic, nitems));
+        SILH_CK(sc.alloc(&ik, nitems));
+        SILH_CK(cudaMemcpyAsync(ic, h_ic.data(), sizeof(int32_t) * nitems, cudaMemcpyHostToDevice,
+                                stream));
+        SILH_CK(cudaMemcpyAsync(ik, h_ik.data(), sizeof(int32_t) * nitems, cudaMemcpyHostToDevice,
+                                stream));
+        size_t smem = sizeof(double) * kF0Group * (size_t)d;
+        SILH_REQ(smem <= 200 * 1024, "d too large for Phase 1 (d <= 3200)");
+        if (dtype == SILH_F32) {
+            if (smem > 48 * 1024)
+                for (auto f : {k_dist_f0<float, 0>, k_dist_f0<float, 1>, k_dist_f0<float, 2>,
+                               k_dist_f0<float, 3>})
+                    SILH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+            launch_dist_f0<float>(metric, nitems, smem, stream, (const float *)X, d, ld, order,
+                                  coff, f0_elem, f0off, doff, ic, ik, D);
+        } else {
+            if (smem > 48 * 1024)
+                for (auto f : {k_dist_f0<__nv_bfloat16, 0>, k_dist_f0<__nv_bfloat16, 1>,
+                               k_dist_f0<__nv_bfloat16, 2>, k_dist_f0<__nv_bfloat16, 3>})
+                    SILH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+            launch_dist_f0<__nv_bfloat16>(metric, nitems, smem, stream,
+                                          (const __nv_bfloat16 *)X, d, ld, order, coff, f0_elem,
+                                          f0off, doff, ic, ik, D);
+        }
+        SILH_CK(cudaGetLastError());
+        k_w0<<<(int)nf0, 256, 0, stream>>>(f0_elem, labels, coff, f0off, doff, D, W0); count_launches(1);
+        SILH_CK(cudaGetLastError());
+    }
+    k_gamma_draw<<<nblk, 256, 0, stream>>>(order, labels, coff, out->sizes, f0off, doff, D, W0, n,
+                                           t, uniform ? 1 : 0, seed, clustering_id, pS, flag1); count_launches(1);
+    SILH_CK(scan_flags(flag1, n, pos1, tot + 1, sc, stream));
+    SILH_CK(cudaMemcpyAsync(&size, tot + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+    SILH_CK(cudaStreamSynchronize(stream));
+    out->size = size;
+    if (size > out->cap) {
+        st = fail(SILH_ECAPACITY, "sample has %lld elements, capacity %lld", (long long)size,
+                  (long long)out->cap);
+        goto done;
+    }
+    k_compact<<<nblk, 256, 0, stream>>>(flag1, pos1, order, n, out->idx, pS, out->p); count_launches(1);
+    k_seg_offsets<<<ceil_div_i(k + 1, 256), 256, 0, stream>>>(pos1, coff, k, n, tot + 1,
+                                                              out->offsets); count_launches(1);
+    SILH_CK(cudaGetLastError());
+    SILH_CK(cudaStreamSynchronize(stream));
+done:
+    return st;
+}

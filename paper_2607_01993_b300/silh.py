@@ -1,0 +1,217 @@
+"""Thin Python binding of libsilh (C ABI in include/silh.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Tensors are torch CUDA tensors; the library receives their device
+pointers and the current torch stream.  If libsilh.so is missing or fails to
+load, every call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsilh.so")
+
+METRICS = {"euclidean": 0, "cosine": 1, "manhattan": 2, "canberra": 3}
+DTYPES = {torch.float32: 0, torch.bfloat16: 1}
+PRECS = {"fp32": 0, "tf32": 1, "3xtf32": 2}
+STATUS = {0: "SILH_OK", -1: "SILH_EINVAL", -2: "SILH_ENOMEM", -3: "SILH_ECUDA",
+          -4: "SILH_ECAPACITY", -5: "SILH_ETIMEOUT"}
+SILH_ECAPACITY = -4
+
+# exported symbols, as declared in include/silh.h
+EXPORTS = ("silh_sample_pps", "silh_estimate", "silh_exact", "silh_global", "silh_t_from_eps",
+           "silh_last_error", "silh_version", "silh_kernel_launches")
+
+
+class SilhError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SilhSample(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("sizes", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("idx", ctypes.c_void_p), ("p", ctypes.c_void_p), ("cap", ctypes.c_int64),
+                ("size", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsilh.so (raises if it is absent: the product has no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsilh.so not built at {path}; run paper_2607_01993_b300/build.py")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    lib.silh_sample_pps.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32, ctypes.c_int, f64,
+                                    f64, f64, ctypes.c_uint64, ctypes.c_uint32, i32,
+                                    ctypes.POINTER(SilhSample), vp]
+    lib.silh_sample_pps.restype = ctypes.c_int
+    lib.silh_estimate.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32, ctypes.c_int,
+                                  ctypes.c_int, ctypes.POINTER(SilhSample), vp, i64, vp, vp, vp, vp]
+    lib.silh_estimate.restype = ctypes.c_int
+    lib.silh_exact.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32, ctypes.c_int,
+                               ctypes.c_int, vp, i64, vp, vp, vp, vp]
+    lib.silh_exact.restype = ctypes.c_int
+    lib.silh_global.argtypes = [vp, i64, vp, vp]
+    lib.silh_global.restype = ctypes.c_int
+    lib.silh_t_from_eps.argtypes = [f64, f64, i64, i32]
+    lib.silh_t_from_eps.restype = f64
+    lib.silh_last_error.argtypes = []
+    lib.silh_last_error.restype = ctypes.c_char_p
+    lib.silh_version.argtypes = []
+    lib.silh_version.restype = ctypes.c_char_p
+    lib.silh_kernel_launches.argtypes = []
+    lib.silh_kernel_launches.restype = ctypes.c_uint64
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise SilhError(rc, load().silh_last_error().decode())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _data(X):
+    if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1 or X.dtype not in DTYPES:
+        raise ValueError("X must be a 2-D CUDA float32/bfloat16 tensor with unit column stride")
+    return DTYPES[X.dtype], X.shape[0], X.shape[1], X.stride(0)
+
+
+def _labels(labels):
+    if not labels.is_cuda or labels.dtype != torch.int32 or not labels.is_contiguous():
+        raise ValueError("labels must be a contiguous CUDA int32 tensor")
+    return labels
+
+
+def _rows(rows):
+    if rows is None:
+        return None, 0
+    if not rows.is_cuda or rows.dtype != torch.int64 or not rows.is_contiguous():
+        raise ValueError("rows must be a contiguous CUDA int64 tensor")
+    return rows, rows.shape[0]
+
+
+@dataclass
+class Sample:
+    """Sample set of Phase 1: per-cluster lists over device tensors."""
+    k: int
+    sizes: torch.Tensor      # int64 [k]
+    offsets: torch.Tensor    # int64 [k+1]
+    idx: torch.Tensor        # int32 [cap]
+    p: torch.Tensor          # float64 [cap]
+    size: int
+
+    def as_struct(self) -> SilhSample:
+        return SilhSample(self.k, self.sizes.data_ptr(), self.offsets.data_ptr(),
+                          self.idx.data_ptr(), self.p.data_ptr(), self.idx.shape[0], self.size)
+
+    @staticmethod
+    def empty(k: int, cap: int, device) -> "Sample":
+        return Sample(k, torch.zeros(k, dtype=torch.int64, device=device),
+                      torch.zeros(k + 1, dtype=torch.int64, device=device),
+                      torch.zeros(max(cap, 1), dtype=torch.int32, device=device),
+                      torch.zeros(max(cap, 1), dtype=torch.float64, device=device), 0)
+
+    @staticmethod
+    def from_lists(sizes, offsets, idx, p, device) -> "Sample":
+        """A sample built elsewhere (host arrays), e.g. for feeding a fixed sample."""
+        idx_t = torch.as_tensor(idx, dtype=torch.int32).to(device)
+        return Sample(len(sizes), torch.as_tensor(sizes, dtype=torch.int64).to(device),
+                      torch.as_tensor(offsets, dtype=torch.int64).to(device), idx_t,
+                      torch.as_tensor(p, dtype=torch.float64).to(device), int(idx_t.shape[0]))
+
+
+def silh_sample_pps(X, labels, k, metric="euclidean", t=64.0, m0=None, delta=0.01, seed=0,
+                    clustering_id=0, uniform=False, cap=None, out=None, stream=None) -> Sample:
+    """Algorithm 1, Phase 1 on the GPU (synchronising)."""
+    lib = load()
+    dt, n, d, ld = _data(X)
+    labels = _labels(labels)
+    smp = out if out is not None else Sample.empty(k, n if cap is None else cap, X.device)
+    st = smp.as_struct()
+    rc = lib.silh_sample_pps(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric], float(t),
+                             -1.0 if m0 is None else float(m0), float(delta), int(seed),
+                             int(clustering_id), 1 if uniform else 0, ctypes.byref(st),
+                             _stream(stream))
+    if rc == SILH_ECAPACITY and out is None:
+        return silh_sample_pps(X, labels, k, metric, t, m0, delta, seed, clustering_id, uniform,
+                               cap=int(st.size), stream=stream)
+    _check(rc)
+    smp.size = int(st.size)
+    return smp
+
+
+def silh_estimate(X, labels, k, sample: Sample, metric="euclidean", prec="fp32", rows=None,
+                  want_ab=False, out=None, stream=None):
+    """Algorithm 1, Phase 2: s_hat (and a_hat, b_hat) for all rows or a row list."""
+    lib = load()
+    dt, n, d, ld = _data(X)
+    labels = _labels(labels)
+    rows, nr = _rows(rows)
+    nrows = n if rows is None else nr
+    s = out if out is not None else torch.empty(nrows, dtype=torch.float32, device=X.device)
+    a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    st = sample.as_struct()
+    _check(lib.silh_estimate(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric],
+                             PRECS[prec], ctypes.byref(st), _ptr(rows), nr, _ptr(s), _ptr(a),
+                             _ptr(b), _stream(stream)))
+    return (s, a, b) if want_ab else s
+
+
+def silh_exact(X, labels, k, metric="euclidean", prec="fp32", rows=None, want_ab=False,
+               stream=None):
+    """Exact silhouette (Eq. 1-2) of all rows or a row list."""
+    lib = load()
+    dt, n, d, ld = _data(X)
+    labels = _labels(labels)
+    rows, nr = _rows(rows)
+    nrows = n if rows is None else nr
+    s = torch.empty(nrows, dtype=torch.float32, device=X.device)
+    a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    _check(lib.silh_exact(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric], PRECS[prec],
+                          _ptr(rows), nr, _ptr(s), _ptr(a), _ptr(b), _stream(stream)))
+    return (s, a, b) if want_ab else s
+
+
+def silh_global(s, out=None, stream=None):
+    """FP64 mean of s (Eq. 3 / 6 / 7); returns a 1-element float64 CUDA tensor."""
+    lib = load()
+    if not s.is_cuda or s.dtype != torch.float32 or not s.is_contiguous():
+        raise ValueError("s must be a contiguous CUDA float32 tensor")
+    o = out if out is not None else torch.empty(1, dtype=torch.float64, device=s.device)
+    _check(lib.silh_global(_ptr(s), s.numel(), _ptr(o), _stream(stream)))
+    return o
+
+
+def silh_t_from_eps(eps, delta, n, k) -> float:
+    return load().silh_t_from_eps(eps, delta, n, k)
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libsilh so far in this process."""
+    return int(load().silh_kernel_launches())
+
+
+def version() -> str:
+    return load().silh_version().decode()

@@ -1,0 +1,203 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Sample sets must be identical: both sides take the inclusion decision
+u < p_e in FP64; a differing element is accepted only inside the tie band
+|u - p_e| <= 1e-12 p_e (the two sides sum W in different orders), and is
+counted.  Silhouette values must agree within 1e-5 absolute (FP32 arithmetic
+on the GPU), a_hat/b_hat within 1e-5 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2607_01993_b300 import silh, synth
+
+pytestmark = pytest.mark.gpu
+METRICS = ["euclidean", "cosine", "manhattan", "canberra"]
+S_TOL = 1e-5
+AB_RTOL = 1e-5
+TIE = 1e-12
+
+
+def _to_dev(X, lab, dtype=torch.float32):
+    Xt = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda().to(dtype)
+    return Xt, torch.from_numpy(lab.astype(np.int32)).cuda()
+
+
+def _host_values(Xt):
+    return Xt.float().cpu().numpy().astype(np.float64)
+
+
+def assert_same_sample(gs: silh.Sample, os_: oracle.Sample, k, seed, cid):
+    g_off = gs.offsets.cpu().numpy()
+    g_idx = gs.idx[: gs.size].cpu().numpy().astype(np.int64)
+    g_p = gs.p[: gs.size].cpu().numpy()
+    ties = 0
+    for j in range(k):
+        a = g_idx[g_off[j]:g_off[j + 1]]
+        b = os_.idx[os_.offsets[j]:os_.offsets[j + 1]]
+        assert (np.diff(a) > 0).all(), "GPU list not ascending"
+        diff = np.setxor1d(a, b)
+        for e in diff:
+            u = oracle.uniform(seed, 1, cid, int(e))
+            assert abs(u - os_.p[e]) <= TIE * os_.p[e], f"element {e} differs outside tie band"
+            ties += 1
+    both = np.intersect1d(g_idx, os_.idx)
+    gp = dict(zip(g_idx.tolist(), g_p.tolist()))
+    got = np.array([gp[e] for e in both])
+    np.testing.assert_allclose(got, os_.p[both], rtol=1e-12, atol=0)
+    return ties
+
+
+def _assert_close(s_g, s_o, a_g=None, a_o=None, b_g=None, b_o=None):
+    s_g = s_g.cpu().numpy().astype(np.float64)
+    assert np.isfinite(s_g).all()
+    err = np.abs(s_g - s_o).max()
+    assert err <= S_TOL, f"max |s diff| = {err}"
+    if a_g is not None:
+        np.testing.assert_allclose(a_g.cpu().numpy(), a_o, rtol=AB_RTOL, atol=1e-30)
+        np.testing.assert_allclose(b_g.cpu().numpy(), b_o, rtol=AB_RTOL, atol=1e-30)
+
+
+def _case(name):
+    if name == "tiny":
+        X, lab, _ = synth.tiny(seed=0)
+        return X, lab, 4, dict(t=64.0, m0=16.0, seed=0)
+    if name == "ragged":
+        X, lab, _ = synth.gaussian_mixture(5003, 13, 6, seed=3, sizes=[2500, 1200, 700, 550, 30, 23])
+        lab = lab.copy()
+        lab[17] = 6                                   # singleton cluster
+        return X, lab, 7, dict(t=40.0, m0=8.0, seed=3)
+    if name == "multitile":
+        X, lab, _ = synth.gaussian_mixture(40000, 32, 16, seed=4,
+                                           sizes=synth.zipf_sizes(40000, 16), sigma_range=(0.5, 3))
+        return X, lab, 16, dict(t=128.0, m0=None, seed=4)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("case", ["tiny", "ragged", "multitile"])
+@pytest.mark.parametrize("metric", METRICS)
+def test_sample_pps_matches_oracle(case, metric):
+    X, lab, k, kw = _case(case)
+    if metric == "canberra":
+        X = synth.abs_shift(X)
+    Xt, lt = _to_dev(X, lab)
+    gs = silh.silh_sample_pps(Xt, lt, k, metric, t=kw["t"], m0=kw["m0"], seed=kw["seed"],
+                              clustering_id=5)
+    os_ = oracle.sample_pps(_host_values(Xt), lab, k, metric, t=kw["t"], m0=kw["m0"],
+                            seed=kw["seed"], cid=5)
+    np.testing.assert_array_equal(gs.sizes.cpu().numpy(), np.bincount(lab, minlength=k))
+    ties = assert_same_sample(gs, os_, k, kw["seed"], 5)
+    assert ties <= 1
+
+
+@pytest.mark.parametrize("case", ["tiny", "ragged", "multitile"])
+@pytest.mark.parametrize("metric", METRICS)
+def test_estimate_matches_oracle_on_oracle_sample(case, metric):
+    X, lab, k, kw = _case(case)
+    if metric == "canberra":
+        X = synth.abs_shift(X)
+    Xt, lt = _to_dev(X, lab)
+    Xh = _host_values(Xt)
+    os_ = oracle.sample_pps(Xh, lab, k, metric, t=kw["t"], m0=kw["m0"], seed=kw["seed"])
+    smp = silh.Sample.from_lists(np.bincount(lab, minlength=k), os_.offsets, os_.idx, os_.ps,
+                                 Xt.device)
+    s, a, b = silh.silh_estimate(Xt, lt, k, smp, metric, want_ab=True)
+    s_o, a_o, b_o = oracle.estimate(Xh, lab, k, metric, os_.offsets, os_.idx, os_.ps)
+    _assert_close(s, s_o, a, a_o, b, b_o)
+
+
+@pytest.mark.parametrize("metric", METRICS)
+def test_end_to_end_tiny(metric):
+    """Phase 1 + Phase 2 + global on the GPU vs the oracle, tiny workload."""
+    X, lab, k, kw = _case("tiny")
+    if metric == "canberra":
+        X = synth.abs_shift(X)
+    Xt, lt = _to_dev(X, lab)
+    Xh = _host_values(Xt)
+    gs = silh.silh_sample_pps(Xt, lt, k, metric, t=64.0, m0=16.0, seed=0)
+    s = silh.silh_estimate(Xt, lt, k, gs, metric)
+    g = silh.silh_global(s).item()
+    os_ = oracle.sample_pps(Xh, lab, k, metric, t=64.0, m0=16.0, seed=0)
+    assert_same_sample(gs, os_, k, 0, 0)
+    s_o, _, _ = oracle.estimate(Xh, lab, k, metric, os_.offsets, os_.idx, os_.ps)
+    _assert_close(s, s_o)
+    assert abs(g - oracle.mean(s_o)) <= S_TOL / 10
+
+
+@pytest.mark.parametrize("case", ["tiny", "ragged"])
+@pytest.mark.parametrize("metric", METRICS)
+def test_exact_matches_oracle(case, metric):
+    X, lab, k, _ = _case(case)
+    if metric == "canberra":
+        X = synth.abs_shift(X)
+    Xt, lt = _to_dev(X, lab)
+    Xh = _host_values(Xt)
+    s, a, b = silh.silh_exact(Xt, lt, k, metric, want_ab=True)
+    s_o, a_o, b_o = oracle.exact(Xh, lab, k, metric)
+    _assert_close(s, s_o, a, a_o, b, b_o)
+    g = silh.silh_global(s).item()
+    assert abs(g - oracle.mean(s_o)) <= S_TOL / 10
+
+
+def test_bf16_storage_matches_oracle_on_rounded_values():
+    X, lab, k, kw = _case("multitile")
+    Xt, lt = _to_dev(X, lab, torch.bfloat16)
+    Xh = _host_values(Xt)           # the BF16-rounded values, exactly
+    gs = silh.silh_sample_pps(Xt, lt, k, "euclidean", t=128.0, seed=4)
+    os_ = oracle.sample_pps(Xh, lab, k, "euclidean", t=128.0, seed=4)
+    assert_same_sample(gs, os_, k, 4, 0)
+    rows = torch.arange(0, 40000, 97, dtype=torch.int64, device="cuda")
+    s = silh.silh_estimate(Xt, lt, k, gs, "euclidean", rows=rows)
+    s_o, _, _ = oracle.estimate(Xh, lab, k, "euclidean", os_.offsets, os_.idx, os_.ps,
+                                rows=rows.cpu().numpy())
+    _assert_close(s, s_o)
+
+
+def test_row_subset_equals_full_rows():
+    X, lab, k, kw = _case("ragged")
+    Xt, lt = _to_dev(X, lab)
+    gs = silh.silh_sample_pps(Xt, lt, k, "manhattan", t=40.0, m0=8.0, seed=1)
+    s_all = silh.silh_estimate(Xt, lt, k, gs, "manhattan")
+    rows = torch.tensor([17, 0, 5002, 1234, 17], dtype=torch.int64, device="cuda")
+    s_sub = silh.silh_estimate(Xt, lt, k, gs, "manhattan", rows=rows)
+    assert torch.equal(s_sub, s_all[rows])
+    assert s_all[17].item() == 0.0                   # singleton
+
+
+def test_uniform_variant_matches_oracle():
+    X, lab, k, kw = _case("multitile")
+    Xt, lt = _to_dev(X, lab)
+    gs = silh.silh_sample_pps(Xt, lt, k, "euclidean", t=128.0, seed=9, uniform=True)
+    os_ = oracle.sample_pps(_host_values(Xt), lab, k, "euclidean", t=128.0, seed=9, uniform=True)
+    assert_same_sample(gs, os_, k, 9, 0)
+
+
+def test_invalid_clusterings_raise():
+    X, lab, k, _ = _case("tiny")
+    Xt, lt = _to_dev(X, lab)
+    with pytest.raises(silh.SilhError) as ei:
+        silh.silh_exact(Xt, lt, 5, "euclidean")                  # cluster 4 empty
+    assert ei.value.status == -1
+    bad = lt.clone(); bad[3] = 9
+    with pytest.raises(silh.SilhError):
+        silh.silh_sample_pps(Xt, bad, 4, "euclidean", t=64.0)    # label out of range
+    with pytest.raises(silh.SilhError):
+        silh.silh_sample_pps(Xt, lt, 1, "euclidean", t=64.0)     # k = 1
+    with pytest.raises(silh.SilhError):
+        silh.silh_sample_pps(Xt, lt, 4, "euclidean", t=0.0)      # t <= 0
+    # the context is still usable afterwards
+    s = silh.silh_exact(Xt, lt, 4, "euclidean")
+    assert torch.isfinite(s).all()
+
+
+def test_capacity_error_reports_needed_size():
+    X, lab, k, _ = _case("tiny")
+    Xt, lt = _to_dev(X, lab)
+    out = silh.Sample.empty(4, 10, Xt.device)
+    with pytest.raises(silh.SilhError) as ei:
+        silh.silh_sample_pps(Xt, lt, 4, "euclidean", t=64.0, m0=16.0, out=out)
+    assert ei.value.status == silh.SILH_ECAPACITY
+    full = silh.silh_sample_pps(Xt, lt, 4, "euclidean", t=64.0, m0=16.0)
+    assert full.size > 10
