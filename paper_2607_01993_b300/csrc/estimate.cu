@@ -30,7 +30,7 @@ namespace {
 template <class T>
 __global__ void k_gather(const T *__restrict__ X, int d, int64_t ld, const int32_t *__restrict__ idx,
                          const double *__restrict__ p, int64_t m, int D, int metric,
-                         float *__restrict__ Y, float *__restrict__ wY) {
+                         float *__restrict__ Y, float *__restrict__ wY, float *__restrict__ zY) {
     int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
     if (i >= m) return;
@@ -47,7 +47,13 @@ __global__ void k_gather(const T *__restrict__ X, int d, int64_t ld, const int32
         scale = s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.0f;
     }
     for (int c = lane; c < D; c += 32) Y[i * D + c] = (c < d) ? to_f32<T>(x[c]) * scale : 0.0f;
-    if (lane == 0) wY[i] = p ? (float)(1.0 / p[i]) : 1.0f;
+    if (lane == 0) {
+        float w = p ? (float)(1.0 / p[i]) : 1.0f;
+        wY[i] = w;
+        // cosine: a zero column is at distance 1 from everything; the unit-vector
+        // form 0.5 |x - y|^2 gives 0.5 for it, so it carries +0.5 w here.
+        zY[i] = (metric == SILH_COSINE && scale == 0.0f) ? 0.5f * w : 0.0f;
+    }
 }
 
 // ------------------------------------------------------- pair kernels
@@ -66,10 +72,12 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 
 // Distance of one row (registers) to one column (shared memory, float4).
 // Euclidean: sqrt(sum (x - y)^2).  Manhattan: sum |x - y|.  Cosine: rows and
-// columns are unit-normalised, d = clamp(1 - <x,y>, 0, 2).  Canberra: terms
-// |x - y| / (|x| + |y|) taken two at a time as (n1 d2 + n2 d1)/(d1 d2) so that
-// one reciprocal serves two coordinates; |x| carries +1e-30 so an all-zero
-// coordinate pair contributes 0 instead of 0/0.
+// columns are unit-normalised and 1 - <x,y> is evaluated as 0.5 |x - y|^2
+// (equal for unit vectors, and free of the cancellation of 1 - <x,y> for
+// nearly parallel pairs).  Canberra: terms |x - y| / (|x| + |y|) taken two at a
+// time as (n1 d2 + n2 d1)/(d1 d2) so that one reciprocal serves two
+// coordinates; each denominator carries +1e-18 so that an all-zero coordinate
+// pair (including padding) contributes 0 and d1 d2 stays a normal float.
 template <int METRIC, int D>
 __device__ __forceinline__ float pair_dist(const float (&x)[D], const float4 *__restrict__ y4) {
     float acc0 = 0.f, acc1 = 0.f;
@@ -92,16 +100,16 @@ __device__ __forceinline__ float pair_dist(const float (&x)[D], const float4 *__
         } else if (METRIC == SILH_COSINE) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                if (c & 1) acc1 = fmaf(x[4 * q + c], ys[c], acc1);
-                else acc0 = fmaf(x[4 * q + c], ys[c], acc0);
+                float t = x[4 * q + c] - ys[c];
+                if (c & 1) acc1 = fmaf(t, t, acc1); else acc0 = fmaf(t, t, acc0);
             }
         } else {
 #pragma unroll
             for (int c = 0; c < 4; c += 2) {
                 float n1 = fabsf(x[4 * q + c] - ys[c]);
                 float n2 = fabsf(x[4 * q + c + 1] - ys[c + 1]);
-                float d1 = fabsf(x[4 * q + c]) + 1e-30f + fabsf(ys[c]);
-                float d2 = fabsf(x[4 * q + c + 1]) + 1e-30f + fabsf(ys[c + 1]);
+                float d1 = fabsf(x[4 * q + c]) + 1e-18f + fabsf(ys[c]);
+                float d2 = fabsf(x[4 * q + c + 1]) + 1e-18f + fabsf(ys[c + 1]);
                 float num = fmaf(n2, d1, n1 * d2);
                 float den = d1 * d2;
                 if (c == 0) acc0 = fmaf(num, rcp_approx(den), acc0);
@@ -111,7 +119,7 @@ __device__ __forceinline__ float pair_dist(const float (&x)[D], const float4 *__
     }
     float a = acc0 + acc1;
     if (METRIC == SILH_EUCLIDEAN) return sqrt_approx(a);
-    if (METRIC == SILH_COSINE) return fminf(fmaxf(1.0f - a, 0.0f), 2.0f);
+    if (METRIC == SILH_COSINE) return 0.5f * a;
     return a;
 }
 
@@ -121,13 +129,15 @@ template <class T, int METRIC, int D, int RPT, int BN>
 __global__ void __launch_bounds__(kThreads)
 k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__restrict__ labels,
         int k, const int64_t *__restrict__ sizes, const int64_t *__restrict__ offsets,
-        const float *__restrict__ Y, const float *__restrict__ wY, const int64_t *__restrict__ rows,
-        int64_t nrows, float *__restrict__ s_out, float *__restrict__ a_out,
-        float *__restrict__ b_out) {
+        const float *__restrict__ Y, const float *__restrict__ wY, const float *__restrict__ zY,
+        const int64_t *__restrict__ rows, int64_t nrows, float *__restrict__ s_out,
+        float *__restrict__ a_out, float *__restrict__ b_out) {
     __shared__ __align__(16) float sh_y[BN * D];
     __shared__ float sh_w[BN];
+    __shared__ float sh_z[BN];
     constexpr int BM = kThreads * RPT;
     float x[RPT][D];
+    float zx[RPT];   // cosine: 0.5 for a zero row (distance 1 to everything)
     int own[RPT];
     double wown[RPT], bmin[RPT];
     int64_t r0 = (int64_t)blockIdx.x * BM;
@@ -140,14 +150,16 @@ k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__
             int l = labels[e];
             own[r] = (l >= 0 && l < k) ? l : -2;
         }
-        float sc = 0.f;
+        double sc = 0.0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             x[r][c] = (e >= 0 && e < n && c < d) ? to_f32<T>(X[e * ld + c]) : 0.f;
-            sc += x[r][c] * x[r][c];
+            sc += (double)x[r][c] * (double)x[r][c];
         }
+        zx[r] = 0.f;
         if (METRIC == SILH_COSINE) {
-            float inv = sc > 0.f ? rsqrtf(sc) : 0.f;
+            float inv = sc > 0.0 ? (float)(1.0 / sqrt(sc)) : 0.f;
+            zx[r] = sc > 0.0 ? 0.f : 0.5f;
 #pragma unroll
             for (int c = 0; c < D; ++c) x[r][c] *= inv;
         }
@@ -165,19 +177,30 @@ k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__
             const float4 *src = reinterpret_cast<const float4 *>(Y + cb * D);
             float4 *dst = reinterpret_cast<float4 *>(sh_y);
             for (int q = threadIdx.x; q < nb * (D / 4); q += kThreads) dst[q] = src[q];
-            for (int q = threadIdx.x; q < BN; q += kThreads) sh_w[q] = (q < nb) ? wY[cb + q] : 0.f;
+            for (int q = threadIdx.x; q < BN; q += kThreads) {
+                sh_w[q] = (q < nb) ? wY[cb + q] : 0.f;
+                if (METRIC == SILH_COSINE) sh_z[q] = (q < nb) ? zY[cb + q] : 0.f;
+            }
             __syncthreads();
             float accf[RPT];
+            float accz = 0.f, accw = 0.f;
 #pragma unroll
             for (int r = 0; r < RPT; ++r) accf[r] = 0.f;
             for (int col = 0; col < nb; ++col) {
                 const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * D);
                 float w = sh_w[col];
+                if (METRIC == SILH_COSINE) {
+                    accz += sh_z[col];
+                    accw += w;
+                }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) accf[r] = fmaf(w, pair_dist<METRIC, D>(x[r], y4), accf[r]);
             }
 #pragma unroll
-            for (int r = 0; r < RPT; ++r) accd[r] += (double)accf[r];
+            for (int r = 0; r < RPT; ++r) {
+                if (METRIC == SILH_COSINE) accf[r] += accz + zx[r] * accw;
+                accd[r] += (double)accf[r];
+            }
         }
         double csz = (double)sizes[j];
 #pragma unroll
@@ -210,24 +233,24 @@ k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__
 template <class T, int METRIC, int D>
 void launch_sweep(cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
                   const int32_t *labels, int k, const int64_t *sizes, const int64_t *offsets,
-                  const float *Y, const float *wY, const int64_t *rows, int64_t nrows, float *s,
-                  float *a, float *b) {
+                  const float *Y, const float *wY, const float *zY, const int64_t *rows,
+                  int64_t nrows, float *s, float *a, float *b) {
     constexpr int RPT = (D <= 32) ? 2 : 1;
     constexpr int BN = (D <= 32) ? 64 : 32;
     int grid = (int)((nrows + kThreads * RPT - 1) / (kThreads * RPT));
     k_sweep<T, METRIC, D, RPT, BN><<<grid, kThreads, 0, stream>>>(
-        X, d, ld, n, labels, k, sizes, offsets, Y, wY, rows, nrows, s, a, b); count_launches(1);
+        X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, rows, nrows, s, a, b); count_launches(1);
 }
 
 template <class T, int METRIC>
 void launch_sweep_d(int D, cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
                     const int32_t *labels, int k, const int64_t *sizes, const int64_t *offsets,
-                    const float *Y, const float *wY, const int64_t *rows, int64_t nrows, float *s,
-                    float *a, float *b) {
-#define SILH_SWEEP_D(DD)                                                                  \
-    case DD:                                                                              \
-        launch_sweep<T, METRIC, DD>(stream, X, d, ld, n, labels, k, sizes, offsets, Y, wY, \
-                                    rows, nrows, s, a, b);                                \
+                    const float *Y, const float *wY, const float *zY, const int64_t *rows,
+                    int64_t nrows, float *s, float *a, float *b) {
+#define SILH_SWEEP_D(DD)                                                                      \
+    case DD:                                                                                  \
+        launch_sweep<T, METRIC, DD>(stream, X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, \
+                                    rows, nrows, s, a, b);                                    \
         break;
     switch (D) {
         SILH_SWEEP_D(8)
@@ -243,24 +266,24 @@ void launch_sweep_d(int D, cudaStream_t stream, const T *X, int d, int64_t ld, i
 template <class T>
 void launch_sweep_m(int metric, int D, cudaStream_t stream, const T *X, int d, int64_t ld,
                     int64_t n, const int32_t *labels, int k, const int64_t *sizes,
-                    const int64_t *offsets, const float *Y, const float *wY, const int64_t *rows,
-                    int64_t nrows, float *s, float *a, float *b) {
+                    const int64_t *offsets, const float *Y, const float *wY, const float *zY,
+                    const int64_t *rows, int64_t nrows, float *s, float *a, float *b) {
     switch (metric) {
         case SILH_EUCLIDEAN:
             launch_sweep_d<T, SILH_EUCLIDEAN>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
-                                              Y, wY, rows, nrows, s, a, b);
+                                              Y, wY, zY, rows, nrows, s, a, b);
             break;
         case SILH_COSINE:
             launch_sweep_d<T, SILH_COSINE>(D, stream, X, d, ld, n, labels, k, sizes, offsets, Y,
-                                           wY, rows, nrows, s, a, b);
+                                           wY, zY, rows, nrows, s, a, b);
             break;
         case SILH_MANHATTAN:
             launch_sweep_d<T, SILH_MANHATTAN>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
-                                              Y, wY, rows, nrows, s, a, b);
+                                              Y, wY, zY, rows, nrows, s, a, b);
             break;
         default:
             launch_sweep_d<T, SILH_CANBERRA>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
-                                             Y, wY, rows, nrows, s, a, b);
+                                             Y, wY, zY, rows, nrows, s, a, b);
             break;
     }
 }
@@ -302,16 +325,16 @@ __global__ void k_sum_final(const double *__restrict__ part, int np, int64_t n,
 
 silh_status gather_columns(const void *X, silh_dtype dtype, int32_t d, int64_t ld,
                            const int32_t *idx, const double *p, int64_t m, int D, int metric,
-                           float *Y, float *wY, cudaStream_t stream) {
+                           float *Y, float *wY, float *zY, cudaStream_t stream) {
     silh_status st = SILH_OK;
     if (m > 0) {
         int grid = ceil_div_i(m, 8);
         if (dtype == SILH_F32)
             k_gather<float><<<grid, 256, 0, stream>>>((const float *)X, d, ld, idx, p, m, D,
-                                                      metric, Y, wY);
+                                                      metric, Y, wY, zY);
         else
             k_gather<__nv_bfloat16><<<grid, 256, 0, stream>>>((const __nv_bfloat16 *)X, d, ld,
-                                                              idx, p, m, D, metric, Y, wY);
+                                                              idx, p, m, D, metric, Y, wY, zY);
         count_launches(1);
     }
     SILH_CK(cudaGetLastError());
@@ -322,18 +345,19 @@ done:
 silh_status phase2_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                          const int32_t *labels, int32_t k, int metric, int prec,
                          const int64_t *sizes, const int64_t *offsets, const float *Y,
-                         const float *wY, int64_t m, int D, const int64_t *rows, int64_t nrows,
-                         float *s, float *a, float *b, cudaStream_t stream) {
+                         const float *wY, const float *zY, int64_t m, int D, const int64_t *rows,
+                         int64_t nrows, float *s, float *a, float *b, cudaStream_t stream) {
     silh_status st = SILH_OK;
     (void)prec;
     (void)m;
     if (nrows > 0) {
         if (dtype == SILH_F32)
             launch_sweep_m<float>(metric, D, stream, (const float *)X, d, ld, n, labels, k, sizes,
-                                  offsets, Y, wY, rows, nrows, s, a, b);
+                                  offsets, Y, wY, zY, rows, nrows, s, a, b);
         else
             launch_sweep_m<__nv_bfloat16>(metric, D, stream, (const __nv_bfloat16 *)X, d, ld, n,
-                                          labels, k, sizes, offsets, Y, wY, rows, nrows, s, a, b);
+                                          labels, k, sizes, offsets, Y, wY, zY, rows, nrows, s,
+                                          a, b);
     }
     SILH_CK(cudaGetLastError());
 done:
@@ -368,7 +392,7 @@ extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n,
     int dev = 0;
     int D = padded_dim(d);
     Scratch sc(stream);
-    float *Y = nullptr, *wY = nullptr;
+    float *Y = nullptr, *wY = nullptr, *zY = nullptr;
     int64_t m = 0;
     SILH_REQ(S && S->k == k && S->sizes && S->offsets, "sample missing or k mismatch");
     m = S->size;
@@ -380,10 +404,11 @@ extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n,
     ensure_pool_retains(dev);
     SILH_CK(sc.alloc(&Y, (size_t)m * D));
     SILH_CK(sc.alloc(&wY, (size_t)m));
-    st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, Y, wY, stream);
+    SILH_CK(sc.alloc(&zY, (size_t)m));
+    st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, Y, wY, zY, stream);
     if (st != SILH_OK) goto done;
-    st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, S->sizes, S->offsets, Y, wY, m,
-                      D, rows, nrows, s_hat, a_hat, b_hat, stream);
+    st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, S->sizes, S->offsets, Y, wY, zY,
+                      m, D, rows, nrows, s_hat, a_hat, b_hat, stream);
 done:
     return st;
 }
@@ -401,7 +426,7 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     std::vector<int64_t> h_sizes, h_coff;
     int64_t *sizes = nullptr, *coff = nullptr;
     int32_t *order = nullptr;
-    float *Y = nullptr, *wY = nullptr;
+    float *Y = nullptr, *wY = nullptr, *zY = nullptr;
     SILH_REQ(s, "s is null");
     if (rows == nullptr) nrows = n;
     SILH_REQ(nrows >= 0, "nrows < 0");
@@ -412,10 +437,11 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     if (st != SILH_OK) goto done;
     SILH_CK(sc.alloc(&Y, (size_t)n * D));
     SILH_CK(sc.alloc(&wY, (size_t)n));
-    st = gather_columns(X, dtype, d, ld, order, nullptr, n, D, metric, Y, wY, stream);
+    SILH_CK(sc.alloc(&zY, (size_t)n));
+    st = gather_columns(X, dtype, d, ld, order, nullptr, n, D, metric, Y, wY, zY, stream);
     if (st != SILH_OK) goto done;
-    st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, Y, wY, n, D, rows,
-                      nrows, s, a, b, stream);
+    st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, Y, wY, zY, n, D,
+                      rows, nrows, s, a, b, stream);
 done:
     return st;
 }

@@ -25,18 +25,18 @@ cudaError_t scan_flags(const int32_t *flags, int64_t n, int64_t *out, int64_t *d
 
 // Rows of the Phase-2 column operand: Y[i, :] = X[idx[i], :] for i < m, padded
 // with zeros to D columns; cosine rows are scaled to unit norm.  wY[i] = 1/p[i]
-// (or 1 when p == nullptr).
+// (or 1 when p == nullptr); zY[i] = 0.5 wY[i] for a zero cosine column, else 0.
 silh_status gather_columns(const void *X, silh_dtype dtype, int32_t d, int64_t ld,
                            const int32_t *idx, const double *p, int64_t m, int D, int metric,
-                           float *Y, float *wY, cudaStream_t stream);
+                           float *Y, float *wY, float *zY, cudaStream_t stream);
 
 // Phase-2 sweep: for every listed row, W_hat_j over the cluster-major column
 // operand (Y, wY, offsets) and the silhouette of Eq. 8.
 silh_status phase2_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                          const int32_t *labels, int32_t k, int metric, int prec,
                          const int64_t *sizes, const int64_t *offsets, const float *Y,
-                         const float *wY, int64_t m, int D, const int64_t *rows, int64_t nrows,
-                         float *s, float *a, float *b, cudaStream_t stream);
+                         const float *wY, const float *zY, int64_t m, int D, const int64_t *rows,
+                         int64_t nrows, float *s, float *a, float *b, cudaStream_t stream);
 
 // Padded row width of the column operand for a given d.
 int padded_dim(int d);

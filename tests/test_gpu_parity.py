@@ -201,3 +201,36 @@ def test_capacity_error_reports_needed_size():
     assert ei.value.status == silh.SILH_ECAPACITY
     full = silh.silh_sample_pps(Xt, lt, 4, "euclidean", t=64.0, m0=16.0)
     assert full.size > 10
+
+
+def _degenerate():
+    """Zero rows, exact-zero coordinates, a cluster of identical points (its
+    W(e0) = 0, so gamma falls back to 1/|Cj|) and a singleton."""
+    X, lab, _ = synth.gaussian_mixture(600, 5, 3, seed=21, sizes=[300, 200, 100])
+    X = X.copy()
+    lab = np.concatenate([lab, np.full(50, 3, np.int32), [4]]).astype(np.int32)
+    X = np.concatenate([X, np.tile(np.array([[1.5, -2.0, 0.0, 3.0, 0.25]], np.float32), (50, 1)),
+                        np.array([[0.5, 0.5, 0.5, 0.5, 0.5]], np.float32)])
+    X[10] = 0.0                     # zero vector (cosine distance 1 to everything)
+    X[20, 1] = 0.0
+    X[21, :2] = 0.0                 # Canberra 0/0 terms where paired with zeros
+    X[300:310, 2] = 0.0
+    return np.ascontiguousarray(X), lab, 5
+
+
+@pytest.mark.parametrize("metric", METRICS)
+def test_degenerate_inputs_match_oracle(metric):
+    X, lab, k = _degenerate()
+    Xt, lt = _to_dev(X, lab)
+    Xh = _host_values(Xt)
+    gs = silh.silh_sample_pps(Xt, lt, k, metric, t=20.0, m0=6.0, seed=2)
+    os_ = oracle.sample_pps(Xh, lab, k, metric, t=20.0, m0=6.0, seed=2)
+    assert_same_sample(gs, os_, k, 2, 0)
+    s, a, b = silh.silh_estimate(Xt, lt, k, gs, metric, want_ab=True)
+    s_o, a_o, b_o = oracle.estimate(Xh, lab, k, metric, os_.offsets, os_.idx, os_.ps)
+    _assert_close(s, s_o)
+    np.testing.assert_allclose(a.cpu().numpy(), a_o, rtol=AB_RTOL, atol=1e-6)
+    se = silh.silh_exact(Xt, lt, k, metric)
+    se_o, _, _ = oracle.exact(Xh, lab, k, metric)
+    _assert_close(se, se_o)
+    assert s[-1].item() == 0.0 and se[-1].item() == 0.0     # singleton
