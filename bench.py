@@ -127,7 +127,7 @@ def cpu_oracle_sample(X, lab, rows_exact, k, t, delta, budget_s=20.0):
     Xc = synth.abs_shift(X).astype(np.float64)
     Xs, ls = Xd[rows_exact], lab[rows_exact]
     Xsc = Xc[rows_exact]
-    m2, m3 = 8192, 1024
+    m2, m3 = min(8192, n), min(1024, len(rows_exact))
     r2 = synth.seeded_rows(n, m2, seed=7)
     r3 = synth.seeded_rows(len(rows_exact), m3, seed=8)
     total = 0.0
@@ -162,7 +162,7 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     silh.load()
     w = WORKLOAD
-    X, lab, rows_ex = make_workload(seed=1 + rank)
+    X, lab, rows_ex = make_workload(seed=1 + rank, scale=args.scale)
     n, d, k = X.shape[0], X.shape[1], w["k"]
     Xc = synth.abs_shift(X)
     sizes = np.bincount(lab, minlength=k)
@@ -271,6 +271,23 @@ def dist_evals(res, t_step_samples):
     return total
 
 
+def _profiled_traffic(kernel_key):
+    """DRAM bytes per full launch from a committed ncu capture, or None when the
+    kernel source has changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel_key)
+        if rec is None:
+            return None
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != rec["source_sha1"]:
+                return None
+        return rec["bytes_per_launch_full"]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def roofline(res, peaks, peak_kind):
     """Dominant kernel: the Phase-2 sweep of the metric with the longest leg.
 
@@ -288,20 +305,27 @@ def roofline(res, peaks, peak_kind):
     achieved = ops / (mean_p2[dom] * 1e-3) / 1e9          # Gop/s
     clock = peaks.get("sm_max_mhz", 2032.0)
     peak = 148 * 128 * clock * 1e6 / 1e9                   # FP32 lanes x clock
+    traffic = _profiled_traffic(f"k_sweep_{dom}") if res["n"] == WORKLOAD["n"] else None
     return dom, {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
-                 "unit": "Gop/s", "frac": round(achieved / peak, 4), "traffic": None,
+                 "unit": "Gop/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                  "kernel": f"k_sweep ({dom}, Phase 2)",
                  "peak_source": f"148 SMs x 128 FP32 lanes x {clock:.0f} MHz ({peak_kind} clock)"}
 
 
 def main():
+    global METRICS
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="silh", choices=["silh", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="scale n and the exact subset (profiling cases only)")
+    ap.add_argument("--metrics", default=",".join(METRICS),
+                    help="comma-separated subset of metrics (profiling cases only)")
     args = ap.parse_args()
+    METRICS = tuple(m for m in args.metrics.split(",") if m)
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -318,7 +342,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        X, lab, rows = make_workload(seed=1)
+        X, lab, rows = make_workload(seed=1, scale=args.scale)
         import oracle
         ts = []
         desc = ""
@@ -326,7 +350,7 @@ def main():
             t_step, desc = cpu_oracle_sample(X, lab, rows, w["k"], w["t"], w["delta"])
             ts.append(t_step)
         t_mean = float(np.mean(ts))
-        value = 4 * w["n"] / t_mean
+        value = len(METRICS) * X.shape[0] / t_mean
         line = {"impl": "reference", "metric": "PPS silhouette points/s", "value": value,
                 "unit": "points/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": t_mean * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -347,7 +371,7 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    pts = 4 * res["n"] * world
+    pts = len(METRICS) * res["n"] * world
     value = pts / (res["ms"] * 1e-3)
     evals = dist_evals(res, None) * world
     dom, roof = roofline(res, peaks, peak_kind)
@@ -367,7 +391,8 @@ def main():
         import oracle
         t_cpu, desc = cpu_oracle_sample(res["X"], res["lab"], res["rows"], res["k"], WORKLOAD["t"],
                                         WORKLOAD["delta"])
-        line["cpu_baseline"] = {"value": round(4 * res["n"] / t_cpu, 1), "unit": "points/s",
+        line["cpu_baseline"] = {"value": round(len(METRICS) * res["n"] / t_cpu, 1),
+                                "unit": "points/s",
                                 "cores": oracle.nthreads(), "kind": "oracle", "sample": desc}
     print(json.dumps(line))
     if world > 1:

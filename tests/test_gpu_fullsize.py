@@ -1,0 +1,77 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py times.
+
+The oracle runs Phase 1 in full (FP64, all n) so the sample sets are compared
+element by element; Phase 2 and the exact silhouette are compared on seeded
+row samples that the oracle evaluates one by one.  The global mean is checked
+as a property that holds at any size (FP64 mean of the GPU's own s values).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2607_01993_b300 import silh, synth
+from test_gpu_parity import S_TOL, _assert_close, _host_values, assert_same_sample
+
+pytestmark = pytest.mark.gpu
+
+LARGE = dict(n=1_000_000, d=32, k=32, t=256.0, delta=0.01, exact_rows=100_000, seed=1)
+
+
+@pytest.fixture(scope="module")
+def large():
+    w = LARGE
+    X, lab, _ = synth.large(seed=w["seed"], n=w["n"], d=w["d"], k=w["k"])
+    rows_ex = synth.seeded_rows(w["n"], w["exact_rows"], seed=w["seed"] + 1000)
+    return X, lab, rows_ex
+
+
+@pytest.mark.parametrize("metric", ["euclidean", "cosine", "manhattan", "canberra"])
+def test_large_workload_sampled_parity(large, metric):
+    w = LARGE
+    X, lab, rows_ex = large
+    if metric == "canberra":
+        X = synth.abs_shift(X)
+    k = w["k"]
+    Xt = torch.from_numpy(X).cuda()
+    lt = torch.from_numpy(lab).cuda()
+    gs = silh.silh_sample_pps(Xt, lt, k, metric, t=w["t"], delta=w["delta"], seed=7,
+                              clustering_id=1)
+    s = silh.silh_estimate(Xt, lt, k, gs, metric)
+    g = silh.silh_global(s).item()
+    Xh = X.astype(np.float64)
+    os_ = oracle.sample_pps(Xh, lab, k, metric, t=w["t"], delta=w["delta"], seed=7, cid=1)
+    ties = assert_same_sample(gs, os_, k, 7, 1)
+    assert ties <= 2
+    rows = synth.seeded_rows(w["n"], 300, seed=11)
+    s_o, _, _ = oracle.estimate(Xh, lab, k, metric, os_.offsets, os_.idx, os_.ps, rows=rows)
+    _assert_close(s[torch.from_numpy(rows).cuda()], s_o)
+    s_h = s.cpu().numpy().astype(np.float64)
+    assert np.isfinite(s_h).all() and (np.abs(s_h) <= 1).all()
+    assert abs(g - s_h.mean()) <= 1e-9
+
+    # exact silhouette of the 100k-row sub-dataset, checked on 200 of its rows
+    Xs = np.ascontiguousarray(X[rows_ex])
+    ls = np.ascontiguousarray(lab[rows_ex])
+    se = silh.silh_exact(torch.from_numpy(Xs).cuda(), torch.from_numpy(ls).cuda(), k, metric)
+    r3 = synth.seeded_rows(len(rows_ex), 200, seed=12)
+    se_o, _, _ = oracle.exact(Xs.astype(np.float64), ls, k, metric, rows=r3)
+    _assert_close(se[torch.from_numpy(r3).cuda()], se_o)
+
+
+def test_precision_workload_bf16_sampled_parity():
+    """n = 4M, d = 64, k = 64, 10% border points, data stored BF16; Euclidean."""
+    X, lab, _ = synth.precision(seed=2)
+    k, t = 64, 128.0
+    Xt = torch.from_numpy(X).cuda().to(torch.bfloat16)
+    del X
+    lt = torch.from_numpy(lab).cuda()
+    gs = silh.silh_sample_pps(Xt, lt, k, "euclidean", t=t, delta=0.01, seed=3)
+    Xh = _host_values(Xt)
+    os_ = oracle.sample_pps(Xh, lab, k, "euclidean", t=t, delta=0.01, seed=3)
+    assert_same_sample(gs, os_, k, 3, 0)
+    rows = synth.seeded_rows(lab.shape[0], 200, seed=13)
+    s = silh.silh_estimate(Xt, lt, k, gs, "euclidean", rows=torch.from_numpy(rows).cuda())
+    s_o, _, _ = oracle.estimate(Xh, lab, k, "euclidean", os_.offsets, os_.idx, os_.ps, rows=rows)
+    _assert_close(s, s_o)
+    assert S_TOL == 1e-5
