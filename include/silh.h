@@ -123,6 +123,34 @@ silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n, int32_t d,
                           const silh_sample *S, const int64_t *rows, int64_t nrows,
                           float *s_hat, float *a_hat, float *b_hat, void *stream);
 
+/* Limits of silh_estimate_noalloc's fixed scratch (8.5 MiB per device). */
+#define SILH_NOALLOC_MAX_COLUMNS 65536
+#define SILH_NOALLOC_MAX_FLOATS 2097152
+
+/* silh_estimate without any device allocation.  The paper has no counterpart:
+ * this is a deployment variant of silh_estimate for callers that cannot
+ * allocate device memory while they run -- a host framework that has already
+ * reserved all of the device's memory for its own allocator, a latency-bound
+ * loop that cannot take an allocation (or its failure) in the middle of a
+ * stream, or code running inside an allocator or driver callback.  Arguments,
+ * results and errors are those of silh_estimate, which it matches exactly; the
+ * caller still provides every input and output buffer.
+ * Scratch: a fixed array in the library's device image (every GPU that loads
+ * libsilh holds it until the process exits) sized for |S| <=
+ * SILH_NOALLOC_MAX_COLUMNS sampled columns and |S| x D <= SILH_NOALLOC_MAX_FLOATS
+ * (D = d rounded up to 8, 16, 32, 64 or 128); larger samples are rejected with
+ * SILH_ECAPACITY before any work is enqueued.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress, no allocation); make that
+ * first call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents; each call rewrites everything it reads, so nothing
+ * needs clearing, but calls whose work overlaps on the GPU race on it and must
+ * be ordered by the caller.  Asynchronous. */
+silh_status silh_estimate_noalloc(const void *X, silh_dtype dtype, int64_t n, int32_t d,
+                                  int64_t ld, const int32_t *labels, int32_t k,
+                                  silh_metric metric, silh_prec prec, const silh_sample *S,
+                                  const int64_t *rows, int64_t nrows, float *s_hat, float *a_hat,
+                                  float *b_hat, void *stream);
+
 /* Exact silhouette (Eq. 1-2) of the listed rows against all n elements:
  * Phase 2 with F_Cj = Cj and p = 1.  Synchronising (validates labels).
  * Errors: as silh_sample_pps. */

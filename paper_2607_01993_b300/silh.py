@@ -25,7 +25,9 @@ SILH_ECAPACITY = -4
 
 # exported symbols, as declared in include/silh.h
 EXPORTS = ("silh_sample_pps", "silh_estimate", "silh_exact", "silh_global", "silh_t_from_eps",
-           "silh_last_error", "silh_version", "silh_kernel_launches")
+           "silh_last_error", "silh_version", "silh_kernel_launches", "silh_estimate_noalloc")
+SILH_NOALLOC_MAX_COLUMNS = 65536
+SILH_NOALLOC_MAX_FLOATS = 2097152
 
 
 class SilhError(RuntimeError):
@@ -59,6 +61,8 @@ def load(path: str = LIB_PATH):
     lib.silh_estimate.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32, ctypes.c_int,
                                   ctypes.c_int, ctypes.POINTER(SilhSample), vp, i64, vp, vp, vp, vp]
     lib.silh_estimate.restype = ctypes.c_int
+    lib.silh_estimate_noalloc.argtypes = list(lib.silh_estimate.argtypes)
+    lib.silh_estimate_noalloc.restype = ctypes.c_int
     lib.silh_exact.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32, ctypes.c_int,
                                ctypes.c_int, vp, i64, vp, vp, vp, vp]
     lib.silh_exact.restype = ctypes.c_int
@@ -175,6 +179,28 @@ def silh_estimate(X, labels, k, sample: Sample, metric="euclidean", prec="fp32",
     _check(lib.silh_estimate(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric],
                              PRECS[prec], ctypes.byref(st), _ptr(rows), nr, _ptr(s), _ptr(a),
                              _ptr(b), _stream(stream)))
+    return (s, a, b) if want_ab else s
+
+
+def silh_estimate_noalloc(X, labels, k, sample: Sample, metric="euclidean", prec="fp32",
+                          rows=None, want_ab=False, out=None, stream=None):
+    """silh_estimate through the no-allocation entry point (fixed device scratch).
+
+    For callers that cannot allocate device memory during the call; the output
+    tensors are allocated here only when the caller does not pass them.
+    """
+    lib = load()
+    dt, n, d, ld = _data(X)
+    labels = _labels(labels)
+    rows, nr = _rows(rows)
+    nrows = n if rows is None else nr
+    s = out if out is not None else torch.empty(nrows, dtype=torch.float32, device=X.device)
+    a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    st = sample.as_struct()
+    _check(lib.silh_estimate_noalloc(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric],
+                                     PRECS[prec], ctypes.byref(st), _ptr(rows), nr, _ptr(s),
+                                     _ptr(a), _ptr(b), _stream(stream)))
     return (s, a, b) if want_ab else s
 
 
