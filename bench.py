@@ -36,6 +36,9 @@ sys.path.insert(0, ROOT)
 from paper_2607_01993_b300 import synth  # noqa: E402
 
 METRICS = ("euclidean", "cosine", "manhattan", "canberra")
+# arithmetic per metric: split-TF32 tensor cores for the inner-product metrics
+# (held to the FP32 bound |ds| <= 1e-5), FP32 CUDA cores for the others
+PREC = {"euclidean": "3xtf32", "cosine": "3xtf32", "manhattan": "fp32", "canberra": "fp32"}
 WORKLOAD = dict(name="large", n=1_000_000, d=32, k=32, t=256.0, delta=0.01, exact_rows=100_000)
 
 
@@ -192,10 +195,10 @@ def run_gpu(args, rank, world, local_rank):
             smp = silh.silh_sample_pps(Xm, bufs["lab"], k, metric, t=w["t"], delta=w["delta"],
                                        seed=seed, clustering_id=mi)
             ev[1].record(stream)
-            s = silh.silh_estimate(Xm, bufs["lab"], k, smp, metric)
+            s = silh.silh_estimate(Xm, bufs["lab"], k, smp, metric, prec=PREC[metric])
             ev[2].record(stream)
             gm = silh.silh_global(s)
-            se = silh.silh_exact(Xsm, bufs["ls"], k, metric)
+            se = silh.silh_exact(Xsm, bufs["ls"], k, metric, prec=PREC[metric])
             ge = silh.silh_global(se)
             ev[3].record(stream)
             results[metric] = (s, gm, ge, smp.size)
@@ -336,7 +339,7 @@ def main():
                           f"mixture; t={int(w['t'])}, delta={w['delta']}; 4 metrics; exact on "
                           f"{w['exact_rows']}-row subset",
               "n": w["n"], "d": w["d"], "k": w["k"], "t": w["t"],
-              "metrics": list(METRICS), "l2": "flushed (256 MB write) between timed steps",
+              "metrics": list(METRICS), "precision": {m: PREC[m] for m in METRICS}, "l2": "flushed (256 MB write) between timed steps",
               "parallelism": f"replicas x{world}"}
 
     if args.impl == "reference":

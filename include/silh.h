@@ -164,6 +164,13 @@ silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, int32_t d, in
  * Asynchronous.  Errors: SILH_EINVAL if n < 1 or a pointer is NULL. */
 silh_status silh_global(const float *s, int64_t n, double *out, void *stream);
 
+/* Waits for all work on stream, then reports whether any bounded device wait
+ * of the library gave up since the previous call (SILH_ETIMEOUT; the results
+ * of the affected call are then incomplete) and clears that record.  Kernels
+ * never trap or spin without limit; this is how a stalled pipeline surfaces.
+ * Synchronising. */
+silh_status silh_stream_status(void *stream);
+
 /* Lemma 1: t = ceil((3c/eps^2) ln(5 n k / delta)) with c = 18.  Host-only. */
 double silh_t_from_eps(double eps, double delta, int64_t n, int32_t k);
 

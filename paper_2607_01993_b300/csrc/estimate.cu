@@ -402,6 +402,11 @@ extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n,
     SILH_REQ(nrows >= 0, "nrows < 0");
     SILH_CK(cudaGetDevice(&dev));
     ensure_pool_retains(dev);
+    if (m > 0 && nrows > 0 && tc_eligible(metric, prec, d)) {
+        st = tc_sweep(X, dtype, n, d, ld, labels, k, metric, prec, S->sizes, S->offsets, S->idx,
+                      S->p, m, rows, nrows, s_hat, a_hat, b_hat, sc, stream);
+        goto done;
+    }
     SILH_CK(sc.alloc(&Y, (size_t)m * D));
     SILH_CK(sc.alloc(&wY, (size_t)m));
     SILH_CK(sc.alloc(&zY, (size_t)m));
@@ -435,6 +440,11 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     SILH_CK(sc.alloc(&sizes, (size_t)k));
     st = cluster_sort(labels, n, k, sc, stream, sizes, &coff, &order, h_sizes, h_coff);
     if (st != SILH_OK) goto done;
+    if (nrows > 0 && tc_eligible(metric, prec, d)) {
+        st = tc_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, order, nullptr, n,
+                      rows, nrows, s, a, b, sc, stream);
+        goto done;
+    }
     SILH_CK(sc.alloc(&Y, (size_t)n * D));
     SILH_CK(sc.alloc(&wY, (size_t)n));
     SILH_CK(sc.alloc(&zY, (size_t)n));
@@ -442,6 +452,17 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     if (st != SILH_OK) goto done;
     st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, Y, wY, zY, n, D,
                       rows, nrows, s, a, b, stream);
+done:
+    return st;
+}
+
+extern "C" silh_status silh_stream_status(void *stream_) {
+    silh_status st = SILH_OK;
+    int e = 0;
+    SILH_CK(cudaStreamSynchronize((cudaStream_t)stream_));
+    e = tc_take_error();
+    if (e < 0) st = fail(SILH_ECUDA, "reading the device error word failed");
+    else if (e > 0) st = fail(SILH_ETIMEOUT, "a bounded device wait gave up");
 done:
     return st;
 }

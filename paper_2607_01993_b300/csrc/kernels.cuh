@@ -41,4 +41,15 @@ silh_status phase2_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
 // Padded row width of the column operand for a given d.
 int padded_dim(int d);
 
+// Tensor-core sweep (Euclidean / cosine, TF32 or split TF32, d <= 64).
+bool tc_eligible(int metric, int prec, int d);
+silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                     const int32_t *labels, int32_t k, int metric, int prec, const int64_t *sizes,
+                     const int64_t *offsets, const int32_t *col_idx, const double *col_p, int64_t m,
+                     const int64_t *rows, int64_t nrows, float *s, float *a, float *b, Scratch &sc,
+                     cudaStream_t stream);
+// 1 if a bounded wait in the tensor-core sweep gave up since the last call
+// (and clears it), 0 if not, -1 on a CUDA error.  Synchronous.
+int tc_take_error();
+
 }  // namespace silh

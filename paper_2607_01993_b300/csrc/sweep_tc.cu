@@ -1,0 +1,802 @@
+// Tensor-core Phase-2 / exact sweep for the Euclidean and cosine distances.
+//
+// The inner products x.y of a 128-row tile against a 128-column tile of the
+// cluster-major sample are one tcgen05 MMA chain (kind::tf32, FP32 accumulate
+// in tensor memory).  SILH_PREC_3XTF32 splits every operand into a TF32 head
+// and an FP32 tail (x = hi + lo) and accumulates hi.hi + hi.lo + lo.hi, which
+// leaves an inner-product error of a few 2^-22 |x||y|; SILH_PREC_TF32 uses the
+// heads only.  The epilogue turns each inner product into a distance
+//   Euclidean: d = sqrt(|x|^2 + |y|^2 - 2 x.y)   cosine: d = 1 - x^.y^
+// multiplies by the inclusion weight 1/p and adds it to the running sum of the
+// current cluster (Algorithm 1, Phase 2); W_hat never leaves the SM.  Pairs
+// whose distance is small against the magnitudes that cancel in it
+// (Euclidean: d^2 < tau (|x|^2 + |y|^2); cosine: d < tau) are recomputed
+// directly in FP32 from the coordinates, so close pairs (mostly a row's own
+// cluster) keep FP32 relative accuracy.
+//
+// Roles (one persistent CTA per SM, 6 warps): warp 0 issues TMA loads of the
+// row tile and of the column tiles into a ring of shared-memory stages, warp 1
+// issues the MMAs into two TMEM accumulators (so the MMA of tile t+1 overlaps
+// the epilogue of tile t), warps 2-5 (128 threads, one per row / TMEM lane) run
+// the epilogue.  Every wait is bounded; on a timeout the CTA records an error
+// and stops.
+//
+// Rows are processed in cluster-sorted order so that a warp's rows share their
+// own cluster and the recompute branch rarely diverges.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <climits>
+#include <cmath>
+#include <mutex>
+
+#include "kernels.cuh"
+#include "tc_util.cuh"
+
+namespace silh {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kTileM = 128;       // rows per tile = TMEM lanes
+constexpr int kTileN = 128;       // columns per tile
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+
+__device__ int g_tc_error = 0;    // set when a bounded wait gives up
+
+template <int KD, bool SPLIT>
+struct TcCfg {
+    static constexpr int KB = KD / 32;                          // 128-byte K blocks
+    static constexpr int PARTS = SPLIT ? 2 : 1;                 // hi (+ lo)
+    static constexpr int SLOTS = (KD == 32) ? 2 : 1;            // row tiles per CTA pass
+    static constexpr int A_SLOT = PARTS * KB * kTileM * 128;
+    static constexpr int A_BYTES = SLOTS * A_SLOT;
+    static constexpr int B_BYTES = PARTS * KB * kTileN * 128;   // one stage
+    static constexpr int STAGES = (KD == 32) ? (SPLIT ? 4 : 8) : (SPLIT ? 2 : 4);
+    static constexpr int SMEM = 1024 + A_BYTES + STAGES * B_BYTES;
+    static constexpr int THREADS = 64 + 128 * SLOTS;            // TMA, MMA, epilogue groups
+    static constexpr uint32_t TMEM_COLS = SLOTS * 2 * kTileN;   // two accumulators per slot
+};
+
+// Named barrier (1 + group) over one epilogue group's 128 threads that also
+// ORs a predicate, so that the whole group takes the same decision to stop.
+__device__ __forceinline__ bool epi_bar_any(int group, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\t"
+        "setp.ne.u32 pi, %2, 0;\n\t"
+        "barrier.red.or.pred po, %1, 128, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"(1 + group), "r"((uint32_t)pred)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ float sqrt_apx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <int METRIC, int KD>
+__device__ __forceinline__ float direct_dist(const float (&x)[KD], const float *__restrict__ y) {
+    const float4 *y4 = reinterpret_cast<const float4 *>(y);
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < KD / 4; ++q) {
+        float4 v = __ldg(y4 + q);
+        float t0 = x[4 * q] - v.x, t1 = x[4 * q + 1] - v.y;
+        float t2 = x[4 * q + 2] - v.z, t3 = x[4 * q + 3] - v.w;
+        a0 = fmaf(t0, t0, a0); a1 = fmaf(t1, t1, a1);
+        a0 = fmaf(t2, t2, a0); a1 = fmaf(t3, t3, a1);
+    }
+    float s = a0 + a1;
+    return METRIC == SILH_EUCLIDEAN ? sqrtf(s) : 0.5f * s;
+}
+
+// Column layout: cluster j occupies padded columns [poff[j], poff[j+1]), its
+// |F_j| sampled columns first, then zero columns of weight 0 up to a multiple
+// of 32, so every 32-column chunk belongs to exactly one cluster.
+template <int METRIC, int KD, bool SPLIT>
+__global__ void __launch_bounds__(TcCfg<KD, SPLIT>::THREADS, 1)
+k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CUtensorMap m_alo,
+           const __grid_constant__ CUtensorMap m_bhi, const __grid_constant__ CUtensorMap m_blo,
+           const float *__restrict__ a_hi, const float *__restrict__ a_lo,
+           const float *__restrict__ a_norm, const int32_t *__restrict__ a_lab,
+           const int64_t *__restrict__ a_out, int64_t nrows, const float *__restrict__ y_full,
+           const float2 *__restrict__ y_wn, const int64_t *__restrict__ poff,
+           const int64_t *__restrict__ sizes, int k, float tau, float *__restrict__ s_out,
+           float *__restrict__ a_out_v, float *__restrict__ b_out_v) {
+    using C = TcCfg<KD, SPLIT>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bar_full[C::STAGES], bar_empty[C::STAGES];
+    __shared__ uint64_t bar_afull, bar_aempty, bar_accf[C::SLOTS][2], bar_acce[C::SLOTS][2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+    __shared__ __align__(16) float2 sh_wn[C::SLOTS][2][kTileN];
+
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    uint8_t *sA = sm;                   // [slot][part][kb][128 rows][128 B]
+    uint8_t *sB = sm + C::A_BYTES;      // [stage][part][kb][128 cols][128 B]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = (nrows + kTileM - 1) / kTileM;
+    const int64_t ngroups = (ntiles + C::SLOTS - 1) / C::SLOTS;
+    const int64_t mp = poff[k];                       // padded column count
+    const int64_t nct = (mp + kTileN - 1) / kTileN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], 1);
+        }
+        mbar_init(&bar_afull, 1);
+        mbar_init(&bar_aempty, 1);
+        for (int g = 0; g < C::SLOTS; ++g)
+            for (int a = 0; a < 2; ++a) {
+                mbar_init(&bar_accf[g][a], 1);
+                mbar_init(&bar_acce[g][a], 4);
+            }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, C::TMEM_COLS);
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            tma_prefetch_desc(&m_ahi);
+            tma_prefetch_desc(&m_bhi);
+            if (SPLIT) {
+                tma_prefetch_desc(&m_alo);
+                tma_prefetch_desc(&m_blo);
+            }
+            int stage = 0;
+            uint32_t phase = 0;
+            int64_t idx = 0;
+            for (int64_t rg = blockIdx.x; rg < ngroups && !abort_flag; rg += gridDim.x, ++idx) {
+                if (idx > 0 && !mbar_wait(&bar_aempty, (uint32_t)((idx - 1) & 1), kWaitNs)) {
+                    abort_flag = 1;
+                    break;
+                }
+                mbar_expect_tx(&bar_afull, C::A_BYTES);
+                for (int g = 0; g < C::SLOTS; ++g) {
+                    const int y = (int)((rg * C::SLOTS + g) * kTileM);
+                    uint8_t *a = sA + g * C::A_SLOT;
+                    for (int kb = 0; kb < C::KB; ++kb) {
+                        tma_load_2d(&m_ahi, &bar_afull, a + kb * kTileM * 128, kb * 32, y);
+                        if (SPLIT)
+                            tma_load_2d(&m_alo, &bar_afull, a + (C::KB + kb) * kTileM * 128,
+                                        kb * 32, y);
+                    }
+                }
+                for (int64_t ct = 0; ct < nct; ++ct) {
+                    if (!mbar_wait(&bar_empty[stage], phase ^ 1u, kWaitNs)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    uint8_t *dst = sB + stage * C::B_BYTES;
+                    mbar_expect_tx(&bar_full[stage], C::B_BYTES);
+                    for (int kb = 0; kb < C::KB; ++kb) {
+                        tma_load_2d(&m_bhi, &bar_full[stage], dst + kb * kTileN * 128, kb * 32,
+                                    (int)(ct * kTileN));
+                        if (SPLIT)
+                            tma_load_2d(&m_blo, &bar_full[stage],
+                                        dst + (C::KB + kb) * kTileN * 128, kb * 32,
+                                        (int)(ct * kTileN));
+                    }
+                    if (++stage == C::STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(kTileM, kTileN);
+            int stage = 0;
+            uint32_t phase = 0, acc = 0, acc_phase = 0;
+            int64_t idx = 0;
+            for (int64_t rg = blockIdx.x; rg < ngroups && !abort_flag; rg += gridDim.x, ++idx) {
+                if (!mbar_wait(&bar_afull, (uint32_t)(idx & 1), kWaitNs)) {
+                    abort_flag = 1;
+                    break;
+                }
+                for (int64_t ct = 0; ct < nct; ++ct) {
+                    if (!mbar_wait(&bar_full[stage], phase, kWaitNs)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    const uint8_t *b = sB + stage * C::B_BYTES;
+                    bool ok = true;
+                    for (int g = 0; g < C::SLOTS; ++g) {
+                        if (!mbar_wait(&bar_acce[g][acc], acc_phase ^ 1u, kWaitNs)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after_sync();
+                        const uint32_t d_tmem = tmem + (uint32_t)(g * 2 + acc) * kTileN;
+                        const uint8_t *a = sA + g * C::A_SLOT;
+                        uint32_t accumulate = 0;
+#pragma unroll
+                        for (int kb = 0; kb < C::KB; ++kb) {
+#pragma unroll
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint32_t off = ks * 32;
+                                const uint64_t ahi =
+                                    sw128_kmajor_desc(smem_u32(a + kb * kTileM * 128) + off);
+                                const uint64_t bhi =
+                                    sw128_kmajor_desc(smem_u32(b + kb * kTileN * 128) + off);
+                                if (SPLIT) {
+                                    const uint64_t alo = sw128_kmajor_desc(
+                                        smem_u32(a + (C::KB + kb) * kTileM * 128) + off);
+                                    const uint64_t blo = sw128_kmajor_desc(
+                                        smem_u32(b + (C::KB + kb) * kTileN * 128) + off);
+                                    mma_tf32(d_tmem, alo, bhi, idesc, accumulate);
+                                    accumulate = 1;
+                                    mma_tf32(d_tmem, ahi, blo, idesc, 1);
+                                }
+                                mma_tf32(d_tmem, ahi, bhi, idesc, accumulate);
+                                accumulate = 1;
+                            }
+                        }
+                        mma_commit(&bar_accf[g][acc]);
+                    }
+                    if (!ok) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    mma_commit(&bar_empty[stage]);
+                    if (++stage == C::STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                    acc ^= 1u;
+                    if (acc == 0) acc_phase ^= 1u;
+                }
+                mma_commit(&bar_aempty);
+                if (abort_flag) break;
+            }
+            // The last A-release arrival must land before the CTA exits.
+            if (!abort_flag && idx > 0 &&
+                !mbar_wait(&bar_aempty, (uint32_t)((idx - 1) & 1), kWaitNs))
+                abort_flag = 1;
+        }
+    } else {
+        // ------------------------------------------------ epilogue groups
+        const int g = (warp - 2) >> 2;          // row-tile slot of this group
+        const int q = warp & 3;                 // TMEM lane quarter of this warp
+        const int r_local = 32 * q + lane;
+        const int et = threadIdx.x - 64 - 128 * g;
+        const uint32_t tlane = (uint32_t)(32 * q) << 16;
+        uint32_t acc = 0, acc_phase = 0;
+        int buf = 0;
+        for (int64_t rg = blockIdx.x; rg < ngroups; rg += gridDim.x) {
+            const int64_t pos = (rg * C::SLOTS + g) * kTileM + r_local;
+            const bool valid = pos < nrows;
+            const int own = valid ? a_lab[pos] : -1;
+            const float xn = valid ? a_norm[pos] : 0.f;
+            float x[KD];
+#pragma unroll
+            for (int c = 0; c < KD; ++c)
+                x[c] = valid ? a_hi[pos * KD + c] + a_lo[pos * KD + c] : 0.f;
+            int j = 0;
+            int64_t pbnd = poff[1];
+            double accd = 0.0, wown = 0.0, bmin = INFINITY;
+            bool dead = false;
+            for (int64_t ct = 0; ct < nct; ++ct) {
+                const int64_t cc = ct * kTileN + et;
+                sh_wn[g][buf][et] = (cc < mp) ? y_wn[cc] : make_float2(0.f, 0.f);
+                const bool ok = !abort_flag && mbar_wait(&bar_accf[g][acc], acc_phase, kWaitNs);
+                if (epi_bar_any(g, !ok)) {      // also orders the sh_wn writes before the reads
+                    abort_flag = 1;
+                    dead = true;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t tcol = tmem + tlane + (uint32_t)(g * 2 + acc) * kTileN;
+#pragma unroll 1
+                for (int ch = 0; ch < kTileN / 32; ++ch) {
+                    const int64_t c0 = ct * kTileN + ch * 32;
+                    // clusters that end here (empty ones included) are complete
+                    while (j < k && c0 == pbnd) {
+                        if (j == own) wown = accd;
+                        else bmin = fmin(bmin, accd / (double)sizes[j]);
+                        accd = 0.0;
+                        ++j;
+                        pbnd = (j < k) ? poff[j + 1] : LLONG_MAX;
+                    }
+                    if (j >= k) continue;                 // padding beyond the last cluster
+                    const float4 *wn4 = reinterpret_cast<const float4 *>(&sh_wn[g][buf][ch * 32]);
+                    float v[32];
+                    __syncwarp();
+                    tmem_ld_32x32(tcol + ch * 32, v);
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                    float flagmin = INFINITY;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float4 wn = wn4[i];         // (w, |y|^2) of columns 2i, 2i+1
+                        float d0, d1;
+                        if (METRIC == SILH_EUCLIDEAN) {
+                            const float s0 = xn + wn.y, s1 = xn + wn.w;
+                            const float q0 = fmaf(-2.f, v[2 * i], s0);
+                            const float q1 = fmaf(-2.f, v[2 * i + 1], s1);
+                            flagmin = fminf(flagmin, fminf(fmaf(-tau, s0, q0), fmaf(-tau, s1, q1)));
+                            d0 = sqrt_apx(q0);
+                            d1 = sqrt_apx(q1);
+                        } else {
+                            d0 = 1.f - v[2 * i];
+                            d1 = 1.f - v[2 * i + 1];
+                            flagmin = fminf(flagmin, fminf(d0, d1) - tau);
+                        }
+                        if (i & 1) {
+                            a2 = fmaf(wn.x, d0, a2);
+                            a3 = fmaf(wn.z, d1, a3);
+                        } else {
+                            a0 = fmaf(wn.x, d0, a0);
+                            a1 = fmaf(wn.z, d1, a1);
+                        }
+                    }
+                    float accf = (a0 + a1) + (a2 + a3);
+                    if (__any_sync(0xffffffffu, flagmin < 0.f)) {
+                        // some lane has a close pair in this chunk: redo the chunk
+                        // column by column, recomputing flagged pairs directly
+                        accf = 0.f;
+#pragma unroll 1
+                        for (int i = 0; i < 32; ++i) {
+                            __syncwarp();
+                            const float dot = tmem_ld_32x1(tcol + ch * 32 + i);
+                            const float2 wn = sh_wn[g][buf][ch * 32 + i];
+                            const float *yc = y_full + (c0 + i) * KD;
+                            float dist;
+                            if (METRIC == SILH_EUCLIDEAN) {
+                                const float s2 = xn + wn.y;
+                                const float d2 = fmaf(-2.f, dot, s2);
+                                dist = (d2 < tau * s2) ? direct_dist<METRIC, KD>(x, yc) : sqrt_apx(d2);
+                            } else {
+                                dist = 1.f - dot;
+                                if (dist < tau) dist = direct_dist<METRIC, KD>(x, yc);
+                            }
+                            accf = fmaf(wn.x, dist, accf);
+                        }
+                    }
+                    accd += (double)accf;
+                }
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_acce[g][acc]);
+                acc ^= 1u;
+                if (acc == 0) acc_phase ^= 1u;
+                buf ^= 1;
+            }
+            if (dead) break;
+            // clusters after the last processed chunk (the current one and empty ones)
+            while (j < k) {
+                if (j == own) wown = accd;
+                else bmin = fmin(bmin, accd / (double)sizes[j]);
+                accd = 0.0;
+                ++j;
+            }
+            if (valid) {
+                const int64_t o = a_out[pos];
+                float sv, av, bv;
+                if (own < 0 || own >= k) {
+                    sv = av = bv = NAN;
+                } else {
+                    const int64_t nc = sizes[own];
+                    const double a = (nc > 1) ? wown / (double)(nc - 1) : 0.0;
+                    const double b = bmin;
+                    const double mx = fmax(a, b);
+                    sv = (float)((nc > 1 && mx > 0.0) ? (b - a) / mx : 0.0);
+                    av = (float)a;
+                    bv = (float)b;
+                }
+                s_out[o] = sv;
+                if (a_out_v) a_out_v[o] = av;
+                if (b_out_v) b_out_v[o] = bv;
+            }
+        }
+    }
+    if (threadIdx.x == 0 && abort_flag) atomicExch(&g_tc_error, 1);
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc(tmem, C::TMEM_COLS);
+    }
+}
+
+// --------------------------------------------------------- row ordering
+
+// Row r of the listed rows (rows == nullptr: row r) gets key = its label, or k
+// when the label is outside [0, k); rows are ordered by key, stably.
+__global__ void k_key_hist(const int32_t *__restrict__ labels, const int64_t *__restrict__ rows,
+                           int64_t nrows, int64_t n, int k, int tile, int ntiles,
+                           int32_t *__restrict__ counts) {
+    extern __shared__ int32_t sh_cnt[];
+    for (int j = threadIdx.x; j <= k; j += 32) sh_cnt[j] = 0;
+    __syncwarp();
+    const int64_t base = (int64_t)blockIdx.x * tile, end = min(base + (int64_t)tile, nrows);
+    for (int64_t r = base + threadIdx.x; r < end; r += 32) {
+        const int64_t e = rows ? rows[r] : r;
+        const int32_t l = (e >= 0 && e < n) ? labels[e] : -1;
+        atomicAdd(&sh_cnt[(l >= 0 && l < k) ? l : k], 1);
+    }
+    __syncwarp();
+    for (int j = threadIdx.x; j <= k; j += 32) counts[(int64_t)j * ntiles + blockIdx.x] = sh_cnt[j];
+}
+
+__global__ void k_key_scan(const int32_t *__restrict__ counts, int ntiles,
+                           int64_t *__restrict__ tile_base, int64_t *__restrict__ totals) {
+    __shared__ int64_t sh[256];
+    const int j = blockIdx.x;
+    const int32_t *c = counts + (int64_t)j * ntiles;
+    int64_t *o = tile_base + (int64_t)j * ntiles;
+    const int per = (ntiles + 255) / 256;
+    const int lo = threadIdx.x * per, hi = min(lo + per, ntiles);
+    int64_t s = 0;
+    for (int i = lo; i < hi; ++i) s += c[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        const int64_t v = (threadIdx.x >= (unsigned)off) ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = sh[threadIdx.x] - s;
+    for (int i = lo; i < hi; ++i) {
+        o[i] = run;
+        run += c[i];
+    }
+    if (threadIdx.x == 255) totals[j] = sh[255];
+}
+
+// boff[j] = sum of totals[0..j), j = 0..nb (single block).
+__global__ void k_key_offsets(const int64_t *__restrict__ totals, int nb, int64_t *__restrict__ boff) {
+    __shared__ int64_t sh[1024];
+    const int per = (nb + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(lo + per, nb);
+    int64_t s = 0;
+    for (int i = lo; i < hi; ++i) s += totals[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int64_t v = (threadIdx.x >= (unsigned)off) ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = sh[threadIdx.x] - s;
+    for (int i = lo; i < hi; ++i) {
+        boff[i] = run;
+        run += totals[i];
+    }
+    if (threadIdx.x == 1023) boff[nb] = sh[1023];
+}
+
+__global__ void k_key_scatter(const int32_t *__restrict__ labels, const int64_t *__restrict__ rows,
+                              int64_t nrows, int64_t n, int k, int tile, int ntiles,
+                              const int64_t *__restrict__ tile_base, const int64_t *__restrict__ boff,
+                              int64_t *__restrict__ perm) {
+    extern __shared__ int32_t sh_cnt[];
+    for (int j = threadIdx.x; j <= k; j += 32) sh_cnt[j] = 0;
+    __syncwarp();
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    const int64_t base = (int64_t)blockIdx.x * tile, end = min(base + (int64_t)tile, nrows);
+    for (int64_t r0 = base; r0 < end; r0 += 32) {
+        const int64_t r = r0 + threadIdx.x;
+        int key = -1;
+        if (r < end) {
+            const int64_t e = rows ? rows[r] : r;
+            const int32_t l = (e >= 0 && e < n) ? labels[e] : -1;
+            key = (l >= 0 && l < k) ? l : k;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int rank = __popc(peers & lt);
+        const int cnt = (key >= 0) ? sh_cnt[key] : 0;
+        __syncwarp();
+        if (key >= 0) {
+            perm[boff[key] + tile_base[(int64_t)key * ntiles + blockIdx.x] + cnt + rank] = r;
+            if (rank == 0) sh_cnt[key] = cnt + __popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------- gathers
+
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Row operand in sorted order: hi/lo split (KD columns, zero padded), squared
+// norm (Euclidean) or unit scaling (cosine), label, and output index.
+template <class T>
+__global__ void k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int64_t n,
+                                 const int32_t *__restrict__ labels, const int64_t *__restrict__ rows,
+                                 const int64_t *__restrict__ perm, int64_t nrows, int KD, int k,
+                                 int metric, float *__restrict__ hi, float *__restrict__ lo,
+                                 float *__restrict__ nrm, int32_t *__restrict__ lab,
+                                 int64_t *__restrict__ outi) {
+    const int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (p >= nrows) return;
+    const int64_t r = perm[p];
+    const int64_t e = rows ? rows[r] : r;
+    const bool ok = e >= 0 && e < n;
+    const T *x = X + (ok ? e : 0) * ld;
+    double s = 0.0;
+    for (int c = lane; c < d; c += 32) {
+        const double v = ok ? (double)to_f32<T>(x[c]) : 0.0;
+        s += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float scale = (metric == SILH_COSINE) ? (s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f) : 1.f;
+    float ss = 0.f;
+    for (int c = lane; c < KD; c += 32) {
+        const float v = (ok && c < d) ? to_f32<T>(x[c]) * scale : 0.f;
+        const float h = to_tf32(v);
+        hi[p * KD + c] = h;
+        lo[p * KD + c] = v - h;
+        ss = fmaf(v, v, ss);
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) {
+        nrm[p] = (metric == SILH_COSINE) ? 1.f : (float)s;
+        const int32_t l = ok ? labels[e] : -1;
+        lab[p] = (l >= 0 && l < k) ? l : -1;
+        outi[p] = r;
+    }
+}
+
+// Padded per-cluster column offsets: poff[j+1] = poff[j] + roundup(|F_j|, 32)
+// (single block).
+__global__ void k_col_poff(const int64_t *__restrict__ offsets, int k, int64_t *__restrict__ poff) {
+    __shared__ int64_t sh[1024];
+    const int per = (k + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(lo + per, k);
+    int64_t s = 0;
+    for (int j = lo; j < hi; ++j) s += (offsets[j + 1] - offsets[j] + 31) & ~int64_t(31);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int64_t v = (threadIdx.x >= (unsigned)off) ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = sh[threadIdx.x] - s;
+    for (int j = lo; j < hi; ++j) {
+        poff[j] = run;
+        run += (offsets[j + 1] - offsets[j] + 31) & ~int64_t(31);
+    }
+    if (threadIdx.x == 1023) poff[k] = sh[1023];
+}
+
+// Column operand in the padded layout (one warp per padded column): full FP32
+// copy, hi/lo split, (weight, squared norm).  Padding columns are zero with
+// weight 0.  Source column of sampled position t is idx[t] (idx == nullptr: t).
+template <class T>
+__global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
+                                 const int32_t *__restrict__ idx, const double *__restrict__ p,
+                                 const int64_t *__restrict__ offsets,
+                                 const int64_t *__restrict__ poff, int k, int64_t mp_max, int KD,
+                                 int metric, float *__restrict__ full, float *__restrict__ hi,
+                                 float *__restrict__ lo, float2 *__restrict__ wn) {
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (i >= mp_max) return;
+    int64_t t = -1;
+    if (i < poff[k]) {
+        int lo_j = 0, hi_j = k - 1;            // last j with poff[j] <= i
+        while (lo_j < hi_j) {
+            const int mid = (lo_j + hi_j + 1) >> 1;
+            if (poff[mid] <= i) lo_j = mid;
+            else hi_j = mid - 1;
+        }
+        const int64_t local = i - poff[lo_j];
+        if (local < offsets[lo_j + 1] - offsets[lo_j]) t = offsets[lo_j] + local;
+    }
+    if (t < 0) {
+        for (int c = lane; c < KD; c += 32) {
+            full[i * KD + c] = 0.f;
+            hi[i * KD + c] = 0.f;
+            lo[i * KD + c] = 0.f;
+        }
+        if (lane == 0) wn[i] = make_float2(0.f, 0.f);
+        return;
+    }
+    const int64_t e = idx ? idx[t] : t;
+    const T *x = X + e * ld;
+    double s = 0.0;
+    for (int c = lane; c < d; c += 32) {
+        const double v = (double)to_f32<T>(x[c]);
+        s += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float scale = (metric == SILH_COSINE) ? (s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f) : 1.f;
+    for (int c = lane; c < KD; c += 32) {
+        const float v = (c < d) ? to_f32<T>(x[c]) * scale : 0.f;
+        const float h = to_tf32(v);
+        full[i * KD + c] = v;
+        hi[i * KD + c] = h;
+        lo[i * KD + c] = v - h;
+    }
+    if (lane == 0) {
+        const float w = p ? (float)(1.0 / p[t]) : 1.0f;
+        wn[i] = make_float2(w, (metric == SILH_COSINE) ? 1.f : (float)s);
+    }
+}
+
+// ------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+bool make_map(CUtensorMap *map, const float *ptr, int KD, int64_t rows, int box_rows) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)KD, (cuuint64_t)rows};
+    cuuint64_t gstr[1] = {(cuuint64_t)KD * sizeof(float)};
+    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, gdim, gstr, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int METRIC, int KD, bool SPLIT>
+cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, const CUtensorMap &alo,
+                      const CUtensorMap &bhi, const CUtensorMap &blo, const float *a_hi,
+                      const float *a_lo, const float *a_norm, const int32_t *a_lab,
+                      const int64_t *a_out, int64_t nrows, const float *y_full, const float2 *y_wn,
+                      const int64_t *poff, const int64_t *sizes, int k, float tau, float *s,
+                      float *a, float *b) {
+    using C = TcCfg<KD, SPLIT>;
+    auto kern = k_sweep_tc<METRIC, KD, SPLIT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    const int64_t groups = ((nrows + kTileM - 1) / kTileM + C::SLOTS - 1) / C::SLOTS;
+    const int grid = (int)std::min<int64_t>(groups, nsm);
+    kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_norm, a_lab,
+                                                a_out, nrows, y_full, y_wn, poff, sizes, k, tau, s,
+                                                a, b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_eligible(int metric, int prec, int d) {
+    return (metric == SILH_EUCLIDEAN || metric == SILH_COSINE) &&
+           (prec == SILH_PREC_TF32 || prec == SILH_PREC_3XTF32) && d <= 64 &&
+           encode_fn() != nullptr;
+}
+
+silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                     const int32_t *labels, int32_t k, int metric, int prec, const int64_t *sizes,
+                     const int64_t *offsets, const int32_t *col_idx, const double *col_p, int64_t m,
+                     const int64_t *rows, int64_t nrows, float *s, float *a, float *b, Scratch &sc,
+                     cudaStream_t stream) {
+    silh_status st = SILH_OK;
+    const int KD = d <= 32 ? 32 : 64;
+    const bool split = prec == SILH_PREC_3XTF32;
+    const int tile = (k <= 512) ? 1024 : 8192;
+    const int ntiles = (int)std::max<int64_t>(1, (nrows + tile - 1) / tile);
+    const size_t hsmem = sizeof(int32_t) * (size_t)(k + 1);
+    const int64_t mp_max = m + 31 * (int64_t)k;   // padded columns, upper bound
+    int dev = 0, nsm = 0;
+    int32_t *counts = nullptr, *lab = nullptr;
+    int64_t *tbase = nullptr, *tot = nullptr, *boff = nullptr, *perm = nullptr, *outi = nullptr;
+    int64_t *poff = nullptr;
+    float *rhi = nullptr, *rlo = nullptr, *rn = nullptr, *yf = nullptr, *yhi = nullptr,
+          *ylo = nullptr;
+    float2 *ywn = nullptr;
+    CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
+    const float tau = (metric == SILH_EUCLIDEAN) ? 0.25f : 0.25f;
+
+    SILH_CK(sc.alloc(&counts, (size_t)(k + 1) * ntiles));
+    SILH_CK(sc.alloc(&tbase, (size_t)(k + 1) * ntiles));
+    SILH_CK(sc.alloc(&tot, (size_t)k + 1));
+    SILH_CK(sc.alloc(&boff, (size_t)k + 2));
+    SILH_CK(sc.alloc(&perm, (size_t)nrows));
+    SILH_CK(sc.alloc(&outi, (size_t)nrows));
+    SILH_CK(sc.alloc(&lab, (size_t)nrows));
+    SILH_CK(sc.alloc(&rhi, (size_t)nrows * KD));
+    SILH_CK(sc.alloc(&rlo, (size_t)nrows * KD));
+    SILH_CK(sc.alloc(&rn, (size_t)nrows));
+    SILH_CK(sc.alloc(&poff, (size_t)k + 1));
+    SILH_CK(sc.alloc(&yf, (size_t)mp_max * KD));
+    SILH_CK(sc.alloc(&yhi, (size_t)mp_max * KD));
+    SILH_CK(sc.alloc(&ylo, (size_t)mp_max * KD));
+    SILH_CK(sc.alloc(&ywn, (size_t)mp_max));
+    if (hsmem > 48 * 1024) {
+        SILH_CK(cudaFuncSetAttribute(k_key_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)hsmem));
+        SILH_CK(cudaFuncSetAttribute(k_key_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)hsmem));
+    }
+    k_key_hist<<<ntiles, 32, hsmem, stream>>>(labels, rows, nrows, n, k, tile, ntiles, counts);
+    k_key_scan<<<k + 1, 256, 0, stream>>>(counts, ntiles, tbase, tot);
+    k_key_offsets<<<1, 1024, 0, stream>>>(tot, k + 1, boff);
+    k_key_scatter<<<ntiles, 32, hsmem, stream>>>(labels, rows, nrows, n, k, tile, ntiles, tbase,
+                                                  boff, perm);
+    k_col_poff<<<1, 1024, 0, stream>>>(offsets, k, poff);
+    count_launches(5);
+    if (dtype == SILH_F32) {
+        k_gather_rows_tc<float><<<ceil_div_i(nrows, 8), 256, 0, stream>>>(
+            (const float *)X, d, ld, n, labels, rows, perm, nrows, KD, k, metric, rhi, rlo, rn, lab,
+            outi);
+        k_gather_cols_tc<float><<<ceil_div_i(mp_max, 8), 256, 0, stream>>>(
+            (const float *)X, d, ld, col_idx, col_p, offsets, poff, k, mp_max, KD, metric, yf,
+            yhi, ylo, ywn);
+    } else {
+        k_gather_rows_tc<__nv_bfloat16><<<ceil_div_i(nrows, 8), 256, 0, stream>>>(
+            (const __nv_bfloat16 *)X, d, ld, n, labels, rows, perm, nrows, KD, k, metric, rhi, rlo,
+            rn, lab, outi);
+        k_gather_cols_tc<__nv_bfloat16><<<ceil_div_i(mp_max, 8), 256, 0, stream>>>(
+            (const __nv_bfloat16 *)X, d, ld, col_idx, col_p, offsets, poff, k, mp_max, KD, metric,
+            yf, yhi, ylo, ywn);
+    }
+    count_launches(2);
+    SILH_CK(cudaGetLastError());
+    SILH_REQ(make_map(&m_ahi, rhi, KD, nrows, kTileM) && make_map(&m_alo, rlo, KD, nrows, kTileM) &&
+                 make_map(&m_bhi, yhi, KD, mp_max, kTileN) &&
+                 make_map(&m_blo, ylo, KD, mp_max, kTileN),
+             "tensor map encoding failed");
+    SILH_CK(cudaGetDevice(&dev));
+    SILH_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+#define SILH_TC_CASE(MET, KDV, SP)                                                              \
+    if (metric == MET && KD == KDV && split == SP) {                                           \
+        SILH_CK((launch_tc<MET, KDV, SP>(nsm, stream, m_ahi, m_alo, m_bhi, m_blo, rhi, rlo, rn, \
+                                         lab, outi, nrows, yf, ywn, poff, sizes, k, tau, s, a,  \
+                                         b)));                                                 \
+    }
+    SILH_TC_CASE(SILH_EUCLIDEAN, 32, true)
+    SILH_TC_CASE(SILH_EUCLIDEAN, 32, false)
+    SILH_TC_CASE(SILH_EUCLIDEAN, 64, true)
+    SILH_TC_CASE(SILH_EUCLIDEAN, 64, false)
+    SILH_TC_CASE(SILH_COSINE, 32, true)
+    SILH_TC_CASE(SILH_COSINE, 32, false)
+    SILH_TC_CASE(SILH_COSINE, 64, true)
+    SILH_TC_CASE(SILH_COSINE, 64, false)
+#undef SILH_TC_CASE
+done:
+    return st;
+}
+
+int tc_take_error() {
+    int h = 0;
+    if (cudaMemcpyFromSymbol(&h, g_tc_error, sizeof(int)) != cudaSuccess) return -1;
+    if (h) {
+        int z = 0;
+        cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int));
+    }
+    return h;
+}
+
+}  // namespace silh

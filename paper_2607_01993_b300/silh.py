@@ -25,7 +25,8 @@ SILH_ECAPACITY = -4
 
 # exported symbols, as declared in include/silh.h
 EXPORTS = ("silh_sample_pps", "silh_estimate", "silh_exact", "silh_global", "silh_t_from_eps",
-           "silh_last_error", "silh_version", "silh_kernel_launches", "silh_estimate_noalloc")
+           "silh_last_error", "silh_version", "silh_kernel_launches", "silh_estimate_noalloc",
+           "silh_stream_status")
 SILH_NOALLOC_MAX_COLUMNS = 65536
 SILH_NOALLOC_MAX_FLOATS = 2097152
 
@@ -74,6 +75,8 @@ def load(path: str = LIB_PATH):
     lib.silh_last_error.restype = ctypes.c_char_p
     lib.silh_version.argtypes = []
     lib.silh_version.restype = ctypes.c_char_p
+    lib.silh_stream_status.argtypes = [vp]
+    lib.silh_stream_status.restype = ctypes.c_int
     lib.silh_kernel_launches.argtypes = []
     lib.silh_kernel_launches.restype = ctypes.c_uint64
     _lib = lib
@@ -232,6 +235,12 @@ def silh_global(s, out=None, stream=None):
 
 def silh_t_from_eps(eps, delta, n, k) -> float:
     return load().silh_t_from_eps(eps, delta, n, k)
+
+
+def silh_stream_status(stream=None):
+    """Synchronise the stream; raise SilhError(SILH_ETIMEOUT) if a bounded device
+    wait gave up since the previous check."""
+    _check(load().silh_stream_status(_stream(stream)))
 
 
 def kernel_launches() -> int:

@@ -26,8 +26,12 @@ def large():
     return X, lab, rows_ex
 
 
+PREC = {"euclidean": "3xtf32", "cosine": "3xtf32", "manhattan": "fp32", "canberra": "fp32"}
+
+
 @pytest.mark.parametrize("metric", ["euclidean", "cosine", "manhattan", "canberra"])
 def test_large_workload_sampled_parity(large, metric):
+    """The launch configuration bench.py times (same precision per metric)."""
     w = LARGE
     X, lab, rows_ex = large
     if metric == "canberra":
@@ -37,8 +41,9 @@ def test_large_workload_sampled_parity(large, metric):
     lt = torch.from_numpy(lab).cuda()
     gs = silh.silh_sample_pps(Xt, lt, k, metric, t=w["t"], delta=w["delta"], seed=7,
                               clustering_id=1)
-    s = silh.silh_estimate(Xt, lt, k, gs, metric)
+    s = silh.silh_estimate(Xt, lt, k, gs, metric, prec=PREC[metric])
     g = silh.silh_global(s).item()
+    silh.silh_stream_status()
     Xh = X.astype(np.float64)
     os_ = oracle.sample_pps(Xh, lab, k, metric, t=w["t"], delta=w["delta"], seed=7, cid=1)
     ties = assert_same_sample(gs, os_, k, 7, 1)
@@ -53,7 +58,8 @@ def test_large_workload_sampled_parity(large, metric):
     # exact silhouette of the 100k-row sub-dataset, checked on 200 of its rows
     Xs = np.ascontiguousarray(X[rows_ex])
     ls = np.ascontiguousarray(lab[rows_ex])
-    se = silh.silh_exact(torch.from_numpy(Xs).cuda(), torch.from_numpy(ls).cuda(), k, metric)
+    se = silh.silh_exact(torch.from_numpy(Xs).cuda(), torch.from_numpy(ls).cuda(), k, metric,
+                         prec=PREC[metric])
     r3 = synth.seeded_rows(len(rows_ex), 200, seed=12)
     se_o, _, _ = oracle.exact(Xs.astype(np.float64), ls, k, metric, rows=r3)
     _assert_close(se[torch.from_numpy(r3).cuda()], se_o)
@@ -71,7 +77,10 @@ def test_precision_workload_bf16_sampled_parity():
     os_ = oracle.sample_pps(Xh, lab, k, "euclidean", t=t, delta=0.01, seed=3)
     assert_same_sample(gs, os_, k, 3, 0)
     rows = synth.seeded_rows(lab.shape[0], 200, seed=13)
-    s = silh.silh_estimate(Xt, lt, k, gs, "euclidean", rows=torch.from_numpy(rows).cuda())
-    s_o, _, _ = oracle.estimate(Xh, lab, k, "euclidean", os_.offsets, os_.idx, os_.ps, rows=rows)
-    _assert_close(s, s_o)
+    for prec in ("fp32", "3xtf32"):
+        s = silh.silh_estimate(Xt, lt, k, gs, "euclidean", prec=prec,
+                               rows=torch.from_numpy(rows).cuda())
+        s_o, _, _ = oracle.estimate(Xh, lab, k, "euclidean", os_.offsets, os_.idx, os_.ps,
+                                    rows=rows)
+        _assert_close(s, s_o)
     assert S_TOL == 1e-5

@@ -244,3 +244,74 @@ def test_degenerate_inputs_match_oracle(metric):
     se_o, _, _ = oracle.exact(Xh, lab, k, metric)
     _assert_close(se, se_o)
     assert s[-1].item() == 0.0 and se[-1].item() == 0.0     # singleton
+
+
+# ------------------------------------------------ tensor-core (tcgen05) sweep
+
+# Plain TF32 keeps 11 significant bits of each coordinate, so inner products
+# carry ~2^-11 relative error; its stated bound on s_hat is 2e-3.  Split TF32
+# (3 MMAs) plus the FP32 recompute of close pairs is held to the FP32 bound.
+TC_TOL = {"3xtf32": S_TOL, "tf32": 2e-3}
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "tf32"])
+@pytest.mark.parametrize("case", ["tiny", "ragged", "multitile"])
+@pytest.mark.parametrize("metric", ["euclidean", "cosine"])
+def test_tensor_core_estimate_matches_oracle(case, metric, prec):
+    X, lab, k, kw = _case(case)
+    Xt, lt = _to_dev(X, lab)
+    Xh = _host_values(Xt)
+    os_ = oracle.sample_pps(Xh, lab, k, metric, t=kw["t"], m0=kw["m0"], seed=kw["seed"])
+    smp = silh.Sample.from_lists(np.bincount(lab, minlength=k), os_.offsets, os_.idx, os_.ps,
+                                 Xt.device)
+    launches = silh.kernel_launches()
+    s, a, b = silh.silh_estimate(Xt, lt, k, smp, metric, prec=prec, want_ab=True)
+    silh.silh_stream_status()
+    assert silh.kernel_launches() > launches
+    s_o, a_o, b_o = oracle.estimate(Xh, lab, k, metric, os_.offsets, os_.idx, os_.ps)
+    s_g = s.cpu().numpy().astype(np.float64)
+    assert np.isfinite(s_g).all()
+    assert np.abs(s_g - s_o).max() <= TC_TOL[prec]
+    if prec == "3xtf32":
+        np.testing.assert_allclose(a.cpu().numpy(), a_o, rtol=AB_RTOL, atol=1e-7)
+        np.testing.assert_allclose(b.cpu().numpy(), b_o, rtol=AB_RTOL, atol=1e-7)
+
+
+@pytest.mark.parametrize("case", ["tiny", "ragged"])
+@pytest.mark.parametrize("metric", ["euclidean", "cosine"])
+def test_tensor_core_exact_matches_oracle(case, metric):
+    X, lab, k, _ = _case(case)
+    Xt, lt = _to_dev(X, lab)
+    Xh = _host_values(Xt)
+    s = silh.silh_exact(Xt, lt, k, metric, prec="3xtf32")
+    silh.silh_stream_status()
+    s_o, _, _ = oracle.exact(Xh, lab, k, metric)
+    _assert_close(s, s_o)
+
+
+@pytest.mark.parametrize("metric", ["euclidean", "cosine"])
+def test_tensor_core_rows_degenerate_and_bf16(metric):
+    X, lab, k = _degenerate()
+    Xt, lt = _to_dev(X, lab)
+    Xh = _host_values(Xt)
+    gs = silh.silh_sample_pps(Xt, lt, k, metric, t=20.0, m0=6.0, seed=2)
+    os_ = oracle.sample_pps(Xh, lab, k, metric, t=20.0, m0=6.0, seed=2)
+    assert_same_sample(gs, os_, k, 2, 0)
+    rows = torch.tensor([650, 3, 10, 21, 600, 0, 640], dtype=torch.int64, device="cuda")
+    s = silh.silh_estimate(Xt, lt, k, gs, metric, prec="3xtf32", rows=rows)
+    s_o, _, _ = oracle.estimate(Xh, lab, k, metric, os_.offsets, os_.idx, os_.ps,
+                                rows=rows.cpu().numpy())
+    _assert_close(s, s_o)
+    # BF16 storage through the tensor-core path
+    X2, lab2, k2, kw2 = _case("multitile")
+    Xb, lb = _to_dev(X2, lab2, torch.bfloat16)
+    Xbh = _host_values(Xb)
+    os2 = oracle.sample_pps(Xbh, lab2, k2, metric, t=128.0, seed=4)
+    smp2 = silh.Sample.from_lists(np.bincount(lab2, minlength=k2), os2.offsets, os2.idx, os2.ps,
+                                  Xb.device)
+    r2 = torch.arange(0, 40000, 131, dtype=torch.int64, device="cuda")
+    s2 = silh.silh_estimate(Xb, lb, k2, smp2, metric, prec="3xtf32", rows=r2)
+    s2_o, _, _ = oracle.estimate(Xbh, lab2, k2, metric, os2.offsets, os2.idx, os2.ps,
+                                 rows=r2.cpu().numpy())
+    _assert_close(s2, s2_o)
+    silh.silh_stream_status()
