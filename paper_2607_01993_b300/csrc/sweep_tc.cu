@@ -107,7 +107,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
            const float *__restrict__ a_norm, const int32_t *__restrict__ a_lab,
            const int64_t *__restrict__ a_out, int64_t nrows, const float *__restrict__ y_full,
            const float2 *__restrict__ y_wn, const int64_t *__restrict__ poff,
-           const int64_t *__restrict__ sizes, int k, float tau, float *__restrict__ s_out,
+           const int64_t *__restrict__ sizes, int k, float tau,
+           const double *__restrict__ w_own, float *__restrict__ s_out,
            float *__restrict__ a_out_v, float *__restrict__ b_out_v) {
     using C = TcCfg<KD, SPLIT>;
     extern __shared__ uint8_t smem_raw[];
@@ -290,7 +291,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 x[c] = valid ? a_hi[pos * KD + c] + a_lo[pos * KD + c] : 0.f;
             int j = 0;
             int64_t pbnd = poff[1];
-            double accd = 0.0, wown = 0.0, bmin = INFINITY;
+            double accd = 0.0, bmin = INFINITY;
+            float accf = 0.f;                         // current cluster, this tile
             bool dead = false;
             for (int64_t ct = 0; ct < nct; ++ct) {
                 const int64_t cc = ct * kTileN + et;
@@ -306,15 +308,19 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
 #pragma unroll 1
                 for (int ch = 0; ch < kTileN / 32; ++ch) {
                     const int64_t c0 = ct * kTileN + ch * 32;
-                    // clusters that end here (empty ones included) are complete
+                    // clusters that end here (empty ones included) are complete;
+                    // the own cluster's sum comes from the direct pass (w_own)
                     while (j < k && c0 == pbnd) {
-                        if (j == own) wown = accd;
-                        else bmin = fmin(bmin, accd / (double)sizes[j]);
+                        accd += (double)accf;
+                        accf = 0.f;
+                        if (j != own) bmin = fmin(bmin, accd / (double)sizes[j]);
                         accd = 0.0;
                         ++j;
                         pbnd = (j < k) ? poff[j + 1] : LLONG_MAX;
                     }
                     if (j >= k) continue;                 // padding beyond the last cluster
+                    const bool mine = (j == own);         // own-cluster pairs: skipped here
+                    if (__all_sync(0xffffffffu, mine)) continue;
                     const float4 *wn4 = reinterpret_cast<const float4 *>(&sh_wn[g][buf][ch * 32]);
                     float v[32];
                     __syncwarp();
@@ -345,11 +351,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             a1 = fmaf(wn.z, d1, a1);
                         }
                     }
-                    float accf = (a0 + a1) + (a2 + a3);
-                    if (__any_sync(0xffffffffu, flagmin < 0.f)) {
-                        // some lane has a close pair in this chunk: redo the chunk
-                        // column by column, recomputing flagged pairs directly
-                        accf = 0.f;
+                    float part = (a0 + a1) + (a2 + a3);
+                    if (__any_sync(0xffffffffu, !mine && flagmin < 0.f)) {
+                        // a lane has a close pair here: redo the chunk column by column,
+                        // recomputing the flagged pairs directly from the coordinates
+                        part = 0.f;
 #pragma unroll 1
                         for (int i = 0; i < 32; ++i) {
                             __syncwarp();
@@ -365,10 +371,10 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                                 dist = 1.f - dot;
                                 if (dist < tau) dist = direct_dist<METRIC, KD>(x, yc);
                             }
-                            accf = fmaf(wn.x, dist, accf);
+                            part = fmaf(wn.x, dist, part);
                         }
                     }
-                    accd += (double)accf;
+                    if (!mine) accf += part;
                 }
                 fence_before_sync();
                 __syncwarp();
@@ -376,15 +382,19 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 acc ^= 1u;
                 if (acc == 0) acc_phase ^= 1u;
                 buf ^= 1;
+                accd += (double)accf;                    // FP64 fold once per tile
+                accf = 0.f;
             }
             if (dead) break;
             // clusters after the last processed chunk (the current one and empty ones)
             while (j < k) {
-                if (j == own) wown = accd;
-                else bmin = fmin(bmin, accd / (double)sizes[j]);
+                accd += (double)accf;
+                accf = 0.f;
+                if (j != own) bmin = fmin(bmin, accd / (double)sizes[j]);
                 accd = 0.0;
                 ++j;
             }
+            const double wown = (valid && own >= 0) ? w_own[pos] : 0.0;
             if (valid) {
                 const int64_t o = a_out[pos];
                 float sv, av, bv;
@@ -412,6 +422,105 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
         __syncwarp();
         tmem_dealloc(tmem, C::TMEM_COLS);
     }
+}
+
+// Own-cluster pass: W_own[pos] = sum over the row's own cluster's sampled
+// columns of w d(x, y), evaluated directly in FP32 from the coordinates (these
+// are the close pairs where |x|^2 + |y|^2 - 2 x.y cancels).  One thread per
+// row in sorted order; a CTA streams the column blocks of the clusters its
+// rows belong to (contiguous, as rows are sorted by cluster).
+template <int METRIC, int KD>
+__global__ void __launch_bounds__(128)
+k_own_direct(const float *__restrict__ a_hi, const float *__restrict__ a_lo,
+             const float *__restrict__ a_norm, const int32_t *__restrict__ a_lab, int64_t nrows,
+             const float *__restrict__ y_full, const float2 *__restrict__ y_wn,
+             const int64_t *__restrict__ poff, int k, double *__restrict__ w_own) {
+    constexpr int BN = 64;
+    __shared__ __align__(16) float sh_y[BN * KD];
+    __shared__ float2 sh_w[BN];
+    const int64_t base = (int64_t)blockIdx.x * 128;
+    const int64_t pos = base + threadIdx.x;
+    const bool valid = pos < nrows;
+    const int own = valid ? a_lab[pos] : -1;
+    float x[KD];
+#pragma unroll
+    for (int c = 0; c < KD; ++c) x[c] = valid ? a_hi[pos * KD + c] + a_lo[pos * KD + c] : 0.f;
+    const float zx = (METRIC == SILH_COSINE && valid && a_norm[pos] == 0.f) ? 0.5f : 0.f;
+    // cluster range of this CTA's rows (labels are sorted; invalid rows last)
+    const int64_t last = min(base + 127, nrows - 1);
+    int j0 = a_lab[base], j1 = a_lab[last];
+    if (j1 < 0) {                       // trailing invalid rows: find the last valid one
+        j1 = -1;
+        for (int64_t p = last; p >= base && j1 < 0; --p) j1 = a_lab[p];
+    }
+    double acc = 0.0;
+    if (j0 >= 0) {
+        for (int j = j0; j <= j1; ++j) {
+            const int64_t cs = poff[j], ce = poff[j + 1];
+            for (int64_t cb = cs; cb < ce; cb += BN) {
+                const int nb = (int)min((int64_t)BN, ce - cb);
+                __syncthreads();
+                const float4 *src = reinterpret_cast<const float4 *>(y_full + cb * KD);
+                float4 *dst = reinterpret_cast<float4 *>(sh_y);
+                for (int q = threadIdx.x; q < nb * (KD / 4); q += 128) dst[q] = src[q];
+                for (int q = threadIdx.x; q < BN; q += 128) sh_w[q] = (q < nb) ? y_wn[cb + q] : make_float2(0.f, 0.f);
+                __syncthreads();
+                if (own == j) {
+                    float part = 0.f;
+                    for (int col = 0; col < nb; ++col) {
+                        const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * KD);
+                        float b0 = 0.f, b1 = 0.f;
+#pragma unroll
+                        for (int q = 0; q < KD / 4; ++q) {
+                            const float4 y = y4[q];
+                            const float t0 = x[4 * q] - y.x, t1 = x[4 * q + 1] - y.y;
+                            const float t2 = x[4 * q + 2] - y.z, t3 = x[4 * q + 3] - y.w;
+                            b0 = fmaf(t0, t0, b0); b1 = fmaf(t1, t1, b1);
+                            b0 = fmaf(t2, t2, b0); b1 = fmaf(t3, t3, b1);
+                        }
+                        const float2 wn = sh_w[col];
+                        float dist;
+                        if (METRIC == SILH_EUCLIDEAN) {
+                            dist = sqrt_apx(b0 + b1);
+                        } else {
+                            // zero vectors sit at cosine distance 1 from everything
+                            const float zy = (wn.y == 0.f) ? 0.5f : 0.f;
+                            dist = 0.5f * (b0 + b1) + zx + zy;
+                        }
+                        part = fmaf(wn.x, dist, part);
+                    }
+                    acc += (double)part;
+                }
+            }
+        }
+    }
+    if (valid) w_own[pos] = acc;
+}
+
+// Mean of the m sampled columns (Euclidean centring): per-block partial sums
+// over a fixed slice of columns, then one block adds them in order.
+template <class T>
+__global__ void k_col_mean_partial(const T *__restrict__ X, int d, int64_t ld,
+                                   const int32_t *__restrict__ idx, int64_t m, int per_block,
+                                   double *__restrict__ part) {
+    const int c = threadIdx.x;                  // coordinate
+    if (c >= d) return;
+    const int64_t lo = (int64_t)blockIdx.x * per_block, hi = min(lo + per_block, m);
+    double s = 0.0;
+    for (int64_t i = lo; i < hi; ++i) {
+        const int64_t e = idx ? idx[i] : i;
+        s += (double)to_f32<T>(X[e * ld + c]);
+    }
+    part[(int64_t)blockIdx.x * d + c] = s;
+}
+
+__global__ void k_col_mean_final(const double *__restrict__ part, int nb, int d, int64_t m,
+                                 float *__restrict__ mu) {
+    const int c = threadIdx.x;
+    if (c >= d) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * d + c];
+    mu[c] = (float)(s / (double)m);
 }
 
 // --------------------------------------------------------- row ordering
@@ -527,9 +636,9 @@ template <class T>
 __global__ void k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int64_t n,
                                  const int32_t *__restrict__ labels, const int64_t *__restrict__ rows,
                                  const int64_t *__restrict__ perm, int64_t nrows, int KD, int k,
-                                 int metric, float *__restrict__ hi, float *__restrict__ lo,
-                                 float *__restrict__ nrm, int32_t *__restrict__ lab,
-                                 int64_t *__restrict__ outi) {
+                                 int metric, const float *__restrict__ mu, float *__restrict__ hi,
+                                 float *__restrict__ lo, float *__restrict__ nrm,
+                                 int32_t *__restrict__ lab, int64_t *__restrict__ outi) {
     const int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (p >= nrows) return;
@@ -544,17 +653,19 @@ __global__ void k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     const float scale = (metric == SILH_COSINE) ? (s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f) : 1.f;
-    float ss = 0.f;
+    double ss = 0.0;
     for (int c = lane; c < KD; c += 32) {
-        const float v = (ok && c < d) ? to_f32<T>(x[c]) * scale : 0.f;
+        float v = (ok && c < d) ? to_f32<T>(x[c]) * scale : 0.f;
+        if (mu != nullptr && c < d) v = v - mu[c];
         const float h = to_tf32(v);
         hi[p * KD + c] = h;
         lo[p * KD + c] = v - h;
-        ss = fmaf(v, v, ss);
+        ss += (double)v * (double)v;
     }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if (lane == 0) {
-        nrm[p] = (metric == SILH_COSINE) ? 1.f : (float)s;
+        // Euclidean: squared norm of the (centred) row; cosine: 1, or 0 for a zero row
+        nrm[p] = (metric == SILH_COSINE) ? (s > 0.0 ? 1.f : 0.f) : (float)ss;
         const int32_t l = ok ? labels[e] : -1;
         lab[p] = (l >= 0 && l < k) ? l : -1;
         outi[p] = r;
@@ -593,8 +704,9 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
                                  const int32_t *__restrict__ idx, const double *__restrict__ p,
                                  const int64_t *__restrict__ offsets,
                                  const int64_t *__restrict__ poff, int k, int64_t mp_max, int KD,
-                                 int metric, float *__restrict__ full, float *__restrict__ hi,
-                                 float *__restrict__ lo, float2 *__restrict__ wn) {
+                                 int metric, const float *__restrict__ mu, float *__restrict__ full,
+                                 float *__restrict__ hi, float *__restrict__ lo,
+                                 float2 *__restrict__ wn) {
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (i >= mp_max) return;
@@ -627,16 +739,21 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     const float scale = (metric == SILH_COSINE) ? (s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f) : 1.f;
+    double ss = 0.0;
     for (int c = lane; c < KD; c += 32) {
-        const float v = (c < d) ? to_f32<T>(x[c]) * scale : 0.f;
+        float v = (c < d) ? to_f32<T>(x[c]) * scale : 0.f;
+        if (mu != nullptr && c < d) v = v - mu[c];
         const float h = to_tf32(v);
         full[i * KD + c] = v;
         hi[i * KD + c] = h;
         lo[i * KD + c] = v - h;
+        ss += (double)v * (double)v;
     }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if (lane == 0) {
         const float w = p ? (float)(1.0 / p[t]) : 1.0f;
-        wn[i] = make_float2(w, (metric == SILH_COSINE) ? 1.f : (float)s);
+        // Euclidean: squared norm of the (centred) column; cosine: 1, or 0 for a zero column
+        wn[i] = make_float2(w, (metric == SILH_COSINE) ? (s > 0.0 ? 1.f : 0.f) : (float)ss);
     }
 }
 
@@ -674,17 +791,20 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
                       const CUtensorMap &bhi, const CUtensorMap &blo, const float *a_hi,
                       const float *a_lo, const float *a_norm, const int32_t *a_lab,
                       const int64_t *a_out, int64_t nrows, const float *y_full, const float2 *y_wn,
-                      const int64_t *poff, const int64_t *sizes, int k, float tau, float *s,
-                      float *a, float *b) {
+                      const int64_t *poff, const int64_t *sizes, int k, float tau,
+                      double *w_own, float *s, float *a, float *b) {
     using C = TcCfg<KD, SPLIT>;
+    k_own_direct<METRIC, KD><<<(int)((nrows + 127) / 128), 128, 0, stream>>>(
+        a_hi, a_lo, a_norm, a_lab, nrows, y_full, y_wn, poff, k, w_own);
+    count_launches(1);
     auto kern = k_sweep_tc<METRIC, KD, SPLIT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     const int64_t groups = ((nrows + kTileM - 1) / kTileM + C::SLOTS - 1) / C::SLOTS;
     const int grid = (int)std::min<int64_t>(groups, nsm);
     kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_norm, a_lab,
-                                                a_out, nrows, y_full, y_wn, poff, sizes, k, tau, s,
-                                                a, b);
+                                                a_out, nrows, y_full, y_wn, poff, sizes, k, tau,
+                                                w_own, s, a, b);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -713,6 +833,9 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     int32_t *counts = nullptr, *lab = nullptr;
     int64_t *tbase = nullptr, *tot = nullptr, *boff = nullptr, *perm = nullptr, *outi = nullptr;
     int64_t *poff = nullptr;
+    double *w_own = nullptr, *mpart = nullptr;
+    float *mu = nullptr;
+    const int mean_blocks = 128;
     float *rhi = nullptr, *rlo = nullptr, *rn = nullptr, *yf = nullptr, *yhi = nullptr,
           *ylo = nullptr;
     float2 *ywn = nullptr;
@@ -730,6 +853,9 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     SILH_CK(sc.alloc(&rlo, (size_t)nrows * KD));
     SILH_CK(sc.alloc(&rn, (size_t)nrows));
     SILH_CK(sc.alloc(&poff, (size_t)k + 1));
+    SILH_CK(sc.alloc(&w_own, (size_t)nrows));
+    SILH_CK(sc.alloc(&mpart, (size_t)mean_blocks * d));
+    SILH_CK(sc.alloc(&mu, (size_t)d));
     SILH_CK(sc.alloc(&yf, (size_t)mp_max * KD));
     SILH_CK(sc.alloc(&yhi, (size_t)mp_max * KD));
     SILH_CK(sc.alloc(&ylo, (size_t)mp_max * KD));
@@ -747,20 +873,34 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
                                                   boff, perm);
     k_col_poff<<<1, 1024, 0, stream>>>(offsets, k, poff);
     count_launches(5);
+    if (metric == SILH_EUCLIDEAN) {
+        // distances are shift invariant: centre rows and columns on the sample mean
+        const int per = (int)((m + mean_blocks - 1) / mean_blocks);
+        if (dtype == SILH_F32)
+            k_col_mean_partial<float><<<mean_blocks, 128, 0, stream>>>((const float *)X, d, ld,
+                                                                       col_idx, m, per, mpart);
+        else
+            k_col_mean_partial<__nv_bfloat16><<<mean_blocks, 128, 0, stream>>>(
+                (const __nv_bfloat16 *)X, d, ld, col_idx, m, per, mpart);
+        k_col_mean_final<<<1, 128, 0, stream>>>(mpart, mean_blocks, d, m, mu);
+        count_launches(2);
+    } else {
+        mu = nullptr;
+    }
     if (dtype == SILH_F32) {
         k_gather_rows_tc<float><<<ceil_div_i(nrows, 8), 256, 0, stream>>>(
-            (const float *)X, d, ld, n, labels, rows, perm, nrows, KD, k, metric, rhi, rlo, rn, lab,
-            outi);
+            (const float *)X, d, ld, n, labels, rows, perm, nrows, KD, k, metric, mu, rhi, rlo, rn,
+            lab, outi);
         k_gather_cols_tc<float><<<ceil_div_i(mp_max, 8), 256, 0, stream>>>(
-            (const float *)X, d, ld, col_idx, col_p, offsets, poff, k, mp_max, KD, metric, yf,
+            (const float *)X, d, ld, col_idx, col_p, offsets, poff, k, mp_max, KD, metric, mu, yf,
             yhi, ylo, ywn);
     } else {
         k_gather_rows_tc<__nv_bfloat16><<<ceil_div_i(nrows, 8), 256, 0, stream>>>(
-            (const __nv_bfloat16 *)X, d, ld, n, labels, rows, perm, nrows, KD, k, metric, rhi, rlo,
-            rn, lab, outi);
+            (const __nv_bfloat16 *)X, d, ld, n, labels, rows, perm, nrows, KD, k, metric, mu, rhi,
+            rlo, rn, lab, outi);
         k_gather_cols_tc<__nv_bfloat16><<<ceil_div_i(mp_max, 8), 256, 0, stream>>>(
             (const __nv_bfloat16 *)X, d, ld, col_idx, col_p, offsets, poff, k, mp_max, KD, metric,
-            yf, yhi, ylo, ywn);
+            mu, yf, yhi, ylo, ywn);
     }
     count_launches(2);
     SILH_CK(cudaGetLastError());
@@ -773,8 +913,8 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
 #define SILH_TC_CASE(MET, KDV, SP)                                                              \
     if (metric == MET && KD == KDV && split == SP) {                                           \
         SILH_CK((launch_tc<MET, KDV, SP>(nsm, stream, m_ahi, m_alo, m_bhi, m_blo, rhi, rlo, rn, \
-                                         lab, outi, nrows, yf, ywn, poff, sizes, k, tau, s, a,  \
-                                         b)));                                                 \
+                                         lab, outi, nrows, yf, ywn, poff, sizes, k, tau, w_own, \
+                                         s, a, b)));                                           \
     }
     SILH_TC_CASE(SILH_EUCLIDEAN, 32, true)
     SILH_TC_CASE(SILH_EUCLIDEAN, 32, false)
