@@ -76,15 +76,22 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // (equal for unit vectors, and free of the cancellation of 1 - <x,y> for
 // nearly parallel pairs).  Canberra: terms |x - y| / (|x| + |y|) taken two at a
 // time as (n1 d2 + n2 d1)/(d1 d2) so that one reciprocal serves two
-// coordinates; each denominator carries +1e-18 so that an all-zero coordinate
-// pair (including padding) contributes 0 and d1 d2 stays a normal float.
+// coordinates; each denominator carries +1e-18 (added to |y| when the column
+// is staged) so that an all-zero coordinate pair (including padding)
+// contributes 0 and d1 d2 stays a normal float.
 template <int METRIC, int D>
-__device__ __forceinline__ float pair_dist(const float (&x)[D], const float4 *__restrict__ y4) {
+__device__ __forceinline__ float pair_dist(const float (&x)[D], const float4 *__restrict__ y4,
+                                           const float4 *__restrict__ ya4) {
     float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
     for (int q = 0; q < D / 4; ++q) {
         float4 y = y4[q];
         float ys[4] = {y.x, y.y, y.z, y.w};
+        float yas[4] = {0.f, 0.f, 0.f, 0.f};
+        if (METRIC == SILH_CANBERRA) {
+            const float4 ya = ya4[q];
+            yas[0] = ya.x; yas[1] = ya.y; yas[2] = ya.z; yas[3] = ya.w;
+        }
         if (METRIC == SILH_EUCLIDEAN) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -108,8 +115,8 @@ __device__ __forceinline__ float pair_dist(const float (&x)[D], const float4 *__
             for (int c = 0; c < 4; c += 2) {
                 float n1 = fabsf(x[4 * q + c] - ys[c]);
                 float n2 = fabsf(x[4 * q + c + 1] - ys[c + 1]);
-                float d1 = fabsf(x[4 * q + c]) + 1e-18f + fabsf(ys[c]);
-                float d2 = fabsf(x[4 * q + c + 1]) + 1e-18f + fabsf(ys[c + 1]);
+                float d1 = fabsf(x[4 * q + c]) + yas[c];          // |x| + (|y| + 1e-18)
+                float d2 = fabsf(x[4 * q + c + 1]) + yas[c + 1];
                 float num = fmaf(n2, d1, n1 * d2);
                 float den = d1 * d2;
                 if (c == 0) acc0 = fmaf(num, rcp_approx(den), acc0);
@@ -133,6 +140,7 @@ k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__
         const int64_t *__restrict__ rows, int64_t nrows, float *__restrict__ s_out,
         float *__restrict__ a_out, float *__restrict__ b_out) {
     __shared__ __align__(16) float sh_y[BN * D];
+    __shared__ __align__(16) float sh_ya[METRIC == SILH_CANBERRA ? BN * D : 4];
     __shared__ float sh_w[BN];
     __shared__ float sh_z[BN];
     constexpr int BM = kThreads * RPT;
@@ -176,7 +184,14 @@ k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__
             __syncthreads();
             const float4 *src = reinterpret_cast<const float4 *>(Y + cb * D);
             float4 *dst = reinterpret_cast<float4 *>(sh_y);
-            for (int q = threadIdx.x; q < nb * (D / 4); q += kThreads) dst[q] = src[q];
+            for (int q = threadIdx.x; q < nb * (D / 4); q += kThreads) {
+                const float4 v = src[q];
+                dst[q] = v;
+                if (METRIC == SILH_CANBERRA)
+                    reinterpret_cast<float4 *>(sh_ya)[q] =
+                        make_float4(fabsf(v.x) + 1e-18f, fabsf(v.y) + 1e-18f, fabsf(v.z) + 1e-18f,
+                                    fabsf(v.w) + 1e-18f);
+            }
             for (int q = threadIdx.x; q < BN; q += kThreads) {
                 sh_w[q] = (q < nb) ? wY[cb + q] : 0.f;
                 if (METRIC == SILH_COSINE) sh_z[q] = (q < nb) ? zY[cb + q] : 0.f;
@@ -188,13 +203,15 @@ k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__
             for (int r = 0; r < RPT; ++r) accf[r] = 0.f;
             for (int col = 0; col < nb; ++col) {
                 const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * D);
+                const float4 *ya4 = reinterpret_cast<const float4 *>(sh_ya + col * D);
                 float w = sh_w[col];
                 if (METRIC == SILH_COSINE) {
                     accz += sh_z[col];
                     accw += w;
                 }
 #pragma unroll
-                for (int r = 0; r < RPT; ++r) accf[r] = fmaf(w, pair_dist<METRIC, D>(x[r], y4), accf[r]);
+                for (int r = 0; r < RPT; ++r)
+                    accf[r] = fmaf(w, pair_dist<METRIC, D>(x[r], y4, ya4), accf[r]);
             }
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
@@ -285,6 +302,191 @@ void launch_sweep_m(int metric, int D, cudaStream_t stream, const T *X, int d, i
             launch_sweep_d<T, SILH_CANBERRA>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
                                              Y, wY, zY, rows, nrows, s, a, b);
             break;
+    }
+}
+
+
+// ----------------------------------------------------- exact, symmetric
+
+// Exact silhouette over all n rows: d(x, y) = d(y, x), so each pair of
+// cluster-sorted position tiles (I <= J) is evaluated once.  A CTA owns the
+// T = 128 RPT positions of tile I as rows and streams tile J as columns:
+// every distance is added to its row's sum for the column's cluster
+// (registers, flushed at cluster changes) and, for I < J, to its column's sum
+// for the row's cluster (reduced over the CTA's rows with warp shuffles and
+// shared memory).  Both land in the n x k FP64 weight matrix W with atomic
+// adds (so results are reproducible to rounding order, not bitwise).
+template <int METRIC, int D, int RPT>
+__global__ void __launch_bounds__(kThreads)
+k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
+            const int32_t *__restrict__ lab_s, int64_t n, int k, int64_t ntiles,
+            double *__restrict__ W) {
+    constexpr int T = kThreads * RPT;
+    constexpr int BN = (D >= 128) ? 32 : 64;   // static shared memory stays under 48 KB
+    constexpr int NW = kThreads / 32;
+    __shared__ __align__(16) float sh_y[BN * D];
+    __shared__ __align__(16) float sh_ya[METRIC == SILH_CANBERRA ? BN * D : 4];
+    __shared__ float sh_z[BN];
+    __shared__ int sh_lab[BN];
+    __shared__ float sh_col[NW][BN];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // upper-triangular tile pair (I, J) from the linear block index
+    const int64_t b = blockIdx.x;
+    int64_t lo = 0, hi = ntiles - 1;   // largest I with start(I) <= b
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        const int64_t st = mid * ntiles - mid * (mid - 1) / 2;
+        if (st <= b) lo = mid; else hi = mid - 1;
+    }
+    const int64_t I = lo;
+    const int64_t J = I + (b - (I * ntiles - I * (I - 1) / 2));
+    const bool diag = (I == J);
+    float x[RPT][D];
+    int lp[RPT];
+    float zx[RPT];
+    int64_t prow[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int64_t p = I * T + threadIdx.x + r * kThreads;
+        prow[r] = p;
+        const bool v = p < n;
+        lp[r] = v ? lab_s[p] : -1;
+        zx[r] = (METRIC == SILH_COSINE && v) ? zY[p] : 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) x[r][c] = v ? Y[p * D + c] : 0.f;
+    }
+    const int64_t rlast = min(I * T + T, n) - 1;
+    const int cI0 = lab_s[I * T], cI1 = lab_s[rlast];
+    const int64_t c_begin = J * T, c_end = min(J * T + T, n);
+    int cur = -1;                      // column cluster of the running row sums
+    float accr[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) accr[r] = 0.f;
+    for (int64_t cb = c_begin; cb < c_end; cb += BN) {
+        const int nb = (int)min((int64_t)BN, c_end - cb);
+        __syncthreads();
+        const float4 *src = reinterpret_cast<const float4 *>(Y + cb * D);
+        for (int q = threadIdx.x; q < nb * (D / 4); q += kThreads) {
+            const float4 v = src[q];
+            reinterpret_cast<float4 *>(sh_y)[q] = v;
+            if (METRIC == SILH_CANBERRA)
+                reinterpret_cast<float4 *>(sh_ya)[q] =
+                    make_float4(fabsf(v.x) + 1e-18f, fabsf(v.y) + 1e-18f, fabsf(v.z) + 1e-18f,
+                                fabsf(v.w) + 1e-18f);
+        }
+        for (int q = threadIdx.x; q < BN; q += kThreads) {
+            sh_lab[q] = (q < nb) ? lab_s[cb + q] : -1;
+            sh_z[q] = (METRIC == SILH_COSINE && q < nb) ? zY[cb + q] : 0.f;
+        }
+        __syncthreads();
+        for (int col = 0; col < nb; ++col) {
+            const int lq = sh_lab[col];
+            if (lq != cur) {           // uniform: columns are cluster-sorted
+                if (cur >= 0) {
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r)
+                        if (prow[r] < n) atomicAdd(&W[prow[r] * k + cur], (double)accr[r]);
+                }
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) accr[r] = 0.f;
+                cur = lq;
+            }
+            const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * D);
+            const float4 *ya4 = reinterpret_cast<const float4 *>(sh_ya + col * D);
+            float dr[RPT];
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                float dd = pair_dist<METRIC, D>(x[r], y4, ya4);
+                if (METRIC == SILH_COSINE) dd += zx[r] + sh_z[col];
+                dr[r] = (prow[r] < n) ? dd : 0.f;
+                accr[r] += dr[r];
+            }
+            if (!diag) {
+                if (cI0 == cI1) {
+                    float v = 0.f;
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) v += dr[r];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) sh_col[warp][col] = v;
+                } else {
+                    // rows of several clusters (tile at a cluster boundary): one sum per cluster
+                    for (int c = cI0; c <= cI1; ++c) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) v += (lp[r] == c) ? dr[r] : 0.f;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (lane == 0 && v != 0.f) atomicAdd(&W[(cb + col) * k + c], (double)v);
+                    }
+                }
+            }
+        }
+        if (!diag && cI0 == cI1) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < nb; q += kThreads) {
+                float v = 0.f;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) v += sh_col[w][q];
+                atomicAdd(&W[(cb + q) * k + cI0], (double)v);
+            }
+        }
+    }
+    if (cur >= 0) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+            if (prow[r] < n) atomicAdd(&W[prow[r] * k + cur], (double)accr[r]);
+    }
+}
+
+// s, a, b of every sorted position from its row of W; written at the element's
+// original index order[pos].
+__global__ void k_exact_finalize(const double *__restrict__ W, const int32_t *__restrict__ lab_s,
+                                 const int32_t *__restrict__ order, const int64_t *__restrict__ sizes,
+                                 int64_t n, int k, float *__restrict__ s_out,
+                                 float *__restrict__ a_out, float *__restrict__ b_out) {
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= n) return;
+    const int own = lab_s[pos];
+    const double *w = W + pos * k;
+    double bmin = INFINITY;
+    for (int j = 0; j < k; ++j)
+        if (j != own) bmin = fmin(bmin, w[j] / (double)sizes[j]);
+    const int64_t nc = sizes[own];
+    const double a = (nc > 1) ? w[own] / (double)(nc - 1) : 0.0;
+    const double mx = fmax(a, bmin);
+    const int64_t o = order[pos];
+    s_out[o] = (float)((nc > 1 && mx > 0.0) ? (bmin - a) / mx : 0.0);
+    if (a_out) a_out[o] = (float)a;
+    if (b_out) b_out[o] = (float)bmin;
+}
+
+__global__ void k_sorted_labels(const int32_t *__restrict__ labels, const int32_t *__restrict__ order,
+                                int64_t n, int32_t *__restrict__ lab_s) {
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos < n) lab_s[pos] = labels[order[pos]];
+}
+
+template <int METRIC, int D>
+void launch_exact_sym(cudaStream_t stream, const float *Y, const float *zY, const int32_t *lab_s,
+                      int64_t n, int k, double *W) {
+    constexpr int RPT = (D <= 32) ? 2 : 1;
+    constexpr int T = kThreads * RPT;
+    const int64_t nt = (n + T - 1) / T;
+    const int64_t nblk = nt * (nt + 1) / 2;
+    k_exact_sym<METRIC, D, RPT><<<(unsigned)nblk, kThreads, 0, stream>>>(Y, zY, lab_s, n, k, nt, W);
+    count_launches(1);
+}
+
+template <int METRIC>
+void launch_exact_sym_d(int D, cudaStream_t stream, const float *Y, const float *zY,
+                        const int32_t *lab_s, int64_t n, int k, double *W) {
+    switch (D) {
+        case 8: launch_exact_sym<METRIC, 8>(stream, Y, zY, lab_s, n, k, W); break;
+        case 16: launch_exact_sym<METRIC, 16>(stream, Y, zY, lab_s, n, k, W); break;
+        case 32: launch_exact_sym<METRIC, 32>(stream, Y, zY, lab_s, n, k, W); break;
+        case 64: launch_exact_sym<METRIC, 64>(stream, Y, zY, lab_s, n, k, W); break;
+        default: launch_exact_sym<METRIC, 128>(stream, Y, zY, lab_s, n, k, W); break;
     }
 }
 
@@ -430,7 +632,8 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     Scratch sc(stream);
     std::vector<int64_t> h_sizes, h_coff;
     int64_t *sizes = nullptr, *coff = nullptr;
-    int32_t *order = nullptr;
+    int32_t *order = nullptr, *lab_s = nullptr;
+    double *W = nullptr;
     float *Y = nullptr, *wY = nullptr, *zY = nullptr;
     SILH_REQ(s, "s is null");
     if (rows == nullptr) nrows = n;
@@ -450,6 +653,25 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     SILH_CK(sc.alloc(&zY, (size_t)n));
     st = gather_columns(X, dtype, d, ld, order, nullptr, n, D, metric, Y, wY, zY, stream);
     if (st != SILH_OK) goto done;
+    if (rows == nullptr && (double)n * (double)k * 8.0 <= 2147483648.0) {
+        // all rows: the symmetric sweep evaluates each pair once
+        SILH_CK(sc.alloc(&lab_s, (size_t)n));
+        SILH_CK(sc.alloc(&W, (size_t)n * k));
+        SILH_CK(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)n * k, stream));
+        k_sorted_labels<<<ceil_div_i(n, 256), 256, 0, stream>>>(labels, order, n, lab_s);
+        count_launches(1);
+        switch (metric) {
+            case SILH_EUCLIDEAN: launch_exact_sym_d<SILH_EUCLIDEAN>(D, stream, Y, zY, lab_s, n, k, W); break;
+            case SILH_COSINE: launch_exact_sym_d<SILH_COSINE>(D, stream, Y, zY, lab_s, n, k, W); break;
+            case SILH_MANHATTAN: launch_exact_sym_d<SILH_MANHATTAN>(D, stream, Y, zY, lab_s, n, k, W); break;
+            default: launch_exact_sym_d<SILH_CANBERRA>(D, stream, Y, zY, lab_s, n, k, W); break;
+        }
+        k_exact_finalize<<<ceil_div_i(n, 256), 256, 0, stream>>>(W, lab_s, order, sizes, n, k, s, a,
+                                                                 b);
+        count_launches(1);
+        SILH_CK(cudaGetLastError());
+        goto done;
+    }
     st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, Y, wY, zY, n, D,
                       rows, nrows, s, a, b, stream);
 done:
