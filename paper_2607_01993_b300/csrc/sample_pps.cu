@@ -7,10 +7,13 @@
 // are kept in an FP64 matrix D_j of |F0_j| x |Cj| (F0-major, so that the W sums
 // and the gamma sweep both read it coalesced).
 //
-// Precision: all of Phase 1 is IEEE FP64.  Each distance is evaluated in
-// ascending coordinate order with explicitly rounded operations (no fused
-// multiply-add) and correctly rounded sqrt/divide, so a pair's distance is the
-// same double the FP64 oracle computes; only the order of the W sums differs.
+// Precision: Phase 1 decides which elements are sampled (u < p_e), so it runs
+// at FP64-class accuracy.  Euclidean, Manhattan and Canberra pair distances use
+// double-float arithmetic (an FP32 pair hi + lo carried with error-free
+// transformations: Knuth's two-sum, the FMA two-product), about 2^-44 relative,
+// which B300 evaluates an order of magnitude faster than native FP64.  Cosine
+// distances are native FP64 in ascending coordinate order with correctly
+// rounded operations.  W sums, gamma and p are FP64.
 #include <algorithm>
 #include <cmath>
 
@@ -297,11 +300,146 @@ __global__ void k_dist_f0(const T *__restrict__ X, int d, int64_t ld,
     }
 }
 
+
+// ------------------------------------------------ double-float arithmetic
+// A value is carried as hi + lo (two FP32 numbers).  two_sum (Knuth) and
+// two_prod (one FMA) return the exact rounding error of an add / a multiply;
+// df_acc adds a nonnegative FP32 term to a nonnegative accumulator and
+// renormalises.  All operations are explicitly rounded (no contraction).
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {  // |a| >= |b|
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+__device__ __forceinline__ void df_acc(float &hi, float &lo, float b) {
+    float s, e;
+    two_sum(hi, b, s, e);
+    e = __fadd_rn(e, lo);
+    fast_two_sum(s, e, hi, lo);
+}
+
+__device__ __forceinline__ float rcp_apx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float sqrt_apx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Phase-1 pair distances for Euclidean, Manhattan and Canberra in double-float
+// arithmetic (layout and work split as k_dist_f0).
+template <class T, int METRIC>
+__global__ void k_dist_f0_df(const T *__restrict__ X, int d, int64_t ld,
+                             const int32_t *__restrict__ order, const int64_t *__restrict__ coff,
+                             const int32_t *__restrict__ f0_elem, const int64_t *__restrict__ f0off,
+                             const int64_t *__restrict__ doff, const int32_t *__restrict__ item_cluster,
+                             const int32_t *__restrict__ item_chunk, double *__restrict__ D) {
+    extern __shared__ float sh_yf[];            // kF0Group x d
+    const int j = item_cluster[blockIdx.x];
+    const int64_t c0 = coff[j], nc = coff[j + 1] - c0;
+    const int64_t i = (int64_t)item_chunk[blockIdx.x] * kDistThreads + threadIdx.x;
+    const bool live = i < nc;
+    const int64_t e = live ? order[c0 + i] : 0;
+    const int64_t g0 = f0off[j], nf = f0off[j + 1] - g0;
+    double *Dj = D + doff[j];
+    for (int64_t gb = 0; gb < nf; gb += kF0Group) {
+        const int gc = (int)min((int64_t)kF0Group, nf - gb);
+        __syncthreads();
+        for (int q = threadIdx.x; q < kF0Group * d; q += blockDim.x) {
+            const int g = q / d, c = q % d;
+            sh_yf[q] = (g < gc) ? to_f32<T>(X[(int64_t)f0_elem[g0 + gb + g] * ld + c]) : 0.f;
+        }
+        __syncthreads();
+        if (!live) continue;
+        float hi[kF0Group], lo[kF0Group];
+#pragma unroll
+        for (int g = 0; g < kF0Group; ++g) hi[g] = lo[g] = 0.f;
+        const T *xr = X + e * ld;
+        for (int c = 0; c < d; ++c) {
+            const float xv = to_f32<T>(xr[c]);
+#pragma unroll
+            for (int g = 0; g < kF0Group; ++g) {
+                const float yv = sh_yf[g * d + c];
+                float s, t;
+                two_sum(xv, -yv, s, t);                 // x - y = s + t exactly
+                if (METRIC == SILH_EUCLIDEAN) {
+                    float p, pe;
+                    two_prod(s, s, p, pe);              // s^2 = p + pe exactly
+                    // (s + t)^2 = p + pe + 2 s t + t^2; t^2 < 2^-46 p is dropped
+                    const float small = __fmaf_rn(__fmul_rn(2.f, s), t, pe);
+                    df_acc(hi[g], lo[g], p);
+                    lo[g] = __fadd_rn(lo[g], small);
+                } else {
+                    if (s < 0.f) {                      // |x - y| = |s + t|
+                        s = -s;
+                        t = -t;
+                    }
+                    if (METRIC == SILH_MANHATTAN) {
+                        df_acc(hi[g], lo[g], s);
+                        lo[g] = __fadd_rn(lo[g], t);
+                    } else {                            // Canberra
+                        float ds, de;
+                        two_sum(fabsf(xv), fabsf(yv), ds, de);   // |x| + |y| exactly
+                        if (ds > 0.f) {
+                            const float rc = rcp_apx(ds);
+                            const float q0 = __fmul_rn(s, rc);
+                            float rr = __fmaf_rn(-q0, ds, s);     // residual of s / ds
+                            rr = __fadd_rn(rr, t);
+                            rr = __fmaf_rn(-q0, de, rr);
+                            const float q1 = __fmul_rn(rr, rc);
+                            df_acc(hi[g], lo[g], q0);
+                            lo[g] = __fadd_rn(lo[g], q1);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < kF0Group; ++g) {
+            if (g >= gc) break;
+            double v;
+            if (METRIC == SILH_EUCLIDEAN) {
+                // sqrt(hi + lo): FP32 estimate y0, one Newton step on the double-float value
+                const float h = hi[g];
+                if (h > 0.f) {
+                    const float y0 = sqrt_apx(h);
+                    float p, pe;
+                    two_prod(y0, y0, p, pe);
+                    const float r = __fadd_rn(__fsub_rn(__fsub_rn(h, p), pe), lo[g]);
+                    const float corr = __fmul_rn(r, __fmul_rn(0.5f, rcp_apx(y0)));
+                    v = (double)y0 + (double)corr;
+                } else {
+                    v = 0.0;
+                }
+            } else {
+                v = (double)hi[g] + (double)lo[g];
+            }
+            Dj[(gb + g) * nc + i] = v;
+        }
+    }
+}
+
 // W(e0) = sum over the members of column e0 of D_j, fixed reduction tree.
 __global__ void k_w0(const int32_t *__restrict__ f0_elem, const int32_t *__restrict__ labels,
                      const int64_t *__restrict__ coff, const int64_t *__restrict__ f0off,
                      const int64_t *__restrict__ doff, const double *__restrict__ D,
-                     double *__restrict__ W0) {
+                     double *__restrict__ W0, double *__restrict__ invW0) {
     __shared__ double sh[256];
     int64_t g = blockIdx.x;
     int j = labels[f0_elem[g]];
@@ -316,14 +454,17 @@ __global__ void k_w0(const int32_t *__restrict__ f0_elem, const int32_t *__restr
         if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
         __syncthreads();
     }
-    if (threadIdx.x == 0) W0[g] = sh[0];
+    if (threadIdx.x == 0) {
+        W0[g] = sh[0];
+        invW0[g] = sh[0] > 0.0 ? __ddiv_rn(1.0, sh[0]) : 0.0;   // W = 0: the term d/W is 0
+    }
 }
 
 // gamma_e, p_e and the final Poisson draw (stream 1), one thread per position.
 __global__ void k_gamma_draw(const int32_t *__restrict__ order, const int32_t *__restrict__ labels,
                              const int64_t *__restrict__ coff, const int64_t *__restrict__ sizes,
                              const int64_t *__restrict__ f0off, const int64_t *__restrict__ doff,
-                             const double *__restrict__ D, const double *__restrict__ W0, int64_t n,
+                             const double *__restrict__ D, const double *__restrict__ invW0, int64_t n,
                              double t, int uniform, uint64_t seed, uint64_t cid,
                              double *__restrict__ pS, int32_t *__restrict__ flag1) {
     int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -343,8 +484,7 @@ __global__ void k_gamma_draw(const int32_t *__restrict__ order, const int32_t *_
         const double *Dj = D + doff[j];
         double g2 = 0.0;
         for (int64_t f = 0; f < nf; ++f) {
-            double W = W0[g0 + f];
-            double r = (W > 0.0) ? __ddiv_rn(Dj[f * nc + i], W) : 0.0;
+            const double r = __dmul_rn(Dj[f * nc + i], invW0[g0 + f]);   // d(e, e0) / W(e0)
             if (r > g2) g2 = r;
         }
         double g1 = __ddiv_rn(1.0, (double)nc);
@@ -361,9 +501,10 @@ void launch_dist_f0(int metric, int nitems, size_t smem, cudaStream_t stream, co
                     int64_t ld, const int32_t *order, const int64_t *coff, const int32_t *f0_elem,
                     const int64_t *f0off, const int64_t *doff, const int32_t *ic,
                     const int32_t *ik, double *D) {
+    const size_t smem_f = smem / 2;       // FP32 staging for the double-float kernels
     switch (metric) {
         case SILH_EUCLIDEAN:
-            k_dist_f0<T, SILH_EUCLIDEAN><<<nitems, kDistThreads, smem, stream>>>(
+            k_dist_f0_df<T, SILH_EUCLIDEAN><<<nitems, kDistThreads, smem_f, stream>>>(
                 X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
             break;
         case SILH_COSINE:
@@ -371,11 +512,11 @@ void launch_dist_f0(int metric, int nitems, size_t smem, cudaStream_t stream, co
                 X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
             break;
         case SILH_MANHATTAN:
-            k_dist_f0<T, SILH_MANHATTAN><<<nitems, kDistThreads, smem, stream>>>(
+            k_dist_f0_df<T, SILH_MANHATTAN><<<nitems, kDistThreads, smem_f, stream>>>(
                 X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
             break;
         default:
-            k_dist_f0<T, SILH_CANBERRA><<<nitems, kDistThreads, smem, stream>>>(
+            k_dist_f0_df<T, SILH_CANBERRA><<<nitems, kDistThreads, smem_f, stream>>>(
                 X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
             break;
     }
@@ -460,7 +601,7 @@ extern "C" silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t 
     int64_t *doff = nullptr;
     int32_t *order = nullptr, *flag0 = nullptr, *flag1 = nullptr, *f0_elem = nullptr;
     int32_t *ic = nullptr, *ik = nullptr;
-    double *D = nullptr, *W0 = nullptr, *pS = nullptr;
+    double *D = nullptr, *W0 = nullptr, *invW0 = nullptr, *pS = nullptr;
     int64_t nf0 = 0, dtot = 0, size = 0;
     int nblk = 0;
 
@@ -522,6 +663,7 @@ extern "C" silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t 
                             cudaMemcpyHostToDevice, stream));
     SILH_CK(sc.alloc(&D, (size_t)std::max<int64_t>(dtot, 1)));
     SILH_CK(sc.alloc(&W0, (size_t)std::max<int64_t>(nf0, 1)));
+    SILH_CK(sc.alloc(&invW0, (size_t)std::max<int64_t>(nf0, 1)));
     SILH_CK(sc.alloc(&f0_elem, (size_t)std::max<int64_t>(nf0, 1)));
     if (nf0 > 0) {
         k_compact<<<nblk, 256, 0, stream>>>(flag0, pos0, order, n, f0_elem, nullptr, nullptr); count_launches(1);
@@ -535,6 +677,11 @@ extern "C" silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t 
         size_t smem = sizeof(double) * kF0Group * (size_t)d;
         SILH_REQ(smem <= 200 * 1024, "d too large for Phase 1 (d <= 3200)");
         if (dtype == SILH_F32) {
+            if (smem / 2 > 48 * 1024)
+                for (auto f : {k_dist_f0_df<float, 0>, k_dist_f0_df<float, 2>,
+                               k_dist_f0_df<float, 3>})
+                    SILH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(smem / 2)));
             if (smem > 48 * 1024)
                 for (auto f : {k_dist_f0<float, 0>, k_dist_f0<float, 1>, k_dist_f0<float, 2>,
                                k_dist_f0<float, 3>})
@@ -543,6 +690,11 @@ extern "C" silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t 
             launch_dist_f0<float>(metric, nitems, smem, stream, (const float *)X, d, ld, order,
                                   coff, f0_elem, f0off, doff, ic, ik, D);
         } else {
+            if (smem / 2 > 48 * 1024)
+                for (auto f : {k_dist_f0_df<__nv_bfloat16, 0>, k_dist_f0_df<__nv_bfloat16, 2>,
+                               k_dist_f0_df<__nv_bfloat16, 3>})
+                    SILH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(smem / 2)));
             if (smem > 48 * 1024)
                 for (auto f : {k_dist_f0<__nv_bfloat16, 0>, k_dist_f0<__nv_bfloat16, 1>,
                                k_dist_f0<__nv_bfloat16, 2>, k_dist_f0<__nv_bfloat16, 3>})
@@ -553,10 +705,10 @@ extern "C" silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t 
                                           f0off, doff, ic, ik, D);
         }
         SILH_CK(cudaGetLastError());
-        k_w0<<<(int)nf0, 256, 0, stream>>>(f0_elem, labels, coff, f0off, doff, D, W0); count_launches(1);
+        k_w0<<<(int)nf0, 256, 0, stream>>>(f0_elem, labels, coff, f0off, doff, D, W0, invW0); count_launches(1);
         SILH_CK(cudaGetLastError());
     }
-    k_gamma_draw<<<nblk, 256, 0, stream>>>(order, labels, coff, out->sizes, f0off, doff, D, W0, n,
+    k_gamma_draw<<<nblk, 256, 0, stream>>>(order, labels, coff, out->sizes, f0off, doff, D, invW0, n,
                                            t, uniform ? 1 : 0, seed, clustering_id, pS, flag1); count_launches(1);
     SILH_CK(scan_flags(flag1, n, pos1, tot + 1, sc, stream));
     SILH_CK(cudaMemcpyAsync(&size, tot + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));

@@ -1,13 +1,16 @@
 """GPU path (through the C ABI) against the FP64 oracle, element by element.
 
 Sample sets must be identical: both sides take the inclusion decision
-u < p_e in FP64.  The per-pair distances are the same doubles on both sides;
-only the order of the W sums differs (the oracle adds the |Cj| terms one after
-another, the GPU in a fixed tree).  A sequential sum of N positive terms is
-within (N - 1) u of the exact sum (u = 2^-53), and so is the tree, so p_e
-agrees within tie(j) = (2 |Cj| + 16) u relative; an element may be in one
-sample and not the other only if |u - p_e| <= tie(j) p_e, and such elements
-are counted.  Silhouette values must agree within 1e-5 absolute (FP32
+u < p_e with FP64-class p_e.  The oracle evaluates every distance in FP64 and
+sums W sequentially; the GPU evaluates Euclidean, Manhattan and Canberra
+distances in double-float arithmetic (relative error below 2^-42 for d <= 128),
+cosine in FP64, sums W in a fixed tree and multiplies by 1/W.  A sequential or
+tree sum of N positive terms is within (N - 1) u of the exact sum
+(u = 2^-53); the per-distance errors (<= (d + 2) u in the oracle, < 2^-42 on the
+GPU) and the 1/W rounding add at most (2d + 8) u + 2^-41, so p_e agrees within
+tie(j) = (2 |Cj| + 2 * 128 + 64) u + 2^-40 relative.  An element may be in one
+sample and not the other only if |u - p_e| <= tie(j) p_e, and such elements are
+counted.  Silhouette values must agree within 1e-5 absolute (FP32
 arithmetic on the GPU), a_hat/b_hat within 1e-5 relative.
 """
 import numpy as np
@@ -25,7 +28,7 @@ U64 = 2.0 ** -53
 
 
 def tie_band(cluster_size):
-    return (2.0 * cluster_size + 16.0) * U64
+    return (2.0 * cluster_size + 2 * 128 + 64.0) * U64 + 2.0 ** -40
 
 
 def _to_dev(X, lab, dtype=torch.float32):
