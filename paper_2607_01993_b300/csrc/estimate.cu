@@ -8,6 +8,7 @@
 // after another through shared memory, so the per-row state is constant:
 // the running FP32 sum of the current column chunk, the FP64 sum of the
 // current cluster, the own-cluster weight and the running minimum for b_hat.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -38,13 +39,13 @@ __global__ void k_gather(const T *__restrict__ X, int d, int64_t ld, const int32
     const T *x = X + e * ld;
     float scale = 1.0f;
     if (metric == SILH_COSINE) {
-        double s = 0.0;
+        float s = 0.f;
         for (int c = lane; c < d; c += 32) {
-            double v = (double)to_f32<T>(x[c]);
-            s += v * v;
+            const float v = to_f32<T>(x[c]);
+            s = fmaf(v, v, s);
         }
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        scale = s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.0f;
+        scale = s > 0.f ? rsqrtf(s) : 0.0f;
     }
     for (int c = lane; c < D; c += 32) Y[i * D + c] = (c < d) ? to_f32<T>(x[c]) * scale : 0.0f;
     if (lane == 0) {
@@ -158,16 +159,16 @@ k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__
             int l = labels[e];
             own[r] = (l >= 0 && l < k) ? l : -2;
         }
-        double sc = 0.0;
+        float sc = 0.f;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             x[r][c] = (e >= 0 && e < n && c < d) ? to_f32<T>(X[e * ld + c]) : 0.f;
-            sc += (double)x[r][c] * (double)x[r][c];
+            sc = fmaf(x[r][c], x[r][c], sc);
         }
         zx[r] = 0.f;
         if (METRIC == SILH_COSINE) {
-            float inv = sc > 0.0 ? (float)(1.0 / sqrt(sc)) : 0.f;
-            zx[r] = sc > 0.0 ? 0.f : 0.5f;
+            float inv = sc > 0.f ? rsqrtf(sc) : 0.f;
+            zx[r] = sc > 0.f ? 0.f : 0.5f;
 #pragma unroll
             for (int c = 0; c < D; ++c) x[r][c] *= inv;
         }
@@ -605,8 +606,9 @@ extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n,
     SILH_CK(cudaGetDevice(&dev));
     ensure_pool_retains(dev);
     if (m > 0 && nrows > 0 && tc_eligible(metric, prec, d)) {
+        // a cluster holds at most all m sampled columns
         st = tc_sweep(X, dtype, n, d, ld, labels, k, metric, prec, S->sizes, S->offsets, S->idx,
-                      S->p, m, rows, nrows, s_hat, a_hat, b_hat, sc, stream);
+                      S->p, m, m, rows, nrows, s_hat, a_hat, b_hat, sc, stream);
         goto done;
     }
     SILH_CK(sc.alloc(&Y, (size_t)m * D));
@@ -644,8 +646,9 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     st = cluster_sort(labels, n, k, sc, stream, sizes, &coff, &order, h_sizes, h_coff);
     if (st != SILH_OK) goto done;
     if (nrows > 0 && tc_eligible(metric, prec, d)) {
+        const int64_t maxc = *std::max_element(h_sizes.begin(), h_sizes.end());
         st = tc_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, order, nullptr, n,
-                      rows, nrows, s, a, b, sc, stream);
+                      maxc, rows, nrows, s, a, b, sc, stream);
         goto done;
     }
     SILH_CK(sc.alloc(&Y, (size_t)n * D));

@@ -46,8 +46,8 @@ bool tc_eligible(int metric, int prec, int d);
 silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                      const int32_t *labels, int32_t k, int metric, int prec, const int64_t *sizes,
                      const int64_t *offsets, const int32_t *col_idx, const double *col_p, int64_t m,
-                     const int64_t *rows, int64_t nrows, float *s, float *a, float *b, Scratch &sc,
-                     cudaStream_t stream);
+                     int64_t max_cluster_cols, const int64_t *rows, int64_t nrows, float *s,
+                     float *a, float *b, Scratch &sc, cudaStream_t stream);
 // 1 if a bounded wait in the tensor-core sweep gave up since the last call
 // (and clears it), 0 if not, -1 on a CUDA error.  Synchronous.
 int tc_take_error();

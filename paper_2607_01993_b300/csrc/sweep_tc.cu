@@ -40,20 +40,24 @@ namespace {
 using namespace tc;
 
 constexpr int kTileM = 128;       // rows per tile = TMEM lanes
-constexpr int kTileN = 128;       // columns per tile
+constexpr int kTileN = 64;        // columns per tile
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 
 __device__ int g_tc_error = 0;    // set when a bounded wait gives up
+
+#define SMEM_CHECK(bytes) ((bytes) + 1024 <= 200 * 1024)
 
 template <int KD, bool SPLIT>
 struct TcCfg {
     static constexpr int KB = KD / 32;                          // 128-byte K blocks
     static constexpr int PARTS = SPLIT ? 2 : 1;                 // hi (+ lo)
-    static constexpr int SLOTS = (KD == 32) ? 2 : 1;            // row tiles per CTA pass
+    static constexpr int SLOTS = (KD == 32) ? 4 : 2;            // row tiles per CTA pass
     static constexpr int A_SLOT = PARTS * KB * kTileM * 128;
     static constexpr int A_BYTES = SLOTS * A_SLOT;
     static constexpr int B_BYTES = PARTS * KB * kTileN * 128;   // one stage
     static constexpr int STAGES = (KD == 32) ? (SPLIT ? 4 : 8) : (SPLIT ? 2 : 4);
+    static_assert(SMEM_CHECK(SLOTS * PARTS * KB * kTileM * 128 + STAGES * PARTS * KB * kTileN * 128),
+                  "dynamic shared memory over budget");
     static constexpr int SMEM = 1024 + A_BYTES + STAGES * B_BYTES;
     static constexpr int THREADS = 64 + 128 * SLOTS;            // TMA, MMA, epilogue groups
     static constexpr uint32_t TMEM_COLS = SLOTS * 2 * kTileN;   // two accumulators per slot
@@ -80,19 +84,24 @@ __device__ __forceinline__ float sqrt_apx(float x) {
     return r;
 }
 
+// Distance of a row (x = hi + lo, global) to a column (y, global), directly
+// from the coordinates in FP32: the rare close pairs the epilogue flags.
 template <int METRIC, int KD>
-__device__ __forceinline__ float direct_dist(const float (&x)[KD], const float *__restrict__ y) {
+__device__ __noinline__ float direct_dist(const float *__restrict__ xh, const float *__restrict__ xl,
+                                          const float *__restrict__ y) {
     const float4 *y4 = reinterpret_cast<const float4 *>(y);
+    const float4 *h4 = reinterpret_cast<const float4 *>(xh);
+    const float4 *l4 = reinterpret_cast<const float4 *>(xl);
     float a0 = 0.f, a1 = 0.f;
-#pragma unroll
+#pragma unroll 4
     for (int q = 0; q < KD / 4; ++q) {
-        float4 v = __ldg(y4 + q);
-        float t0 = x[4 * q] - v.x, t1 = x[4 * q + 1] - v.y;
-        float t2 = x[4 * q + 2] - v.z, t3 = x[4 * q + 3] - v.w;
+        const float4 v = __ldg(y4 + q), h = __ldg(h4 + q), l = __ldg(l4 + q);
+        const float t0 = (h.x + l.x) - v.x, t1 = (h.y + l.y) - v.y;
+        const float t2 = (h.z + l.z) - v.z, t3 = (h.w + l.w) - v.w;
         a0 = fmaf(t0, t0, a0); a1 = fmaf(t1, t1, a1);
         a0 = fmaf(t2, t2, a0); a1 = fmaf(t3, t3, a1);
     }
-    float s = a0 + a1;
+    const float s = a0 + a1;
     return METRIC == SILH_EUCLIDEAN ? sqrtf(s) : 0.5f * s;
 }
 
@@ -285,10 +294,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             const bool valid = pos < nrows;
             const int own = valid ? a_lab[pos] : -1;
             const float xn = valid ? a_norm[pos] : 0.f;
-            float x[KD];
-#pragma unroll
-            for (int c = 0; c < KD; ++c)
-                x[c] = valid ? a_hi[pos * KD + c] + a_lo[pos * KD + c] : 0.f;
+            const float *xh = a_hi + (valid ? pos : 0) * KD, *xl = a_lo + (valid ? pos : 0) * KD;
             int j = 0;
             int64_t pbnd = poff[1];
             double accd = 0.0, bmin = INFINITY;
@@ -296,7 +302,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             bool dead = false;
             for (int64_t ct = 0; ct < nct; ++ct) {
                 const int64_t cc = ct * kTileN + et;
-                sh_wn[g][buf][et] = (cc < mp) ? y_wn[cc] : make_float2(0.f, 0.f);
+                if (et < kTileN) sh_wn[g][buf][et] = (cc < mp) ? y_wn[cc] : make_float2(0.f, 0.f);
                 const bool ok = !abort_flag && mbar_wait(&bar_accf[g][acc], acc_phase, kWaitNs);
                 if (epi_bar_any(g, !ok)) {      // also orders the sh_wn writes before the reads
                     abort_flag = 1;
@@ -366,10 +372,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             if (METRIC == SILH_EUCLIDEAN) {
                                 const float s2 = xn + wn.y;
                                 const float d2 = fmaf(-2.f, dot, s2);
-                                dist = (d2 < tau * s2) ? direct_dist<METRIC, KD>(x, yc) : sqrt_apx(d2);
+                                dist = (d2 < tau * s2) ? direct_dist<METRIC, KD>(xh, xl, yc)
+                                                       : sqrt_apx(d2);
                             } else {
                                 dist = 1.f - dot;
-                                if (dist < tau) dist = direct_dist<METRIC, KD>(x, yc);
+                                if (dist < tau) dist = direct_dist<METRIC, KD>(xh, xl, yc);
                             }
                             part = fmaf(wn.x, dist, part);
                         }
@@ -426,75 +433,103 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
 
 // Own-cluster pass: W_own[pos] = sum over the row's own cluster's sampled
 // columns of w d(x, y), evaluated directly in FP32 from the coordinates (these
-// are the close pairs where |x|^2 + |y|^2 - 2 x.y cancels).  One thread per
-// row in sorted order; a CTA streams the column blocks of the clusters its
-// rows belong to (contiguous, as rows are sorted by cluster).
+// are the close pairs where |x|^2 + |y|^2 - 2 x.y cancels).  Two rows per
+// thread in sorted order; a CTA streams one chunk (blockIdx.y) of the column
+// blocks of the clusters its rows belong to (contiguous, as rows are sorted by
+// cluster) and adds its partial sums to W_own (zeroed beforehand).
 template <int METRIC, int KD>
 __global__ void __launch_bounds__(128)
 k_own_direct(const float *__restrict__ a_hi, const float *__restrict__ a_lo,
              const float *__restrict__ a_norm, const int32_t *__restrict__ a_lab, int64_t nrows,
              const float *__restrict__ y_full, const float2 *__restrict__ y_wn,
-             const int64_t *__restrict__ poff, int k, double *__restrict__ w_own) {
+             const int64_t *__restrict__ poff, int k, int64_t chunk_cols,
+             double *__restrict__ w_own) {
     constexpr int BN = 64;
+    constexpr int RPT = 2;                       // rows per thread: two 128-row halves
     __shared__ __align__(16) float sh_y[BN * KD];
     __shared__ float2 sh_w[BN];
-    const int64_t base = (int64_t)blockIdx.x * 128;
-    const int64_t pos = base + threadIdx.x;
-    const bool valid = pos < nrows;
-    const int own = valid ? a_lab[pos] : -1;
-    float x[KD];
-#pragma unroll
-    for (int c = 0; c < KD; ++c) x[c] = valid ? a_hi[pos * KD + c] + a_lo[pos * KD + c] : 0.f;
-    const float zx = (METRIC == SILH_COSINE && valid && a_norm[pos] == 0.f) ? 0.5f : 0.f;
+    const int64_t base = (int64_t)blockIdx.x * 128 * RPT;
     // cluster range of this CTA's rows (labels are sorted; invalid rows last)
-    const int64_t last = min(base + 127, nrows - 1);
-    int j0 = a_lab[base], j1 = a_lab[last];
-    if (j1 < 0) {                       // trailing invalid rows: find the last valid one
-        j1 = -1;
-        for (int64_t p = last; p >= base && j1 < 0; --p) j1 = a_lab[p];
+    const int64_t last = min(base + 128 * RPT - 1, nrows - 1);
+    const int j0 = a_lab[base];
+    int j1 = a_lab[last];
+    for (int64_t p = last; p >= base && j1 < 0; --p) j1 = a_lab[p];
+    if (j0 < 0) return;
+    {   // nothing to do when this column chunk is empty for every cluster of the rows
+        bool work = false;
+        for (int j = j0; j <= j1 && !work; ++j)
+            work = poff[j] + (int64_t)blockIdx.y * chunk_cols < poff[j + 1];
+        if (!work) return;
     }
-    double acc = 0.0;
+    float x[RPT][KD];
+    int own[RPT];
+    float zx[RPT];
+    int64_t pos[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        pos[r] = base + threadIdx.x + r * 128;
+        const bool valid = pos[r] < nrows;
+        own[r] = valid ? a_lab[pos[r]] : -1;
+#pragma unroll
+        for (int c = 0; c < KD; ++c)
+            x[r][c] = valid ? a_hi[pos[r] * KD + c] + a_lo[pos[r] * KD + c] : 0.f;
+        zx[r] = (METRIC == SILH_COSINE && valid && a_norm[pos[r]] == 0.f) ? 0.5f : 0.f;
+    }
+    double acc[RPT] = {};
     if (j0 >= 0) {
         for (int j = j0; j <= j1; ++j) {
-            const int64_t cs = poff[j], ce = poff[j + 1];
+            // this block's chunk of cluster j's columns (blockIdx.y-th of chunk_cols)
+            const int64_t cs = poff[j] + (int64_t)blockIdx.y * chunk_cols;
+            const int64_t ce = min(cs + chunk_cols, poff[j + 1]);
+            if (cs >= ce) continue;
+            bool any = false;
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) any |= (own[r] == j);
             for (int64_t cb = cs; cb < ce; cb += BN) {
                 const int nb = (int)min((int64_t)BN, ce - cb);
                 __syncthreads();
                 const float4 *src = reinterpret_cast<const float4 *>(y_full + cb * KD);
                 float4 *dst = reinterpret_cast<float4 *>(sh_y);
                 for (int q = threadIdx.x; q < nb * (KD / 4); q += 128) dst[q] = src[q];
-                for (int q = threadIdx.x; q < BN; q += 128) sh_w[q] = (q < nb) ? y_wn[cb + q] : make_float2(0.f, 0.f);
+                for (int q = threadIdx.x; q < BN; q += 128)
+                    sh_w[q] = (q < nb) ? y_wn[cb + q] : make_float2(0.f, 0.f);
                 __syncthreads();
-                if (own == j) {
-                    float part = 0.f;
-                    for (int col = 0; col < nb; ++col) {
-                        const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * KD);
-                        float b0 = 0.f, b1 = 0.f;
+                if (!any) continue;
+                float part[RPT] = {};
+                for (int col = 0; col < nb; ++col) {
+                    const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * KD);
+                    float b0[RPT] = {}, b1[RPT] = {};
 #pragma unroll
-                        for (int q = 0; q < KD / 4; ++q) {
-                            const float4 y = y4[q];
-                            const float t0 = x[4 * q] - y.x, t1 = x[4 * q + 1] - y.y;
-                            const float t2 = x[4 * q + 2] - y.z, t3 = x[4 * q + 3] - y.w;
-                            b0 = fmaf(t0, t0, b0); b1 = fmaf(t1, t1, b1);
-                            b0 = fmaf(t2, t2, b0); b1 = fmaf(t3, t3, b1);
+                    for (int q = 0; q < KD / 4; ++q) {
+                        const float4 y = y4[q];
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) {
+                            const float t0 = x[r][4 * q] - y.x, t1 = x[r][4 * q + 1] - y.y;
+                            const float t2 = x[r][4 * q + 2] - y.z, t3 = x[r][4 * q + 3] - y.w;
+                            b0[r] = fmaf(t0, t0, b0[r]); b1[r] = fmaf(t1, t1, b1[r]);
+                            b0[r] = fmaf(t2, t2, b0[r]); b1[r] = fmaf(t3, t3, b1[r]);
                         }
-                        const float2 wn = sh_w[col];
-                        float dist;
-                        if (METRIC == SILH_EUCLIDEAN) {
-                            dist = sqrt_apx(b0 + b1);
-                        } else {
-                            // zero vectors sit at cosine distance 1 from everything
-                            const float zy = (wn.y == 0.f) ? 0.5f : 0.f;
-                            dist = 0.5f * (b0 + b1) + zx + zy;
-                        }
-                        part = fmaf(wn.x, dist, part);
                     }
-                    acc += (double)part;
+                    const float2 wn = sh_w[col];
+                    const float zy = (METRIC == SILH_COSINE && wn.y == 0.f) ? 0.5f : 0.f;
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        // zero vectors sit at cosine distance 1 from everything
+                        const float dist = (METRIC == SILH_EUCLIDEAN)
+                                               ? sqrt_apx(b0[r] + b1[r])
+                                               : 0.5f * (b0[r] + b1[r]) + zx[r] + zy;
+                        part[r] = fmaf(wn.x, dist, part[r]);
+                    }
                 }
+#pragma unroll
+                for (int r = 0; r < RPT; ++r)
+                    if (own[r] == j) acc[r] += (double)part[r];
             }
         }
     }
-    if (valid) w_own[pos] = acc;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+        if (pos[r] < nrows && acc[r] != 0.0) atomicAdd(&w_own[pos[r]], acc[r]);
 }
 
 // Mean of the m sampled columns (Euclidean centring): per-block partial sums
@@ -646,26 +681,29 @@ __global__ void k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int
     const int64_t e = rows ? rows[r] : r;
     const bool ok = e >= 0 && e < n;
     const T *x = X + (ok ? e : 0) * ld;
-    double s = 0.0;
-    for (int c = lane; c < d; c += 32) {
-        const double v = ok ? (double)to_f32<T>(x[c]) : 0.0;
-        s += v * v;
+    // norms in FP32 (pairwise over the lanes): they enter the epilogue in FP32
+    float s = 0.f;
+    if (metric == SILH_COSINE) {
+        for (int c = lane; c < d; c += 32) {
+            const float v = ok ? to_f32<T>(x[c]) : 0.f;
+            s = fmaf(v, v, s);
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const float scale = (metric == SILH_COSINE) ? (s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f) : 1.f;
-    double ss = 0.0;
+    const float scale = (metric == SILH_COSINE) ? (s > 0.f ? rsqrtf(s) : 0.f) : 1.f;
+    float ss = 0.f;
     for (int c = lane; c < KD; c += 32) {
         float v = (ok && c < d) ? to_f32<T>(x[c]) * scale : 0.f;
         if (mu != nullptr && c < d) v = v - mu[c];
         const float h = to_tf32(v);
         hi[p * KD + c] = h;
         lo[p * KD + c] = v - h;
-        ss += (double)v * (double)v;
+        ss = fmaf(v, v, ss);
     }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if (lane == 0) {
         // Euclidean: squared norm of the (centred) row; cosine: 1, or 0 for a zero row
-        nrm[p] = (metric == SILH_COSINE) ? (s > 0.0 ? 1.f : 0.f) : (float)ss;
+        nrm[p] = (metric == SILH_COSINE) ? (s > 0.f ? 1.f : 0.f) : ss;
         const int32_t l = ok ? labels[e] : -1;
         lab[p] = (l >= 0 && l < k) ? l : -1;
         outi[p] = r;
@@ -732,14 +770,16 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
     }
     const int64_t e = idx ? idx[t] : t;
     const T *x = X + e * ld;
-    double s = 0.0;
-    for (int c = lane; c < d; c += 32) {
-        const double v = (double)to_f32<T>(x[c]);
-        s += v * v;
+    float s = 0.f;
+    if (metric == SILH_COSINE) {
+        for (int c = lane; c < d; c += 32) {
+            const float v = to_f32<T>(x[c]);
+            s = fmaf(v, v, s);
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const float scale = (metric == SILH_COSINE) ? (s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f) : 1.f;
-    double ss = 0.0;
+    const float scale = (metric == SILH_COSINE) ? (s > 0.f ? rsqrtf(s) : 0.f) : 1.f;
+    float ss = 0.f;
     for (int c = lane; c < KD; c += 32) {
         float v = (c < d) ? to_f32<T>(x[c]) * scale : 0.f;
         if (mu != nullptr && c < d) v = v - mu[c];
@@ -747,13 +787,13 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
         full[i * KD + c] = v;
         hi[i * KD + c] = h;
         lo[i * KD + c] = v - h;
-        ss += (double)v * (double)v;
+        ss = fmaf(v, v, ss);
     }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if (lane == 0) {
         const float w = p ? (float)(1.0 / p[t]) : 1.0f;
         // Euclidean: squared norm of the (centred) column; cosine: 1, or 0 for a zero column
-        wn[i] = make_float2(w, (metric == SILH_COSINE) ? (s > 0.0 ? 1.f : 0.f) : (float)ss);
+        wn[i] = make_float2(w, (metric == SILH_COSINE) ? (s > 0.f ? 1.f : 0.f) : ss);
     }
 }
 
@@ -792,10 +832,14 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
                       const float *a_lo, const float *a_norm, const int32_t *a_lab,
                       const int64_t *a_out, int64_t nrows, const float *y_full, const float2 *y_wn,
                       const int64_t *poff, const int64_t *sizes, int k, float tau,
-                      double *w_own, float *s, float *a, float *b) {
+                      int64_t max_cluster_cols, double *w_own, float *s, float *a, float *b) {
     using C = TcCfg<KD, SPLIT>;
-    k_own_direct<METRIC, KD><<<(int)((nrows + 127) / 128), 128, 0, stream>>>(
-        a_hi, a_lo, a_norm, a_lab, nrows, y_full, y_wn, poff, k, w_own);
+    constexpr int64_t kChunk = 2048;
+    const int64_t nchunk = std::max<int64_t>(1, (max_cluster_cols + 31 + kChunk - 1) / kChunk);
+    cudaError_t e0 = cudaMemsetAsync(w_own, 0, sizeof(double) * (size_t)nrows, stream);
+    if (e0 != cudaSuccess) return e0;
+    k_own_direct<METRIC, KD><<<dim3((unsigned)((nrows + 255) / 256), (unsigned)nchunk), 128, 0, stream>>>(
+        a_hi, a_lo, a_norm, a_lab, nrows, y_full, y_wn, poff, k, kChunk, w_own);
     count_launches(1);
     auto kern = k_sweep_tc<METRIC, KD, SPLIT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
@@ -820,8 +864,8 @@ bool tc_eligible(int metric, int prec, int d) {
 silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                      const int32_t *labels, int32_t k, int metric, int prec, const int64_t *sizes,
                      const int64_t *offsets, const int32_t *col_idx, const double *col_p, int64_t m,
-                     const int64_t *rows, int64_t nrows, float *s, float *a, float *b, Scratch &sc,
-                     cudaStream_t stream) {
+                     int64_t max_cluster_cols, const int64_t *rows, int64_t nrows, float *s,
+                     float *a, float *b, Scratch &sc, cudaStream_t stream) {
     silh_status st = SILH_OK;
     const int KD = d <= 32 ? 32 : 64;
     const bool split = prec == SILH_PREC_3XTF32;
@@ -913,8 +957,8 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
 #define SILH_TC_CASE(MET, KDV, SP)                                                              \
     if (metric == MET && KD == KDV && split == SP) {                                           \
         SILH_CK((launch_tc<MET, KDV, SP>(nsm, stream, m_ahi, m_alo, m_bhi, m_blo, rhi, rlo, rn, \
-                                         lab, outi, nrows, yf, ywn, poff, sizes, k, tau, w_own, \
-                                         s, a, b)));                                           \
+                                         lab, outi, nrows, yf, ywn, poff, sizes, k, tau,        \
+                                         max_cluster_cols, w_own, s, a, b)));                  \
     }
     SILH_TC_CASE(SILH_EUCLIDEAN, 32, true)
     SILH_TC_CASE(SILH_EUCLIDEAN, 32, false)
