@@ -8,12 +8,11 @@
 // and the gamma sweep both read it coalesced).
 //
 // Precision: Phase 1 decides which elements are sampled (u < p_e), so it runs
-// at FP64-class accuracy.  Euclidean, Manhattan and Canberra pair distances use
-// double-float arithmetic (an FP32 pair hi + lo carried with error-free
-// transformations: Knuth's two-sum, the FMA two-product), about 2^-44 relative,
-// which B300 evaluates an order of magnitude faster than native FP64.  Cosine
-// distances are native FP64 in ascending coordinate order with correctly
-// rounded operations.  W sums, gamma and p are FP64.
+// at FP64-class accuracy.  Pair distances use double-float arithmetic (an FP32
+// pair hi + lo carried with error-free transformations: Knuth's two-sum, the
+// FMA two-product), about 2^-44 relative (cosine: its inner product and norms,
+// then 1 - <x,y>/(|x||y|) in FP64), which B300 evaluates an order of magnitude
+// faster than native FP64.  W sums, gamma and p are FP64.
 #include <algorithm>
 #include <cmath>
 
@@ -216,91 +215,6 @@ __global__ void k_seg_offsets(const int64_t *__restrict__ pos_of, const int64_t 
 constexpr int kF0Group = 8;     // F0 rows staged in shared memory at a time
 constexpr int kDistThreads = 128;
 
-template <class T>
-__device__ __forceinline__ double ld64(const T *X, int64_t off) {
-    return (double)to_f32<T>(X[off]);
-}
-
-// D_j[f, i] = d(member i, F0_j[f]) in FP64, one thread per member, F0 rows in
-// shared memory.  Work item w covers members [chunk*128, chunk*128+128) of
-// cluster item_cluster[w].
-template <class T, int METRIC>
-__global__ void k_dist_f0(const T *__restrict__ X, int d, int64_t ld,
-                          const int32_t *__restrict__ order, const int64_t *__restrict__ coff,
-                          const int32_t *__restrict__ f0_elem, const int64_t *__restrict__ f0off,
-                          const int64_t *__restrict__ doff, const int32_t *__restrict__ item_cluster,
-                          const int32_t *__restrict__ item_chunk, double *__restrict__ D) {
-    extern __shared__ double sh_y[];            // kF0Group x d
-    __shared__ double sh_ny[kF0Group];
-    int j = item_cluster[blockIdx.x];
-    int64_t c0 = coff[j], nc = coff[j + 1] - c0;
-    int64_t i = (int64_t)item_chunk[blockIdx.x] * kDistThreads + threadIdx.x;
-    bool live = i < nc;
-    int64_t e = live ? order[c0 + i] : 0;
-    int64_t g0 = f0off[j], nf = f0off[j + 1] - g0;
-    double *Dj = D + doff[j];
-    for (int64_t gb = 0; gb < nf; gb += kF0Group) {
-        int gc = (int)min((int64_t)kF0Group, nf - gb);
-        __syncthreads();
-        for (int q = threadIdx.x; q < kF0Group * d; q += blockDim.x) {
-            int g = q / d, c = q % d;
-            sh_y[q] = (g < gc) ? ld64(X, (int64_t)f0_elem[g0 + gb + g] * ld + c) : 0.0;
-        }
-        __syncthreads();
-        if (METRIC == SILH_COSINE && threadIdx.x < kF0Group) {
-            double s = 0.0;
-            for (int c = 0; c < d; ++c)
-                s = __dadd_rn(s, __dmul_rn(sh_y[threadIdx.x * d + c], sh_y[threadIdx.x * d + c]));
-            sh_ny[threadIdx.x] = s;
-        }
-        __syncthreads();
-        if (!live) continue;
-        double acc[kF0Group];
-        double nx = 0.0;
-#pragma unroll
-        for (int g = 0; g < kF0Group; ++g) acc[g] = 0.0;
-        const T *xr = X + e * ld;
-        for (int c = 0; c < d; ++c) {
-            double xv = (double)to_f32<T>(xr[c]);
-            if (METRIC == SILH_COSINE) nx = __dadd_rn(nx, __dmul_rn(xv, xv));
-#pragma unroll
-            for (int g = 0; g < kF0Group; ++g) {
-                double yv = sh_y[g * d + c];
-                if (METRIC == SILH_EUCLIDEAN) {
-                    double t = __dsub_rn(xv, yv);
-                    acc[g] = __dadd_rn(acc[g], __dmul_rn(t, t));
-                } else if (METRIC == SILH_MANHATTAN) {
-                    acc[g] = __dadd_rn(acc[g], fabs(__dsub_rn(xv, yv)));
-                } else if (METRIC == SILH_CANBERRA) {
-                    double num = fabs(__dsub_rn(xv, yv));
-                    double den = __dadd_rn(fabs(xv), fabs(yv));
-                    if (den > 0.0) acc[g] = __dadd_rn(acc[g], __ddiv_rn(num, den));
-                } else {
-                    acc[g] = __dadd_rn(acc[g], __dmul_rn(xv, yv));
-                }
-            }
-        }
-#pragma unroll
-        for (int g = 0; g < kF0Group; ++g) {
-            if (g >= gc) break;
-            double v = acc[g];
-            if (METRIC == SILH_EUCLIDEAN) {
-                v = __dsqrt_rn(v);
-            } else if (METRIC == SILH_COSINE) {
-                double ny = sh_ny[g];
-                if (nx == 0.0 || ny == 0.0) {
-                    v = 1.0;
-                } else {
-                    v = __dsub_rn(1.0, __ddiv_rn(v, __dmul_rn(__dsqrt_rn(nx), __dsqrt_rn(ny))));
-                    v = v < 0.0 ? 0.0 : (v > 2.0 ? 2.0 : v);
-                }
-            }
-            Dj[(gb + g) * nc + i] = v;
-        }
-    }
-}
-
-
 // ------------------------------------------------ double-float arithmetic
 // A value is carried as hi + lo (two FP32 numbers).  two_sum (Knuth) and
 // two_prod (one FMA) return the exact rounding error of an add / a multiply;
@@ -343,7 +257,9 @@ __device__ __forceinline__ float sqrt_apx(float x) {
 }
 
 // Phase-1 pair distances for Euclidean, Manhattan and Canberra in double-float
-// arithmetic (layout and work split as k_dist_f0).
+// arithmetic.  D_j[f, i] = d(member i, F0_j[f]), one thread per member, F0
+// rows staged in shared memory kF0Group at a time; work item w covers members
+// [chunk*128, chunk*128+128) of cluster item_cluster[w].
 template <class T, int METRIC>
 __global__ void k_dist_f0_df(const T *__restrict__ X, int d, int64_t ld,
                              const int32_t *__restrict__ order, const int64_t *__restrict__ coff,
@@ -351,6 +267,7 @@ __global__ void k_dist_f0_df(const T *__restrict__ X, int d, int64_t ld,
                              const int64_t *__restrict__ doff, const int32_t *__restrict__ item_cluster,
                              const int32_t *__restrict__ item_chunk, double *__restrict__ D) {
     extern __shared__ float sh_yf[];            // kF0Group x d
+    __shared__ double sh_inv[kF0Group];         // cosine: 1/|y| of the staged rows (0: zero row)
     const int j = item_cluster[blockIdx.x];
     const int64_t c0 = coff[j], nc = coff[j + 1] - c0;
     const int64_t i = (int64_t)item_chunk[blockIdx.x] * kDistThreads + threadIdx.x;
@@ -358,12 +275,38 @@ __global__ void k_dist_f0_df(const T *__restrict__ X, int d, int64_t ld,
     const int64_t e = live ? order[c0 + i] : 0;
     const int64_t g0 = f0off[j], nf = f0off[j + 1] - g0;
     double *Dj = D + doff[j];
+    double inv_x = 0.0;                         // cosine: 1/|x| of this member (0: zero row)
+    if (METRIC == SILH_COSINE && live) {
+        float nh = 0.f, nl = 0.f;
+        for (int c = 0; c < d; ++c) {
+            const float xv = to_f32<T>(X[e * ld + c]);
+            float p, pe;
+            two_prod(xv, xv, p, pe);
+            df_acc(nh, nl, p);
+            nl = __fadd_rn(nl, pe);
+        }
+        const double n2 = (double)nh + (double)nl;
+        inv_x = n2 > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(n2)) : 0.0;
+    }
     for (int64_t gb = 0; gb < nf; gb += kF0Group) {
         const int gc = (int)min((int64_t)kF0Group, nf - gb);
         __syncthreads();
         for (int q = threadIdx.x; q < kF0Group * d; q += blockDim.x) {
             const int g = q / d, c = q % d;
             sh_yf[q] = (g < gc) ? to_f32<T>(X[(int64_t)f0_elem[g0 + gb + g] * ld + c]) : 0.f;
+        }
+        __syncthreads();
+        if (METRIC == SILH_COSINE && threadIdx.x < kF0Group) {
+            float nh = 0.f, nl = 0.f;
+            for (int c = 0; c < d; ++c) {
+                const float yv = sh_yf[threadIdx.x * d + c];
+                float p, pe;
+                two_prod(yv, yv, p, pe);
+                df_acc(nh, nl, p);
+                nl = __fadd_rn(nl, pe);
+            }
+            const double n2 = (double)nh + (double)nl;
+            sh_inv[threadIdx.x] = n2 > 0.0 ? __ddiv_rn(1.0, __dsqrt_rn(n2)) : 0.0;
         }
         __syncthreads();
         if (!live) continue;
@@ -376,6 +319,14 @@ __global__ void k_dist_f0_df(const T *__restrict__ X, int d, int64_t ld,
 #pragma unroll
             for (int g = 0; g < kF0Group; ++g) {
                 const float yv = sh_yf[g * d + c];
+                if (METRIC == SILH_COSINE) {            // signed double-float dot product
+                    float p, pe, s2, e2;
+                    two_prod(xv, yv, p, pe);
+                    two_sum(hi[g], p, s2, e2);
+                    e2 = __fadd_rn(__fadd_rn(e2, pe), lo[g]);
+                    two_sum(s2, e2, hi[g], lo[g]);
+                    continue;
+                }
                 float s, t;
                 two_sum(xv, -yv, s, t);                 // x - y = s + t exactly
                 if (METRIC == SILH_EUCLIDEAN) {
@@ -426,6 +377,15 @@ __global__ void k_dist_f0_df(const T *__restrict__ X, int d, int64_t ld,
                     v = (double)y0 + (double)corr;
                 } else {
                     v = 0.0;
+                }
+            } else if (METRIC == SILH_COSINE) {
+                const double iy = sh_inv[g];
+                if (inv_x == 0.0 || iy == 0.0) {
+                    v = 1.0;                             // a zero-norm operand
+                } else {
+                    const double dot = (double)hi[g] + (double)lo[g];
+                    v = __dsub_rn(1.0, __dmul_rn(__dmul_rn(dot, inv_x), iy));
+                    v = v < 0.0 ? 0.0 : (v > 2.0 ? 2.0 : v);
                 }
             } else {
                 v = (double)hi[g] + (double)lo[g];
@@ -508,7 +468,7 @@ void launch_dist_f0(int metric, int nitems, size_t smem, cudaStream_t stream, co
                 X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
             break;
         case SILH_COSINE:
-            k_dist_f0<T, SILH_COSINE><<<nitems, kDistThreads, smem, stream>>>(
+            k_dist_f0_df<T, SILH_COSINE><<<nitems, kDistThreads, smem_f, stream>>>(
                 X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
             break;
         case SILH_MANHATTAN:
@@ -678,28 +638,18 @@ extern "C" silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t 
         SILH_REQ(smem <= 200 * 1024, "d too large for Phase 1 (d <= 3200)");
         if (dtype == SILH_F32) {
             if (smem / 2 > 48 * 1024)
-                for (auto f : {k_dist_f0_df<float, 0>, k_dist_f0_df<float, 2>,
-                               k_dist_f0_df<float, 3>})
+                for (auto f : {k_dist_f0_df<float, 0>, k_dist_f0_df<float, 1>,
+                               k_dist_f0_df<float, 2>, k_dist_f0_df<float, 3>})
                     SILH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)(smem / 2)));
-            if (smem > 48 * 1024)
-                for (auto f : {k_dist_f0<float, 0>, k_dist_f0<float, 1>, k_dist_f0<float, 2>,
-                               k_dist_f0<float, 3>})
-                    SILH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem));
             launch_dist_f0<float>(metric, nitems, smem, stream, (const float *)X, d, ld, order,
                                   coff, f0_elem, f0off, doff, ic, ik, D);
         } else {
             if (smem / 2 > 48 * 1024)
-                for (auto f : {k_dist_f0_df<__nv_bfloat16, 0>, k_dist_f0_df<__nv_bfloat16, 2>,
-                               k_dist_f0_df<__nv_bfloat16, 3>})
+                for (auto f : {k_dist_f0_df<__nv_bfloat16, 0>, k_dist_f0_df<__nv_bfloat16, 1>,
+                               k_dist_f0_df<__nv_bfloat16, 2>, k_dist_f0_df<__nv_bfloat16, 3>})
                     SILH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)(smem / 2)));
-            if (smem > 48 * 1024)
-                for (auto f : {k_dist_f0<__nv_bfloat16, 0>, k_dist_f0<__nv_bfloat16, 1>,
-                               k_dist_f0<__nv_bfloat16, 2>, k_dist_f0<__nv_bfloat16, 3>})
-                    SILH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem));
             launch_dist_f0<__nv_bfloat16>(metric, nitems, smem, stream,
                                           (const __nv_bfloat16 *)X, d, ld, order, coff, f0_elem,
                                           f0off, doff, ic, ik, D);

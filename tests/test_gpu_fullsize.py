@@ -46,7 +46,7 @@ def test_large_workload_sampled_parity(large, metric):
     silh.silh_stream_status()
     Xh = X.astype(np.float64)
     os_ = oracle.sample_pps(Xh, lab, k, metric, t=w["t"], delta=w["delta"], seed=7, cid=1)
-    ties = assert_same_sample(gs, os_, k, 7, 1)
+    ties = assert_same_sample(gs, os_, k, 7, 1, metric, lab)
     assert ties <= 2
     rows = synth.seeded_rows(w["n"], 300, seed=11)
     s_o, _, _ = oracle.estimate(Xh, lab, k, metric, os_.offsets, os_.idx, os_.ps, rows=rows)
