@@ -300,9 +300,13 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             double accd = 0.0, bmin = INFINITY;
             float accf = 0.f;                         // current cluster, this tile
             bool dead = false;
+            // (weight, |y|^2) of this thread's column, fetched one tile ahead
+            float2 wn_next = (et < kTileN && et < mp) ? y_wn[et] : make_float2(0.f, 0.f);
             for (int64_t ct = 0; ct < nct; ++ct) {
-                const int64_t cc = ct * kTileN + et;
-                if (et < kTileN) sh_wn[g][buf][et] = (cc < mp) ? y_wn[cc] : make_float2(0.f, 0.f);
+                const float2 wn_cur = wn_next;
+                const int64_t cn = (ct + 1) * kTileN + et;
+                if (et < kTileN) wn_next = (cn < mp) ? y_wn[cn] : make_float2(0.f, 0.f);
+                if (et < kTileN) sh_wn[g][buf][et] = wn_cur;
                 const bool ok = !abort_flag && mbar_wait(&bar_accf[g][acc], acc_phase, kWaitNs);
                 if (epi_bar_any(g, !ok)) {      // also orders the sh_wn writes before the reads
                     abort_flag = 1;
