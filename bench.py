@@ -315,6 +315,75 @@ def roofline(res, peaks, peak_kind):
                  "peak_source": f"148 SMs x 128 FP32 lanes x {clock:.0f} MHz ({peak_kind} clock)"}
 
 
+def run_batching(args):
+    """Batching workload: one dataset (n = 500k, d = 16), 256 clusterings
+    (k = 2..257, nearest random data-row centres), t = 128.  Phase 1 per
+    clustering; Phase 2 of all clusterings as one graph-captured persistent
+    launch (autotuned tile shape) against 256 separate launches."""
+    import torch
+    from paper_2607_01993_b300 import autotune, silh
+    torch.cuda.set_device(0)
+    X = synth.batching(seed=3)
+    n = X.shape[0]
+    Xt = torch.from_numpy(X).cuda()
+    ks = list(range(2, 2 + args.clusterings))
+    items = []
+    t0 = time.perf_counter()
+    for c, k in enumerate(ks):
+        lt = synth.nearest_centre_labels_device(Xt, k, seed=1000 + k)
+        items.append((lt, silh.silh_sample_pps(Xt, lt, k, "euclidean", t=128.0, seed=7,
+                                               clustering_id=c)))
+    torch.cuda.synchronize()
+    t_phase1 = time.perf_counter() - t0
+    sub = items[:: max(1, len(items) // 8)]          # a representative spread of k
+    variant, tune_ms = autotune.tune_batched(Xt, sub, "euclidean", reps=1, force=True)
+    outs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in items]
+    silh.silh_estimate_batched(Xt, items, "euclidean", variant=variant, outs=outs)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        silh.silh_estimate_batched(Xt, items, "euclidean", variant=variant, outs=outs)
+    g.replay()
+    torch.cuda.synchronize()
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    ms_batched = timed(g.replay, args.steps)
+    sep_outs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in items]
+
+    def separate():
+        for (lt, smp), k, o in zip(items, ks, sep_outs):
+            silh.silh_estimate(Xt, lt, k, smp, "euclidean", prec="fp32", out=o)
+
+    separate()
+    ms_separate = timed(separate, max(1, args.steps // 2))
+    same = all(torch.equal(a, b) for a, b in zip(outs, sep_outs)) if variant == -1 else None
+    maxdiff = max((a - b).abs().max().item() for a, b in zip(outs, sep_outs))
+    pairs = float(n) * sum(smp.size for _, smp in items)
+    line = {"metric": "batched PPS silhouette points/s (Phase 2, all clusterings)",
+            "value": round(len(items) * n / (ms_batched * 1e-3), 1), "unit": "points/s",
+            "n_gpus": 1, "steps": args.steps, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "batched_ms": round(ms_batched, 3),
+            "separate_ms": round(ms_separate, 3), "speedup_vs_separate": round(ms_separate / ms_batched, 3),
+            "pairs_per_s": round(pairs / (ms_batched * 1e-3), 1), "variant": variant,
+            "autotune_ms": tune_ms, "phase1_s_all": round(t_phase1, 3),
+            "max_abs_diff_vs_separate": maxdiff,
+            "config": {"workload": f"batching: n={n}, d=16 FP32, {len(items)} clusterings k=2..{ks[-1]} "
+                                   f"(nearest random data-row centres), t=128, Euclidean, FP32 CUDA cores",
+                       "graph": "CUDA graph of one persistent launch"}}
+    print(json.dumps(line))
+
+
 def main():
     global METRICS
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
@@ -327,7 +396,13 @@ def main():
                     help="scale n and the exact subset (profiling cases only)")
     ap.add_argument("--metrics", default=",".join(METRICS),
                     help="comma-separated subset of metrics (profiling cases only)")
+    ap.add_argument("--workload", default="large", choices=["large", "batching"],
+                    help="large: the default step; batching: 256 clusterings in one launch")
+    ap.add_argument("--clusterings", type=int, default=256)
     args = ap.parse_args()
+    if args.workload == "batching":
+        run_batching(args)
+        return
     METRICS = tuple(m for m in args.metrics.split(",") if m)
 
     rank = int(os.environ.get("RANK", 0))

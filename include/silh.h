@@ -151,6 +151,27 @@ silh_status silh_estimate_noalloc(const void *X, silh_dtype dtype, int64_t n, in
                                   const int64_t *rows, int64_t nrows, float *s_hat, float *a_hat,
                                   float *b_hat, void *stream);
 
+/* One clustering of the dataset in a batched call: its labels, its sample set
+ * (from silh_sample_pps on these labels) and its FP32 output of n s_hat values. */
+typedef struct silh_batch_item {
+    const int32_t *labels;
+    const silh_sample *sample;
+    float *s_hat;
+} silh_batch_item;
+
+/* Phase 2 of Algorithm 1 for many clusterings of the same data X in one
+ * persistent launch (the work items are (clustering, row tile) pairs, taken
+ * round-robin by CTAs sized to fill the GPU).  Same arithmetic and results as
+ * silh_estimate with SILH_PREC_FP32 on each item, all rows.  variant selects
+ * the tile shape (rows per thread x columns per stage: 0 = 1x32, 1 = 1x64,
+ * 2 = 2x32, 3 = 2x64; -1 = default) -- the choice an autotuner makes by
+ * timing.  Asynchronous and free of host synchronisation, so the call can be
+ * captured in a CUDA graph; items are passed to the kernels as launch
+ * parameters, 256 per launch.  Errors: SILH_EINVAL for bad arguments. */
+silh_status silh_estimate_batched(const void *X, silh_dtype dtype, int64_t n, int32_t d,
+                                  int64_t ld, silh_metric metric, silh_prec prec, int32_t nitems,
+                                  const silh_batch_item *items, int32_t variant, void *stream);
+
 /* Exact silhouette (Eq. 1-2) of the listed rows against all n elements:
  * Phase 2 with F_Cj = Cj and p = 1.  Synchronising (validates labels).
  * Errors: as silh_sample_pps. */

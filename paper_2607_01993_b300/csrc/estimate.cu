@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstring>
 
 #include "kernels.cuh"
 
@@ -133,23 +134,25 @@ __device__ __forceinline__ float pair_dist(const float (&x)[D], const float4 *__
 
 constexpr int kThreads = 128;
 
+// One CTA's tile of BM = 128 RPT rows [r0, r0 + BM) against the whole
+// cluster-major column operand (Y, wY, zY, offsets): W_hat_j for every cluster
+// and the silhouette of Eq. 8.  Shared by the single and the batched sweeps.
 template <class T, int METRIC, int D, int RPT, int BN>
-__global__ void __launch_bounds__(kThreads)
-k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__restrict__ labels,
-        int k, const int64_t *__restrict__ sizes, const int64_t *__restrict__ offsets,
-        const float *__restrict__ Y, const float *__restrict__ wY, const float *__restrict__ zY,
+__device__ __forceinline__ void sweep_rows(
+        int64_t r0, const T *__restrict__ X, int d, int64_t ld, int64_t n,
+        const int32_t *__restrict__ labels, int k, const int64_t *__restrict__ sizes,
+        const int64_t *__restrict__ offsets, const float *__restrict__ Y,
+        const float *__restrict__ wY, const float *__restrict__ zY,
         const int64_t *__restrict__ rows, int64_t nrows, float *__restrict__ s_out,
         float *__restrict__ a_out, float *__restrict__ b_out) {
     __shared__ __align__(16) float sh_y[BN * D];
     __shared__ __align__(16) float sh_ya[METRIC == SILH_CANBERRA ? BN * D : 4];
     __shared__ float sh_w[BN];
     __shared__ float sh_z[BN];
-    constexpr int BM = kThreads * RPT;
     float x[RPT][D];
     float zx[RPT];   // cosine: 0.5 for a zero row (distance 1 to everything)
     int own[RPT];
     double wown[RPT], bmin[RPT];
-    int64_t r0 = (int64_t)blockIdx.x * BM;
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         int64_t rr = r0 + threadIdx.x + r * kThreads;
@@ -245,6 +248,174 @@ k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__
         s_out[rr] = sv;
         if (a_out) a_out[rr] = av;
         if (b_out) b_out[rr] = bv;
+    }
+}
+
+template <class T, int METRIC, int D, int RPT, int BN>
+__global__ void __launch_bounds__(kThreads)
+k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__restrict__ labels,
+        int k, const int64_t *__restrict__ sizes, const int64_t *__restrict__ offsets,
+        const float *__restrict__ Y, const float *__restrict__ wY, const float *__restrict__ zY,
+        const int64_t *__restrict__ rows, int64_t nrows, float *__restrict__ s_out,
+        float *__restrict__ a_out, float *__restrict__ b_out) {
+    sweep_rows<T, METRIC, D, RPT, BN>((int64_t)blockIdx.x * kThreads * RPT, X, d, ld, n, labels, k,
+                                      sizes, offsets, Y, wY, zY, rows, nrows, s_out, a_out, b_out);
+}
+
+// ------------------------------------------------------------ batched
+
+// Many clusterings of one dataset in one persistent launch: item c has its own
+// labels, cluster sizes, sample offsets (relative to its block of the
+// concatenated column operand, starting at col_base) and output.  Work item w
+// is (item, row tile); CTAs claim work items from a global counter, items in
+// decreasing order of their column count (longest tiles first).
+struct BatchItem {
+    const int32_t *labels;
+    const int64_t *sizes;
+    const int64_t *offsets;
+    const int32_t *idx;
+    const double *p;
+    float *s_out;
+    int64_t col_base;
+    int64_t m;
+    int64_t tile_base;
+    int32_t k;
+    int32_t pad_;
+};
+
+constexpr int kMaxBatch = 256;
+
+struct BatchParams {
+    int32_t nitems;
+    int64_t total_tiles;
+    int64_t total_cols;
+    BatchItem items[kMaxBatch];
+};
+
+template <class T, int METRIC, int D, int RPT, int BN>
+__global__ void __launch_bounds__(kThreads)
+k_sweep_batched(const __grid_constant__ BatchParams bp, const T *__restrict__ X, int d, int64_t ld,
+                int64_t n, const float *__restrict__ Y, const float *__restrict__ wY,
+                const float *__restrict__ zY, unsigned long long *__restrict__ next_work) {
+    __shared__ int64_t sh_work;
+    for (;;) {
+        // dynamic schedule: claim the next work item (items are ordered by cost, largest first)
+        __syncthreads();
+        if (threadIdx.x == 0) sh_work = (int64_t)atomicAdd(next_work, 1ull);
+        __syncthreads();
+        const int64_t w = sh_work;
+        if (w >= bp.total_tiles) break;
+        int lo = 0, hi = bp.nitems - 1;          // last item with tile_base <= w
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bp.items[mid].tile_base <= w) lo = mid; else hi = mid - 1;
+        }
+        const BatchItem &it = bp.items[lo];
+        const int64_t rt = w - it.tile_base;
+        sweep_rows<T, METRIC, D, RPT, BN>(rt * kThreads * RPT, X, d, ld, n, it.labels, it.k,
+                                          it.sizes, it.offsets, Y + it.col_base * D,
+                                          wY + it.col_base, zY + it.col_base, nullptr, n,
+                                          it.s_out, nullptr, nullptr);
+    }
+}
+
+// Concatenated column operand of all items (one warp per column).
+template <class T>
+__global__ void k_gather_batched(const __grid_constant__ BatchParams bp, const T *__restrict__ X,
+                                 int d, int64_t ld, int D, int metric, float *__restrict__ Y,
+                                 float *__restrict__ wY, float *__restrict__ zY) {
+    const int64_t g = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (g >= bp.total_cols) return;
+    int lo = 0, hi = bp.nitems - 1;              // last item with col_base <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bp.items[mid].col_base <= g) lo = mid; else hi = mid - 1;
+    }
+    const BatchItem &it = bp.items[lo];
+    const int64_t i = g - it.col_base;
+    const T *x = X + (int64_t)it.idx[i] * ld;
+    float scale = 1.0f;
+    if (metric == SILH_COSINE) {
+        float sq = 0.f;
+        for (int c = lane; c < d; c += 32) {
+            const float v = to_f32<T>(x[c]);
+            sq = fmaf(v, v, sq);
+        }
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        scale = sq > 0.f ? rsqrtf(sq) : 0.0f;
+    }
+    for (int c = lane; c < D; c += 32) Y[g * D + c] = (c < d) ? to_f32<T>(x[c]) * scale : 0.0f;
+    if (lane == 0) {
+        const float w = (float)(1.0 / it.p[i]);
+        wY[g] = w;
+        zY[g] = (metric == SILH_COSINE && scale == 0.0f) ? 0.5f * w : 0.0f;
+    }
+}
+
+template <class T, int METRIC, int D, int RPT, int BN>
+cudaError_t launch_batched_v(const BatchParams &bp, cudaStream_t stream, const T *X, int d,
+                             int64_t ld, int64_t n, const float *Y, const float *wY,
+                             const float *zY, unsigned long long *next_work) {
+    auto kern = k_sweep_batched<T, METRIC, D, RPT, BN>;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>(bp.total_tiles, (int64_t)nsm * std::max(per_sm, 1));
+    e = cudaMemsetAsync(next_work, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)std::max<int64_t>(grid, 1), kThreads, 0, stream>>>(bp, X, d, ld, n, Y, wY, zY,
+                                                                       next_work);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Tile-shape variants the autotuner chooses from: (rows per thread, columns per stage).
+constexpr int kBatchVariants = 4;
+
+template <class T, int METRIC, int D>
+cudaError_t launch_batched(int variant, const BatchParams &bp, cudaStream_t stream, const T *X,
+                           int d, int64_t ld, int64_t n, const float *Y, const float *wY,
+                           const float *zY, unsigned long long *nw) {
+    if (variant < 0) variant = (D <= 32) ? 3 : 0;     // as the single sweep: (2, 64) / (1, 32)
+    switch (variant) {
+        case 0: return launch_batched_v<T, METRIC, D, 1, 32>(bp, stream, X, d, ld, n, Y, wY, zY, nw);
+        case 1: return launch_batched_v<T, METRIC, D, 1, 64>(bp, stream, X, d, ld, n, Y, wY, zY, nw);
+        case 2: return launch_batched_v<T, METRIC, D, 2, 32>(bp, stream, X, d, ld, n, Y, wY, zY, nw);
+        default: return launch_batched_v<T, METRIC, D, 2, (D >= 128 ? 32 : 64)>(bp, stream, X, d, ld,
+                                                                               n, Y, wY, zY, nw);
+    }
+}
+
+template <class T, int METRIC>
+cudaError_t launch_batched_d(int D, int variant, const BatchParams &bp, cudaStream_t stream,
+                             const T *X, int d, int64_t ld, int64_t n, const float *Y,
+                             const float *wY, const float *zY, unsigned long long *nw) {
+    switch (D) {
+        case 8: return launch_batched<T, METRIC, 8>(variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+        case 16: return launch_batched<T, METRIC, 16>(variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+        case 32: return launch_batched<T, METRIC, 32>(variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+        case 64: return launch_batched<T, METRIC, 64>(variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+        default: return launch_batched<T, METRIC, 128>(variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+    }
+}
+
+template <class T>
+cudaError_t launch_batched_m(int metric, int D, int variant, const BatchParams &bp,
+                             cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
+                             const float *Y, const float *wY, const float *zY,
+                             unsigned long long *nw) {
+    switch (metric) {
+        case SILH_EUCLIDEAN:
+            return launch_batched_d<T, SILH_EUCLIDEAN>(D, variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+        case SILH_COSINE:
+            return launch_batched_d<T, SILH_COSINE>(D, variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+        case SILH_MANHATTAN:
+            return launch_batched_d<T, SILH_MANHATTAN>(D, variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+        default:
+            return launch_batched_d<T, SILH_CANBERRA>(D, variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
     }
 }
 
@@ -677,6 +848,94 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     }
     st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, Y, wY, zY, n, D,
                       rows, nrows, s, a, b, stream);
+done:
+    return st;
+}
+
+extern "C" silh_status silh_estimate_batched(const void *X, silh_dtype dtype, int64_t n,
+                                             int32_t d, int64_t ld, silh_metric metric,
+                                             silh_prec prec, int32_t nitems,
+                                             const silh_batch_item *items, int32_t variant,
+                                             void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    silh_status st = SILH_OK;
+    const int D = padded_dim(d);
+    Scratch sc(stream);
+    float *Y = nullptr, *wY = nullptr, *zY = nullptr;
+    unsigned long long *next_work = nullptr;
+    BatchParams *bp = nullptr;
+    std::vector<BatchParams> parts;
+    std::vector<int32_t> order;
+    SILH_REQ(X && items, "null pointer argument");
+    SILH_REQ(n >= 2 && n < (int64_t(1) << 31), "n must be in [2, 2^31)");
+    SILH_REQ(d >= 1 && d <= 128 && ld >= d, "need 1 <= d <= 128 and ld >= d");
+    SILH_REQ(metric >= SILH_EUCLIDEAN && metric <= SILH_CANBERRA, "unknown metric");
+    SILH_REQ(dtype == SILH_F32 || dtype == SILH_BF16, "unknown dtype");
+    SILH_REQ(prec >= SILH_PREC_FP32 && prec <= SILH_PREC_3XTF32, "unknown precision");
+    SILH_REQ(nitems >= 1, "need at least one item");
+    SILH_REQ(variant >= -1 && variant < kBatchVariants, "variant must be -1 .. %d",
+             kBatchVariants - 1);
+    // largest items first (longest row tiles), then kMaxBatch per launch as launch parameters
+    for (int32_t i = 0; i < nitems; ++i) {
+        SILH_REQ(items[i].sample, "item %d: null sample", i);
+        order.push_back(i);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return items[a].sample->size > items[b].sample->size;
+    });
+    for (int32_t c0 = 0; c0 < nitems; c0 += kMaxBatch) {
+        parts.emplace_back();
+        BatchParams &b = parts.back();
+        std::memset(&b, 0, sizeof(b));
+        b.nitems = std::min<int32_t>(kMaxBatch, nitems - c0);
+        int64_t tiles = 0, cols = 0;
+        const int64_t bm = kThreads * ((variant < 0 ? (D <= 32 ? 3 : 0) : variant) >= 2 ? 2 : 1);
+        for (int i = 0; i < b.nitems; ++i) {
+            const silh_batch_item &src = items[order[c0 + i]];
+            SILH_REQ(src.labels && src.s_hat && src.sample, "item %d: null pointer", c0 + i);
+            const silh_sample *S = src.sample;
+            SILH_REQ(S->k >= 2 && S->k <= SILH_MAX_K && S->sizes && S->offsets,
+                     "item %d: bad sample", c0 + i);
+            SILH_REQ(S->size >= 1 && S->size <= S->cap && S->idx && S->p, "item %d: empty sample",
+                     c0 + i);
+            BatchItem &it = b.items[i];
+            it.labels = src.labels;
+            it.sizes = S->sizes;
+            it.offsets = S->offsets;
+            it.idx = S->idx;
+            it.p = S->p;
+            it.s_out = src.s_hat;
+            it.k = S->k;
+            it.col_base = cols;
+            it.m = S->size;
+            it.tile_base = tiles;
+            cols += S->size;
+            tiles += (n + bm - 1) / bm;
+        }
+        b.total_tiles = tiles;
+        b.total_cols = cols;
+    }
+    SILH_CK(sc.alloc(&next_work, 1));
+    for (BatchParams &b : parts) {
+        SILH_CK(sc.alloc(&Y, (size_t)b.total_cols * D));
+        SILH_CK(sc.alloc(&wY, (size_t)b.total_cols));
+        SILH_CK(sc.alloc(&zY, (size_t)b.total_cols));
+        if (dtype == SILH_F32) {
+            k_gather_batched<float><<<ceil_div_i(b.total_cols, 8), 256, 0, stream>>>(
+                b, (const float *)X, d, ld, D, metric, Y, wY, zY);
+            count_launches(1);
+            SILH_CK(launch_batched_m<float>(metric, D, variant, b, stream, (const float *)X, d, ld,
+                                            n, Y, wY, zY, next_work));
+        } else {
+            k_gather_batched<__nv_bfloat16><<<ceil_div_i(b.total_cols, 8), 256, 0, stream>>>(
+                b, (const __nv_bfloat16 *)X, d, ld, D, metric, Y, wY, zY);
+            count_launches(1);
+            SILH_CK(launch_batched_m<__nv_bfloat16>(metric, D, variant, b, stream,
+                                                    (const __nv_bfloat16 *)X, d, ld, n, Y, wY,
+                                                    zY, next_work));
+        }
+    }
+    (void)bp;
 done:
     return st;
 }

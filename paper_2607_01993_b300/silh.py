@@ -26,7 +26,7 @@ SILH_ECAPACITY = -4
 # exported symbols, as declared in include/silh.h
 EXPORTS = ("silh_sample_pps", "silh_estimate", "silh_exact", "silh_global", "silh_t_from_eps",
            "silh_last_error", "silh_version", "silh_kernel_launches", "silh_estimate_noalloc",
-           "silh_stream_status")
+           "silh_stream_status", "silh_estimate_batched")
 SILH_NOALLOC_MAX_COLUMNS = 65536
 SILH_NOALLOC_MAX_FLOATS = 2097152
 
@@ -41,6 +41,11 @@ class SilhSample(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("sizes", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
                 ("idx", ctypes.c_void_p), ("p", ctypes.c_void_p), ("cap", ctypes.c_int64),
                 ("size", ctypes.c_int64)]
+
+
+class SilhBatchItem(ctypes.Structure):
+    _fields_ = [("labels", ctypes.c_void_p), ("sample", ctypes.POINTER(SilhSample)),
+                ("s_hat", ctypes.c_void_p)]
 
 
 _lib = None
@@ -75,6 +80,10 @@ def load(path: str = LIB_PATH):
     lib.silh_last_error.restype = ctypes.c_char_p
     lib.silh_version.argtypes = []
     lib.silh_version.restype = ctypes.c_char_p
+    lib.silh_estimate_batched.argtypes = [vp, ctypes.c_int, i64, i32, i64, ctypes.c_int,
+                                          ctypes.c_int, i32, ctypes.POINTER(SilhBatchItem), i32,
+                                          vp]
+    lib.silh_estimate_batched.restype = ctypes.c_int
     lib.silh_stream_status.argtypes = [vp]
     lib.silh_stream_status.restype = ctypes.c_int
     lib.silh_kernel_launches.argtypes = []
@@ -205,6 +214,31 @@ def silh_estimate_noalloc(X, labels, k, sample: Sample, metric="euclidean", prec
                                      PRECS[prec], ctypes.byref(st), _ptr(rows), nr, _ptr(s),
                                      _ptr(a), _ptr(b), _stream(stream)))
     return (s, a, b) if want_ab else s
+
+
+BATCH_VARIANTS = 4   # tile shapes of the batched sweep (see include/silh.h)
+
+
+def silh_estimate_batched(X, items, metric="euclidean", variant=-1, outs=None, stream=None):
+    """Phase 2 for many clusterings of X in one persistent launch.
+
+    items: list of (labels, sample) pairs (int32 CUDA labels, Sample from
+    silh_sample_pps on those labels).  Returns one FP32 s_hat tensor per item.
+    Asynchronous and graph-capturable when outs are preallocated.
+    """
+    lib = load()
+    dt, n, d, ld = _data(X)
+    if outs is None:
+        outs = [torch.empty(n, dtype=torch.float32, device=X.device) for _ in items]
+    structs = [smp.as_struct() for _, smp in items]
+    arr = (SilhBatchItem * len(items))()
+    for i, ((labels, _), st, out) in enumerate(zip(items, structs, outs)):
+        arr[i].labels = _labels(labels).data_ptr()
+        arr[i].sample = ctypes.pointer(st)
+        arr[i].s_hat = out.data_ptr()
+    _check(lib.silh_estimate_batched(_ptr(X), dt, n, d, ld, METRICS[metric], PRECS["fp32"],
+                                     len(items), arr, int(variant), _stream(stream)))
+    return outs
 
 
 def silh_exact(X, labels, k, metric="euclidean", prec="fp32", rows=None, want_ab=False,

@@ -96,6 +96,23 @@ def nearest_centre_labels(X: np.ndarray, k: int, *, seed: int):
     return lab
 
 
+def nearest_centre_labels_device(Xt, k: int, *, seed: int, chunk: int = 1 << 18):
+    """As nearest_centre_labels, on the device tensor Xt (torch), for large n."""
+    import torch
+    rng = np.random.default_rng(seed)
+    n = Xt.shape[0]
+    cidx = rng.choice(n, size=k, replace=False)
+    C = Xt[torch.from_numpy(cidx).to(Xt.device)].double()
+    lab = torch.empty(n, dtype=torch.int32, device=Xt.device)
+    cn = (C * C).sum(1)
+    for s0 in range(0, n, chunk):
+        xb = Xt[s0:s0 + chunk].double()
+        dist = (xb * xb).sum(1, keepdim=True) - 2.0 * xb @ C.T + cn[None, :]
+        lab[s0:s0 + chunk] = dist.argmin(1).to(torch.int32)
+    lab[torch.from_numpy(cidx).to(Xt.device)] = torch.arange(k, dtype=torch.int32, device=Xt.device)
+    return lab
+
+
 # ----------------------------------------------------------------- workloads
 
 def tiny(seed: int = 0):
@@ -113,6 +130,13 @@ def precision(seed: int = 2, n: int = 4_000_000, d: int = 64, k: int = 64):
     """n=4M, d=64, k=64 Zipf sizes, 10% of points on cluster borders."""
     return gaussian_mixture(n, d, k, seed=seed, sizes=zipf_sizes(n, k, 1.1),
                             sigma_range=(0.5, 3.0), border_frac=0.10)
+
+
+def batching(seed: int = 3, n: int = 500_000, d: int = 16):
+    """n=500k, d=16 data from a 16-component mixture; clusterings are made by
+    nearest_centre_labels(_device) with k = 2..257 random data rows as centres."""
+    X, _, _ = gaussian_mixture(n, d, 16, seed=seed, sigma_range=(0.5, 3.0))
+    return X
 
 
 def seeded_rows(n: int, m: int, *, seed: int) -> np.ndarray:

@@ -1,0 +1,112 @@
+"""Batched Phase 2: many clusterings of one dataset in one persistent launch.
+
+Each item's result must equal the single-clustering sweep (same arithmetic),
+match the oracle on sampled rows within the FP32 bound, survive CUDA-graph
+capture and replay, and agree across the autotuner's tile variants.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2607_01993_b300 import autotune, silh, synth
+
+pytestmark = pytest.mark.gpu
+S_TOL = 1e-5
+
+
+def _dataset(n, d, seed, ks):
+    X, _, _ = synth.gaussian_mixture(n, d, 16, seed=seed, sigma=1.5)
+    labels = [synth.nearest_centre_labels(X, k, seed=seed + 10 * k) for k in ks]
+    return X, labels
+
+
+@pytest.fixture(scope="module")
+def batch():
+    ks = [2, 3, 5, 9, 17, 33]
+    X, labels = _dataset(30000, 16, 40, ks)
+    Xt = torch.from_numpy(X).cuda()
+    items = []
+    for c, (k, lab) in enumerate(zip(ks, labels)):
+        lt = torch.from_numpy(lab).cuda()
+        smp = silh.silh_sample_pps(Xt, lt, k, "euclidean", t=64.0, seed=5, clustering_id=c)
+        items.append((lt, smp))
+    return X, Xt, ks, labels, items
+
+
+def test_batched_equals_single_sweeps(batch):
+    X, Xt, ks, labels, items = batch
+    outs = silh.silh_estimate_batched(Xt, items, "euclidean")
+    for (lt, smp), k, out in zip(items, ks, outs):
+        ref = silh.silh_estimate(Xt, lt, k, smp, "euclidean", prec="fp32")
+        assert torch.equal(out, ref)
+
+
+def test_batched_matches_oracle_on_sampled_rows(batch):
+    X, Xt, ks, labels, items = batch
+    outs = silh.silh_estimate_batched(Xt, items, "euclidean")
+    Xh = X.astype(np.float64)
+    rows = synth.seeded_rows(X.shape[0], 150, seed=3)
+    for c in (0, 4, 5):
+        os_ = oracle.sample_pps(Xh, labels[c], ks[c], "euclidean", t=64.0, seed=5, cid=c)
+        s_o, _, _ = oracle.estimate(Xh, labels[c], ks[c], "euclidean", os_.offsets, os_.idx,
+                                    os_.ps, rows=rows)
+        got = outs[c][torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+        assert np.abs(got - s_o).max() <= S_TOL
+
+
+@pytest.mark.parametrize("variant", range(silh.BATCH_VARIANTS))
+def test_variants_agree(batch, variant):
+    X, Xt, ks, labels, items = batch
+    ref = silh.silh_estimate_batched(Xt, items, "euclidean", variant=-1)
+    got = silh.silh_estimate_batched(Xt, items, "euclidean", variant=variant)
+    for a, b in zip(got, ref):
+        assert (a - b).abs().max().item() <= 1e-6
+
+
+def test_graph_capture_and_replay(batch):
+    X, Xt, ks, labels, items = batch
+    outs = [torch.empty(X.shape[0], dtype=torch.float32, device="cuda") for _ in items]
+    silh.silh_estimate_batched(Xt, items, "euclidean", outs=outs)      # warm-up off-graph
+    torch.cuda.synchronize()
+    ref = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(7.0)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        silh.silh_estimate_batched(Xt, items, "euclidean", outs=outs)
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(outs, ref):
+        assert torch.equal(a, b)
+    for o in outs:
+        o.fill_(7.0)
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(outs, ref):
+        assert torch.equal(a, b)
+
+
+def test_autotuner_picks_a_variant(batch, tmp_path, monkeypatch):
+    X, Xt, ks, labels, items = batch
+    monkeypatch.setenv("SILH_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    v, times = autotune.tune_batched(Xt, items[:3], "euclidean", reps=1)
+    assert 0 <= v < silh.BATCH_VARIANTS and len(times) == silh.BATCH_VARIANTS
+    v2, _ = autotune.tune_batched(Xt, items[:3], "euclidean")        # cached
+    assert v2 == v
+
+
+@pytest.mark.parametrize("metric", ["cosine", "manhattan", "canberra"])
+def test_batched_other_metrics(metric):
+    X, labels = _dataset(8000, 13, 41, [3, 7])
+    if metric == "canberra":
+        X = synth.abs_shift(X)
+    Xt = torch.from_numpy(X).cuda()
+    items = []
+    for c, (k, lab) in enumerate(zip([3, 7], labels)):
+        lt = torch.from_numpy(lab).cuda()
+        items.append((lt, silh.silh_sample_pps(Xt, lt, k, metric, t=32.0, m0=8.0, seed=c)))
+    outs = silh.silh_estimate_batched(Xt, items, metric)
+    for (lt, smp), k, out in zip(items, [3, 7], outs):
+        ref = silh.silh_estimate(Xt, lt, k, smp, metric, prec="fp32")
+        assert torch.equal(out, ref)

@@ -84,3 +84,29 @@ def test_precision_workload_bf16_sampled_parity():
                                     rows=rows)
         _assert_close(s, s_o)
     assert S_TOL == 1e-5
+
+
+def test_batching_workload_sampled_parity():
+    """n = 500k, d = 16; clusterings with k in {2, 3, 17, 64, 257} (nearest random
+    data-row centres) of the 256-clustering batching workload, t = 128, in one
+    batched launch; each checked against the oracle on 100 seeded rows."""
+    X = synth.batching(seed=3)
+    Xt = torch.from_numpy(X).cuda()
+    ks = [2, 3, 17, 64, 257]
+    items, labs = [], []
+    for k in ks:
+        lt = synth.nearest_centre_labels_device(Xt, k, seed=1000 + k)
+        labs.append(lt.cpu().numpy())
+        items.append((lt, silh.silh_sample_pps(Xt, lt, k, "euclidean", t=128.0, seed=7,
+                                               clustering_id=k - 2)))
+    outs = silh.silh_estimate_batched(Xt, items, "euclidean")
+    Xh = X.astype(np.float64)
+    rows = synth.seeded_rows(X.shape[0], 100, seed=21)
+    for k, lab, (lt, smp), out in zip(ks, labs, items, outs):
+        sizes = np.bincount(lab, minlength=k)
+        assert sizes.min() >= 1
+        os_ = oracle.sample_pps(Xh, lab, k, "euclidean", t=128.0, seed=7, cid=k - 2)
+        assert_same_sample(smp, os_, k, 7, k - 2)
+        s_o, _, _ = oracle.estimate(Xh, lab, k, "euclidean", os_.offsets, os_.idx, os_.ps,
+                                    rows=rows)
+        _assert_close(out[torch.from_numpy(rows).cuda()], s_o)
