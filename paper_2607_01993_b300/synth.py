@@ -113,6 +113,37 @@ def nearest_centre_labels_device(Xt, k: int, *, seed: int, chunk: int = 1 << 18)
     return lab
 
 
+def gaussian_mixture_device(n: int, d: int, k: int, *, seed: int, device="cuda",
+                            sigma_range=(0.5, 3.0), box: float = 10.0):
+    """A Gaussian mixture drawn on the device from a seeded torch generator
+    (for the many large resident datasets of the serving workload)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    centres = (torch.rand(k, d, generator=g, device=device) * 2 - 1) * box
+    sig = torch.rand(k, generator=g, device=device) * (sigma_range[1] - sigma_range[0]) + sigma_range[0]
+    comp = torch.randint(0, k, (n,), generator=g, device=device)
+    X = centres[comp] + sig[comp, None] * torch.randn(n, d, generator=g, device=device)
+    return X.float().contiguous()
+
+
+def serving(seed: int = 4, ndatasets: int = 64, device="cuda"):
+    """64 resident datasets: n log-uniform in [5k, 2M], d in {8, 16, 64, 128},
+    stored FP32 or BF16; returns (list of tensors, list of (n, d, dtype))."""
+    import torch
+    rng = np.random.default_rng(seed)
+    out, spec = [], []
+    for i in range(ndatasets):
+        n = int(round(np.exp(rng.uniform(np.log(5e3), np.log(2e6)))))
+        d = int(rng.choice([8, 16, 64, 128]))
+        dt = torch.bfloat16 if rng.random() < 0.5 else torch.float32
+        X = gaussian_mixture_device(n, d, int(rng.integers(4, 33)), seed=seed * 1000 + i,
+                                    device=device).to(dt)
+        out.append(X)
+        spec.append((n, d, str(dt).replace("torch.", "")))
+    return out, spec
+
+
 # ----------------------------------------------------------------- workloads
 
 def tiny(seed: int = 0):
