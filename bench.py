@@ -154,6 +154,25 @@ def cpu_oracle_sample(X, lab, rows_exact, k, t, delta, budget_s=20.0):
     return total, desc
 
 
+# --------------------------------------------------------- multi-process
+
+def reduce_max_over_ranks(values, device=None):
+    """Max over ranks of each value (all_reduce MAX); the values unchanged when
+    the process group is not initialised or has one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def replica_throughput(points_per_rank, world, max_ms):
+    """Whole-job throughput of independent replicas: every rank's points over the
+    slowest rank's time (weak scaling)."""
+    return points_per_rank * world / (max_ms * 1e-3)
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def run_gpu(args, rank, world, local_rank):
@@ -253,10 +272,7 @@ def run_gpu(args, rank, world, local_rank):
     d2h = sum(o[0].numel() * 4 + 16 for o in host_out)
     del host_out
 
-    times = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    ms_max, e2e_max = float(times[0]), float(times[1])
+    ms_max, e2e_max = reduce_max_over_ranks([ms, e2e_s], device=dev)
     return dict(ms=ms_max, e2e_s=e2e_max, step_ms=step_ms, legs=leg_ms, info=info,
                 launches=int(launches), clocks=clk.summary(), h2d=h2d, d2h=d2h, n=n, d=d, k=k,
                 sizes=sizes, rows_ex=len(rows_ex), X=X, lab=lab, rows=rows_ex)
@@ -529,7 +545,7 @@ def main():
             dist.destroy_process_group()
         return
     pts = len(METRICS) * res["n"] * world
-    value = pts / (res["ms"] * 1e-3)
+    value = replica_throughput(len(METRICS) * res["n"], world, res["ms"])
     evals = dist_evals(res, None) * world
     dom, roof = roofline(res, peaks, peak_kind)
     legs = {m: {leg: round(float(np.mean(v)), 3) for leg, v in res["legs"][m].items()}
