@@ -81,6 +81,8 @@ def _load():
                                      ctypes.c_int, _i64p, _i64p, _f64p, _i64p, ctypes.c_int64,
                                      _f64p, _f64p, _f64p, _f64p]
         lib.orc_estimate.restype = ctypes.c_int
+        lib.orc_cohsep.argtypes = [_f64p, _i32p, ctypes.c_int64, ctypes.c_int, _f64p, _f64p]
+        lib.orc_cohsep.restype = ctypes.c_int
         lib.orc_mean.argtypes = [_f64p, ctypes.c_int64]
         lib.orc_mean.restype = ctypes.c_double
         lib.orc_t_from_eps.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int64,
@@ -244,6 +246,18 @@ def estimate(X, labels, k, metric, offsets, idx, ps, rows=None, want_w=False):
     if rc != 0:
         raise ValueError("invalid arguments")
     return (s, a, b, W) if want_w else (s, a, b)
+
+
+def cohsep(W, labels, k):
+    """Cohesion and separation from per-element cluster weights W (n x k)."""
+    W = _f64(W)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    coh = np.zeros(1); sep = np.zeros(1)
+    rc = _load().orc_cohsep(_p(W, _f64p), _p(labels, _i32p), labels.shape[0], k,
+                            _p(coh, _f64p), _p(sep, _f64p))
+    if rc != 0:
+        raise ValueError("invalid clustering")
+    return float(coh[0]), float(sep[0])
 
 
 def mean(v) -> float:

@@ -366,6 +366,34 @@ int orc_estimate(const double *X, int64_t n, int d, const int32_t *labels, int k
     return 0;
 }
 
+/* --------------------------------------------------- cohesion, separation */
+
+/* Cohesion and separation of the clustering (Sec. "Estimating other clustering
+ * validation measures") from the per-element cluster weights W (n x k; the
+ * exact W of Eq. 4 or the estimates W_hat):
+ *   Coh = (1/2) sum_j sum_{e in Cj} W_Cj(e) / sum_j C(|Cj|, 2)
+ *   Sep = sum_{j1 < j2} sum_{e in Cj1} W_Cj2(e) / sum_{j1 < j2} |Cj1| |Cj2|
+ * (the printed |C_{j-1}| in Sep's denominator is read as |C_{j1}|). */
+int orc_cohsep(const double *W, const int32_t *labels, int64_t n, int k, double *coh, double *sep)
+{
+    int64_t *sizes = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    if (orc_cluster_sizes(labels, n, k, sizes) != 0) { free(sizes); return -1; }
+    double num_c = 0.0, num_s = 0.0, den_c = 0.0, den_s = 0.0;
+    for (int64_t e = 0; e < n; ++e) {
+        int c = labels[e];
+        num_c = num_c + W[e * k + c];
+        for (int j = c + 1; j < k; ++j) num_s = num_s + W[e * k + j];
+    }
+    for (int j = 0; j < k; ++j) {
+        den_c = den_c + 0.5 * (double)sizes[j] * (double)(sizes[j] - 1);
+        for (int j2 = j + 1; j2 < k; ++j2) den_s = den_s + (double)sizes[j] * (double)sizes[j2];
+    }
+    *coh = den_c > 0.0 ? 0.5 * num_c / den_c : 0.0;
+    *sep = den_s > 0.0 ? num_s / den_s : 0.0;
+    free(sizes);
+    return 0;
+}
+
 /* ------------------------------------------------------------- global */
 
 /* Mean of n values (Eq. 3 / Eq. 6), Neumaier-compensated sum. */

@@ -339,3 +339,61 @@ def test_global_mean_is_exact_mean():
 def test_t_from_eps_lemma1():
     # Lemma 1: t = ceil((3c/eps^2) ln(5nk/delta)) with c = 18.
     assert oracle.t_from_eps(0.5, 0.01, 1000, 4) == math.ceil(216 * math.log(5 * 4000 / 0.01))
+
+
+# ------------------------------------------------- cohesion and separation
+
+@pytest.mark.parametrize("metric", ["euclidean", "cosine", "manhattan", "canberra"])
+def test_cohesion_separation_are_mean_pair_distances(metric):
+    # Coh is the mean distance over unordered same-cluster pairs, Sep the mean
+    # over unordered cross-cluster pairs; scipy's pdist gives both by brute
+    # force.  Exact W (all p = 1) must reproduce them through the estimator.
+    from scipy.spatial.distance import pdist
+    X, lab = _blobs(160, 5, 4, seed=21, sigma=2.0, shift=(metric == "canberra"))
+    k = 4
+    iu = np.triu_indices(X.shape[0], 1)
+    dv = pdist(X, SCIPY[metric])
+    same = lab[iu[0]] == lab[iu[1]]
+    coh_ref, sep_ref = dv[same].mean(), dv[~same].mean()
+    W, _ = _cluster_weights(X, lab, k, metric)
+    coh, sep = oracle.cohsep(W, lab, k)
+    assert coh == pytest.approx(coh_ref, rel=1e-12)
+    assert sep == pytest.approx(sep_ref, rel=1e-12)
+    smp = oracle.sample_pps(X, lab, k, metric, t=1e9, seed=1)
+    _, _, _, Wh = oracle.estimate(X, lab, k, metric, smp.offsets, smp.idx, smp.ps, want_w=True)
+    coh2, sep2 = oracle.cohsep(Wh, lab, k)
+    assert coh2 == pytest.approx(coh_ref, rel=1e-12)
+    assert sep2 == pytest.approx(sep_ref, rel=1e-12)
+
+
+def test_cohesion_separation_two_clusters_and_singletons():
+    # k = 2: Sep = sum_{e in C0} W_C1(e) / (|C0| |C1|).  Singleton clusters add
+    # no same-cluster pairs; all-singleton clusterings have Coh = 0.
+    X, lab = _blobs(50, 3, 2, seed=22)
+    W, D = _cluster_weights(X, lab, 2, "euclidean")
+    _, sep = oracle.cohsep(W, lab, 2)
+    c0, c1 = lab == 0, lab == 1
+    assert sep == pytest.approx(D[np.ix_(c0, c1)].sum() / (c0.sum() * c1.sum()), rel=1e-12)
+    lab1 = np.arange(6, dtype=np.int32)
+    W1, D1 = _cluster_weights(X[:6], lab1, 6, "euclidean")
+    coh, sep = oracle.cohsep(W1, lab1, 6)
+    assert coh == 0.0
+    assert sep == pytest.approx(D1[np.triu_indices(6, 1)].mean(), rel=1e-12)
+
+
+def test_cohesion_separation_error_bounded_by_weight_error():
+    # Both numerators are positive combinations of the W_hat_j(e), so if every
+    # W_hat_j(e) is within relative eps of W_j(e) the estimates are within eps
+    # of Coh and Sep (the argument behind the appendix's theorem).
+    X, lab = _blobs(900, 4, 5, seed=23, sigma=2.0)
+    k = 5
+    W, _ = _cluster_weights(X, lab, k, "euclidean")
+    coh, sep = oracle.cohsep(W, lab, k)
+    for seed in range(3):
+        smp = oracle.sample_pps(X, lab, k, "euclidean", t=40.0, seed=seed)
+        _, _, _, Wh = oracle.estimate(X, lab, k, "euclidean", smp.offsets, smp.idx, smp.ps,
+                                      want_w=True)
+        eps = np.max(np.abs(Wh - W) / W)
+        ch, sh = oracle.cohsep(Wh, lab, k)
+        assert abs(ch - coh) <= eps * coh * (1 + 1e-12)
+        assert abs(sh - sep) <= eps * sep * (1 + 1e-12)
