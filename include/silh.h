@@ -180,6 +180,18 @@ silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, int32_t d, in
                        const int64_t *rows, int64_t nrows, float *s, float *a, float *b,
                        void *stream);
 
+/* Cohesion and separation of the clustering estimated from the Phase-2 weights
+ * (the paper's section on other clustering validation measures):
+ *   Coh = (1/2) sum_j sum_{e in Cj} W_hat_Cj(e) / sum_j C(|Cj|, 2)
+ *   Sep = sum_{j1<j2} sum_{e in Cj1} W_hat_Cj2(e) / sum_{j1<j2} |Cj1||Cj2|
+ * (the printed |C_{j-1}| in Sep's denominator is read as |C_{j1}|).  With
+ * every p = 1 (t >= max |Cj|) these are the exact values.  out: two doubles in
+ * device memory, (Coh, Sep).  FP32 CUDA-core distances, FP64 sums.
+ * Asynchronous.  Errors: as silh_estimate. */
+silh_status silh_cohsep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                        const int32_t *labels, int32_t k, silh_metric metric, const silh_sample *S,
+                        double *out, void *stream);
+
 /* Mean of n FP32 values in FP64 with a fixed reduction tree (Eq. 3 for exact
  * s, Eq. 6 for s_hat, Eq. 7 for a row subset).  out: one double, device memory.
  * Asynchronous.  Errors: SILH_EINVAL if n < 1 or a pointer is NULL. */

@@ -144,7 +144,8 @@ __device__ __forceinline__ void sweep_rows(
         const int64_t *__restrict__ offsets, const float *__restrict__ Y,
         const float *__restrict__ wY, const float *__restrict__ zY,
         const int64_t *__restrict__ rows, int64_t nrows, float *__restrict__ s_out,
-        float *__restrict__ a_out, float *__restrict__ b_out) {
+        float *__restrict__ a_out, float *__restrict__ b_out,
+        double *__restrict__ wown_out = nullptr, double *__restrict__ wsep_out = nullptr) {
     __shared__ __align__(16) float sh_y[BN * D];
     __shared__ __align__(16) float sh_ya[METRIC == SILH_CANBERRA ? BN * D : 4];
     __shared__ float sh_w[BN];
@@ -153,6 +154,7 @@ __device__ __forceinline__ void sweep_rows(
     float zx[RPT];   // cosine: 0.5 for a zero row (distance 1 to everything)
     int own[RPT];
     double wown[RPT], bmin[RPT];
+    double wsep[RPT];   // sum of W_hat_j over clusters j > own (separation numerator)
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         int64_t rr = r0 + threadIdx.x + r * kThreads;
@@ -177,6 +179,7 @@ __device__ __forceinline__ void sweep_rows(
         }
         wown[r] = 0.0;
         bmin[r] = INFINITY;
+        wsep[r] = 0.0;
     }
     for (int j = 0; j < k; ++j) {
         int64_t cs = offsets[j], ce = offsets[j + 1];
@@ -228,6 +231,7 @@ __device__ __forceinline__ void sweep_rows(
         for (int r = 0; r < RPT; ++r) {
             if (j == own[r]) wown[r] = accd[r];
             else bmin[r] = fmin(bmin[r], accd[r] / csz);
+            if (j > own[r]) wsep[r] += accd[r];
         }
     }
 #pragma unroll
@@ -245,9 +249,59 @@ __device__ __forceinline__ void sweep_rows(
             double s = (nc > 1 && mx > 0.0) ? (b - a) / mx : 0.0;
             sv = (float)s; av = (float)a; bv = (float)b;
         }
-        s_out[rr] = sv;
+        if (s_out) s_out[rr] = sv;
         if (a_out) a_out[rr] = av;
         if (b_out) b_out[rr] = bv;
+        if (wown_out) wown_out[rr] = (own[r] >= 0) ? wown[r] : 0.0;
+        if (wsep_out) wsep_out[rr] = (own[r] >= 0) ? wsep[r] : 0.0;
+    }
+}
+
+// Per-row own-cluster and separation sums for Coh/Sep (all rows, in order).
+template <class T, int METRIC, int D, int RPT, int BN>
+__global__ void __launch_bounds__(kThreads)
+k_sweep_cohsep(const T *__restrict__ X, int d, int64_t ld, int64_t n,
+               const int32_t *__restrict__ labels, int k, const int64_t *__restrict__ sizes,
+               const int64_t *__restrict__ offsets, const float *__restrict__ Y,
+               const float *__restrict__ wY, const float *__restrict__ zY,
+               double *__restrict__ wown, double *__restrict__ wsep) {
+    sweep_rows<T, METRIC, D, RPT, BN>((int64_t)blockIdx.x * kThreads * RPT, X, d, ld, n, labels, k,
+                                      sizes, offsets, Y, wY, zY, nullptr, n, nullptr, nullptr,
+                                      nullptr, wown, wsep);
+}
+
+// Coh = (1/2) sum wown / sum_j C(|Cj|,2), Sep = sum wsep / sum_{j1<j2} |Cj1||Cj2|
+// (single block, fixed reduction order).
+__global__ void k_cohsep_final(const double *__restrict__ wown, const double *__restrict__ wsep,
+                               int64_t n, const int64_t *__restrict__ sizes, int k,
+                               double *__restrict__ out) {
+    __shared__ double sh[3][256];
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 256) {
+        a += wown[i];
+        b += wsep[i];
+    }
+    for (int j = threadIdx.x; j < k; j += 256) c += (double)sizes[j];
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    sh[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off)
+            for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double pairs_in = 0.0, sq = 0.0;
+        for (int j = 0; j < k; ++j) {
+            const double s = (double)sizes[j];
+            pairs_in += 0.5 * s * (s - 1.0);
+            sq += s * s;
+        }
+        const double tot = sh[2][0];
+        const double pairs_out = 0.5 * (tot * tot - sq);          // sum_{j1<j2} |Cj1||Cj2|
+        out[0] = pairs_in > 0.0 ? 0.5 * sh[0][0] / pairs_in : 0.0;
+        out[1] = pairs_out > 0.0 ? sh[1][0] / pairs_out : 0.0;
     }
 }
 
@@ -260,6 +314,21 @@ k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__
         float *__restrict__ a_out, float *__restrict__ b_out) {
     sweep_rows<T, METRIC, D, RPT, BN>((int64_t)blockIdx.x * kThreads * RPT, X, d, ld, n, labels, k,
                                       sizes, offsets, Y, wY, zY, rows, nrows, s_out, a_out, b_out);
+}
+
+template <class T, int METRIC>
+void launch_cohsep_d(int D, cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
+                     const int32_t *labels, int k, const int64_t *sizes, const int64_t *offsets,
+                     const float *Y, const float *wY, const float *zY, double *wown, double *wsep) {
+    const int grid1 = (int)((n + kThreads - 1) / kThreads), grid2 = (int)((n + 2 * kThreads - 1) / (2 * kThreads));
+    switch (D) {
+        case 8: k_sweep_cohsep<T, METRIC, 8, 2, 64><<<grid2, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, wown, wsep); break;
+        case 16: k_sweep_cohsep<T, METRIC, 16, 2, 64><<<grid2, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, wown, wsep); break;
+        case 32: k_sweep_cohsep<T, METRIC, 32, 2, 64><<<grid2, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, wown, wsep); break;
+        case 64: k_sweep_cohsep<T, METRIC, 64, 1, 32><<<grid1, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, wown, wsep); break;
+        default: k_sweep_cohsep<T, METRIC, 128, 1, 32><<<grid1, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, wown, wsep); break;
+    }
+    count_launches(1);
 }
 
 // ------------------------------------------------------------ batched
@@ -936,6 +1005,50 @@ extern "C" silh_status silh_estimate_batched(const void *X, silh_dtype dtype, in
         }
     }
     (void)bp;
+done:
+    return st;
+}
+
+extern "C" silh_status silh_cohsep(const void *X, silh_dtype dtype, int64_t n, int32_t d,
+                                   int64_t ld, const int32_t *labels, int32_t k, silh_metric metric,
+                                   const silh_sample *S, double *out, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    silh_status st = check_data_args(X, dtype, n, d, ld, labels, k, metric, SILH_PREC_FP32);
+    if (st != SILH_OK) return st;
+    const int D = padded_dim(d);
+    Scratch sc(stream);
+    float *Y = nullptr, *wY = nullptr, *zY = nullptr;
+    double *wown = nullptr, *wsep = nullptr;
+    int64_t m = 0;
+    SILH_REQ(S && S->k == k && S->sizes && S->offsets && out, "sample or output missing");
+    m = S->size;
+    SILH_REQ(m >= 0 && m <= S->cap && (m == 0 || (S->idx && S->p)), "bad sample size");
+    SILH_CK(sc.alloc(&Y, (size_t)m * D));
+    SILH_CK(sc.alloc(&wY, (size_t)m));
+    SILH_CK(sc.alloc(&zY, (size_t)m));
+    SILH_CK(sc.alloc(&wown, (size_t)n));
+    SILH_CK(sc.alloc(&wsep, (size_t)n));
+    st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, Y, wY, zY, stream);
+    if (st != SILH_OK) goto done;
+    if (dtype == SILH_F32) {
+        switch (metric) {
+            case SILH_EUCLIDEAN: launch_cohsep_d<float, SILH_EUCLIDEAN>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
+            case SILH_COSINE: launch_cohsep_d<float, SILH_COSINE>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
+            case SILH_MANHATTAN: launch_cohsep_d<float, SILH_MANHATTAN>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
+            default: launch_cohsep_d<float, SILH_CANBERRA>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
+        }
+    } else {
+        const __nv_bfloat16 *Xb = (const __nv_bfloat16 *)X;
+        switch (metric) {
+            case SILH_EUCLIDEAN: launch_cohsep_d<__nv_bfloat16, SILH_EUCLIDEAN>(D, stream, Xb, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
+            case SILH_COSINE: launch_cohsep_d<__nv_bfloat16, SILH_COSINE>(D, stream, Xb, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
+            case SILH_MANHATTAN: launch_cohsep_d<__nv_bfloat16, SILH_MANHATTAN>(D, stream, Xb, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
+            default: launch_cohsep_d<__nv_bfloat16, SILH_CANBERRA>(D, stream, Xb, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
+        }
+    }
+    k_cohsep_final<<<1, 256, 0, stream>>>(wown, wsep, n, S->sizes, k, out);
+    count_launches(1);
+    SILH_CK(cudaGetLastError());
 done:
     return st;
 }

@@ -26,7 +26,7 @@ SILH_ECAPACITY = -4
 # exported symbols, as declared in include/silh.h
 EXPORTS = ("silh_sample_pps", "silh_estimate", "silh_exact", "silh_global", "silh_t_from_eps",
            "silh_last_error", "silh_version", "silh_kernel_launches", "silh_estimate_noalloc",
-           "silh_stream_status", "silh_estimate_batched")
+           "silh_stream_status", "silh_estimate_batched", "silh_cohsep")
 SILH_NOALLOC_MAX_COLUMNS = 65536
 SILH_NOALLOC_MAX_FLOATS = 2097152
 
@@ -84,6 +84,9 @@ def load(path: str = LIB_PATH):
                                           ctypes.c_int, i32, ctypes.POINTER(SilhBatchItem), i32,
                                           vp]
     lib.silh_estimate_batched.restype = ctypes.c_int
+    lib.silh_cohsep.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32, ctypes.c_int,
+                                ctypes.POINTER(SilhSample), vp, vp]
+    lib.silh_cohsep.restype = ctypes.c_int
     lib.silh_stream_status.argtypes = [vp]
     lib.silh_stream_status.restype = ctypes.c_int
     lib.silh_kernel_launches.argtypes = []
@@ -255,6 +258,18 @@ def silh_exact(X, labels, k, metric="euclidean", prec="fp32", rows=None, want_ab
     _check(lib.silh_exact(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric], PRECS[prec],
                           _ptr(rows), nr, _ptr(s), _ptr(a), _ptr(b), _stream(stream)))
     return (s, a, b) if want_ab else s
+
+
+def silh_cohsep(X, labels, k, sample: Sample, metric="euclidean", stream=None):
+    """Estimated cohesion and separation; returns a 2-element float64 CUDA tensor."""
+    lib = load()
+    dt, n, d, ld = _data(X)
+    labels = _labels(labels)
+    out = torch.empty(2, dtype=torch.float64, device=X.device)
+    st = sample.as_struct()
+    _check(lib.silh_cohsep(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric],
+                           ctypes.byref(st), _ptr(out), _stream(stream)))
+    return out
 
 
 def silh_global(s, out=None, stream=None):

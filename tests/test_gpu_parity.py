@@ -325,3 +325,43 @@ def test_tensor_core_rows_degenerate_and_bf16(metric):
                                  rows=r2.cpu().numpy())
     _assert_close(s2, s2_o)
     silh.silh_stream_status()
+
+
+# ------------------------------------------------- cohesion and separation
+
+COHSEP_TOL = 1e-5     # relative: FP32 distances (<= a few ulp each), FP64 sums
+
+
+@pytest.mark.parametrize("case", ["tiny", "ragged", "multitile"])
+@pytest.mark.parametrize("metric", METRICS)
+def test_cohsep_matches_oracle_on_oracle_sample(case, metric):
+    X, lab, k, kw = _case(case)
+    if metric == "canberra":
+        X = synth.abs_shift(X)
+    Xt, lt = _to_dev(X, lab)
+    Xh = _host_values(Xt)
+    os_ = oracle.sample_pps(Xh, lab, k, metric, t=kw["t"], m0=kw["m0"], seed=kw["seed"])
+    smp = silh.Sample.from_lists(np.bincount(lab, minlength=k), os_.offsets, os_.idx, os_.ps,
+                                 Xt.device)
+    out = silh.silh_cohsep(Xt, lt, k, smp, metric).cpu().numpy()
+    _, _, _, Wh = oracle.estimate(Xh, lab, k, metric, os_.offsets, os_.idx, os_.ps, want_w=True)
+    coh, sep = oracle.cohsep(Wh, lab, k)
+    assert out[0] == pytest.approx(coh, rel=COHSEP_TOL)
+    assert out[1] == pytest.approx(sep, rel=COHSEP_TOL)
+
+
+def test_cohsep_all_sampled_is_exact_and_bf16():
+    """t above every cluster size: the estimate is the exact Coh/Sep; BF16 storage."""
+    X, lab, k, _ = _case("ragged")
+    for dtype in (torch.float32, torch.bfloat16):
+        Xt, lt = _to_dev(X, lab, dtype)
+        Xh = _host_values(Xt)
+        gs = silh.silh_sample_pps(Xt, lt, k, "manhattan", t=1e9, seed=1)
+        assert gs.size == X.shape[0]
+        out = silh.silh_cohsep(Xt, lt, k, gs, "manhattan").cpu().numpy()
+        os_ = oracle.sample_pps(Xh, lab, k, "manhattan", t=1e9, seed=1)
+        _, _, _, W = oracle.estimate(Xh, lab, k, "manhattan", os_.offsets, os_.idx, os_.ps,
+                                     want_w=True)
+        coh, sep = oracle.cohsep(W, lab, k)
+        assert out[0] == pytest.approx(coh, rel=COHSEP_TOL)
+        assert out[1] == pytest.approx(sep, rel=COHSEP_TOL)
