@@ -72,7 +72,8 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return r;
 }
 
-// Distance of one row (registers) to one column (shared memory, float4).
+// Distance of one row (registers, coordinate pairs) to one column (shared
+// memory, float4 of NEGATED coordinates, so x - y is one packed add).
 // Euclidean: sqrt(sum (x - y)^2).  Manhattan: sum |x - y|.  Cosine: rows and
 // columns are unit-normalised and 1 - <x,y> is evaluated as 0.5 |x - y|^2
 // (equal for unit vectors, and free of the cancellation of 1 - <x,y> for
@@ -80,56 +81,73 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // time as (n1 d2 + n2 d1)/(d1 d2) so that one reciprocal serves two
 // coordinates; each denominator carries +1e-18 (added to |y| when the column
 // is staged) so that an all-zero coordinate pair (including padding)
-// contributes 0 and d1 d2 stays a normal float.
-template <int METRIC, int D>
-__device__ __forceinline__ float pair_dist(const float (&x)[D], const float4 *__restrict__ y4,
+// contributes 0 and d1 d2 stays a normal float.  ax holds |x| when the caller
+// keeps it in registers (NA = D / 2), else NA = 1 and |x| is formed here.
+// The differences and sums of coordinate pairs are packed two-lane FP32
+// operations (one instruction for two coordinates), the reductions scalar:
+// the sweep is issue-bound, and packing halves the issue slots of the
+// element-wise part without changing any rounding.
+template <int METRIC, int D, int NA>
+__device__ __forceinline__ float pair_dist(const float2 (&x)[D / 2], const float2 (&ax)[NA],
+                                           const float4 *__restrict__ ny4,
                                            const float4 *__restrict__ ya4) {
-    float acc0 = 0.f, acc1 = 0.f;
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+    float2 sq0 = make_float2(0.f, 0.f), sq1 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < D / 4; ++q) {
-        float4 y = y4[q];
-        float ys[4] = {y.x, y.y, y.z, y.w};
-        float yas[4] = {0.f, 0.f, 0.f, 0.f};
-        if (METRIC == SILH_CANBERRA) {
-            const float4 ya = ya4[q];
-            yas[0] = ya.x; yas[1] = ya.y; yas[2] = ya.z; yas[3] = ya.w;
-        }
-        if (METRIC == SILH_EUCLIDEAN) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                float t = x[4 * q + c] - ys[c];
-                if (c & 1) acc1 = fmaf(t, t, acc1); else acc0 = fmaf(t, t, acc0);
-            }
+        const float4 y = ny4[q];
+        const float2 t0 = __fadd2_rn(x[2 * q], make_float2(y.x, y.y));
+        const float2 t1 = __fadd2_rn(x[2 * q + 1], make_float2(y.z, y.w));
+        if (METRIC == SILH_EUCLIDEAN || METRIC == SILH_COSINE) {
+            sq0 = __ffma2_rn(t0, t0, sq0);
+            sq1 = __ffma2_rn(t1, t1, sq1);
         } else if (METRIC == SILH_MANHATTAN) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                float t = fabsf(x[4 * q + c] - ys[c]);
-                if (c & 1) acc1 += t; else acc0 += t;
-            }
-        } else if (METRIC == SILH_COSINE) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                float t = x[4 * q + c] - ys[c];
-                if (c & 1) acc1 = fmaf(t, t, acc1); else acc0 = fmaf(t, t, acc0);
-            }
+            sq0 = __fadd2_rn(sq0, make_float2(fabsf(t0.x), fabsf(t0.y)));
+            sq1 = __fadd2_rn(sq1, make_float2(fabsf(t1.x), fabsf(t1.y)));
         } else {
-#pragma unroll
-            for (int c = 0; c < 4; c += 2) {
-                float n1 = fabsf(x[4 * q + c] - ys[c]);
-                float n2 = fabsf(x[4 * q + c + 1] - ys[c + 1]);
-                float d1 = fabsf(x[4 * q + c]) + yas[c];          // |x| + (|y| + 1e-18)
-                float d2 = fabsf(x[4 * q + c + 1]) + yas[c + 1];
-                float num = fmaf(n2, d1, n1 * d2);
-                float den = d1 * d2;
-                if (c == 0) acc0 = fmaf(num, rcp_approx(den), acc0);
-                else acc1 = fmaf(num, rcp_approx(den), acc1);
+            const float4 ya = ya4[q];
+            float2 a0, a1;
+            if (NA == D / 2) {
+                a0 = ax[(2 * q) % NA];
+                a1 = ax[(2 * q + 1) % NA];
+            } else {
+                a0 = make_float2(fabsf(x[2 * q].x), fabsf(x[2 * q].y));
+                a1 = make_float2(fabsf(x[2 * q + 1].x), fabsf(x[2 * q + 1].y));
             }
+            const float2 d0 = __fadd2_rn(a0, make_float2(ya.x, ya.y));   // |x| + (|y| + 1e-18)
+            const float2 d1 = __fadd2_rn(a1, make_float2(ya.z, ya.w));
+            const float num0 = fmaf(fabsf(t0.y), d0.x, fabsf(t0.x) * d0.y);
+            const float num1 = fmaf(fabsf(t1.y), d1.x, fabsf(t1.x) * d1.y);
+            acc0 = fmaf(num0, rcp_approx(d0.x * d0.y), acc0);
+            acc1 = fmaf(num1, rcp_approx(d1.x * d1.y), acc1);
         }
     }
-    float a = acc0 + acc1;
-    if (METRIC == SILH_EUCLIDEAN) return sqrt_approx(a);
-    if (METRIC == SILH_COSINE) return 0.5f * a;
-    return a;
+    if (METRIC == SILH_EUCLIDEAN) return sqrt_approx((sq0.x + sq0.y) + (sq1.x + sq1.y));
+    if (METRIC == SILH_COSINE) return 0.5f * ((sq0.x + sq0.y) + (sq1.x + sq1.y));
+    if (METRIC == SILH_MANHATTAN) return (sq0.x + sq0.y) + (sq1.x + sq1.y);
+    return (acc0 + acc1) + (acc2 + acc3);
+}
+
+// Whether a row tile keeps |x| in registers for Canberra (register budget).
+template <int METRIC, int D, int RPT>
+struct RowAbs {
+    static constexpr int NA = (METRIC == SILH_CANBERRA && D * RPT <= 32) ? D / 2 : 1;
+};
+
+// Stage nq float4 of column coordinates as their negation (and, for Canberra,
+// |y| + 1e-18 beside them).
+template <int METRIC>
+__device__ __forceinline__ void stage_columns(const float4 *__restrict__ src, int nq,
+                                              float *__restrict__ sh_ny, float *__restrict__ sh_ya,
+                                              int tid, int nthreads) {
+    for (int q = tid; q < nq; q += nthreads) {
+        const float4 v = src[q];
+        reinterpret_cast<float4 *>(sh_ny)[q] = make_float4(-v.x, -v.y, -v.z, -v.w);
+        if (METRIC == SILH_CANBERRA)
+            reinterpret_cast<float4 *>(sh_ya)[q] =
+                make_float4(fabsf(v.x) + 1e-18f, fabsf(v.y) + 1e-18f, fabsf(v.z) + 1e-18f,
+                            fabsf(v.w) + 1e-18f);
+    }
 }
 
 constexpr int kThreads = 128;
@@ -150,7 +168,9 @@ __device__ __forceinline__ void sweep_rows(
     __shared__ __align__(16) float sh_ya[METRIC == SILH_CANBERRA ? BN * D : 4];
     __shared__ float sh_w[BN];
     __shared__ float sh_z[BN];
-    float x[RPT][D];
+    constexpr int NA = RowAbs<METRIC, D, RPT>::NA;
+    float2 x[RPT][D / 2];
+    float2 ax[RPT][NA];
     float zx[RPT];   // cosine: 0.5 for a zero row (distance 1 to everything)
     int own[RPT];
     double wown[RPT], bmin[RPT];
@@ -166,17 +186,26 @@ __device__ __forceinline__ void sweep_rows(
         }
         float sc = 0.f;
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            x[r][c] = (e >= 0 && e < n && c < d) ? to_f32<T>(X[e * ld + c]) : 0.f;
-            sc = fmaf(x[r][c], x[r][c], sc);
+        for (int c = 0; c < D; c += 2) {
+            const bool ok = e >= 0 && e < n;
+            x[r][c / 2].x = (ok && c < d) ? to_f32<T>(X[e * ld + c]) : 0.f;
+            x[r][c / 2].y = (ok && c + 1 < d) ? to_f32<T>(X[e * ld + c + 1]) : 0.f;
+            sc = fmaf(x[r][c / 2].x, x[r][c / 2].x, sc);
+            sc = fmaf(x[r][c / 2].y, x[r][c / 2].y, sc);
         }
         zx[r] = 0.f;
         if (METRIC == SILH_COSINE) {
             float inv = sc > 0.f ? rsqrtf(sc) : 0.f;
             zx[r] = sc > 0.f ? 0.f : 0.5f;
 #pragma unroll
-            for (int c = 0; c < D; ++c) x[r][c] *= inv;
+            for (int c = 0; c < D / 2; ++c) {
+                x[r][c].x *= inv;
+                x[r][c].y *= inv;
+            }
         }
+#pragma unroll
+        for (int c = 0; c < NA; ++c)
+            ax[r][c] = make_float2(fabsf(x[r][c].x), fabsf(x[r][c].y));
         wown[r] = 0.0;
         bmin[r] = INFINITY;
         wsep[r] = 0.0;
@@ -189,16 +218,8 @@ __device__ __forceinline__ void sweep_rows(
         for (int64_t cb = cs; cb < ce; cb += BN) {
             int nb = (int)min((int64_t)BN, ce - cb);
             __syncthreads();
-            const float4 *src = reinterpret_cast<const float4 *>(Y + cb * D);
-            float4 *dst = reinterpret_cast<float4 *>(sh_y);
-            for (int q = threadIdx.x; q < nb * (D / 4); q += kThreads) {
-                const float4 v = src[q];
-                dst[q] = v;
-                if (METRIC == SILH_CANBERRA)
-                    reinterpret_cast<float4 *>(sh_ya)[q] =
-                        make_float4(fabsf(v.x) + 1e-18f, fabsf(v.y) + 1e-18f, fabsf(v.z) + 1e-18f,
-                                    fabsf(v.w) + 1e-18f);
-            }
+            stage_columns<METRIC>(reinterpret_cast<const float4 *>(Y + cb * D), nb * (D / 4), sh_y,
+                                  sh_ya, threadIdx.x, kThreads);
             for (int q = threadIdx.x; q < BN; q += kThreads) {
                 sh_w[q] = (q < nb) ? wY[cb + q] : 0.f;
                 if (METRIC == SILH_COSINE) sh_z[q] = (q < nb) ? zY[cb + q] : 0.f;
@@ -218,7 +239,7 @@ __device__ __forceinline__ void sweep_rows(
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r)
-                    accf[r] = fmaf(w, pair_dist<METRIC, D>(x[r], y4, ya4), accf[r]);
+                    accf[r] = fmaf(w, pair_dist<METRIC, D, NA>(x[r], ax[r], y4, ya4), accf[r]);
             }
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
@@ -582,7 +603,9 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
     const int64_t I = lo;
     const int64_t J = I + (b - (I * ntiles - I * (I - 1) / 2));
     const bool diag = (I == J);
-    float x[RPT][D];
+    constexpr int NA = RowAbs<METRIC, D, RPT>::NA;
+    float2 x[RPT][D / 2];
+    float2 ax[RPT][NA];
     int lp[RPT];
     float zx[RPT];
     int64_t prow[RPT];
@@ -594,7 +617,10 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
         lp[r] = v ? lab_s[p] : -1;
         zx[r] = (METRIC == SILH_COSINE && v) ? zY[p] : 0.f;
 #pragma unroll
-        for (int c = 0; c < D; ++c) x[r][c] = v ? Y[p * D + c] : 0.f;
+        for (int c = 0; c < D / 2; ++c)
+            x[r][c] = v ? make_float2(Y[p * D + 2 * c], Y[p * D + 2 * c + 1]) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < NA; ++c) ax[r][c] = make_float2(fabsf(x[r][c].x), fabsf(x[r][c].y));
     }
     const int64_t rlast = min(I * T + T, n) - 1;
     const int cI0 = lab_s[I * T], cI1 = lab_s[rlast];
@@ -606,15 +632,8 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
     for (int64_t cb = c_begin; cb < c_end; cb += BN) {
         const int nb = (int)min((int64_t)BN, c_end - cb);
         __syncthreads();
-        const float4 *src = reinterpret_cast<const float4 *>(Y + cb * D);
-        for (int q = threadIdx.x; q < nb * (D / 4); q += kThreads) {
-            const float4 v = src[q];
-            reinterpret_cast<float4 *>(sh_y)[q] = v;
-            if (METRIC == SILH_CANBERRA)
-                reinterpret_cast<float4 *>(sh_ya)[q] =
-                    make_float4(fabsf(v.x) + 1e-18f, fabsf(v.y) + 1e-18f, fabsf(v.z) + 1e-18f,
-                                fabsf(v.w) + 1e-18f);
-        }
+        stage_columns<METRIC>(reinterpret_cast<const float4 *>(Y + cb * D), nb * (D / 4), sh_y,
+                              sh_ya, threadIdx.x, kThreads);
         for (int q = threadIdx.x; q < BN; q += kThreads) {
             sh_lab[q] = (q < nb) ? lab_s[cb + q] : -1;
             sh_z[q] = (METRIC == SILH_COSINE && q < nb) ? zY[cb + q] : 0.f;
@@ -637,7 +656,7 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
             float dr[RPT];
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
-                float dd = pair_dist<METRIC, D>(x[r], y4, ya4);
+                float dd = pair_dist<METRIC, D, NA>(x[r], ax[r], y4, ya4);
                 if (METRIC == SILH_COSINE) dd += zx[r] + sh_z[col];
                 dr[r] = (prow[r] < n) ? dd : 0.f;
                 accr[r] += dr[r];
