@@ -272,10 +272,44 @@ def run_gpu(args, rank, world, local_rank):
     d2h = sum(o[0].numel() * 4 + 16 for o in host_out)
     del host_out
 
+    if "cosine" in METRICS:
+        info["cosine_collapsed"] = time_cosine_collapsed(g, k, w, flush, stream)
+
     ms_max, e2e_max = reduce_max_over_ranks([ms, e2e_s], device=dev)
     return dict(ms=ms_max, e2e_s=e2e_max, step_ms=step_ms, legs=leg_ms, info=info,
                 launches=int(launches), clocks=clk.summary(), h2d=h2d, d2h=d2h, n=n, d=d, k=k,
                 sizes=sizes, rows_ex=len(rows_ex), X=X, lab=lab, rows=rows_ex)
+
+
+def time_cosine_collapsed(g, k, w, flush, stream, reps=5):
+    """The O(n k d) cosine Phase 2 (parallel-axis collapse), timed beside the
+    per-pair path on one sample of the same workload (outside the step), and
+    its largest |s_hat difference| from the per-pair estimate over all rows."""
+    import torch
+    from paper_2607_01993_b300 import silh
+    smp = silh.silh_sample_pps(g["X"], g["lab"], k, "cosine", t=w["t"], delta=w["delta"],
+                               seed=300, clustering_id=1)
+    sp = silh.silh_estimate(g["X"], g["lab"], k, smp, "cosine", prec=PREC["cosine"])
+    sc = silh.silh_estimate_cosine_collapsed(g["X"], g["lab"], k, smp)
+    times = {"per_pair": [], "collapsed": []}
+    for _ in range(reps):
+        for name in times:
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if name == "per_pair":
+                silh.silh_estimate(g["X"], g["lab"], k, smp, "cosine", prec=PREC["cosine"], out=sp)
+            else:
+                silh.silh_estimate_cosine_collapsed(g["X"], g["lab"], k, smp, out=sc)
+            e1.record(stream)
+            times[name].append((e0, e1))
+    torch.cuda.synchronize()
+    out = {f"{name}_ms": round(float(np.median([a.elapsed_time(b) for a, b in v])), 3)
+           for name, v in times.items()}
+    out["max_abs_s_diff_vs_per_pair"] = float((sc - sp).abs().max().item())
+    out["sample_size"] = smp.size
+    return out
 
 
 def dist_evals(res, t_step_samples):
@@ -560,6 +594,8 @@ def main():
             "e2e": {"value": round(pts / res["e2e_s"], 1), "unit": "points/s",
                     "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
             "gpu_launches": res["launches"], "clocks": res["clocks"]}
+    if "cosine_collapsed" in res["info"]:
+        line["cosine_collapsed"] = res["info"]["cosine_collapsed"]
     if not args.no_cpu_baseline and world == 1:
         import oracle
         t_cpu, desc = cpu_oracle_sample(res["X"], res["lab"], res["rows"], res["k"], WORKLOAD["t"],

@@ -123,6 +123,25 @@ silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n, int32_t d,
                           const silh_sample *S, const int64_t *rows, int64_t nrows,
                           float *s_hat, float *a_hat, float *b_hat, void *stream);
 
+/* Phase 2 of Algorithm 1 (Eq. 8) for the cosine distance in O(n k d): with unit
+ * vectors d_cos = 1 - <x^, y^> = 0.5 |x^ - y^|^2 (the cosine distance of
+ * Sec. 5.1.1, read as in the exact definition), and the weighted sum over a
+ * cluster's sample collapses by the parallel-axis identity to
+ *   W_hat_j(e) = Z_j + 0.5 (S_j |x^ - mu_j|^2 + R_j),
+ * S_j = sum of 1/p over the non-zero sampled vectors, mu_j their weighted mean
+ * direction, R_j = sum (1/p) |y^ - mu_j|^2, Z_j = sum of 1/p over zero sampled
+ * vectors (distance 1 to everything; a zero row has W_hat_j = S_j + Z_j).
+ * Per-cluster constants in FP64, per-row distances in FP32 with mu_j carried
+ * as two FP32 words; no cancellation, since both terms are non-negative.  The
+ * same real-arithmetic result as silh_estimate(metric = SILH_COSINE), which
+ * stays the reference path; this one costs n k d instead of n |S| d.
+ * Arguments, layouts and errors as silh_estimate (no metric or precision). */
+silh_status silh_estimate_cosine_collapsed(const void *X, silh_dtype dtype, int64_t n, int32_t d,
+                                           int64_t ld, const int32_t *labels, int32_t k,
+                                           const silh_sample *S, const int64_t *rows,
+                                           int64_t nrows, float *s_hat, float *a_hat,
+                                           float *b_hat, void *stream);
+
 /* Limits of silh_estimate_noalloc's fixed scratch (8.5 MiB per device). */
 #define SILH_NOALLOC_MAX_COLUMNS 65536
 #define SILH_NOALLOC_MAX_FLOATS 2097152

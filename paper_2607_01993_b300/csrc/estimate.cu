@@ -84,9 +84,9 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // contributes 0 and d1 d2 stays a normal float.  ax holds |x| when the caller
 // keeps it in registers (NA = D / 2), else NA = 1 and |x| is formed here.
 // The differences and sums of coordinate pairs are packed two-lane FP32
-// operations (one instruction for two coordinates), the reductions scalar:
-// the sweep is issue-bound, and packing halves the issue slots of the
-// element-wise part without changing any rounding.
+// operations (one instruction for two coordinates), as are the Euclidean,
+// cosine and Manhattan accumulations: the sweep is issue-bound, and packing
+// halves the issue slots of the element-wise part.
 template <int METRIC, int D, int NA>
 __device__ __forceinline__ float pair_dist(const float2 (&x)[D / 2], const float2 (&ax)[NA],
                                            const float4 *__restrict__ ny4,
@@ -639,38 +639,89 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
             sh_z[q] = (METRIC == SILH_COSINE && q < nb) ? zY[cb + q] : 0.f;
         }
         __syncthreads();
-        for (int col = 0; col < nb; ++col) {
-            const int lq = sh_lab[col];
-            if (lq != cur) {           // uniform: columns are cluster-sorted
-                if (cur >= 0) {
+        if (!diag && cI0 == cI1) {
+            // One row cluster: the column sums are reduced across the warp eight
+            // columns at a time (transpose-reduce: 9 shuffles for 8 columns).
+            for (int col0 = 0; col0 < nb; col0 += 8) {
+                float cs[8];
 #pragma unroll
-                    for (int r = 0; r < RPT; ++r)
-                        if (prow[r] < n) atomicAdd(&W[prow[r] * k + cur], (double)accr[r]);
+                for (int c = 0; c < 8; ++c) {
+                    const int col = col0 + c;
+                    cs[c] = 0.f;
+                    if (col < nb) {
+                        const int lq = sh_lab[col];
+                        if (lq != cur) {
+                            if (cur >= 0) {
+#pragma unroll
+                                for (int r = 0; r < RPT; ++r)
+                                    if (prow[r] < n)
+                                        atomicAdd(&W[prow[r] * k + cur], (double)accr[r]);
+                            }
+#pragma unroll
+                            for (int r = 0; r < RPT; ++r) accr[r] = 0.f;
+                            cur = lq;
+                        }
+                        const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * D);
+                        const float4 *ya4 = reinterpret_cast<const float4 *>(sh_ya + col * D);
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) {
+                            float dd = pair_dist<METRIC, D, NA>(x[r], ax[r], y4, ya4);
+                            if (METRIC == SILH_COSINE) dd += zx[r] + sh_z[col];
+                            dd = (prow[r] < n) ? dd : 0.f;
+                            accr[r] += dd;
+                            cs[c] += dd;
+                        }
+                    }
+                }
+                // lanes 0-15 keep columns 0-3, 16-31 columns 4-7; then 2, then 1
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const bool up = lane & 16;
+                    const float send = up ? cs[h] : cs[h + 4];
+                    cs[h] = (up ? cs[h + 4] : cs[h]) + __shfl_xor_sync(0xffffffffu, send, 16);
                 }
 #pragma unroll
-                for (int r = 0; r < RPT; ++r) accr[r] = 0.f;
-                cur = lq;
+                for (int h = 0; h < 2; ++h) {
+                    const bool up = lane & 8;
+                    const float send = up ? cs[h] : cs[h + 2];
+                    cs[h] = (up ? cs[h + 2] : cs[h]) + __shfl_xor_sync(0xffffffffu, send, 8);
+                }
+                {
+                    const bool up = lane & 4;
+                    const float send = up ? cs[0] : cs[1];
+                    cs[0] = (up ? cs[1] : cs[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+                }
+                cs[0] += __shfl_xor_sync(0xffffffffu, cs[0], 2);
+                cs[0] += __shfl_xor_sync(0xffffffffu, cs[0], 1);
+                const int mine = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                if ((lane & 3) == 0 && col0 + mine < nb) sh_col[warp][col0 + mine] = cs[0];
             }
-            const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * D);
-            const float4 *ya4 = reinterpret_cast<const float4 *>(sh_ya + col * D);
-            float dr[RPT];
+        } else {
+            // Diagonal tile (row sums only), or rows of several clusters (a tile
+            // at a cluster boundary): one column sum per row cluster.
+            for (int col = 0; col < nb; ++col) {
+                const int lq = sh_lab[col];
+                if (lq != cur) {           // uniform: columns are cluster-sorted
+                    if (cur >= 0) {
 #pragma unroll
-            for (int r = 0; r < RPT; ++r) {
-                float dd = pair_dist<METRIC, D, NA>(x[r], ax[r], y4, ya4);
-                if (METRIC == SILH_COSINE) dd += zx[r] + sh_z[col];
-                dr[r] = (prow[r] < n) ? dd : 0.f;
-                accr[r] += dr[r];
-            }
-            if (!diag) {
-                if (cI0 == cI1) {
-                    float v = 0.f;
+                        for (int r = 0; r < RPT; ++r)
+                            if (prow[r] < n) atomicAdd(&W[prow[r] * k + cur], (double)accr[r]);
+                    }
 #pragma unroll
-                    for (int r = 0; r < RPT; ++r) v += dr[r];
+                    for (int r = 0; r < RPT; ++r) accr[r] = 0.f;
+                    cur = lq;
+                }
+                const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * D);
+                const float4 *ya4 = reinterpret_cast<const float4 *>(sh_ya + col * D);
+                float dr[RPT];
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0) sh_col[warp][col] = v;
-                } else {
-                    // rows of several clusters (tile at a cluster boundary): one sum per cluster
+                for (int r = 0; r < RPT; ++r) {
+                    float dd = pair_dist<METRIC, D, NA>(x[r], ax[r], y4, ya4);
+                    if (METRIC == SILH_COSINE) dd += zx[r] + sh_z[col];
+                    dr[r] = (prow[r] < n) ? dd : 0.f;
+                    accr[r] += dr[r];
+                }
+                if (!diag) {
                     for (int c = cI0; c <= cI1; ++c) {
                         float v = 0.f;
 #pragma unroll

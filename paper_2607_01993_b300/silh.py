@@ -26,7 +26,8 @@ SILH_ECAPACITY = -4
 # exported symbols, as declared in include/silh.h
 EXPORTS = ("silh_sample_pps", "silh_estimate", "silh_exact", "silh_global", "silh_t_from_eps",
            "silh_last_error", "silh_version", "silh_kernel_launches", "silh_estimate_noalloc",
-           "silh_stream_status", "silh_estimate_batched", "silh_cohsep")
+           "silh_stream_status", "silh_estimate_batched", "silh_cohsep",
+           "silh_estimate_cosine_collapsed")
 SILH_NOALLOC_MAX_COLUMNS = 65536
 SILH_NOALLOC_MAX_FLOATS = 2097152
 
@@ -84,6 +85,10 @@ def load(path: str = LIB_PATH):
                                           ctypes.c_int, i32, ctypes.POINTER(SilhBatchItem), i32,
                                           vp]
     lib.silh_estimate_batched.restype = ctypes.c_int
+    lib.silh_estimate_cosine_collapsed.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32,
+                                                   ctypes.POINTER(SilhSample), vp, i64, vp, vp,
+                                                   vp, vp]
+    lib.silh_estimate_cosine_collapsed.restype = ctypes.c_int
     lib.silh_cohsep.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32, ctypes.c_int,
                                 ctypes.POINTER(SilhSample), vp, vp]
     lib.silh_cohsep.restype = ctypes.c_int
@@ -216,6 +221,24 @@ def silh_estimate_noalloc(X, labels, k, sample: Sample, metric="euclidean", prec
     _check(lib.silh_estimate_noalloc(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric],
                                      PRECS[prec], ctypes.byref(st), _ptr(rows), nr, _ptr(s),
                                      _ptr(a), _ptr(b), _stream(stream)))
+    return (s, a, b) if want_ab else s
+
+
+def silh_estimate_cosine_collapsed(X, labels, k, sample: Sample, rows=None, want_ab=False,
+                                   out=None, stream=None):
+    """Cosine Phase 2 in O(n k d) (parallel-axis collapse of the weighted sums)."""
+    lib = load()
+    dt, n, d, ld = _data(X)
+    labels = _labels(labels)
+    rows, nr = _rows(rows)
+    nrows = n if rows is None else nr
+    s = out if out is not None else torch.empty(nrows, dtype=torch.float32, device=X.device)
+    a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    st = sample.as_struct()
+    _check(lib.silh_estimate_cosine_collapsed(_ptr(X), dt, n, d, ld, _ptr(labels), k,
+                                              ctypes.byref(st), _ptr(rows), nr, _ptr(s), _ptr(a),
+                                              _ptr(b), _stream(stream)))
     return (s, a, b) if want_ab else s
 
 

@@ -65,6 +65,27 @@ def test_large_workload_sampled_parity(large, metric):
     _assert_close(se[torch.from_numpy(r3).cuda()], se_o)
 
 
+def test_large_workload_cosine_collapsed(large):
+    """The O(n k d) cosine path at n = 1M: sampled rows against the oracle, and
+    every row against the per-pair tensor-core estimate on the same sample."""
+    w = LARGE
+    X, lab, _ = large
+    k = w["k"]
+    Xt = torch.from_numpy(X).cuda()
+    lt = torch.from_numpy(lab).cuda()
+    gs = silh.silh_sample_pps(Xt, lt, k, "cosine", t=w["t"], delta=w["delta"], seed=7,
+                              clustering_id=1)
+    sc = silh.silh_estimate_cosine_collapsed(Xt, lt, k, gs)
+    sp = silh.silh_estimate(Xt, lt, k, gs, "cosine", prec="3xtf32")
+    assert (sc - sp).abs().max().item() <= 2 * S_TOL
+    Xh = X.astype(np.float64)
+    os_ = oracle.sample_pps(Xh, lab, k, "cosine", t=w["t"], delta=w["delta"], seed=7, cid=1)
+    assert_same_sample(gs, os_, k, 7, 1, "cosine", lab)
+    rows = synth.seeded_rows(w["n"], 300, seed=11)
+    s_o, _, _ = oracle.estimate(Xh, lab, k, "cosine", os_.offsets, os_.idx, os_.ps, rows=rows)
+    _assert_close(sc[torch.from_numpy(rows).cuda()], s_o)
+
+
 def test_precision_workload_bf16_sampled_parity():
     """n = 4M, d = 64, k = 64, 10% border points, data stored BF16; Euclidean."""
     X, lab, _ = synth.precision(seed=2)

@@ -365,3 +365,38 @@ def test_cohsep_all_sampled_is_exact_and_bf16():
         coh, sep = oracle.cohsep(W, lab, k)
         assert out[0] == pytest.approx(coh, rel=COHSEP_TOL)
         assert out[1] == pytest.approx(sep, rel=COHSEP_TOL)
+
+
+# ---------------------------------------- cosine: parallel-axis collapse
+
+@pytest.mark.parametrize("case", ["tiny", "ragged", "multitile"])
+def test_cosine_collapsed_matches_oracle(case):
+    """The O(n k d) cosine path against the oracle's per-pair Eq. 8 estimate."""
+    X, lab, k, kw = _case(case)
+    Xt, lt = _to_dev(X, lab)
+    Xh = _host_values(Xt)
+    os_ = oracle.sample_pps(Xh, lab, k, "cosine", t=kw["t"], m0=kw["m0"], seed=kw["seed"])
+    smp = silh.Sample.from_lists(np.bincount(lab, minlength=k), os_.offsets, os_.idx, os_.ps,
+                                 Xt.device)
+    s, a, b = silh.silh_estimate_cosine_collapsed(Xt, lt, k, smp, want_ab=True)
+    s_o, a_o, b_o = oracle.estimate(Xh, lab, k, "cosine", os_.offsets, os_.idx, os_.ps)
+    _assert_close(s, s_o, a, a_o, b, b_o)
+
+
+def test_cosine_collapsed_degenerate_bf16_and_rows():
+    """Zero vectors (distance 1 to everything), identical points, a singleton;
+    BF16 storage; a row subset equals the same rows of the full output."""
+    X, lab, k = _degenerate()
+    for dtype in (torch.float32, torch.bfloat16):
+        Xt, lt = _to_dev(X, lab, dtype)
+        Xh = _host_values(Xt)
+        gs = silh.silh_sample_pps(Xt, lt, k, "cosine", t=20.0, m0=6.0, seed=2)
+        os_ = oracle.sample_pps(Xh, lab, k, "cosine", t=20.0, m0=6.0, seed=2)
+        assert_same_sample(gs, os_, k, 2, 0, "cosine", lab)
+        s = silh.silh_estimate_cosine_collapsed(Xt, lt, k, gs)
+        s_o, _, _ = oracle.estimate(Xh, lab, k, "cosine", os_.offsets, os_.idx, os_.ps)
+        _assert_close(s, s_o)
+        assert s[-1].item() == 0.0
+        rows = torch.tensor([10, 0, 650, 599, 10], dtype=torch.int64, device=Xt.device)
+        sr = silh.silh_estimate_cosine_collapsed(Xt, lt, k, gs, rows=rows)
+        assert torch.equal(sr, s[rows])
