@@ -434,6 +434,81 @@ def run_batching(args):
     print(json.dumps(line))
 
 
+def run_precision(args):
+    """Precision workload: n = 4M, d = 64, k = 64 (Zipf sizes, 10% border
+    points), stored BF16 with FP32 masters, t = 128; Euclidean and cosine.
+    Phase 1 once per metric; Phase 2 over all rows in every precision mode,
+    timed with CUDA events (median of --steps, L2 flushed); the error of s_hat
+    against the FP64 oracle on a seeded row subset, both on the BF16-rounded
+    data (arithmetic error) and on the FP32 masters (total error, including
+    the storage rounding); the global silhouette of the subset likewise."""
+    import torch
+    import oracle
+    from paper_2607_01993_b300 import silh
+    torch.cuda.set_device(0)
+    X, lab, _ = synth.precision(seed=2)
+    n, d, k, t = X.shape[0], X.shape[1], 64, 128.0
+    Xb = torch.from_numpy(X).cuda().to(torch.bfloat16)
+    lt = torch.from_numpy(lab).cuda()
+    Xr = Xb.float().cpu().numpy().astype(np.float64)        # BF16-rounded values
+    Xm = X.astype(np.float64)                                # FP32 masters
+    del X
+    rows = synth.seeded_rows(n, args.precision_rows, seed=13)
+    rows_t = torch.from_numpy(rows).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    modes = ["fp32", "3xtf32", "tf32", "bf16x3", "bf16"]
+    out = {}
+    for mi, metric in enumerate(["euclidean", "cosine"]):
+        smp = silh.silh_sample_pps(Xb, lt, k, metric, t=t, delta=0.01, seed=3, clustering_id=mi)
+        osr = oracle.sample_pps(Xr, lab, k, metric, t=t, delta=0.01, seed=3, cid=mi)
+        s_ref, _, _ = oracle.estimate(Xr, lab, k, metric, osr.offsets, osr.idx, osr.ps, rows=rows)
+        # total error: the oracle on the FP32 masters, with the same sample lists
+        s_mst, _, _ = oracle.estimate(Xm, lab, k, metric, osr.offsets, osr.idx, osr.ps, rows=rows)
+        same_sample = bool(np.array_equal(smp.idx[:smp.size].cpu().numpy().astype(np.int64),
+                                          osr.idx))
+        # errors are measured on the oracle's own sample lists (fed to the GPU)
+        smp_o = silh.Sample.from_lists(np.bincount(lab, minlength=k), osr.offsets, osr.idx,
+                                       osr.ps, Xb.device)
+        per = {}
+        for prec in modes:
+            s = silh.silh_estimate(Xb, lt, k, smp, metric, prec=prec)
+            ts = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                silh.silh_estimate(Xb, lt, k, smp, metric, prec=prec, out=s)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            silh.silh_stream_status()
+            g = silh.silh_global(s).item()
+            sg = silh.silh_estimate(Xb, lt, k, smp_o, metric, prec=prec, rows=rows_t)
+            sg = sg.cpu().numpy().astype(np.float64)
+            ms = float(np.median(ts))
+            per[prec] = {
+                "phase2_ms": round(ms, 3), "points_per_s": round(n / (ms * 1e-3), 1),
+                "pairs_per_s": round(n * smp.size / (ms * 1e-3), 1),
+                "max_abs_err_vs_oracle_bf16_data": float(np.abs(sg - s_ref).max()),
+                "mean_abs_err_vs_oracle_bf16_data": float(np.abs(sg - s_ref).mean()),
+                "subset_global_err_bf16_data": float(abs(sg.mean() - s_ref.mean())),
+                "max_abs_err_vs_oracle_fp32_masters": float(np.abs(sg - s_mst).max()),
+                "subset_global_err_fp32_masters": float(abs(sg.mean() - s_mst.mean())),
+                "global_s_hat": g}
+        out[metric] = {"sample_size": smp.size, "sample_identical_to_oracle": same_sample,
+                       "modes": per}
+    line = {"metric": "precision workload: Phase-2 points/s and |s_hat error| vs the FP64 oracle "
+                      "per precision mode",
+            "unit": "points/s", "n_gpus": 1, "steps": args.steps, "higher_is_better": True,
+            "data": "synthetic",
+            "config": {"workload": f"precision: n={n}, d={d}, k={k} Zipf(1.1), 10% border points, "
+                                   f"stored BF16 (FP32 masters), t={t}, delta=0.01",
+                       "error_rows": len(rows), "l2": "flushed (256 MB write) before each timing"},
+            "results": out}
+    print(json.dumps(line))
+
+
 def run_serving(args):
     """Serving workload: Poisson streams of silhouette requests over 64 resident
     datasets (n log-uniform 5k-2M, d in {8,16,64,128}, FP32/BF16), k uniform
@@ -518,9 +593,12 @@ def main():
                     help="scale n and the exact subset (profiling cases only)")
     ap.add_argument("--metrics", default=",".join(METRICS),
                     help="comma-separated subset of metrics (profiling cases only)")
-    ap.add_argument("--workload", default="large", choices=["large", "batching", "serving"],
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "batching", "serving", "precision"],
                     help="large: the default step; batching: 256 clusterings in one launch; "
-                         "serving: Poisson request streams")
+                         "serving: Poisson request streams; precision: error and time per "
+                         "precision mode at n = 4M, BF16 storage")
+    ap.add_argument("--precision-rows", type=int, default=2000)
     ap.add_argument("--clusterings", type=int, default=256)
     ap.add_argument("--serve-cal", type=int, default=48)
     ap.add_argument("--serve-spec", type=int, default=400)
@@ -531,6 +609,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload == "precision":
+        run_precision(args)
         return
     METRICS = tuple(m for m in args.metrics.split(",") if m)
 

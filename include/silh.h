@@ -50,14 +50,22 @@ typedef enum {
 typedef enum { SILH_F32 = 0, SILH_BF16 = 1 } silh_dtype;
 
 /* Arithmetic of the Phase-2 / exact distance evaluation.
- *   SILH_PREC_FP32   FP32 on CUDA cores (reference precision, |ds| <= 1e-5);
- *   SILH_PREC_TF32   Euclidean/cosine inner products on tensor cores (TF32);
- *   SILH_PREC_3XTF32 split-TF32 (hi*hi + hi*lo + lo*hi) on tensor cores.
- * Manhattan and Canberra always run on CUDA cores in FP32. */
+ *   SILH_PREC_FP32    FP32 on CUDA cores (reference precision, |ds| <= 1e-5);
+ *   SILH_PREC_TF32    Euclidean/cosine inner products on tensor cores (TF32);
+ *   SILH_PREC_3XTF32  split-TF32 (hi*hi + hi*lo + lo*hi) on tensor cores;
+ *   SILH_PREC_BF16    inner products of BF16-rounded operands on tensor cores;
+ *   SILH_PREC_BF16X3  split-BF16 (BF16 head and tail, three products).
+ * All tensor-core modes accumulate in FP32, keep the per-cluster sums in FP64
+ * and recompute in FP32, from the coordinates, the pairs whose distance is
+ * small against the magnitudes that cancel in it.  The tensor-core modes
+ * apply to Euclidean and cosine with d <= 64; Manhattan, Canberra and d > 64
+ * run on CUDA cores in FP32 whatever the mode. */
 typedef enum {
     SILH_PREC_FP32 = 0,
     SILH_PREC_TF32 = 1,
-    SILH_PREC_3XTF32 = 2
+    SILH_PREC_3XTF32 = 2,
+    SILH_PREC_BF16 = 3,
+    SILH_PREC_BF16X3 = 4
 } silh_prec;
 
 typedef enum {

@@ -890,7 +890,7 @@ static silh_status check_data_args(const void *X, silh_dtype dtype, int64_t n, i
     if (k < 2 || k > SILH_MAX_K) return fail(SILH_EINVAL, "k must be in [2, %d]", SILH_MAX_K);
     if (metric < SILH_EUCLIDEAN || metric > SILH_CANBERRA) return fail(SILH_EINVAL, "unknown metric");
     if (dtype != SILH_F32 && dtype != SILH_BF16) return fail(SILH_EINVAL, "unknown dtype");
-    if (prec < SILH_PREC_FP32 || prec > SILH_PREC_3XTF32) return fail(SILH_EINVAL, "unknown precision");
+    if (prec < SILH_PREC_FP32 || prec > SILH_PREC_BF16X3) return fail(SILH_EINVAL, "unknown precision");
     return SILH_OK;
 }
 
@@ -1002,7 +1002,6 @@ extern "C" silh_status silh_estimate_batched(const void *X, silh_dtype dtype, in
     Scratch sc(stream);
     float *Y = nullptr, *wY = nullptr, *zY = nullptr;
     unsigned long long *next_work = nullptr;
-    BatchParams *bp = nullptr;
     std::vector<BatchParams> parts;
     std::vector<int32_t> order;
     SILH_REQ(X && items, "null pointer argument");
@@ -1010,7 +1009,7 @@ extern "C" silh_status silh_estimate_batched(const void *X, silh_dtype dtype, in
     SILH_REQ(d >= 1 && d <= 128 && ld >= d, "need 1 <= d <= 128 and ld >= d");
     SILH_REQ(metric >= SILH_EUCLIDEAN && metric <= SILH_CANBERRA, "unknown metric");
     SILH_REQ(dtype == SILH_F32 || dtype == SILH_BF16, "unknown dtype");
-    SILH_REQ(prec >= SILH_PREC_FP32 && prec <= SILH_PREC_3XTF32, "unknown precision");
+    SILH_REQ(prec >= SILH_PREC_FP32 && prec <= SILH_PREC_BF16X3, "unknown precision");
     SILH_REQ(nitems >= 1, "need at least one item");
     SILH_REQ(variant >= -1 && variant < kBatchVariants, "variant must be -1 .. %d",
              kBatchVariants - 1);
@@ -1074,7 +1073,6 @@ extern "C" silh_status silh_estimate_batched(const void *X, silh_dtype dtype, in
                                                     zY, next_work));
         }
     }
-    (void)bp;
 done:
     return st;
 }

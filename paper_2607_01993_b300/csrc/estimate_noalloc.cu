@@ -75,7 +75,7 @@ extern "C" silh_status silh_estimate_noalloc(const void *X, silh_dtype dtype, in
     SILH_REQ(k >= 2 && k <= SILH_MAX_K, "k must be in [2, %d]", SILH_MAX_K);
     SILH_REQ(metric >= SILH_EUCLIDEAN && metric <= SILH_CANBERRA, "unknown metric");
     SILH_REQ(dtype == SILH_F32 || dtype == SILH_BF16, "unknown dtype");
-    SILH_REQ(prec >= SILH_PREC_FP32 && prec <= SILH_PREC_3XTF32, "unknown precision");
+    SILH_REQ(prec >= SILH_PREC_FP32 && prec <= SILH_PREC_BF16X3, "unknown precision");
     SILH_REQ(S && S->k == k && S->sizes && S->offsets, "sample missing or k mismatch");
     m = S->size;
     SILH_REQ(m >= 0 && m <= S->cap && (m == 0 || (S->idx && S->p)), "bad sample size");

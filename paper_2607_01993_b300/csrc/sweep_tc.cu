@@ -1,11 +1,16 @@
 // Tensor-core Phase-2 / exact sweep for the Euclidean and cosine distances.
 //
-// The inner products x.y of a 128-row tile against a 128-column tile of the
-// cluster-major sample are one tcgen05 MMA chain (kind::tf32, FP32 accumulate
-// in tensor memory).  SILH_PREC_3XTF32 splits every operand into a TF32 head
-// and an FP32 tail (x = hi + lo) and accumulates hi.hi + hi.lo + lo.hi, which
-// leaves an inner-product error of a few 2^-22 |x||y|; SILH_PREC_TF32 uses the
-// heads only.  The epilogue turns each inner product into a distance
+// The inner products x.y of a 128-row tile against a 64-column tile of the
+// cluster-major sample are one tcgen05 MMA chain (FP32 accumulate in tensor
+// memory).  SILH_PREC_3XTF32 splits every operand into a TF32 head and an
+// FP32 tail (x = hi + lo, kind::tf32) and accumulates hi.hi + hi.lo + lo.hi,
+// which leaves an inner-product error of a few 2^-22 |x||y|; SILH_PREC_TF32
+// uses the heads only.  SILH_PREC_BF16X3 / SILH_PREC_BF16 do the same with
+// BF16 heads and BF16 tails (kind::f16; x = hi + lo to ~2^-17, so an
+// inner-product error of ~2^-17 |x||y|), or BF16 heads only (2^-8).  Both
+// operand kinds fill 128-byte shared-memory rows (32 TF32 or 64 BF16
+// elements), so the layouts, TMA boxes and descriptors are shared; each MMA
+// consumes 32 bytes of K (8 TF32 or 16 BF16 elements).  The epilogue turns each inner product into a distance
 //   Euclidean: d = sqrt(|x|^2 + |y|^2 - 2 x.y)   cosine: d = 1 - x^.y^
 // multiplies by the inclusion weight 1/p and adds it to the running sum of the
 // current cluster (Algorithm 1, Phase 2); W_hat never leaves the SM.  Pairs
@@ -47,15 +52,19 @@ __device__ int g_tc_error = 0;    // set when a bounded wait gives up
 
 #define SMEM_CHECK(bytes) ((bytes) + 1024 <= 200 * 1024)
 
-template <int KD, bool SPLIT>
+// KD: padded FP32 row length (32 or 64); BF: BF16 operands (one 128-byte K
+// block of 64 elements) instead of TF32 (KD / 32 blocks of 32 elements).
+template <int KD, bool SPLIT, bool BF = false>
 struct TcCfg {
-    static constexpr int KB = KD / 32;                          // 128-byte K blocks
+    static constexpr int KB = BF ? 1 : KD / 32;                 // 128-byte K blocks
+    static constexpr int KSTEPS = BF ? KD / 16 : 4;             // 32-byte MMA K steps per block
+    static constexpr int KELEM = BF ? 64 : 32;                  // elements per 128-byte row
     static constexpr int PARTS = SPLIT ? 2 : 1;                 // hi (+ lo)
-    static constexpr int SLOTS = (KD == 32) ? 4 : 2;            // row tiles per CTA pass
+    static constexpr int SLOTS = (KB == 1) ? 4 : 2;             // row tiles per CTA pass
     static constexpr int A_SLOT = PARTS * KB * kTileM * 128;
     static constexpr int A_BYTES = SLOTS * A_SLOT;
     static constexpr int B_BYTES = PARTS * KB * kTileN * 128;   // one stage
-    static constexpr int STAGES = (KD == 32) ? (SPLIT ? 4 : 8) : (SPLIT ? 2 : 4);
+    static constexpr int STAGES = (KB == 1) ? (SPLIT ? 4 : 8) : (SPLIT ? 2 : 4);
     static_assert(SMEM_CHECK(SLOTS * PARTS * KB * kTileM * 128 + STAGES * PARTS * KB * kTileN * 128),
                   "dynamic shared memory over budget");
     static constexpr int SMEM = 1024 + A_BYTES + STAGES * B_BYTES;
@@ -84,9 +93,11 @@ __device__ __forceinline__ float sqrt_apx(float x) {
     return r;
 }
 
-// Distance of a row (x = hi + lo, global) to a column (y, global), directly
-// from the coordinates in FP32: the rare close pairs the epilogue flags.
-template <int METRIC, int KD>
+// Distance of a row (global; TF32 operands: x = hi + lo exactly, BF16
+// operands: xh is the FP32 row and xl is unused) to a column (y, global),
+// directly from the coordinates in FP32: the rare close pairs the epilogue
+// flags.
+template <int METRIC, int KD, bool BF>
 __device__ __noinline__ float direct_dist(const float *__restrict__ xh, const float *__restrict__ xl,
                                           const float *__restrict__ y) {
     const float4 *y4 = reinterpret_cast<const float4 *>(y);
@@ -95,7 +106,8 @@ __device__ __noinline__ float direct_dist(const float *__restrict__ xh, const fl
     float a0 = 0.f, a1 = 0.f;
 #pragma unroll 4
     for (int q = 0; q < KD / 4; ++q) {
-        const float4 v = __ldg(y4 + q), h = __ldg(h4 + q), l = __ldg(l4 + q);
+        const float4 v = __ldg(y4 + q), h = __ldg(h4 + q);
+        const float4 l = BF ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(l4 + q);
         const float t0 = (h.x + l.x) - v.x, t1 = (h.y + l.y) - v.y;
         const float t2 = (h.z + l.z) - v.z, t3 = (h.w + l.w) - v.w;
         a0 = fmaf(t0, t0, a0); a1 = fmaf(t1, t1, a1);
@@ -108,8 +120,8 @@ __device__ __noinline__ float direct_dist(const float *__restrict__ xh, const fl
 // Column layout: cluster j occupies padded columns [poff[j], poff[j+1]), its
 // |F_j| sampled columns first, then zero columns of weight 0 up to a multiple
 // of 32, so every 32-column chunk belongs to exactly one cluster.
-template <int METRIC, int KD, bool SPLIT>
-__global__ void __launch_bounds__(TcCfg<KD, SPLIT>::THREADS, 1)
+template <int METRIC, int KD, bool SPLIT, bool BF>
+__global__ void __launch_bounds__(TcCfg<KD, SPLIT, BF>::THREADS, 1)
 k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CUtensorMap m_alo,
            const __grid_constant__ CUtensorMap m_bhi, const __grid_constant__ CUtensorMap m_blo,
            const float *__restrict__ a_hi, const float *__restrict__ a_lo,
@@ -119,7 +131,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
            const int64_t *__restrict__ sizes, int k, float tau,
            const double *__restrict__ w_own, float *__restrict__ s_out,
            float *__restrict__ a_out_v, float *__restrict__ b_out_v) {
-    using C = TcCfg<KD, SPLIT>;
+    using C = TcCfg<KD, SPLIT, BF>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_full[C::STAGES], bar_empty[C::STAGES];
     __shared__ uint64_t bar_afull, bar_aempty, bar_accf[C::SLOTS][2], bar_acce[C::SLOTS][2];
@@ -180,10 +192,10 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     const int y = (int)((rg * C::SLOTS + g) * kTileM);
                     uint8_t *a = sA + g * C::A_SLOT;
                     for (int kb = 0; kb < C::KB; ++kb) {
-                        tma_load_2d(&m_ahi, &bar_afull, a + kb * kTileM * 128, kb * 32, y);
+                        tma_load_2d(&m_ahi, &bar_afull, a + kb * kTileM * 128, kb * C::KELEM, y);
                         if (SPLIT)
                             tma_load_2d(&m_alo, &bar_afull, a + (C::KB + kb) * kTileM * 128,
-                                        kb * 32, y);
+                                        kb * C::KELEM, y);
                     }
                 }
                 for (int64_t ct = 0; ct < nct; ++ct) {
@@ -194,11 +206,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     uint8_t *dst = sB + stage * C::B_BYTES;
                     mbar_expect_tx(&bar_full[stage], C::B_BYTES);
                     for (int kb = 0; kb < C::KB; ++kb) {
-                        tma_load_2d(&m_bhi, &bar_full[stage], dst + kb * kTileN * 128, kb * 32,
-                                    (int)(ct * kTileN));
+                        tma_load_2d(&m_bhi, &bar_full[stage], dst + kb * kTileN * 128,
+                                    kb * C::KELEM, (int)(ct * kTileN));
                         if (SPLIT)
                             tma_load_2d(&m_blo, &bar_full[stage],
-                                        dst + (C::KB + kb) * kTileN * 128, kb * 32,
+                                        dst + (C::KB + kb) * kTileN * 128, kb * C::KELEM,
                                         (int)(ct * kTileN));
                     }
                     if (++stage == C::STAGES) {
@@ -211,7 +223,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32(kTileM, kTileN);
+            constexpr uint32_t idesc = BF ? idesc_bf16(kTileM, kTileN) : idesc_tf32(kTileM, kTileN);
             int stage = 0;
             uint32_t phase = 0, acc = 0, acc_phase = 0;
             int64_t idx = 0;
@@ -239,7 +251,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
 #pragma unroll
                         for (int kb = 0; kb < C::KB; ++kb) {
 #pragma unroll
-                            for (int ks = 0; ks < 4; ++ks) {
+                            for (int ks = 0; ks < C::KSTEPS; ++ks) {
                                 const uint32_t off = ks * 32;
                                 const uint64_t ahi =
                                     sw128_kmajor_desc(smem_u32(a + kb * kTileM * 128) + off);
@@ -250,11 +262,17 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                                         smem_u32(a + (C::KB + kb) * kTileM * 128) + off);
                                     const uint64_t blo = sw128_kmajor_desc(
                                         smem_u32(b + (C::KB + kb) * kTileN * 128) + off);
-                                    mma_tf32(d_tmem, alo, bhi, idesc, accumulate);
+                                    if (BF) {
+                                        mma_bf16(d_tmem, alo, bhi, idesc, accumulate);
+                                        mma_bf16(d_tmem, ahi, blo, idesc, 1);
+                                    } else {
+                                        mma_tf32(d_tmem, alo, bhi, idesc, accumulate);
+                                        mma_tf32(d_tmem, ahi, blo, idesc, 1);
+                                    }
                                     accumulate = 1;
-                                    mma_tf32(d_tmem, ahi, blo, idesc, 1);
                                 }
-                                mma_tf32(d_tmem, ahi, bhi, idesc, accumulate);
+                                if (BF) mma_bf16(d_tmem, ahi, bhi, idesc, accumulate);
+                                else mma_tf32(d_tmem, ahi, bhi, idesc, accumulate);
                                 accumulate = 1;
                             }
                         }
@@ -294,7 +312,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             const bool valid = pos < nrows;
             const int own = valid ? a_lab[pos] : -1;
             const float xn = valid ? a_norm[pos] : 0.f;
-            const float *xh = a_hi + (valid ? pos : 0) * KD, *xl = a_lo + (valid ? pos : 0) * KD;
+            const float *xh = a_hi + (valid ? pos : 0) * KD;
+            const float *xl = BF ? xh : a_lo + (valid ? pos : 0) * KD;
             int j = 0;
             int64_t pbnd = poff[1];
             double accd = 0.0, bmin = INFINITY;
@@ -376,11 +395,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             if (METRIC == SILH_EUCLIDEAN) {
                                 const float s2 = xn + wn.y;
                                 const float d2 = fmaf(-2.f, dot, s2);
-                                dist = (d2 < tau * s2) ? direct_dist<METRIC, KD>(xh, xl, yc)
+                                dist = (d2 < tau * s2) ? direct_dist<METRIC, KD, BF>(xh, xl, yc)
                                                        : sqrt_apx(d2);
                             } else {
                                 dist = 1.f - dot;
-                                if (dist < tau) dist = direct_dist<METRIC, KD>(xh, xl, yc);
+                                if (dist < tau) dist = direct_dist<METRIC, KD, BF>(xh, xl, yc);
                             }
                             part = fmaf(wn.x, dist, part);
                         }
@@ -441,7 +460,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
 // thread in sorted order; a CTA streams one chunk (blockIdx.y) of the column
 // blocks of the clusters its rows belong to (contiguous, as rows are sorted by
 // cluster) and adds its partial sums to W_own (zeroed beforehand).
-template <int METRIC, int KD>
+template <int METRIC, int KD, bool BF>
 __global__ void __launch_bounds__(128)
 k_own_direct(const float *__restrict__ a_hi, const float *__restrict__ a_lo,
              const float *__restrict__ a_norm, const int32_t *__restrict__ a_lab, int64_t nrows,
@@ -476,7 +495,8 @@ k_own_direct(const float *__restrict__ a_hi, const float *__restrict__ a_lo,
         own[r] = valid ? a_lab[pos[r]] : -1;
 #pragma unroll
         for (int c = 0; c < KD; ++c)
-            x[r][c] = valid ? a_hi[pos[r] * KD + c] + a_lo[pos[r] * KD + c] : 0.f;
+            x[r][c] = valid ? (BF ? a_hi[pos[r] * KD + c] : a_hi[pos[r] * KD + c] + a_lo[pos[r] * KD + c])
+                            : 0.f;
         zx[r] = (METRIC == SILH_COSINE && valid && a_norm[pos[r]] == 0.f) ? 0.5f : 0.f;
     }
     double acc[RPT] = {};
@@ -669,15 +689,34 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
-// Row operand in sorted order: hi/lo split (KD columns, zero padded), squared
-// norm (Euclidean) or unit scaling (cosine), label, and output index.
-template <class T>
+// Operand split of one (scaled, centred) coordinate v at element c of a row:
+// TF32 head + FP32 tail into float rows of KD elements, or BF16 head + BF16
+// tail into 64-element BF16 rows (128 bytes).
+template <bool BF>
+__device__ __forceinline__ void store_split(float v, int64_t row, int c, int KD, void *hi, void *lo) {
+    if (BF) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        reinterpret_cast<__nv_bfloat16 *>(hi)[row * 64 + c] = h;
+        reinterpret_cast<__nv_bfloat16 *>(lo)[row * 64 + c] = l;
+    } else {
+        const float h = to_tf32(v);
+        reinterpret_cast<float *>(hi)[row * KD + c] = h;
+        reinterpret_cast<float *>(lo)[row * KD + c] = v - h;
+    }
+}
+
+// Row operand in sorted order: hi/lo split (zero padded), the FP32 row when
+// the operands are BF16 (full, KD columns; the direct recompute reads it),
+// squared norm (Euclidean) or unit scaling (cosine), label, output index.
+template <class T, bool BF>
 __global__ void k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int64_t n,
                                  const int32_t *__restrict__ labels, const int64_t *__restrict__ rows,
                                  const int64_t *__restrict__ perm, int64_t nrows, int KD, int k,
-                                 int metric, const float *__restrict__ mu, float *__restrict__ hi,
-                                 float *__restrict__ lo, float *__restrict__ nrm,
-                                 int32_t *__restrict__ lab, int64_t *__restrict__ outi) {
+                                 int metric, const float *__restrict__ mu, void *__restrict__ hi,
+                                 void *__restrict__ lo, float *__restrict__ full,
+                                 float *__restrict__ nrm, int32_t *__restrict__ lab,
+                                 int64_t *__restrict__ outi) {
     const int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (p >= nrows) return;
@@ -696,12 +735,12 @@ __global__ void k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int
     }
     const float scale = (metric == SILH_COSINE) ? (s > 0.f ? rsqrtf(s) : 0.f) : 1.f;
     float ss = 0.f;
-    for (int c = lane; c < KD; c += 32) {
+    const int KE = BF ? 64 : KD;
+    for (int c = lane; c < KE; c += 32) {
         float v = (ok && c < d) ? to_f32<T>(x[c]) * scale : 0.f;
         if (mu != nullptr && c < d) v = v - mu[c];
-        const float h = to_tf32(v);
-        hi[p * KD + c] = h;
-        lo[p * KD + c] = v - h;
+        store_split<BF>(v, p, c, KD, hi, lo);
+        if (BF && c < KD) full[p * KD + c] = v;
         ss = fmaf(v, v, ss);
     }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
@@ -741,13 +780,13 @@ __global__ void k_col_poff(const int64_t *__restrict__ offsets, int k, int64_t *
 // Column operand in the padded layout (one warp per padded column): full FP32
 // copy, hi/lo split, (weight, squared norm).  Padding columns are zero with
 // weight 0.  Source column of sampled position t is idx[t] (idx == nullptr: t).
-template <class T>
+template <class T, bool BF>
 __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
                                  const int32_t *__restrict__ idx, const double *__restrict__ p,
                                  const int64_t *__restrict__ offsets,
                                  const int64_t *__restrict__ poff, int k, int64_t mp_max, int KD,
                                  int metric, const float *__restrict__ mu, float *__restrict__ full,
-                                 float *__restrict__ hi, float *__restrict__ lo,
+                                 void *__restrict__ hi, void *__restrict__ lo,
                                  float2 *__restrict__ wn) {
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
@@ -763,11 +802,11 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
         const int64_t local = i - poff[lo_j];
         if (local < offsets[lo_j + 1] - offsets[lo_j]) t = offsets[lo_j] + local;
     }
+    const int KE = BF ? 64 : KD;
     if (t < 0) {
-        for (int c = lane; c < KD; c += 32) {
-            full[i * KD + c] = 0.f;
-            hi[i * KD + c] = 0.f;
-            lo[i * KD + c] = 0.f;
+        for (int c = lane; c < KE; c += 32) {
+            if (c < KD) full[i * KD + c] = 0.f;
+            store_split<BF>(0.f, i, c, KD, hi, lo);
         }
         if (lane == 0) wn[i] = make_float2(0.f, 0.f);
         return;
@@ -784,13 +823,11 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
     }
     const float scale = (metric == SILH_COSINE) ? (s > 0.f ? rsqrtf(s) : 0.f) : 1.f;
     float ss = 0.f;
-    for (int c = lane; c < KD; c += 32) {
+    for (int c = lane; c < KE; c += 32) {
         float v = (c < d) ? to_f32<T>(x[c]) * scale : 0.f;
         if (mu != nullptr && c < d) v = v - mu[c];
-        const float h = to_tf32(v);
-        full[i * KD + c] = v;
-        hi[i * KD + c] = h;
-        lo[i * KD + c] = v - h;
+        if (c < KD) full[i * KD + c] = v;
+        store_split<BF>(v, i, c, KD, hi, lo);
         ss = fmaf(v, v, ss);
     }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
@@ -817,35 +854,40 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap *map, const float *ptr, int KD, int64_t rows, int box_rows) {
+// 2-D map over a row-major operand with 128-byte boxes along K: FP32 rows of
+// KD elements (box 32 x box_rows), or BF16 rows of 64 elements (box 64 x
+// box_rows); 128-byte swizzle, matching sw128_kmajor_desc.
+bool make_map(CUtensorMap *map, const void *ptr, int KD, int64_t rows, int box_rows, bool bf) {
     auto enc = encode_fn();
     if (!enc) return false;
-    cuuint64_t gdim[2] = {(cuuint64_t)KD, (cuuint64_t)rows};
-    cuuint64_t gstr[1] = {(cuuint64_t)KD * sizeof(float)};
-    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    const int ke = bf ? 64 : KD, es_bytes = bf ? 2 : 4;
+    cuuint64_t gdim[2] = {(cuuint64_t)ke, (cuuint64_t)rows};
+    cuuint64_t gstr[1] = {(cuuint64_t)ke * es_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es_bytes), (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, gdim, gstr, box, es,
+    return enc(map, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+               (void *)ptr, gdim, gstr, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int METRIC, int KD, bool SPLIT>
+template <int METRIC, int KD, bool SPLIT, bool BF>
 cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, const CUtensorMap &alo,
                       const CUtensorMap &bhi, const CUtensorMap &blo, const float *a_hi,
                       const float *a_lo, const float *a_norm, const int32_t *a_lab,
                       const int64_t *a_out, int64_t nrows, const float *y_full, const float2 *y_wn,
                       const int64_t *poff, const int64_t *sizes, int k, float tau,
                       int64_t max_cluster_cols, double *w_own, float *s, float *a, float *b) {
-    using C = TcCfg<KD, SPLIT>;
+    using C = TcCfg<KD, SPLIT, BF>;
     constexpr int64_t kChunk = 2048;
     const int64_t nchunk = std::max<int64_t>(1, (max_cluster_cols + 31 + kChunk - 1) / kChunk);
     cudaError_t e0 = cudaMemsetAsync(w_own, 0, sizeof(double) * (size_t)nrows, stream);
     if (e0 != cudaSuccess) return e0;
-    k_own_direct<METRIC, KD><<<dim3((unsigned)((nrows + 255) / 256), (unsigned)nchunk), 128, 0, stream>>>(
+    k_own_direct<METRIC, KD, BF><<<dim3((unsigned)((nrows + 255) / 256), (unsigned)nchunk), 128, 0, stream>>>(
         a_hi, a_lo, a_norm, a_lab, nrows, y_full, y_wn, poff, k, kChunk, w_own);
     count_launches(1);
-    auto kern = k_sweep_tc<METRIC, KD, SPLIT>;
+    auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     const int64_t groups = ((nrows + kTileM - 1) / kTileM + C::SLOTS - 1) / C::SLOTS;
@@ -861,8 +903,9 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
 
 bool tc_eligible(int metric, int prec, int d) {
     return (metric == SILH_EUCLIDEAN || metric == SILH_COSINE) &&
-           (prec == SILH_PREC_TF32 || prec == SILH_PREC_3XTF32) && d <= 64 &&
-           encode_fn() != nullptr;
+           (prec == SILH_PREC_TF32 || prec == SILH_PREC_3XTF32 || prec == SILH_PREC_BF16 ||
+            prec == SILH_PREC_BF16X3) &&
+           d <= 64 && encode_fn() != nullptr;
 }
 
 silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
@@ -872,7 +915,10 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
                      float *a, float *b, Scratch &sc, cudaStream_t stream) {
     silh_status st = SILH_OK;
     const int KD = d <= 32 ? 32 : 64;
-    const bool split = prec == SILH_PREC_3XTF32;
+    const bool split = prec == SILH_PREC_3XTF32 || prec == SILH_PREC_BF16X3;
+    const bool bf = prec == SILH_PREC_BF16 || prec == SILH_PREC_BF16X3;
+    const int KE = bf ? 64 : KD;                  // operand row length (128 B per K block)
+    const size_t ebytes = bf ? 2 : 4;
     const int tile = (k <= 512) ? 1024 : 8192;
     const int ntiles = (int)std::max<int64_t>(1, (nrows + tile - 1) / tile);
     const size_t hsmem = sizeof(int32_t) * (size_t)(k + 1);
@@ -884,8 +930,8 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     double *w_own = nullptr, *mpart = nullptr;
     float *mu = nullptr;
     const int mean_blocks = 128;
-    float *rhi = nullptr, *rlo = nullptr, *rn = nullptr, *yf = nullptr, *yhi = nullptr,
-          *ylo = nullptr;
+    uint8_t *rhi = nullptr, *rlo = nullptr, *yhi = nullptr, *ylo = nullptr;
+    float *rfull = nullptr, *rn = nullptr, *yf = nullptr;
     float2 *ywn = nullptr;
     CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
     const float tau = (metric == SILH_EUCLIDEAN) ? 0.25f : 0.25f;
@@ -897,16 +943,17 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     SILH_CK(sc.alloc(&perm, (size_t)nrows));
     SILH_CK(sc.alloc(&outi, (size_t)nrows));
     SILH_CK(sc.alloc(&lab, (size_t)nrows));
-    SILH_CK(sc.alloc(&rhi, (size_t)nrows * KD));
-    SILH_CK(sc.alloc(&rlo, (size_t)nrows * KD));
+    SILH_CK(sc.alloc(&rhi, (size_t)nrows * KE * ebytes));
+    SILH_CK(sc.alloc(&rlo, (size_t)nrows * KE * ebytes));
+    if (bf) SILH_CK(sc.alloc(&rfull, (size_t)nrows * KD));
     SILH_CK(sc.alloc(&rn, (size_t)nrows));
     SILH_CK(sc.alloc(&poff, (size_t)k + 1));
     SILH_CK(sc.alloc(&w_own, (size_t)nrows));
     SILH_CK(sc.alloc(&mpart, (size_t)mean_blocks * d));
     SILH_CK(sc.alloc(&mu, (size_t)d));
     SILH_CK(sc.alloc(&yf, (size_t)mp_max * KD));
-    SILH_CK(sc.alloc(&yhi, (size_t)mp_max * KD));
-    SILH_CK(sc.alloc(&ylo, (size_t)mp_max * KD));
+    SILH_CK(sc.alloc(&yhi, (size_t)mp_max * KE * ebytes));
+    SILH_CK(sc.alloc(&ylo, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&ywn, (size_t)mp_max));
     if (hsmem > 48 * 1024) {
         SILH_CK(cudaFuncSetAttribute(k_key_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -935,43 +982,47 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     } else {
         mu = nullptr;
     }
+#define SILH_TC_GATHER(T, BFV)                                                                  \
+    k_gather_rows_tc<T, BFV><<<ceil_div_i(nrows, 8), 256, 0, stream>>>(                        \
+        (const T *)X, d, ld, n, labels, rows, perm, nrows, KD, k, metric, mu, rhi, rlo, rfull, rn, \
+        lab, outi);                                                                             \
+    k_gather_cols_tc<T, BFV><<<ceil_div_i(mp_max, 8), 256, 0, stream>>>(                       \
+        (const T *)X, d, ld, col_idx, col_p, offsets, poff, k, mp_max, KD, metric, mu, yf, yhi,  \
+        ylo, ywn);
     if (dtype == SILH_F32) {
-        k_gather_rows_tc<float><<<ceil_div_i(nrows, 8), 256, 0, stream>>>(
-            (const float *)X, d, ld, n, labels, rows, perm, nrows, KD, k, metric, mu, rhi, rlo, rn,
-            lab, outi);
-        k_gather_cols_tc<float><<<ceil_div_i(mp_max, 8), 256, 0, stream>>>(
-            (const float *)X, d, ld, col_idx, col_p, offsets, poff, k, mp_max, KD, metric, mu, yf,
-            yhi, ylo, ywn);
+        if (bf) { SILH_TC_GATHER(float, true) } else { SILH_TC_GATHER(float, false) }
     } else {
-        k_gather_rows_tc<__nv_bfloat16><<<ceil_div_i(nrows, 8), 256, 0, stream>>>(
-            (const __nv_bfloat16 *)X, d, ld, n, labels, rows, perm, nrows, KD, k, metric, mu, rhi,
-            rlo, rn, lab, outi);
-        k_gather_cols_tc<__nv_bfloat16><<<ceil_div_i(mp_max, 8), 256, 0, stream>>>(
-            (const __nv_bfloat16 *)X, d, ld, col_idx, col_p, offsets, poff, k, mp_max, KD, metric,
-            mu, yf, yhi, ylo, ywn);
+        if (bf) { SILH_TC_GATHER(__nv_bfloat16, true) } else { SILH_TC_GATHER(__nv_bfloat16, false) }
     }
+#undef SILH_TC_GATHER
     count_launches(2);
     SILH_CK(cudaGetLastError());
-    SILH_REQ(make_map(&m_ahi, rhi, KD, nrows, kTileM) && make_map(&m_alo, rlo, KD, nrows, kTileM) &&
-                 make_map(&m_bhi, yhi, KD, mp_max, kTileN) &&
-                 make_map(&m_blo, ylo, KD, mp_max, kTileN),
+    SILH_REQ(make_map(&m_ahi, rhi, KD, nrows, kTileM, bf) &&
+                 make_map(&m_alo, rlo, KD, nrows, kTileM, bf) &&
+                 make_map(&m_bhi, yhi, KD, mp_max, kTileN, bf) &&
+                 make_map(&m_blo, ylo, KD, mp_max, kTileN, bf),
              "tensor map encoding failed");
     SILH_CK(cudaGetDevice(&dev));
     SILH_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-#define SILH_TC_CASE(MET, KDV, SP)                                                              \
-    if (metric == MET && KD == KDV && split == SP) {                                           \
-        SILH_CK((launch_tc<MET, KDV, SP>(nsm, stream, m_ahi, m_alo, m_bhi, m_blo, rhi, rlo, rn, \
-                                         lab, outi, nrows, yf, ywn, poff, sizes, k, tau,        \
-                                         max_cluster_cols, w_own, s, a, b)));                  \
+    // the direct recompute and the own-cluster pass read FP32 rows: hi + lo for
+    // TF32 operands (exact), the separate FP32 copy for BF16 operands
+#define SILH_TC_CASE(MET, KDV, SP, BFV)                                                        \
+    if (metric == MET && KD == KDV && split == SP && bf == BFV) {                              \
+        SILH_CK((launch_tc<MET, KDV, SP, BFV>(                                                  \
+            nsm, stream, m_ahi, m_alo, m_bhi, m_blo, BFV ? rfull : (const float *)rhi,         \
+            BFV ? nullptr : (const float *)rlo, rn, lab, outi, nrows, yf, ywn, poff, sizes, k, \
+            tau, max_cluster_cols, w_own, s, a, b)));                                         \
     }
-    SILH_TC_CASE(SILH_EUCLIDEAN, 32, true)
-    SILH_TC_CASE(SILH_EUCLIDEAN, 32, false)
-    SILH_TC_CASE(SILH_EUCLIDEAN, 64, true)
-    SILH_TC_CASE(SILH_EUCLIDEAN, 64, false)
-    SILH_TC_CASE(SILH_COSINE, 32, true)
-    SILH_TC_CASE(SILH_COSINE, 32, false)
-    SILH_TC_CASE(SILH_COSINE, 64, true)
-    SILH_TC_CASE(SILH_COSINE, 64, false)
+#define SILH_TC_CASES(MET, KDV)             \
+    SILH_TC_CASE(MET, KDV, true, false)     \
+    SILH_TC_CASE(MET, KDV, false, false)    \
+    SILH_TC_CASE(MET, KDV, true, true)      \
+    SILH_TC_CASE(MET, KDV, false, true)
+    SILH_TC_CASES(SILH_EUCLIDEAN, 32)
+    SILH_TC_CASES(SILH_EUCLIDEAN, 64)
+    SILH_TC_CASES(SILH_COSINE, 32)
+    SILH_TC_CASES(SILH_COSINE, 64)
+#undef SILH_TC_CASES
 #undef SILH_TC_CASE
 done:
     return st;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libsilh.so")
 
 METRICS = {"euclidean": 0, "cosine": 1, "manhattan": 2, "canberra": 3}
 DTYPES = {torch.float32: 0, torch.bfloat16: 1}
-PRECS = {"fp32": 0, "tf32": 1, "3xtf32": 2}
+PRECS = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16": 3, "bf16x3": 4}
 STATUS = {0: "SILH_OK", -1: "SILH_EINVAL", -2: "SILH_ENOMEM", -3: "SILH_ECUDA",
           -4: "SILH_ECAPACITY", -5: "SILH_ETIMEOUT"}
 SILH_ECAPACITY = -4

@@ -98,12 +98,13 @@ def test_precision_workload_bf16_sampled_parity():
     os_ = oracle.sample_pps(Xh, lab, k, "euclidean", t=t, delta=0.01, seed=3)
     assert_same_sample(gs, os_, k, 3, 0)
     rows = synth.seeded_rows(lab.shape[0], 200, seed=13)
-    for prec in ("fp32", "3xtf32"):
+    s_o, _, _ = oracle.estimate(Xh, lab, k, "euclidean", os_.offsets, os_.idx, os_.ps, rows=rows)
+    tol = {"fp32": S_TOL, "3xtf32": S_TOL, "bf16x3": 2e-5, "bf16": 5e-3}
+    for prec in ("fp32", "3xtf32", "bf16x3", "bf16"):
         s = silh.silh_estimate(Xt, lt, k, gs, "euclidean", prec=prec,
                                rows=torch.from_numpy(rows).cuda())
-        s_o, _, _ = oracle.estimate(Xh, lab, k, "euclidean", os_.offsets, os_.idx, os_.ps,
-                                    rows=rows)
-        _assert_close(s, s_o)
+        err = np.abs(s.cpu().numpy().astype(np.float64) - s_o).max()
+        assert err <= tol[prec], (prec, err)
     assert S_TOL == 1e-5
 
 

@@ -261,14 +261,25 @@ def test_degenerate_inputs_match_oracle(metric):
 # Plain TF32 keeps 11 significant bits of each coordinate, so inner products
 # carry ~2^-11 relative error; its stated bound on s_hat is 2e-3.  Split TF32
 # (3 MMAs) plus the FP32 recompute of close pairs is held to the FP32 bound.
-TC_TOL = {"3xtf32": S_TOL, "tf32": 2e-3}
+# Split BF16 keeps ~17 significant bits of each coordinate (inner products to
+# ~2^-17 |x||y|): 2e-5.  Plain BF16 rounds each coordinate to 8 bits: 5e-3.
+TC_TOL = {"3xtf32": S_TOL, "tf32": 2e-3, "bf16x3": 2e-5, "bf16": 5e-3}
+TC_PRECS = ["3xtf32", "tf32", "bf16x3", "bf16"]
 
 
-@pytest.mark.parametrize("prec", ["3xtf32", "tf32"])
-@pytest.mark.parametrize("case", ["tiny", "ragged", "multitile"])
+def _tc_case(name):
+    if name == "wide":     # d = 50: two 128-byte TF32 K blocks, one BF16 block of 4 K steps
+        X, lab, _ = synth.gaussian_mixture(12000, 50, 8, seed=9, sizes=synth.zipf_sizes(12000, 8),
+                                           sigma_range=(0.5, 3))
+        return X, lab, 8, dict(t=96.0, m0=None, seed=9)
+    return _case(name)
+
+
+@pytest.mark.parametrize("prec", TC_PRECS)
+@pytest.mark.parametrize("case", ["tiny", "ragged", "multitile", "wide"])
 @pytest.mark.parametrize("metric", ["euclidean", "cosine"])
 def test_tensor_core_estimate_matches_oracle(case, metric, prec):
-    X, lab, k, kw = _case(case)
+    X, lab, k, kw = _tc_case(case)
     Xt, lt = _to_dev(X, lab)
     Xh = _host_values(Xt)
     os_ = oracle.sample_pps(Xh, lab, k, metric, t=kw["t"], m0=kw["m0"], seed=kw["seed"])
@@ -285,22 +296,33 @@ def test_tensor_core_estimate_matches_oracle(case, metric, prec):
     if prec == "3xtf32":
         np.testing.assert_allclose(a.cpu().numpy(), a_o, rtol=AB_RTOL, atol=1e-7)
         np.testing.assert_allclose(b.cpu().numpy(), b_o, rtol=AB_RTOL, atol=1e-7)
+    if prec == "bf16x3":
+        np.testing.assert_allclose(a.cpu().numpy(), a_o, rtol=2 * AB_RTOL, atol=1e-7)
+        np.testing.assert_allclose(b.cpu().numpy(), b_o, rtol=2 * AB_RTOL, atol=1e-7)
 
 
-@pytest.mark.parametrize("case", ["tiny", "ragged"])
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
+@pytest.mark.parametrize("case", ["tiny", "ragged", "wide"])
 @pytest.mark.parametrize("metric", ["euclidean", "cosine"])
-def test_tensor_core_exact_matches_oracle(case, metric):
-    X, lab, k, _ = _case(case)
+def test_tensor_core_exact_matches_oracle(case, metric, prec):
+    X, lab, k, _ = _tc_case(case)
+    if case == "wide":
+        X, lab = X[:3000], lab[:3000]
+        k = int(lab.max()) + 1
+        assert (np.bincount(lab, minlength=k) > 0).all()
     Xt, lt = _to_dev(X, lab)
     Xh = _host_values(Xt)
-    s = silh.silh_exact(Xt, lt, k, metric, prec="3xtf32")
+    s = silh.silh_exact(Xt, lt, k, metric, prec=prec)
     silh.silh_stream_status()
     s_o, _, _ = oracle.exact(Xh, lab, k, metric)
-    _assert_close(s, s_o)
+    s_g = s.cpu().numpy().astype(np.float64)
+    assert np.isfinite(s_g).all()
+    assert np.abs(s_g - s_o).max() <= TC_TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
 @pytest.mark.parametrize("metric", ["euclidean", "cosine"])
-def test_tensor_core_rows_degenerate_and_bf16(metric):
+def test_tensor_core_rows_degenerate_and_bf16(metric, prec):
     X, lab, k = _degenerate()
     Xt, lt = _to_dev(X, lab)
     Xh = _host_values(Xt)
@@ -308,10 +330,10 @@ def test_tensor_core_rows_degenerate_and_bf16(metric):
     os_ = oracle.sample_pps(Xh, lab, k, metric, t=20.0, m0=6.0, seed=2)
     assert_same_sample(gs, os_, k, 2, 0, metric, lab)
     rows = torch.tensor([650, 3, 10, 21, 600, 0, 640], dtype=torch.int64, device="cuda")
-    s = silh.silh_estimate(Xt, lt, k, gs, metric, prec="3xtf32", rows=rows)
+    s = silh.silh_estimate(Xt, lt, k, gs, metric, prec=prec, rows=rows)
     s_o, _, _ = oracle.estimate(Xh, lab, k, metric, os_.offsets, os_.idx, os_.ps,
                                 rows=rows.cpu().numpy())
-    _assert_close(s, s_o)
+    assert np.abs(s.cpu().numpy().astype(np.float64) - s_o).max() <= TC_TOL[prec]
     # BF16 storage through the tensor-core path
     X2, lab2, k2, kw2 = _case("multitile")
     Xb, lb = _to_dev(X2, lab2, torch.bfloat16)
@@ -320,10 +342,10 @@ def test_tensor_core_rows_degenerate_and_bf16(metric):
     smp2 = silh.Sample.from_lists(np.bincount(lab2, minlength=k2), os2.offsets, os2.idx, os2.ps,
                                   Xb.device)
     r2 = torch.arange(0, 40000, 131, dtype=torch.int64, device="cuda")
-    s2 = silh.silh_estimate(Xb, lb, k2, smp2, metric, prec="3xtf32", rows=r2)
+    s2 = silh.silh_estimate(Xb, lb, k2, smp2, metric, prec=prec, rows=r2)
     s2_o, _, _ = oracle.estimate(Xbh, lab2, k2, metric, os2.offsets, os2.idx, os2.ps,
                                  rows=r2.cpu().numpy())
-    _assert_close(s2, s2_o)
+    assert np.abs(s2.cpu().numpy().astype(np.float64) - s2_o).max() <= TC_TOL[prec]
     silh.silh_stream_status()
 
 
