@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <vector>
@@ -65,6 +66,25 @@ struct Scratch {
 
 // Keep freed scratch cached in the device's default pool between calls.
 void ensure_pool_retains(int device);
+
+// ------------------------------------------------- b_hat without division
+
+// Running minimum over clusters of acc_j / |C_j| (b_hat, Eq. 8) with no
+// division per cluster: a candidate (acc, size) replaces the best (bacc, bsz)
+// when acc * bsz < bacc * size (sizes are positive; each product is rounded
+// once), and the minimum itself is formed once, bacc / bsz.  Ties keep the
+// lower cluster index.  FP64 division is many times the cost of a multiply.
+struct RatioMin {
+    double acc, size;
+    __device__ __forceinline__ RatioMin() : acc(INFINITY), size(1.0) {}
+    __device__ __forceinline__ void add(double a, double sz) {
+        if (a * size < acc * sz) {
+            acc = a;
+            size = sz;
+        }
+    }
+    __device__ __forceinline__ double value() const { return acc / size; }
+};
 
 // ----------------------------------------------------------- Philox4x64-10
 

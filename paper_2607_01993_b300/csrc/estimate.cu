@@ -173,7 +173,8 @@ __device__ __forceinline__ void sweep_rows(
     float2 ax[RPT][NA];
     float zx[RPT];   // cosine: 0.5 for a zero row (distance 1 to everything)
     int own[RPT];
-    double wown[RPT], bmin[RPT];
+    double wown[RPT];
+    RatioMin bmin[RPT];
     double wsep[RPT];   // sum of W_hat_j over clusters j > own (separation numerator)
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
@@ -207,7 +208,7 @@ __device__ __forceinline__ void sweep_rows(
         for (int c = 0; c < NA; ++c)
             ax[r][c] = make_float2(fabsf(x[r][c].x), fabsf(x[r][c].y));
         wown[r] = 0.0;
-        bmin[r] = INFINITY;
+        bmin[r] = RatioMin();
         wsep[r] = 0.0;
     }
     for (int j = 0; j < k; ++j) {
@@ -251,7 +252,7 @@ __device__ __forceinline__ void sweep_rows(
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             if (j == own[r]) wown[r] = accd[r];
-            else bmin[r] = fmin(bmin[r], accd[r] / csz);
+            else bmin[r].add(accd[r], csz);
             if (j > own[r]) wsep[r] += accd[r];
         }
     }
@@ -265,7 +266,7 @@ __device__ __forceinline__ void sweep_rows(
         } else {
             int64_t nc = sizes[own[r]];
             double a = (nc > 1) ? wown[r] / (double)(nc - 1) : 0.0;
-            double b = bmin[r];
+            double b = bmin[r].value();
             double mx = fmax(a, b);
             double s = (nc > 1 && mx > 0.0) ? (b - a) / mx : 0.0;
             sv = (float)s; av = (float)a; bv = (float)b;
@@ -760,9 +761,10 @@ __global__ void k_exact_finalize(const double *__restrict__ W, const int32_t *__
     if (pos >= n) return;
     const int own = lab_s[pos];
     const double *w = W + pos * k;
-    double bmin = INFINITY;
+    RatioMin bm;
     for (int j = 0; j < k; ++j)
-        if (j != own) bmin = fmin(bmin, w[j] / (double)sizes[j]);
+        if (j != own) bm.add(w[j], (double)sizes[j]);
+    const double bmin = bm.value();
     const int64_t nc = sizes[own];
     const double a = (nc > 1) ? w[own] / (double)(nc - 1) : 0.0;
     const double mx = fmax(a, bmin);

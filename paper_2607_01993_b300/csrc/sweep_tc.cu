@@ -117,6 +117,38 @@ __device__ __noinline__ float direct_dist(const float *__restrict__ xh, const fl
     return METRIC == SILH_EUCLIDEAN ? sqrtf(s) : 0.5f * s;
 }
 
+// Fast-path epilogue of 16 accumulator columns (inner products r) of one row,
+// two columns per packed two-lane FP32 instruction: part += sum w d, and
+// flagmin tracks the pairs that need the direct recompute (Euclidean:
+// d^2 - tau (|x|^2 + |y|^2) < 0; cosine: d - tau < 0).  wn4 holds
+// (w_2i, w_2i+1, |y_2i|^2, |y_2i+1|^2).
+template <int METRIC>
+__device__ __forceinline__ void half_chunk(const uint32_t (&r)[16], const float4 *wn4, float xn,
+                                           float tau, float &part, float &flagmin) {
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    float dmin = INFINITY;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 wn = wn4[i];
+        const float2 v = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+        float2 d;
+        if (METRIC == SILH_EUCLIDEAN) {
+            const float2 s = __fadd2_rn(make_float2(xn, xn), make_float2(wn.z, wn.w));
+            const float2 q = __ffma2_rn(make_float2(-2.f, -2.f), v, s);
+            const float2 f = __ffma2_rn(make_float2(-tau, -tau), s, q);
+            flagmin = fminf(flagmin, fminf(f.x, f.y));
+            d = make_float2(sqrt_apx(q.x), sqrt_apx(q.y));
+        } else {
+            d = __ffma2_rn(v, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));   // 1 - x^.y^
+            dmin = fminf(dmin, fminf(d.x, d.y));
+        }
+        if (i & 1) acc1 = __ffma2_rn(make_float2(wn.x, wn.y), d, acc1);
+        else acc0 = __ffma2_rn(make_float2(wn.x, wn.y), d, acc0);
+    }
+    if (METRIC == SILH_COSINE) flagmin = fminf(flagmin, dmin - tau);
+    part += (acc0.x + acc0.y) + (acc1.x + acc1.y);
+}
+
 // Column layout: cluster j occupies padded columns [poff[j], poff[j+1]), its
 // |F_j| sampled columns first, then zero columns of weight 0 up to a multiple
 // of 32, so every 32-column chunk belongs to exactly one cluster.
@@ -137,7 +169,9 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     __shared__ uint64_t bar_afull, bar_aempty, bar_accf[C::SLOTS][2], bar_acce[C::SLOTS][2];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
-    __shared__ __align__(16) float2 sh_wn[C::SLOTS][2][kTileN];
+    // (w, |y|^2) of the current tile's columns, two columns per float4 as
+    // (w_2i, w_2i+1, n_2i, n_2i+1) so that the epilogue reads lane pairs
+    __shared__ __align__(16) float4 sh_wn[C::SLOTS][2][kTileN / 2];
 
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -224,6 +258,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = BF ? idesc_bf16(kTileM, kTileN) : idesc_tf32(kTileM, kTileN);
+            const uint64_t adesc0 = sw128_kmajor_desc(smem_u32(sA));
+            const uint64_t bdesc0 = sw128_kmajor_desc(smem_u32(sB));
             int stage = 0;
             uint32_t phase = 0, acc = 0, acc_phase = 0;
             int64_t idx = 0;
@@ -237,8 +273,12 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         abort_flag = 1;
                         break;
                     }
-                    const uint8_t *b = sB + stage * C::B_BYTES;
+                    // descriptors differ from the stage / slot bases only in the
+                    // start-address field (bits 0-13, address >> 4), so each one
+                    // is a base plus a compile-time offset
+                    const uint64_t bd = bdesc0 + (uint64_t)((stage * C::B_BYTES) >> 4);
                     bool ok = true;
+#pragma unroll
                     for (int g = 0; g < C::SLOTS; ++g) {
                         if (!mbar_wait(&bar_acce[g][acc], acc_phase ^ 1u, kWaitNs)) {
                             ok = false;
@@ -246,34 +286,32 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         }
                         fence_after_sync();
                         const uint32_t d_tmem = tmem + (uint32_t)(g * 2 + acc) * kTileN;
-                        const uint8_t *a = sA + g * C::A_SLOT;
-                        uint32_t accumulate = 0;
+                        const uint64_t ad = adesc0 + (uint64_t)((g * C::A_SLOT) >> 4);
 #pragma unroll
                         for (int kb = 0; kb < C::KB; ++kb) {
 #pragma unroll
                             for (int ks = 0; ks < C::KSTEPS; ++ks) {
-                                const uint32_t off = ks * 32;
-                                const uint64_t ahi =
-                                    sw128_kmajor_desc(smem_u32(a + kb * kTileM * 128) + off);
-                                const uint64_t bhi =
-                                    sw128_kmajor_desc(smem_u32(b + kb * kTileN * 128) + off);
+                                const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;
+                                const uint64_t ahi = ad + (uint64_t)((kb * kTileM * 128 + ks * 32) >> 4);
+                                const uint64_t bhi = bd + (uint64_t)((kb * kTileN * 128 + ks * 32) >> 4);
                                 if (SPLIT) {
-                                    const uint64_t alo = sw128_kmajor_desc(
-                                        smem_u32(a + (C::KB + kb) * kTileM * 128) + off);
-                                    const uint64_t blo = sw128_kmajor_desc(
-                                        smem_u32(b + (C::KB + kb) * kTileN * 128) + off);
+                                    const uint64_t alo =
+                                        ad + (uint64_t)(((C::KB + kb) * kTileM * 128 + ks * 32) >> 4);
+                                    const uint64_t blo =
+                                        bd + (uint64_t)(((C::KB + kb) * kTileN * 128 + ks * 32) >> 4);
                                     if (BF) {
-                                        mma_bf16(d_tmem, alo, bhi, idesc, accumulate);
+                                        mma_bf16(d_tmem, alo, bhi, idesc, first);
                                         mma_bf16(d_tmem, ahi, blo, idesc, 1);
+                                        mma_bf16(d_tmem, ahi, bhi, idesc, 1);
                                     } else {
-                                        mma_tf32(d_tmem, alo, bhi, idesc, accumulate);
+                                        mma_tf32(d_tmem, alo, bhi, idesc, first);
                                         mma_tf32(d_tmem, ahi, blo, idesc, 1);
+                                        mma_tf32(d_tmem, ahi, bhi, idesc, 1);
                                     }
-                                    accumulate = 1;
+                                } else {
+                                    if (BF) mma_bf16(d_tmem, ahi, bhi, idesc, first);
+                                    else mma_tf32(d_tmem, ahi, bhi, idesc, first);
                                 }
-                                if (BF) mma_bf16(d_tmem, ahi, bhi, idesc, accumulate);
-                                else mma_tf32(d_tmem, ahi, bhi, idesc, accumulate);
-                                accumulate = 1;
                             }
                         }
                         mma_commit(&bar_accf[g][acc]);
@@ -316,7 +354,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             const float *xl = BF ? xh : a_lo + (valid ? pos : 0) * KD;
             int j = 0;
             int64_t pbnd = poff[1];
-            double accd = 0.0, bmin = INFINITY;
+            double accd = 0.0;
+            RatioMin bmin;
             float accf = 0.f;                         // current cluster, this tile
             bool dead = false;
             // (weight, |y|^2) of this thread's column, fetched one tile ahead
@@ -325,7 +364,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 const float2 wn_cur = wn_next;
                 const int64_t cn = (ct + 1) * kTileN + et;
                 if (et < kTileN) wn_next = (cn < mp) ? y_wn[cn] : make_float2(0.f, 0.f);
-                if (et < kTileN) sh_wn[g][buf][et] = wn_cur;
+                if (et < kTileN) {
+                    float *f = reinterpret_cast<float *>(&sh_wn[g][buf][et >> 1]);
+                    f[et & 1] = wn_cur.x;
+                    f[2 + (et & 1)] = wn_cur.y;
+                }
                 const bool ok = !abort_flag && mbar_wait(&bar_accf[g][acc], acc_phase, kWaitNs);
                 if (epi_bar_any(g, !ok)) {      // also orders the sh_wn writes before the reads
                     abort_flag = 1;
@@ -334,7 +377,13 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 }
                 fence_after_sync();
                 const uint32_t tcol = tmem + tlane + (uint32_t)(g * 2 + acc) * kTileN;
-#pragma unroll 1
+                // The tile's 64 accumulator columns are read in four 16-column
+                // halves; each half's load is issued before the previous half's
+                // arithmetic, so the TMEM latency overlaps it.
+                uint32_t ra[16], rb[16];
+                __syncwarp();
+                tmem_ld16_issue(tcol, ra);
+#pragma unroll
                 for (int ch = 0; ch < kTileN / 32; ++ch) {
                     const int64_t c0 = ct * kTileN + ch * 32;
                     // clusters that end here (empty ones included) are complete;
@@ -342,46 +391,27 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     while (j < k && c0 == pbnd) {
                         accd += (double)accf;
                         accf = 0.f;
-                        if (j != own) bmin = fmin(bmin, accd / (double)sizes[j]);
+                        if (j != own) bmin.add(accd, (double)sizes[j]);
                         accd = 0.0;
                         ++j;
                         pbnd = (j < k) ? poff[j + 1] : LLONG_MAX;
                     }
-                    if (j >= k) continue;                 // padding beyond the last cluster
-                    const bool mine = (j == own);         // own-cluster pairs: skipped here
-                    if (__all_sync(0xffffffffu, mine)) continue;
-                    const float4 *wn4 = reinterpret_cast<const float4 *>(&sh_wn[g][buf][ch * 32]);
-                    float v[32];
+                    const bool live = j < k;              // else padding beyond the last cluster
+                    const bool mine = live && (j == own); // own-cluster pairs: skipped here
+                    const bool skip = !live || __all_sync(0xffffffffu, mine);
+                    const float4 *wn4 = &sh_wn[g][buf][ch * 16];
+                    float part = 0.f, flagmin = INFINITY;
+                    tmem_wait_16(ra);                     // first half of this chunk
                     __syncwarp();
-                    tmem_ld_32x32(tcol + ch * 32, v);
-                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-                    float flagmin = INFINITY;
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float4 wn = wn4[i];         // (w, |y|^2) of columns 2i, 2i+1
-                        float d0, d1;
-                        if (METRIC == SILH_EUCLIDEAN) {
-                            const float s0 = xn + wn.y, s1 = xn + wn.w;
-                            const float q0 = fmaf(-2.f, v[2 * i], s0);
-                            const float q1 = fmaf(-2.f, v[2 * i + 1], s1);
-                            flagmin = fminf(flagmin, fminf(fmaf(-tau, s0, q0), fmaf(-tau, s1, q1)));
-                            d0 = sqrt_apx(q0);
-                            d1 = sqrt_apx(q1);
-                        } else {
-                            d0 = 1.f - v[2 * i];
-                            d1 = 1.f - v[2 * i + 1];
-                            flagmin = fminf(flagmin, fminf(d0, d1) - tau);
-                        }
-                        if (i & 1) {
-                            a2 = fmaf(wn.x, d0, a2);
-                            a3 = fmaf(wn.z, d1, a3);
-                        } else {
-                            a0 = fmaf(wn.x, d0, a0);
-                            a1 = fmaf(wn.z, d1, a1);
-                        }
+                    tmem_ld16_issue(tcol + ch * 32 + 16, rb);
+                    if (!skip) half_chunk<METRIC>(ra, wn4, xn, tau, part, flagmin);
+                    tmem_wait_16(rb);                     // second half
+                    if (ch + 1 < kTileN / 32) {
+                        __syncwarp();
+                        tmem_ld16_issue(tcol + (ch + 1) * 32, ra);
                     }
-                    float part = (a0 + a1) + (a2 + a3);
-                    if (__any_sync(0xffffffffu, !mine && flagmin < 0.f)) {
+                    if (!skip) half_chunk<METRIC>(rb, wn4 + 8, xn, tau, part, flagmin);
+                    if (!skip && __any_sync(0xffffffffu, !mine && flagmin < 0.f)) {
                         // a lane has a close pair here: redo the chunk column by column,
                         // recomputing the flagged pairs directly from the coordinates
                         part = 0.f;
@@ -389,7 +419,9 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         for (int i = 0; i < 32; ++i) {
                             __syncwarp();
                             const float dot = tmem_ld_32x1(tcol + ch * 32 + i);
-                            const float2 wn = sh_wn[g][buf][ch * 32 + i];
+                            const float *f = reinterpret_cast<const float *>(
+                                &sh_wn[g][buf][ch * 16 + (i >> 1)]);
+                            const float2 wn = make_float2(f[i & 1], f[2 + (i & 1)]);
                             const float *yc = y_full + (c0 + i) * KD;
                             float dist;
                             if (METRIC == SILH_EUCLIDEAN) {
@@ -404,7 +436,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             part = fmaf(wn.x, dist, part);
                         }
                     }
-                    if (!mine) accf += part;
+                    if (live && !mine) accf += part;
                 }
                 fence_before_sync();
                 __syncwarp();
@@ -420,7 +452,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             while (j < k) {
                 accd += (double)accf;
                 accf = 0.f;
-                if (j != own) bmin = fmin(bmin, accd / (double)sizes[j]);
+                if (j != own) bmin.add(accd, (double)sizes[j]);
                 accd = 0.0;
                 ++j;
             }
@@ -433,7 +465,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 } else {
                     const int64_t nc = sizes[own];
                     const double a = (nc > 1) ? wown / (double)(nc - 1) : 0.0;
-                    const double b = bmin;
+                    const double b = bmin.value();
                     const double mx = fmax(a, b);
                     sv = (float)((nc > 1 && mx > 0.0) ? (b - a) / mx : 0.0);
                     av = (float)a;
@@ -484,7 +516,7 @@ k_own_direct(const float *__restrict__ a_hi, const float *__restrict__ a_lo,
             work = poff[j] + (int64_t)blockIdx.y * chunk_cols < poff[j + 1];
         if (!work) return;
     }
-    float x[RPT][KD];
+    float2 x[RPT][KD / 2];     // coordinate pairs (packed two-lane FP32 arithmetic)
     int own[RPT];
     float zx[RPT];
     int64_t pos[RPT];
@@ -494,9 +526,18 @@ k_own_direct(const float *__restrict__ a_hi, const float *__restrict__ a_lo,
         const bool valid = pos[r] < nrows;
         own[r] = valid ? a_lab[pos[r]] : -1;
 #pragma unroll
-        for (int c = 0; c < KD; ++c)
-            x[r][c] = valid ? (BF ? a_hi[pos[r] * KD + c] : a_hi[pos[r] * KD + c] + a_lo[pos[r] * KD + c])
-                            : 0.f;
+        for (int c = 0; c < KD; c += 2) {
+            float v0 = 0.f, v1 = 0.f;
+            if (valid) {
+                v0 = a_hi[pos[r] * KD + c];
+                v1 = a_hi[pos[r] * KD + c + 1];
+                if (!BF) {
+                    v0 += a_lo[pos[r] * KD + c];
+                    v1 += a_lo[pos[r] * KD + c + 1];
+                }
+            }
+            x[r][c / 2] = make_float2(v0, v1);
+        }
         zx[r] = (METRIC == SILH_COSINE && valid && a_norm[pos[r]] == 0.f) ? 0.5f : 0.f;
     }
     double acc[RPT] = {};
@@ -514,7 +555,10 @@ k_own_direct(const float *__restrict__ a_hi, const float *__restrict__ a_lo,
                 __syncthreads();
                 const float4 *src = reinterpret_cast<const float4 *>(y_full + cb * KD);
                 float4 *dst = reinterpret_cast<float4 *>(sh_y);
-                for (int q = threadIdx.x; q < nb * (KD / 4); q += 128) dst[q] = src[q];
+                for (int q = threadIdx.x; q < nb * (KD / 4); q += 128) {
+                    const float4 v = src[q];                 // staged negated: x + (-y)
+                    dst[q] = make_float4(-v.x, -v.y, -v.z, -v.w);
+                }
                 for (int q = threadIdx.x; q < BN; q += 128)
                     sh_w[q] = (q < nb) ? y_wn[cb + q] : make_float2(0.f, 0.f);
                 __syncthreads();
@@ -522,16 +566,18 @@ k_own_direct(const float *__restrict__ a_hi, const float *__restrict__ a_lo,
                 float part[RPT] = {};
                 for (int col = 0; col < nb; ++col) {
                     const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * KD);
-                    float b0[RPT] = {}, b1[RPT] = {};
+                    float2 b0[RPT], b1[RPT];
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) b0[r] = b1[r] = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int q = 0; q < KD / 4; ++q) {
                         const float4 y = y4[q];
 #pragma unroll
                         for (int r = 0; r < RPT; ++r) {
-                            const float t0 = x[r][4 * q] - y.x, t1 = x[r][4 * q + 1] - y.y;
-                            const float t2 = x[r][4 * q + 2] - y.z, t3 = x[r][4 * q + 3] - y.w;
-                            b0[r] = fmaf(t0, t0, b0[r]); b1[r] = fmaf(t1, t1, b1[r]);
-                            b0[r] = fmaf(t2, t2, b0[r]); b1[r] = fmaf(t3, t3, b1[r]);
+                            const float2 t0 = __fadd2_rn(x[r][2 * q], make_float2(y.x, y.y));
+                            const float2 t1 = __fadd2_rn(x[r][2 * q + 1], make_float2(y.z, y.w));
+                            b0[r] = __ffma2_rn(t0, t0, b0[r]);
+                            b1[r] = __ffma2_rn(t1, t1, b1[r]);
                         }
                     }
                     const float2 wn = sh_w[col];
@@ -539,9 +585,9 @@ k_own_direct(const float *__restrict__ a_hi, const float *__restrict__ a_lo,
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
                         // zero vectors sit at cosine distance 1 from everything
-                        const float dist = (METRIC == SILH_EUCLIDEAN)
-                                               ? sqrt_apx(b0[r] + b1[r])
-                                               : 0.5f * (b0[r] + b1[r]) + zx[r] + zy;
+                        const float q2 = (b0[r].x + b0[r].y) + (b1[r].x + b1[r].y);
+                        const float dist = (METRIC == SILH_EUCLIDEAN) ? sqrt_apx(q2)
+                                                                      : 0.5f * q2 + zx[r] + zy;
                         part[r] = fmaf(wn.x, dist, part[r]);
                     }
                 }
