@@ -28,6 +28,23 @@ silh_status fail(silh_status st, const char *fmt, ...) {
     return st;
 }
 
+bool device_accessible(const void *p) {
+    if (p == nullptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return true;
+    // page-locked host memory counts only when it is mapped at the same address
+    return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
+bool sample_accessible(const silh_sample *S) {
+    return S != nullptr && device_accessible(S->sizes) && device_accessible(S->offsets) &&
+           (S->size == 0 || (device_accessible(S->idx) && device_accessible(S->p)));
+}
+
 void ensure_pool_retains(int device) {
     static std::mutex mu;
     static bool done[64] = {false};

@@ -64,6 +64,22 @@ struct Scratch {
     }
 };
 
+// True when p is memory a kernel may read or write: device, managed, or
+// page-locked host memory (mapped into the unified address space).  Plain
+// pageable host memory and null are not.
+bool device_accessible(const void *p);
+
+// The arrays of a sample set (sizes, offsets, and idx / p when non-empty).
+bool sample_accessible(const silh_sample *S);
+
+// A caller pointer that must be kernel-accessible (SILH_EINVAL otherwise);
+// nullable ones are checked only when non-null.
+#define SILH_DEVPTR(ptr, name) \
+    SILH_REQ(::silh::device_accessible(ptr), "%s is not device-accessible memory", name)
+#define SILH_DEVPTR_OPT(ptr, name) \
+    SILH_REQ((ptr) == nullptr || ::silh::device_accessible(ptr), \
+             "%s is not device-accessible memory", name)
+
 // Keep freed scratch cached in the device's default pool between calls.
 void ensure_pool_retains(int device);
 

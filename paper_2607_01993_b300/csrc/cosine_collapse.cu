@@ -259,6 +259,13 @@ extern "C" silh_status silh_estimate_cosine_collapsed(
     SILH_REQ(S->size >= 0 && S->size <= S->cap && (S->size == 0 || (S->idx && S->p)),
              "bad sample size");
     SILH_REQ(s_hat, "s_hat is null");
+    SILH_DEVPTR(X, "X");
+    SILH_DEVPTR(labels, "labels");
+    SILH_REQ(sample_accessible(S), "sample arrays are not device-accessible memory");
+    SILH_DEVPTR(s_hat, "s_hat");
+    SILH_DEVPTR_OPT(a_hat, "a_hat");
+    SILH_DEVPTR_OPT(b_hat, "b_hat");
+    SILH_DEVPTR_OPT(rows, "rows");
     if (rows == nullptr) nrows = n;
     SILH_REQ(nrows >= 0, "nrows < 0");
     SILH_CK(cudaGetDevice(&dev));

@@ -887,6 +887,8 @@ static silh_status check_data_args(const void *X, silh_dtype dtype, int64_t n, i
                                    int64_t ld, const int32_t *labels, int32_t k,
                                    silh_metric metric, silh_prec prec) {
     if (!X || !labels) return fail(SILH_EINVAL, "null pointer argument");
+    if (!device_accessible(X)) return fail(SILH_EINVAL, "X is not device-accessible memory");
+    if (!device_accessible(labels)) return fail(SILH_EINVAL, "labels is not device-accessible memory");
     if (n < 2 || n >= (int64_t(1) << 31)) return fail(SILH_EINVAL, "n must be in [2, 2^31)");
     if (d < 1 || d > 128 || ld < d) return fail(SILH_EINVAL, "need 1 <= d <= 128 and ld >= d");
     if (k < 2 || k > SILH_MAX_K) return fail(SILH_EINVAL, "k must be in [2, %d]", SILH_MAX_K);
@@ -913,6 +915,11 @@ extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n,
     m = S->size;
     SILH_REQ(m >= 0 && m <= S->cap && (m == 0 || (S->idx && S->p)), "bad sample size");
     SILH_REQ(s_hat, "s_hat is null");
+    SILH_REQ(sample_accessible(S), "sample arrays are not device-accessible memory");
+    SILH_DEVPTR(s_hat, "s_hat");
+    SILH_DEVPTR_OPT(a_hat, "a_hat");
+    SILH_DEVPTR_OPT(b_hat, "b_hat");
+    SILH_DEVPTR_OPT(rows, "rows");
     if (rows == nullptr) nrows = n;
     SILH_REQ(nrows >= 0, "nrows < 0");
     SILH_CK(cudaGetDevice(&dev));
@@ -950,6 +957,10 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     double *W = nullptr;
     float *Y = nullptr, *wY = nullptr, *zY = nullptr;
     SILH_REQ(s, "s is null");
+    SILH_DEVPTR(s, "s");
+    SILH_DEVPTR_OPT(a, "a");
+    SILH_DEVPTR_OPT(b, "b");
+    SILH_DEVPTR_OPT(rows, "rows");
     if (rows == nullptr) nrows = n;
     SILH_REQ(nrows >= 0, "nrows < 0");
     SILH_CK(cudaGetDevice(&dev));
@@ -1007,6 +1018,7 @@ extern "C" silh_status silh_estimate_batched(const void *X, silh_dtype dtype, in
     std::vector<BatchParams> parts;
     std::vector<int32_t> order;
     SILH_REQ(X && items, "null pointer argument");
+    SILH_DEVPTR(X, "X");
     SILH_REQ(n >= 2 && n < (int64_t(1) << 31), "n must be in [2, 2^31)");
     SILH_REQ(d >= 1 && d <= 128 && ld >= d, "need 1 <= d <= 128 and ld >= d");
     SILH_REQ(metric >= SILH_EUCLIDEAN && metric <= SILH_CANBERRA, "unknown metric");
@@ -1038,6 +1050,9 @@ extern "C" silh_status silh_estimate_batched(const void *X, silh_dtype dtype, in
                      "item %d: bad sample", c0 + i);
             SILH_REQ(S->size >= 1 && S->size <= S->cap && S->idx && S->p, "item %d: empty sample",
                      c0 + i);
+            SILH_REQ(device_accessible(src.labels) && device_accessible(src.s_hat) &&
+                         sample_accessible(S),
+                     "item %d: buffers are not device-accessible memory", c0 + i);
             BatchItem &it = b.items[i];
             it.labels = src.labels;
             it.sizes = S->sizes;
@@ -1093,6 +1108,8 @@ extern "C" silh_status silh_cohsep(const void *X, silh_dtype dtype, int64_t n, i
     SILH_REQ(S && S->k == k && S->sizes && S->offsets && out, "sample or output missing");
     m = S->size;
     SILH_REQ(m >= 0 && m <= S->cap && (m == 0 || (S->idx && S->p)), "bad sample size");
+    SILH_REQ(sample_accessible(S), "sample arrays are not device-accessible memory");
+    SILH_DEVPTR(out, "out");
     SILH_CK(sc.alloc(&Y, (size_t)m * D));
     SILH_CK(sc.alloc(&wY, (size_t)m));
     SILH_CK(sc.alloc(&zY, (size_t)m));
@@ -1142,6 +1159,8 @@ extern "C" silh_status silh_global(const float *s, int64_t n, double *out, void 
     int np = 0;
     SILH_REQ(s && out, "null pointer argument");
     SILH_REQ(n >= 1, "n must be >= 1");
+    SILH_DEVPTR(s, "s");
+    SILH_DEVPTR(out, "out");
     np = (int)std::min<int64_t>(1024, (n + kSumThreads - 1) / kSumThreads);
     SILH_CK(sc.alloc(&part, np));
     k_sum_partial<<<np, kSumThreads, 0, stream>>>(s, n, part); count_launches(1);

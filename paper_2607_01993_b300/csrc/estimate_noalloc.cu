@@ -80,6 +80,13 @@ extern "C" silh_status silh_estimate_noalloc(const void *X, silh_dtype dtype, in
     m = S->size;
     SILH_REQ(m >= 0 && m <= S->cap && (m == 0 || (S->idx && S->p)), "bad sample size");
     SILH_REQ(s_hat, "s_hat is null");
+    SILH_DEVPTR(X, "X");
+    SILH_DEVPTR(labels, "labels");
+    SILH_REQ(sample_accessible(S), "sample arrays are not device-accessible memory");
+    SILH_DEVPTR(s_hat, "s_hat");
+    SILH_DEVPTR_OPT(a_hat, "a_hat");
+    SILH_DEVPTR_OPT(b_hat, "b_hat");
+    SILH_DEVPTR_OPT(rows, "rows");
     D = padded_dim(d);
     if (m > kNoAllocMaxColumns || m * D > kNoAllocMaxFloats) {
         st = fail(SILH_ECAPACITY,

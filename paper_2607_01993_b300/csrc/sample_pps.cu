@@ -574,6 +574,12 @@ extern "C" silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t 
     SILH_REQ(t > 0.0 && std::isfinite(t), "t must be positive");
     SILH_REQ(metric >= SILH_EUCLIDEAN && metric <= SILH_CANBERRA, "unknown metric");
     SILH_REQ(dtype == SILH_F32 || dtype == SILH_BF16, "unknown dtype");
+    SILH_DEVPTR(X, "X");
+    SILH_DEVPTR(labels, "labels");
+    SILH_DEVPTR(out->sizes, "sample sizes");
+    SILH_DEVPTR(out->offsets, "sample offsets");
+    SILH_DEVPTR(out->idx, "sample idx");
+    SILH_DEVPTR(out->p, "sample p");
     if (!(m0 > 0.0)) {
         SILH_REQ(delta > 0.0 && delta < 1.0, "delta must be in (0, 1)");
         m0 = 2.0 * std::log(5.0 * (double)k / delta);

@@ -422,3 +422,44 @@ def test_cosine_collapsed_degenerate_bf16_and_rows():
         rows = torch.tensor([10, 0, 650, 599, 10], dtype=torch.int64, device=Xt.device)
         sr = silh.silh_estimate_cosine_collapsed(Xt, lt, k, gs, rows=rows)
         assert torch.equal(sr, s[rows])
+
+
+# ------------------------------------------------------ boundary checks
+
+def test_pageable_host_buffers_are_rejected_before_any_launch():
+    """A pageable host pointer in place of device memory is SILH_EINVAL, with
+    nothing launched (the check is on the host, before the first kernel)."""
+    import ctypes
+    lib = silh.load()
+    X, lab, k, _ = _case("tiny")
+    Xt, lt = _to_dev(X, lab)
+    n, d = X.shape
+    gs = silh.silh_sample_pps(Xt, lt, k, "euclidean", t=64.0, m0=16.0, seed=0)
+    torch.cuda.synchronize()
+    Xh = np.ascontiguousarray(X, dtype=np.float32)
+    lh = np.ascontiguousarray(lab, dtype=np.int32)
+    sh = np.zeros(n, dtype=np.float32)
+    s = torch.empty(n, dtype=torch.float32, device="cuda")
+    g = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = gs.as_struct()
+    launches = silh.kernel_launches()
+    cases = [
+        lib.silh_estimate(Xh.ctypes.data, 0, n, d, d, lt.data_ptr(), k, 0, 0, ctypes.byref(st),
+                          None, 0, s.data_ptr(), None, None, None),
+        lib.silh_estimate(Xt.data_ptr(), 0, n, d, d, lh.ctypes.data, k, 0, 0, ctypes.byref(st),
+                          None, 0, s.data_ptr(), None, None, None),
+        lib.silh_estimate(Xt.data_ptr(), 0, n, d, d, lt.data_ptr(), k, 0, 0, ctypes.byref(st),
+                          None, 0, sh.ctypes.data, None, None, None),
+        lib.silh_exact(Xh.ctypes.data, 0, n, d, d, lt.data_ptr(), k, 0, 0, None, 0,
+                       s.data_ptr(), None, None, None),
+        lib.silh_global(sh.ctypes.data, n, g.data_ptr(), None),
+        lib.silh_global(s.data_ptr(), n, sh.ctypes.data, None),
+    ]
+    assert all(rc == -1 for rc in cases), cases
+    assert b"device-accessible" in lib.silh_last_error()
+    smp = silh.Sample.empty(k, n, "cuda")
+    st2 = smp.as_struct()
+    rc = lib.silh_sample_pps(Xh.ctypes.data, 0, n, d, d, lt.data_ptr(), k, 0, 64.0, 16.0, 0.01,
+                             0, 0, 0, ctypes.byref(st2), None)
+    assert rc == -1
+    assert silh.kernel_launches() == launches
