@@ -326,16 +326,21 @@ def dist_evals(res, t_step_samples):
 
 def _profiled_traffic(kernel_key):
     """DRAM bytes per full launch from a committed ncu capture, or None when the
-    kernel source has changed since the counters were taken."""
+    kernel's source section (between the recorded markers) has changed since
+    the counters were taken."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel_key)
         if rec is None:
             return None
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            if hashlib.sha1(f.read()).hexdigest() != rec["source_sha1"]:
-                return None
+        with open(os.path.join(ROOT, rec["source"])) as f:
+            text = f.read()
+        start, end = rec["region"]
+        i = text.index(start)
+        j = text.index(end, i)
+        if hashlib.sha1(text[i:j].encode()).hexdigest() != rec["region_sha1"]:
+            return None
         return rec["bytes_per_launch_full"]
     except (OSError, ValueError, KeyError):
         return None
