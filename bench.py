@@ -350,12 +350,14 @@ def roofline(res, peaks, peak_kind):
     """Dominant kernel: the Phase-2 sweep of the metric with the longest leg.
 
     Algorithmic FP32-pipe work per pair (d = 32 coordinates): euclidean 2d
-    (sub, fma) + sqrt, cosine d (fma), manhattan 2d (sub, add), canberra 3.5d
-    FP32 + d/2 reciprocals; the reported unit is FP32 lane-operations.
+    (sub, fma) + sqrt, cosine d (fma), manhattan 2d (sub, add), canberra 4d + 1
+    (per coordinate x - y and |x| + |y|; per coordinate pair n1 d2, + n2 d1,
+    d1 d2 and the FMA of num / den into the sum; plus the weight FMA) with d/2
+    reciprocals on the MUFU pipe; the reported unit is FP32 lane-operations.
     """
     d = res["d"]
     per_pair = {"euclidean": 2 * d + 2, "cosine": d + 3, "manhattan": 2 * d + 1,
-                "canberra": 3.5 * d + 1}
+                "canberra": 4 * d + 1}
     mean_p2 = {m: float(np.mean(res["legs"][m]["phase2"])) for m in METRICS}
     dom = max(mean_p2, key=mean_p2.get)
     S = res["info"]["sample_size"][dom]
