@@ -579,6 +579,29 @@ void launch_sweep_m(int metric, int D, cudaStream_t stream, const T *X, int d, i
 // for the row's cluster (reduced over the CTA's rows with warp shuffles and
 // shared memory).  Both land in the n x k FP64 weight matrix W with atomic
 // adds (so results are reproducible to rounding order, not bitwise).
+// Sums over the 32 lanes of CB per-lane values at once: halving exchanges
+// (lanes below / above the offset keep the lower / upper half of the values)
+// leave each lane one partial sum of column `col`, which plain butterfly steps
+// then complete; lanes whose low log2(32 / CB) bits are zero hold the totals.
+template <int CB>
+__device__ __forceinline__ float transpose_reduce(float (&cs)[CB], int lane, int &col) {
+    int base = 0, o = 16;
+#pragma unroll
+    for (int w = CB; w > 1; w >>= 1, o >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int h = 0; h < w / 2; ++h) {
+            const float send = up ? cs[h] : cs[h + w / 2];
+            cs[h] = (up ? cs[h + w / 2] : cs[h]) + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+        if (up) base += w / 2;
+    }
+#pragma unroll
+    for (; o > 0; o >>= 1) cs[0] += __shfl_xor_sync(0xffffffffu, cs[0], o);
+    col = base;
+    return cs[0];
+}
+
 template <int METRIC, int D, int RPT>
 __global__ void __launch_bounds__(kThreads)
 k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
@@ -641,12 +664,15 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
         }
         __syncthreads();
         if (!diag && cI0 == cI1) {
-            // One row cluster: the column sums are reduced across the warp eight
-            // columns at a time (transpose-reduce: 9 shuffles for 8 columns).
-            for (int col0 = 0; col0 < nb; col0 += 8) {
-                float cs[8];
+            // One row cluster: the column sums are reduced across the warp CB
+            // columns at a time (transpose-reduce: 9 shuffles for 8 columns,
+            // 6 for 4; Canberra's larger body takes 4 to stay in the
+            // instruction cache).
+            constexpr int CB = (METRIC == SILH_CANBERRA) ? 4 : 8;
+            for (int col0 = 0; col0 < nb; col0 += CB) {
+                float cs[CB];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
+                for (int c = 0; c < CB; ++c) {
                     const int col = col0 + c;
                     cs[c] = 0.f;
                     if (col < nb) {
@@ -674,28 +700,9 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
                         }
                     }
                 }
-                // lanes 0-15 keep columns 0-3, 16-31 columns 4-7; then 2, then 1
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const bool up = lane & 16;
-                    const float send = up ? cs[h] : cs[h + 4];
-                    cs[h] = (up ? cs[h + 4] : cs[h]) + __shfl_xor_sync(0xffffffffu, send, 16);
-                }
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const bool up = lane & 8;
-                    const float send = up ? cs[h] : cs[h + 2];
-                    cs[h] = (up ? cs[h + 2] : cs[h]) + __shfl_xor_sync(0xffffffffu, send, 8);
-                }
-                {
-                    const bool up = lane & 4;
-                    const float send = up ? cs[0] : cs[1];
-                    cs[0] = (up ? cs[1] : cs[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
-                }
-                cs[0] += __shfl_xor_sync(0xffffffffu, cs[0], 2);
-                cs[0] += __shfl_xor_sync(0xffffffffu, cs[0], 1);
-                const int mine = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                if ((lane & 3) == 0 && col0 + mine < nb) sh_col[warp][col0 + mine] = cs[0];
+                int mine = 0;
+                const float tot = transpose_reduce<CB>(cs, lane, mine);
+                if ((lane & (32 / CB - 1)) == 0 && col0 + mine < nb) sh_col[warp][col0 + mine] = tot;
             }
         } else {
             // Diagonal tile (row sums only), or rows of several clusters (a tile
