@@ -115,7 +115,8 @@ def _ptr(t):
 
 
 def _data(X):
-    if not X.is_cuda or X.dim() != 2 or X.stride(1) != 1 or X.dtype not in DTYPES:
+    if (not X.is_cuda or X.dim() != 2 or (X.stride(1) != 1 and X.shape[1] > 1)
+            or X.stride(0) < X.shape[1] or X.dtype not in DTYPES):
         raise ValueError("X must be a 2-D CUDA float32/bfloat16 tensor with unit column stride")
     return DTYPES[X.dtype], X.shape[0], X.shape[1], X.stride(0)
 
@@ -132,6 +133,21 @@ def _rows(rows):
     if not rows.is_cuda or rows.dtype != torch.int64 or not rows.is_contiguous():
         raise ValueError("rows must be a contiguous CUDA int64 tensor")
     return rows, rows.shape[0]
+
+
+def _out(out, nrows, device):
+    """A caller output tensor must hold nrows float32 values on the device."""
+    if out is None:
+        return torch.empty(nrows, dtype=torch.float32, device=device)
+    if (not out.is_cuda or out.dtype != torch.float32 or not out.is_contiguous()
+            or out.numel() < nrows):
+        raise ValueError(f"out must be a contiguous CUDA float32 tensor of >= {nrows} elements")
+    return out
+
+
+def _empty_rows(rows, nr):
+    """An empty row list: nothing to compute (a null pointer would mean all rows)."""
+    return rows is not None and nr == 0
 
 
 @dataclass
@@ -192,9 +208,11 @@ def silh_estimate(X, labels, k, sample: Sample, metric="euclidean", prec="fp32",
     labels = _labels(labels)
     rows, nr = _rows(rows)
     nrows = n if rows is None else nr
-    s = out if out is not None else torch.empty(nrows, dtype=torch.float32, device=X.device)
+    s = _out(out, nrows, X.device)
     a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
     b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    if _empty_rows(rows, nr):
+        return (s, a, b) if want_ab else s
     st = sample.as_struct()
     _check(lib.silh_estimate(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric],
                              PRECS[prec], ctypes.byref(st), _ptr(rows), nr, _ptr(s), _ptr(a),
@@ -214,9 +232,11 @@ def silh_estimate_noalloc(X, labels, k, sample: Sample, metric="euclidean", prec
     labels = _labels(labels)
     rows, nr = _rows(rows)
     nrows = n if rows is None else nr
-    s = out if out is not None else torch.empty(nrows, dtype=torch.float32, device=X.device)
+    s = _out(out, nrows, X.device)
     a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
     b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    if _empty_rows(rows, nr):
+        return (s, a, b) if want_ab else s
     st = sample.as_struct()
     _check(lib.silh_estimate_noalloc(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric],
                                      PRECS[prec], ctypes.byref(st), _ptr(rows), nr, _ptr(s),
@@ -232,9 +252,11 @@ def silh_estimate_cosine_collapsed(X, labels, k, sample: Sample, rows=None, want
     labels = _labels(labels)
     rows, nr = _rows(rows)
     nrows = n if rows is None else nr
-    s = out if out is not None else torch.empty(nrows, dtype=torch.float32, device=X.device)
+    s = _out(out, nrows, X.device)
     a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
     b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    if _empty_rows(rows, nr):
+        return (s, a, b) if want_ab else s
     st = sample.as_struct()
     _check(lib.silh_estimate_cosine_collapsed(_ptr(X), dt, n, d, ld, _ptr(labels), k,
                                               ctypes.byref(st), _ptr(rows), nr, _ptr(s), _ptr(a),
@@ -256,6 +278,9 @@ def silh_estimate_batched(X, items, metric="euclidean", variant=-1, outs=None, s
     dt, n, d, ld = _data(X)
     if outs is None:
         outs = [torch.empty(n, dtype=torch.float32, device=X.device) for _ in items]
+    if len(outs) != len(items):
+        raise ValueError("one output tensor per item")
+    outs = [_out(o, n, X.device) for o in outs]
     structs = [smp.as_struct() for _, smp in items]
     arr = (SilhBatchItem * len(items))()
     for i, ((labels, _), st, out) in enumerate(zip(items, structs, outs)):
@@ -278,6 +303,8 @@ def silh_exact(X, labels, k, metric="euclidean", prec="fp32", rows=None, want_ab
     s = torch.empty(nrows, dtype=torch.float32, device=X.device)
     a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
     b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    if _empty_rows(rows, nr):
+        return (s, a, b) if want_ab else s
     _check(lib.silh_exact(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric], PRECS[prec],
                           _ptr(rows), nr, _ptr(s), _ptr(a), _ptr(b), _stream(stream)))
     return (s, a, b) if want_ab else s
