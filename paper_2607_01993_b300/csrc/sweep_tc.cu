@@ -118,13 +118,13 @@ __device__ __noinline__ float direct_dist(const float *__restrict__ xh, const fl
 }
 
 // Fast-path epilogue of 16 accumulator columns (inner products r) of one row,
-// two columns per packed two-lane FP32 instruction: part += sum w d, and
-// flagmin tracks the pairs that need the direct recompute (Euclidean:
-// d^2 - tau (|x|^2 + |y|^2) < 0; cosine: d - tau < 0).  wn4 holds
-// (w_2i, w_2i+1, |y_2i|^2, |y_2i+1|^2).
+// two columns per packed two-lane FP32 instruction: part += sum w d, and the
+// sign bit of flag is set when a pair needs the direct recompute (Euclidean:
+// d^2 - tau (|x|^2 + |y|^2) < 0, OR-ed over the raw bits of that difference;
+// cosine: d - tau < 0).  wn4 holds (w_2i, w_2i+1, |y_2i|^2, |y_2i+1|^2).
 template <int METRIC>
 __device__ __forceinline__ void half_chunk(const uint32_t (&r)[16], const float4 *wn4, float xn,
-                                           float tau, float &part, float &flagmin) {
+                                           float tau, float &part, uint32_t &flag) {
     float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
     float dmin = INFINITY;
 #pragma unroll
@@ -136,7 +136,7 @@ __device__ __forceinline__ void half_chunk(const uint32_t (&r)[16], const float4
             const float2 s = __fadd2_rn(make_float2(xn, xn), make_float2(wn.z, wn.w));
             const float2 q = __ffma2_rn(make_float2(-2.f, -2.f), v, s);
             const float2 f = __ffma2_rn(make_float2(-tau, -tau), s, q);
-            flagmin = fminf(flagmin, fminf(f.x, f.y));
+            flag |= __float_as_uint(f.x) | __float_as_uint(f.y);
             d = make_float2(sqrt_apx(q.x), sqrt_apx(q.y));
         } else {
             d = __ffma2_rn(v, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));   // 1 - x^.y^
@@ -145,7 +145,7 @@ __device__ __forceinline__ void half_chunk(const uint32_t (&r)[16], const float4
         if (i & 1) acc1 = __ffma2_rn(make_float2(wn.x, wn.y), d, acc1);
         else acc0 = __ffma2_rn(make_float2(wn.x, wn.y), d, acc0);
     }
-    if (METRIC == SILH_COSINE) flagmin = fminf(flagmin, dmin - tau);
+    if (METRIC == SILH_COSINE) flag |= __float_as_uint(dmin - tau);
     part += (acc0.x + acc0.y) + (acc1.x + acc1.y);
 }
 
@@ -400,18 +400,19 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     const bool mine = live && (j == own); // own-cluster pairs: skipped here
                     const bool skip = !live || __all_sync(0xffffffffu, mine);
                     const float4 *wn4 = &sh_wn[g][buf][ch * 16];
-                    float part = 0.f, flagmin = INFINITY;
+                    float part = 0.f;
+                    uint32_t flag = 0;
                     tmem_wait_16(ra);                     // first half of this chunk
                     __syncwarp();
                     tmem_ld16_issue(tcol + ch * 32 + 16, rb);
-                    if (!skip) half_chunk<METRIC>(ra, wn4, xn, tau, part, flagmin);
+                    if (!skip) half_chunk<METRIC>(ra, wn4, xn, tau, part, flag);
                     tmem_wait_16(rb);                     // second half
                     if (ch + 1 < kTileN / 32) {
                         __syncwarp();
                         tmem_ld16_issue(tcol + (ch + 1) * 32, ra);
                     }
-                    if (!skip) half_chunk<METRIC>(rb, wn4 + 8, xn, tau, part, flagmin);
-                    if (!skip && __any_sync(0xffffffffu, !mine && flagmin < 0.f)) {
+                    if (!skip) half_chunk<METRIC>(rb, wn4 + 8, xn, tau, part, flag);
+                    if (!skip && __any_sync(0xffffffffu, !mine && (flag >> 31) != 0u)) {
                         // a lane has a close pair here: redo the chunk column by column,
                         // recomputing the flagged pairs directly from the coordinates
                         part = 0.f;
