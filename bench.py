@@ -433,7 +433,7 @@ def run_batching(args):
             "data": "synthetic", "batched_ms": round(ms_batched, 3),
             "separate_ms": round(ms_separate, 3), "speedup_vs_separate": round(ms_separate / ms_batched, 3),
             "pairs_per_s": round(pairs / (ms_batched * 1e-3), 1), "variant": variant,
-            "autotune_ms": tune_ms, "phase1_s_all": round(t_phase1, 3),
+            "autotune_ms": tune_ms, "labels_and_phase1_s_all": round(t_phase1, 3),
             "max_abs_diff_vs_separate": maxdiff,
             "config": {"workload": f"batching: n={n}, d=16 FP32, {len(items)} clusterings k=2..{ks[-1]} "
                                    f"(nearest random data-row centres), t=128, Euclidean, FP32 CUDA cores",
