@@ -516,6 +516,33 @@ def run_precision(args):
     print(json.dumps(line))
 
 
+def run_peaks(args):
+    """Measured rates of the pipes the Phase-2 kernels are bound by (FP32 FMA,
+    packed FMA, MUFU reciprocal and square root, FP32 min/max): per second for
+    the whole GPU, and per clock per SM at the SM clock sampled during the run."""
+    import torch
+    from paper_2607_01993_b300 import silh
+    torch.cuda.set_device(0)
+    silh.pipe_rates()                                   # warm-up
+    reps = 10                                           # a few seconds, so the clock is sampled
+    acc = {}
+    with ClockSampler(0) as clk:
+        for _ in range(reps):
+            for key, v in silh.pipe_rates().items():
+                acc[key] = acc.get(key, 0.0) + v / reps
+    rates = acc
+    clocks = clk.summary()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = clocks.get("sm_mhz") or _peaks()[0].get("sm_max_mhz", 2032.0)
+    line = {"metric": "arithmetic pipe rates", "unit": "lane-ops/clk/SM", "n_gpus": 1,
+            "data": "synthetic",
+            "rates_per_clk_per_sm": {k: round(v / (mhz * 1e6), 2) for k, v in rates.items()},
+            "gpu_rates_per_s": {k: round(v * nsm, 1) for k, v in rates.items()},
+            "clocks": clocks,
+            "config": {"workload": "pipe microbenchmarks", "sms": nsm, "clock_mhz_used": mhz}}
+    print(json.dumps(line))
+
+
 def run_serving(args):
     """Serving workload: Poisson streams of silhouette requests over 64 resident
     datasets (n log-uniform 5k-2M, d in {8,16,64,128}, FP32/BF16), k uniform
@@ -601,7 +628,7 @@ def main():
     ap.add_argument("--metrics", default=",".join(METRICS),
                     help="comma-separated subset of metrics (profiling cases only)")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "batching", "serving", "precision"],
+                    choices=["large", "batching", "serving", "precision", "peaks"],
                     help="large: the default step; batching: 256 clusterings in one launch; "
                          "serving: Poisson request streams; precision: error and time per "
                          "precision mode at n = 4M, BF16 storage")
@@ -619,6 +646,9 @@ def main():
         return
     if args.workload == "precision":
         run_precision(args)
+        return
+    if args.workload == "peaks":
+        run_peaks(args)
         return
     METRICS = tuple(m for m in args.metrics.split(",") if m)
 

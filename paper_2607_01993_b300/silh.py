@@ -27,7 +27,7 @@ SILH_ECAPACITY = -4
 EXPORTS = ("silh_sample_pps", "silh_estimate", "silh_exact", "silh_global", "silh_t_from_eps",
            "silh_last_error", "silh_version", "silh_kernel_launches", "silh_estimate_noalloc",
            "silh_stream_status", "silh_estimate_batched", "silh_cohsep",
-           "silh_estimate_cosine_collapsed")
+           "silh_estimate_cosine_collapsed", "silh_pipe_rates")
 SILH_NOALLOC_MAX_COLUMNS = 65536
 SILH_NOALLOC_MAX_FLOATS = 2097152
 
@@ -89,6 +89,8 @@ def load(path: str = LIB_PATH):
                                                    ctypes.POINTER(SilhSample), vp, i64, vp, vp,
                                                    vp, vp]
     lib.silh_estimate_cosine_collapsed.restype = ctypes.c_int
+    lib.silh_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
+    lib.silh_pipe_rates.restype = ctypes.c_int
     lib.silh_cohsep.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32, ctypes.c_int,
                                 ctypes.POINTER(SilhSample), vp, vp]
     lib.silh_cohsep.restype = ctypes.c_int
@@ -262,6 +264,14 @@ def silh_estimate_cosine_collapsed(X, labels, k, sample: Sample, rows=None, want
                                               ctypes.byref(st), _ptr(rows), nr, _ptr(s), _ptr(a),
                                               _ptr(b), _stream(stream)))
     return (s, a, b) if want_ab else s
+
+
+def pipe_rates(stream=None):
+    """Measured lane-operations per second per SM of the arithmetic pipes."""
+    lib = load()
+    out = (ctypes.c_double * 5)()
+    _check(lib.silh_pipe_rates(out, _stream(stream)))
+    return dict(zip(("ffma", "ffma2_lanes", "mufu_rcp", "mufu_sqrt", "fmnmx"), list(out)))
 
 
 BATCH_VARIANTS = 4   # tile shapes of the batched sweep (see include/silh.h)
