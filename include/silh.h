@@ -243,8 +243,8 @@ const char *silh_version(void);
 /* Measured arithmetic rates of the current device, in lane-operations per
  * second per SM (device wall-clock time): out[0] FP32 FMA, out[1] packed
  * two-lane FP32 FMA (lanes), out[2] MUFU reciprocal (rcp.approx), out[3] MUFU
- * square root (sqrt.approx), out[4] FP32 min/max.  Divide by the SM clock for
- * per-clock figures.  out: host array of 5 doubles.
+ * square root (sqrt.approx), out[4] FP32 min/max, out[5] FP64 FMA.  Divide by
+ * the SM clock for per-clock figures.  out: host array of 6 doubles.
  * Synchronous.  Diagnostic with no counterpart in the paper: the bounds of the
  * Phase-2 kernels are stated in these units. */
 silh_status silh_pipe_rates(double *out, void *stream);

@@ -269,9 +269,9 @@ def silh_estimate_cosine_collapsed(X, labels, k, sample: Sample, rows=None, want
 def pipe_rates(stream=None):
     """Measured lane-operations per second per SM of the arithmetic pipes."""
     lib = load()
-    out = (ctypes.c_double * 5)()
+    out = (ctypes.c_double * 6)()
     _check(lib.silh_pipe_rates(out, _stream(stream)))
-    return dict(zip(("ffma", "ffma2_lanes", "mufu_rcp", "mufu_sqrt", "fmnmx"), list(out)))
+    return dict(zip(("ffma", "ffma2_lanes", "mufu_rcp", "mufu_sqrt", "fmnmx", "dfma"), list(out)))
 
 
 BATCH_VARIANTS = 4   # tile shapes of the batched sweep (see include/silh.h)
