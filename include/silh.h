@@ -228,6 +228,9 @@ silh_status silh_global(const float *s, int64_t n, double *out, void *stream);
  * of the library gave up since the previous call (SILH_ETIMEOUT; the results
  * of the affected call are then incomplete) and clears that record.  Kernels
  * never trap or spin without limit; this is how a stalled pipeline surfaces.
+ * The record is one per device and process: with calls in flight on several
+ * streams, a timeout is reported to whichever caller checks first, so a
+ * multi-stream caller treats SILH_ETIMEOUT as "some call since the last check".
  * Synchronising. */
 silh_status silh_stream_status(void *stream);
 
