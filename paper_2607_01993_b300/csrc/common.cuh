@@ -20,14 +20,18 @@ namespace silh {
 void set_error(const char *fmt, ...);
 silh_status fail(silh_status st, const char *fmt, ...);
 
-#define SILH_CK(call)                                                               \
-    do {                                                                            \
-        cudaError_t e_ = (call);                                                    \
-        if (e_ != cudaSuccess) {                                                    \
-            st = ::silh::fail(SILH_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, \
-                              cudaGetErrorString(e_));                              \
-            goto done;                                                              \
-        }                                                                           \
+// A failed CUDA call: SILH_ENOMEM when the device is out of memory (the error
+// is cleared, the context stays usable), SILH_ECUDA otherwise.
+#define SILH_CK(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            if (e_ == cudaErrorMemoryAllocation) cudaGetLastError();                       \
+            st = ::silh::fail(e_ == cudaErrorMemoryAllocation ? SILH_ENOMEM : SILH_ECUDA,   \
+                              "%s:%d %s: %s", __FILE__, __LINE__, #call,                   \
+                              cudaGetErrorString(e_));                                     \
+            goto done;                                                                     \
+        }                                                                                  \
     } while (0)
 
 #define SILH_REQ(cond, ...)                                   \

@@ -117,3 +117,27 @@ def test_empty_row_list_and_short_outputs():
         silh.silh_estimate(Xt, lt, 4, gs, "euclidean", out=short)
     with pytest.raises(ValueError):
         silh.silh_estimate_batched(Xt, [(lt, gs)], "euclidean", outs=[short])
+
+
+def test_scratch_exhaustion_is_enomem_and_the_context_survives():
+    """A sample whose column operand cannot fit in device memory (its stated
+    size, 2^40 columns, is checked before anything is launched) returns
+    SILH_ENOMEM; the next call on the same context works."""
+    import ctypes
+    lib = silh.load()
+    X, lab, _ = synth.tiny(seed=0)
+    Xt, lt = _to_dev(X, lab)
+    n, d = X.shape
+    gs = silh.silh_sample_pps(Xt, lt, 4, "manhattan", t=64.0, m0=16.0, seed=0)
+    torch.cuda.synchronize()
+    huge = silh.SilhSample(4, gs.sizes.data_ptr(), gs.offsets.data_ptr(), gs.idx.data_ptr(),
+                           gs.p.data_ptr(), 1 << 40, 1 << 40)
+    s = torch.empty(n, dtype=torch.float32, device="cuda")
+    launches = silh.kernel_launches()
+    rc = lib.silh_estimate(Xt.data_ptr(), 0, n, d, d, lt.data_ptr(), 4, 2, 0, ctypes.byref(huge),
+                           None, 0, s.data_ptr(), None, None, None)
+    assert rc == -2, (rc, lib.silh_last_error())
+    assert silh.kernel_launches() == launches
+    s2 = silh.silh_estimate(Xt, lt, 4, gs, "manhattan")
+    torch.cuda.synchronize()
+    assert torch.isfinite(s2).all()
