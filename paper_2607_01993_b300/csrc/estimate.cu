@@ -665,10 +665,10 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
         __syncthreads();
         if (!diag && cI0 == cI1) {
             // One row cluster: the column sums are reduced across the warp CB
-            // columns at a time (transpose-reduce: 9 shuffles for 8 columns,
+            // columns at a time (transpose-reduce: 16 shuffles for 16 columns,
             // 6 for 4; Canberra's larger body takes 4 to stay in the
             // instruction cache).
-            constexpr int CB = (METRIC == SILH_CANBERRA) ? 4 : 8;
+            constexpr int CB = (METRIC == SILH_CANBERRA) ? 4 : 16;
             for (int col0 = 0; col0 < nb; col0 += CB) {
                 float cs[CB];
 #pragma unroll
