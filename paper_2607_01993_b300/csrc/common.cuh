@@ -106,6 +106,31 @@ struct RatioMin {
     __device__ __forceinline__ double value() const { return acc / size; }
 };
 
+// ----------------------------------------------- warp column reduction
+
+// Sums over the 32 lanes of CB per-lane values at once: halving exchanges
+// (lanes below / above the offset keep the lower / upper half of the values)
+// leave each lane one partial sum of column `col`, which plain butterfly steps
+// then complete; lanes whose low log2(32 / CB) bits are zero hold the totals.
+template <int CB>
+__device__ __forceinline__ float transpose_reduce(float (&cs)[CB], int lane, int &col) {
+    int base = 0, o = 16;
+#pragma unroll
+    for (int w = CB; w > 1; w >>= 1, o >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int h = 0; h < w / 2; ++h) {
+            const float send = up ? cs[h] : cs[h + w / 2];
+            cs[h] = (up ? cs[h + w / 2] : cs[h]) + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+        if (up) base += w / 2;
+    }
+#pragma unroll
+    for (; o > 0; o >>= 1) cs[0] += __shfl_xor_sync(0xffffffffu, cs[0], o);
+    col = base;
+    return cs[0];
+}
+
 // ----------------------------------------------------------- Philox4x64-10
 
 // Salmon et al., "Parallel random numbers: as easy as 1, 2, 3" (SC'11):

@@ -579,29 +579,6 @@ void launch_sweep_m(int metric, int D, cudaStream_t stream, const T *X, int d, i
 // for the row's cluster (reduced over the CTA's rows with warp shuffles and
 // shared memory).  Both land in the n x k FP64 weight matrix W with atomic
 // adds (so results are reproducible to rounding order, not bitwise).
-// Sums over the 32 lanes of CB per-lane values at once: halving exchanges
-// (lanes below / above the offset keep the lower / upper half of the values)
-// leave each lane one partial sum of column `col`, which plain butterfly steps
-// then complete; lanes whose low log2(32 / CB) bits are zero hold the totals.
-template <int CB>
-__device__ __forceinline__ float transpose_reduce(float (&cs)[CB], int lane, int &col) {
-    int base = 0, o = 16;
-#pragma unroll
-    for (int w = CB; w > 1; w >>= 1, o >>= 1) {
-        const bool up = lane & o;
-#pragma unroll
-        for (int h = 0; h < w / 2; ++h) {
-            const float send = up ? cs[h] : cs[h + w / 2];
-            cs[h] = (up ? cs[h + w / 2] : cs[h]) + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-        if (up) base += w / 2;
-    }
-#pragma unroll
-    for (; o > 0; o >>= 1) cs[0] += __shfl_xor_sync(0xffffffffu, cs[0], o);
-    col = base;
-    return cs[0];
-}
-
 template <int METRIC, int D, int RPT>
 __global__ void __launch_bounds__(kThreads)
 k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
@@ -977,8 +954,15 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     if (st != SILH_OK) goto done;
     if (nrows > 0 && tc_eligible(metric, prec, d)) {
         const int64_t maxc = *std::max_element(h_sizes.begin(), h_sizes.end());
-        st = tc_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, order, nullptr, n,
-                      maxc, rows, nrows, s, a, b, sc, stream);
+        if (rows == nullptr &&
+            (double)(n + 31.0 * k) * (double)k * 8.0 <= 4294967296.0) {
+            // all points: each pair once, row and column sums into an FP64 matrix
+            st = tc_exact_sym(X, dtype, n, d, ld, k, metric, prec, sizes, coff, order, maxc, s, a,
+                              b, sc, stream);
+        } else {
+            st = tc_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, order, nullptr,
+                          n, maxc, rows, nrows, s, a, b, sc, stream);
+        }
         goto done;
     }
     SILH_CK(sc.alloc(&Y, (size_t)n * D));

@@ -149,10 +149,55 @@ __device__ __forceinline__ void half_chunk(const uint32_t (&r)[16], const float4
     part += (acc0.x + acc0.y) + (acc1.x + acc1.y);
 }
 
+// half_chunk for the symmetric exact sweep: also returns, for the column
+// `col` this lane ends up holding, the sum over the warp's 32 rows of d times
+// the row weight rw (1 for a point, 0 for padding) -- the column side of the
+// pairs; lanes with an odd index hold a duplicate.
+template <int METRIC>
+__device__ __forceinline__ float half_chunk_sym(const uint32_t (&r)[16], const float4 *wn4,
+                                                float xn, float tau, float rw, int lane,
+                                                float &part, uint32_t &flag, int &col) {
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    float cs[16];
+    float dmin = INFINITY;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 wn = wn4[i];
+        const float2 v = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+        float2 d;
+        if (METRIC == SILH_EUCLIDEAN) {
+            const float2 s = __fadd2_rn(make_float2(xn, xn), make_float2(wn.z, wn.w));
+            const float2 q = __ffma2_rn(make_float2(-2.f, -2.f), v, s);
+            const float2 f = __ffma2_rn(make_float2(-tau, -tau), s, q);
+            flag |= __float_as_uint(f.x) | __float_as_uint(f.y);
+            d = make_float2(sqrt_apx(q.x), sqrt_apx(q.y));
+        } else {
+            d = __ffma2_rn(v, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));   // 1 - x^.y^
+            dmin = fminf(dmin, fminf(d.x, d.y));
+        }
+        if (i & 1) acc1 = __ffma2_rn(make_float2(wn.x, wn.y), d, acc1);
+        else acc0 = __ffma2_rn(make_float2(wn.x, wn.y), d, acc0);
+        cs[2 * i] = d.x * rw;
+        cs[2 * i + 1] = d.y * rw;
+    }
+    if (METRIC == SILH_COSINE) flag |= __float_as_uint(dmin - tau);
+    part += (acc0.x + acc0.y) + (acc1.x + acc1.y);
+    return transpose_reduce<16>(cs, lane, col);
+}
+
 // Column layout: cluster j occupies padded columns [poff[j], poff[j+1]), its
 // |F_j| sampled columns first, then zero columns of weight 0 up to a multiple
 // of 32, so every 32-column chunk belongs to exactly one cluster.
-template <int METRIC, int KD, bool SPLIT, bool BF>
+//
+// SYM (the exact silhouette over all points, rows = columns in the padded
+// layout): each unordered pair is evaluated once.  A row group streams only
+// the column tiles from its own first row on; a warp's 32-row block takes a
+// 32-column chunk only when the chunk lies entirely after the block (blocks
+// are 32-aligned and never straddle clusters, so the diagonal blocks are own
+// cluster pairs, which the direct pass covers).  Row sums per cluster and the
+// column sums (per column, over the warp's rows, which share one cluster) are
+// added to W (FP64, position x cluster); a separate pass forms s, a, b.
+template <int METRIC, int KD, bool SPLIT, bool BF, bool SYM = false>
 __global__ void __launch_bounds__(TcCfg<KD, SPLIT, BF>::THREADS, 1)
 k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CUtensorMap m_alo,
            const __grid_constant__ CUtensorMap m_bhi, const __grid_constant__ CUtensorMap m_blo,
@@ -162,7 +207,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
            const float2 *__restrict__ y_wn, const int64_t *__restrict__ poff,
            const int64_t *__restrict__ sizes, int k, float tau,
            const double *__restrict__ w_own, float *__restrict__ s_out,
-           float *__restrict__ a_out_v, float *__restrict__ b_out_v) {
+           float *__restrict__ a_out_v, float *__restrict__ b_out_v,
+           double *__restrict__ W = nullptr) {
     using C = TcCfg<KD, SPLIT, BF>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_full[C::STAGES], bar_empty[C::STAGES];
@@ -183,6 +229,19 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     const int64_t ngroups = (ntiles + C::SLOTS - 1) / C::SLOTS;
     const int64_t mp = poff[k];                       // padded column count
     const int64_t nct = (mp + kTileN - 1) / kTileN;
+    // Row group of this CTA's it-th round: blockIdx.x + it * gridDim.x, except
+    // that SYM (whose groups shrink with their index) reverses odd rounds so
+    // that the CTAs' totals even out; -1 when the round has no group for it,
+    // -2 past the last round.  Its column tiles start at ct_first(rg).
+    auto group_of = [&](int64_t it) -> int64_t {
+        const int64_t base = it * gridDim.x;
+        if (base >= ngroups) return -2;
+        const int64_t rg = (SYM && (it & 1)) ? base + gridDim.x - 1 - blockIdx.x : base + blockIdx.x;
+        return rg < ngroups ? rg : -1;
+    };
+    auto ct_first = [&](int64_t rg) -> int64_t {
+        return SYM ? (rg * C::SLOTS * kTileM) / kTileN : 0;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -216,7 +275,10 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             int stage = 0;
             uint32_t phase = 0;
             int64_t idx = 0;
-            for (int64_t rg = blockIdx.x; rg < ngroups && !abort_flag; rg += gridDim.x, ++idx) {
+            for (int64_t it = 0; !abort_flag; ++it) {
+                const int64_t rg = group_of(it);
+                if (rg == -2) break;
+                if (rg < 0) continue;
                 if (idx > 0 && !mbar_wait(&bar_aempty, (uint32_t)((idx - 1) & 1), kWaitNs)) {
                     abort_flag = 1;
                     break;
@@ -232,7 +294,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                                         kb * C::KELEM, y);
                     }
                 }
-                for (int64_t ct = 0; ct < nct; ++ct) {
+                for (int64_t ct = ct_first(rg); ct < nct; ++ct) {
                     if (!mbar_wait(&bar_empty[stage], phase ^ 1u, kWaitNs)) {
                         abort_flag = 1;
                         break;
@@ -252,6 +314,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         phase ^= 1u;
                     }
                 }
+                ++idx;
             }
         }
     } else if (warp == 1) {
@@ -263,12 +326,15 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             int stage = 0;
             uint32_t phase = 0, acc = 0, acc_phase = 0;
             int64_t idx = 0;
-            for (int64_t rg = blockIdx.x; rg < ngroups && !abort_flag; rg += gridDim.x, ++idx) {
+            for (int64_t it = 0; !abort_flag; ++it) {
+                const int64_t rg = group_of(it);
+                if (rg == -2) break;
+                if (rg < 0) continue;
                 if (!mbar_wait(&bar_afull, (uint32_t)(idx & 1), kWaitNs)) {
                     abort_flag = 1;
                     break;
                 }
-                for (int64_t ct = 0; ct < nct; ++ct) {
+                for (int64_t ct = ct_first(rg); ct < nct; ++ct) {
                     if (!mbar_wait(&bar_full[stage], phase, kWaitNs)) {
                         abort_flag = 1;
                         break;
@@ -329,6 +395,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     if (acc == 0) acc_phase ^= 1u;
                 }
                 mma_commit(&bar_aempty);
+                ++idx;
                 if (abort_flag) break;
             }
             // The last A-release arrival must land before the CTA exits.
@@ -345,22 +412,35 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
         const uint32_t tlane = (uint32_t)(32 * q) << 16;
         uint32_t acc = 0, acc_phase = 0;
         int buf = 0;
-        for (int64_t rg = blockIdx.x; rg < ngroups; rg += gridDim.x) {
+        for (int64_t it = 0;; ++it) {
+            const int64_t rg = group_of(it);
+            if (rg == -2) break;
+            if (rg < 0) continue;
             const int64_t pos = (rg * C::SLOTS + g) * kTileM + r_local;
             const bool valid = pos < nrows;
             const int own = valid ? a_lab[pos] : -1;
             const float xn = valid ? a_norm[pos] : 0.f;
             const float *xh = a_hi + (valid ? pos : 0) * KD;
-            const float *xl = BF ? xh : a_lo + (valid ? pos : 0) * KD;
+            // FP32 rows for the direct recompute: hi + lo for TF32 operands, the
+            // FP32 copy (a_hi) for BF16 operands and for the symmetric layout
+            constexpr bool kFull = BF || SYM;
+            const float *xl = kFull ? xh : a_lo + (valid ? pos : 0) * KD;
+            // SYM: this warp's 32-row block starts at wblk; rows are the padded
+            // columns, so a row's weight (1 point / 0 padding) is its column weight
+            const int64_t wblk = (rg * C::SLOTS + g) * kTileM + 32 * q;
+            const float rw = (SYM && valid) ? y_wn[pos].x : 0.f;
+            const int64_t ct0 = ct_first(rg);
             int j = 0;
-            int64_t pbnd = poff[1];
+            while (SYM && j < k && poff[j + 1] <= ct0 * kTileN) ++j;
+            int64_t pbnd = (j < k) ? poff[j + 1] : LLONG_MAX;
             double accd = 0.0;
             RatioMin bmin;
             float accf = 0.f;                         // current cluster, this tile
             bool dead = false;
             // (weight, |y|^2) of this thread's column, fetched one tile ahead
-            float2 wn_next = (et < kTileN && et < mp) ? y_wn[et] : make_float2(0.f, 0.f);
-            for (int64_t ct = 0; ct < nct; ++ct) {
+            const int64_t c_first = ct0 * kTileN + et;
+            float2 wn_next = (et < kTileN && c_first < mp) ? y_wn[c_first] : make_float2(0.f, 0.f);
+            for (int64_t ct = ct0; ct < nct; ++ct) {
                 const float2 wn_cur = wn_next;
                 const int64_t cn = (ct + 1) * kTileN + et;
                 if (et < kTileN) wn_next = (cn < mp) ? y_wn[cn] : make_float2(0.f, 0.f);
@@ -391,28 +471,47 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     while (j < k && c0 == pbnd) {
                         accd += (double)accf;
                         accf = 0.f;
-                        if (j != own) bmin.add(accd, (double)sizes[j]);
+                        if (SYM) {
+                            if (accd != 0.0 && rw != 0.f) atomicAdd(&W[pos * k + j], accd);
+                        } else if (j != own) {
+                            bmin.add(accd, (double)sizes[j]);
+                        }
                         accd = 0.0;
                         ++j;
                         pbnd = (j < k) ? poff[j + 1] : LLONG_MAX;
                     }
                     const bool live = j < k;              // else padding beyond the last cluster
                     const bool mine = live && (j == own); // own-cluster pairs: skipped here
-                    const bool skip = !live || __all_sync(0xffffffffu, mine);
+                    // SYM: own is uniform over the warp (one cluster per 32-row block)
+                    const bool skip = SYM ? (!live || mine || c0 <= wblk)
+                                          : (!live || __all_sync(0xffffffffu, mine));
                     const float4 *wn4 = &sh_wn[g][buf][ch * 16];
                     float part = 0.f;
                     uint32_t flag = 0;
+                    float cs0 = 0.f, cs1 = 0.f;           // SYM: column sums of the two halves
+                    int col0 = 0, col1 = 0;
                     tmem_wait_16(ra);                     // first half of this chunk
                     __syncwarp();
                     tmem_ld16_issue(tcol + ch * 32 + 16, rb);
-                    if (!skip) half_chunk<METRIC>(ra, wn4, xn, tau, part, flag);
+                    if (!skip) {
+                        if (SYM) cs0 = half_chunk_sym<METRIC>(ra, wn4, xn, tau, rw, lane, part, flag, col0);
+                        else half_chunk<METRIC>(ra, wn4, xn, tau, part, flag);
+                    }
                     tmem_wait_16(rb);                     // second half
                     if (ch + 1 < kTileN / 32) {
                         __syncwarp();
                         tmem_ld16_issue(tcol + (ch + 1) * 32, ra);
                     }
-                    if (!skip) half_chunk<METRIC>(rb, wn4 + 8, xn, tau, part, flag);
-                    if (!skip && __any_sync(0xffffffffu, !mine && (flag >> 31) != 0u)) {
+                    if (!skip) {
+                        if (SYM) cs1 = half_chunk_sym<METRIC>(rb, wn4 + 8, xn, tau, rw, lane, part, flag, col1);
+                        else half_chunk<METRIC>(rb, wn4 + 8, xn, tau, part, flag);
+                    }
+                    const bool redo = !skip && __any_sync(0xffffffffu, !mine && (flag >> 31) != 0u);
+                    if (SYM && !skip && !redo && (lane & 1) == 0) {
+                        atomicAdd(&W[(c0 + col0) * k + own], (double)cs0);
+                        atomicAdd(&W[(c0 + 16 + col1) * k + own], (double)cs1);
+                    }
+                    if (redo) {
                         // a lane has a close pair here: redo the chunk column by column,
                         // recomputing the flagged pairs directly from the coordinates
                         part = 0.f;
@@ -428,13 +527,19 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             if (METRIC == SILH_EUCLIDEAN) {
                                 const float s2 = xn + wn.y;
                                 const float d2 = fmaf(-2.f, dot, s2);
-                                dist = (d2 < tau * s2) ? direct_dist<METRIC, KD, BF>(xh, xl, yc)
+                                dist = (d2 < tau * s2) ? direct_dist<METRIC, KD, kFull>(xh, xl, yc)
                                                        : sqrt_apx(d2);
                             } else {
                                 dist = 1.f - dot;
-                                if (dist < tau) dist = direct_dist<METRIC, KD, BF>(xh, xl, yc);
+                                if (dist < tau) dist = direct_dist<METRIC, KD, kFull>(xh, xl, yc);
                             }
                             part = fmaf(wn.x, dist, part);
+                            if (SYM) {                // column side of this pair
+                                float v = dist * rw;
+#pragma unroll
+                                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                                if (lane == 0) atomicAdd(&W[(c0 + i) * k + own], (double)v);
+                            }
                         }
                     }
                     if (live && !mine) accf += part;
@@ -449,6 +554,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 accf = 0.f;
             }
             if (dead) break;
+            if (SYM) {                                // row side of the last cluster reached
+                accd += (double)accf;
+                if (j < k && accd != 0.0 && rw != 0.f) atomicAdd(&W[pos * k + j], accd);
+                continue;
+            }
             // clusters after the last processed chunk (the current one and empty ones)
             while (j < k) {
                 accd += (double)accf;
@@ -885,6 +995,58 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
     }
 }
 
+// Symmetric exact: per padded position i, the cluster of its 32-aligned block
+// (padding included, so a warp's rows share it; -1 past the last cluster), the
+// original element index (-1 for padding) and the squared norm (from wn).
+__global__ void k_padded_meta(const int64_t *__restrict__ offsets, const int64_t *__restrict__ poff,
+                              const int32_t *__restrict__ order, int k, int64_t mp_max,
+                              const float2 *__restrict__ wn, int32_t *__restrict__ plab,
+                              int64_t *__restrict__ outi, float *__restrict__ nrm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= mp_max) return;
+    int32_t lab = -1;
+    int64_t o = -1;
+    if (i < poff[k]) {
+        int lo = 0, hi = k - 1;                // last j with poff[j] <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (poff[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        lab = lo;
+        const int64_t local = i - poff[lo];
+        if (local < offsets[lo + 1] - offsets[lo]) o = order[offsets[lo] + local];
+    }
+    plab[i] = lab;
+    outi[i] = o;
+    nrm[i] = wn[i].y;
+}
+
+// s, a, b of every point from its row of W (the cross-cluster sums) and its
+// own-cluster sum, written at the point's original index.
+__global__ void k_tc_sym_finalize(const double *__restrict__ W, const double *__restrict__ w_own,
+                                  const int32_t *__restrict__ plab, const int64_t *__restrict__ outi,
+                                  const int64_t *__restrict__ sizes, int64_t mp_max, int k,
+                                  float *__restrict__ s_out, float *__restrict__ a_out,
+                                  float *__restrict__ b_out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= mp_max) return;
+    const int64_t o = outi[i];
+    if (o < 0) return;
+    const int own = plab[i];
+    const double *w = W + i * k;
+    RatioMin bm;
+    for (int j = 0; j < k; ++j)
+        if (j != own) bm.add(w[j], (double)sizes[j]);
+    const double bmin = bm.value();
+    const int64_t nc = sizes[own];
+    const double a = (nc > 1) ? w_own[i] / (double)(nc - 1) : 0.0;
+    const double mx = fmax(a, bmin);
+    s_out[o] = (float)((nc > 1 && mx > 0.0) ? (bmin - a) / mx : 0.0);
+    if (a_out) a_out[o] = (float)a;
+    if (b_out) b_out[o] = (float)bmin;
+}
+
 // ------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -919,29 +1081,32 @@ bool make_map(CUtensorMap *map, const void *ptr, int KD, int64_t rows, int box_r
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int METRIC, int KD, bool SPLIT, bool BF>
+template <int METRIC, int KD, bool SPLIT, bool BF, bool SYM = false>
 cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, const CUtensorMap &alo,
                       const CUtensorMap &bhi, const CUtensorMap &blo, const float *a_hi,
                       const float *a_lo, const float *a_norm, const int32_t *a_lab,
                       const int64_t *a_out, int64_t nrows, const float *y_full, const float2 *y_wn,
                       const int64_t *poff, const int64_t *sizes, int k, float tau,
-                      int64_t max_cluster_cols, double *w_own, float *s, float *a, float *b) {
+                      int64_t max_cluster_cols, double *w_own, float *s, float *a, float *b,
+                      double *W = nullptr) {
     using C = TcCfg<KD, SPLIT, BF>;
     constexpr int64_t kChunk = 2048;
     const int64_t nchunk = std::max<int64_t>(1, (max_cluster_cols + 31 + kChunk - 1) / kChunk);
     cudaError_t e0 = cudaMemsetAsync(w_own, 0, sizeof(double) * (size_t)nrows, stream);
     if (e0 != cudaSuccess) return e0;
-    k_own_direct<METRIC, KD, BF><<<dim3((unsigned)((nrows + 255) / 256), (unsigned)nchunk), 128, 0, stream>>>(
+    // the own-cluster pass reads FP32 rows: hi + lo (TF32 operands) or the FP32
+    // copy (BF16 operands, and the symmetric layout whose rows are the columns)
+    k_own_direct<METRIC, KD, BF || SYM><<<dim3((unsigned)((nrows + 255) / 256), (unsigned)nchunk), 128, 0, stream>>>(
         a_hi, a_lo, a_norm, a_lab, nrows, y_full, y_wn, poff, k, kChunk, w_own);
     count_launches(1);
-    auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF>;
+    auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF, SYM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     const int64_t groups = ((nrows + kTileM - 1) / kTileM + C::SLOTS - 1) / C::SLOTS;
     const int grid = (int)std::min<int64_t>(groups, nsm);
     kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_norm, a_lab,
                                                 a_out, nrows, y_full, y_wn, poff, sizes, k, tau,
-                                                w_own, s, a, b);
+                                                w_own, s, a, b, W);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1071,6 +1236,109 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     SILH_TC_CASES(SILH_COSINE, 64)
 #undef SILH_TC_CASES
 #undef SILH_TC_CASE
+done:
+    return st;
+}
+
+// Exact silhouette of all n points on the tensor cores, each unordered pair
+// once (the SYM sweep).  Points are laid out cluster-major and padded per
+// cluster to multiples of 32 (the column layout of tc_sweep, weights 1), and
+// that one layout is both the row and the column operand.  coff / order: the
+// cluster offsets and the cluster-sorted element ids; max_cluster: the largest
+// cluster.  Needs (n + 31 k) * k doubles of scratch for the sums.
+silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                         int32_t k, int metric, int prec, const int64_t *sizes,
+                         const int64_t *coff, const int32_t *order, int64_t max_cluster,
+                         float *s, float *a, float *b, Scratch &sc, cudaStream_t stream) {
+    silh_status st = SILH_OK;
+    const int KD = d <= 32 ? 32 : 64;
+    const bool split = prec == SILH_PREC_3XTF32 || prec == SILH_PREC_BF16X3;
+    const bool bf = prec == SILH_PREC_BF16 || prec == SILH_PREC_BF16X3;
+    const int KE = bf ? 64 : KD;
+    const size_t ebytes = bf ? 2 : 4;
+    const int64_t mp_max = n + 31 * (int64_t)k;
+    const int mean_blocks = 128;
+    int dev = 0, nsm = 0;
+    int64_t *poff = nullptr, *outi = nullptr;
+    int32_t *plab = nullptr;
+    double *w_own = nullptr, *W = nullptr, *mpart = nullptr;
+    float *mu = nullptr, *yf = nullptr, *rn = nullptr;
+    uint8_t *yhi = nullptr, *ylo = nullptr;
+    float2 *ywn = nullptr;
+    CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
+    const float tau = 0.25f;
+
+    SILH_CK(sc.alloc(&poff, (size_t)k + 1));
+    SILH_CK(sc.alloc(&outi, (size_t)mp_max));
+    SILH_CK(sc.alloc(&plab, (size_t)mp_max));
+    SILH_CK(sc.alloc(&rn, (size_t)mp_max));
+    SILH_CK(sc.alloc(&w_own, (size_t)mp_max));
+    SILH_CK(sc.alloc(&W, (size_t)mp_max * k));
+    SILH_CK(sc.alloc(&mpart, (size_t)mean_blocks * d));
+    SILH_CK(sc.alloc(&mu, (size_t)d));
+    SILH_CK(sc.alloc(&yf, (size_t)mp_max * KD));
+    SILH_CK(sc.alloc(&yhi, (size_t)mp_max * KE * ebytes));
+    SILH_CK(sc.alloc(&ylo, (size_t)mp_max * KE * ebytes));
+    SILH_CK(sc.alloc(&ywn, (size_t)mp_max));
+    SILH_CK(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)mp_max * k, stream));
+    k_col_poff<<<1, 1024, 0, stream>>>(coff, k, poff);
+    count_launches(1);
+    if (metric == SILH_EUCLIDEAN) {
+        // distances are shift invariant: centre on the mean of all points
+        const int per = (int)((n + mean_blocks - 1) / mean_blocks);
+        if (dtype == SILH_F32)
+            k_col_mean_partial<float><<<mean_blocks, 128, 0, stream>>>((const float *)X, d, ld,
+                                                                       order, n, per, mpart);
+        else
+            k_col_mean_partial<__nv_bfloat16><<<mean_blocks, 128, 0, stream>>>(
+                (const __nv_bfloat16 *)X, d, ld, order, n, per, mpart);
+        k_col_mean_final<<<1, 128, 0, stream>>>(mpart, mean_blocks, d, n, mu);
+        count_launches(2);
+    } else {
+        mu = nullptr;
+    }
+#define SILH_TC_GATHER_SYM(T, BFV)                                                              \
+    k_gather_cols_tc<T, BFV><<<ceil_div_i(mp_max, 8), 256, 0, stream>>>(                       \
+        (const T *)X, d, ld, order, nullptr, coff, poff, k, mp_max, KD, metric, mu, yf, yhi,    \
+        ylo, ywn);
+    if (dtype == SILH_F32) {
+        if (bf) { SILH_TC_GATHER_SYM(float, true) } else { SILH_TC_GATHER_SYM(float, false) }
+    } else {
+        if (bf) { SILH_TC_GATHER_SYM(__nv_bfloat16, true) } else { SILH_TC_GATHER_SYM(__nv_bfloat16, false) }
+    }
+#undef SILH_TC_GATHER_SYM
+    k_padded_meta<<<ceil_div_i(mp_max, 256), 256, 0, stream>>>(coff, poff, order, k, mp_max, ywn,
+                                                               plab, outi, rn);
+    count_launches(2);
+    SILH_CK(cudaGetLastError());
+    SILH_REQ(make_map(&m_ahi, yhi, KD, mp_max, kTileM, bf) &&
+                 make_map(&m_alo, ylo, KD, mp_max, kTileM, bf) &&
+                 make_map(&m_bhi, yhi, KD, mp_max, kTileN, bf) &&
+                 make_map(&m_blo, ylo, KD, mp_max, kTileN, bf),
+             "tensor map encoding failed");
+    SILH_CK(cudaGetDevice(&dev));
+    SILH_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+#define SILH_TC_SYM_CASE(MET, KDV, SP, BFV)                                                    \
+    if (metric == MET && KD == KDV && split == SP && bf == BFV) {                              \
+        SILH_CK((launch_tc<MET, KDV, SP, BFV, true>(                                            \
+            nsm, stream, m_ahi, m_alo, m_bhi, m_blo, yf, nullptr, rn, plab, outi, mp_max, yf,  \
+            ywn, poff, sizes, k, tau, max_cluster, w_own, nullptr, nullptr, nullptr, W)));     \
+    }
+#define SILH_TC_SYM_CASES(MET, KDV)             \
+    SILH_TC_SYM_CASE(MET, KDV, true, false)     \
+    SILH_TC_SYM_CASE(MET, KDV, false, false)    \
+    SILH_TC_SYM_CASE(MET, KDV, true, true)      \
+    SILH_TC_SYM_CASE(MET, KDV, false, true)
+    SILH_TC_SYM_CASES(SILH_EUCLIDEAN, 32)
+    SILH_TC_SYM_CASES(SILH_EUCLIDEAN, 64)
+    SILH_TC_SYM_CASES(SILH_COSINE, 32)
+    SILH_TC_SYM_CASES(SILH_COSINE, 64)
+#undef SILH_TC_SYM_CASES
+#undef SILH_TC_SYM_CASE
+    k_tc_sym_finalize<<<ceil_div_i(mp_max, 256), 256, 0, stream>>>(W, w_own, plab, outi, sizes,
+                                                                   mp_max, k, s, a, b);
+    count_launches(1);
+    SILH_CK(cudaGetLastError());
 done:
     return st;
 }

@@ -312,12 +312,18 @@ def test_tensor_core_exact_matches_oracle(case, metric, prec):
         assert (np.bincount(lab, minlength=k) > 0).all()
     Xt, lt = _to_dev(X, lab)
     Xh = _host_values(Xt)
-    s = silh.silh_exact(Xt, lt, k, metric, prec=prec)
+    s, a, b = silh.silh_exact(Xt, lt, k, metric, prec=prec, want_ab=True)   # each pair once
     silh.silh_stream_status()
-    s_o, _, _ = oracle.exact(Xh, lab, k, metric)
+    s_o, a_o, b_o = oracle.exact(Xh, lab, k, metric)
     s_g = s.cpu().numpy().astype(np.float64)
     assert np.isfinite(s_g).all()
     assert np.abs(s_g - s_o).max() <= TC_TOL[prec]
+    np.testing.assert_allclose(a.cpu().numpy(), a_o, rtol=2 * AB_RTOL, atol=1e-7)
+    np.testing.assert_allclose(b.cpu().numpy(), b_o, rtol=2 * AB_RTOL, atol=1e-7)
+    # a row list takes the row-streaming tensor-core sweep instead
+    rows = np.arange(0, X.shape[0], 5, dtype=np.int64)
+    sr = silh.silh_exact(Xt, lt, k, metric, prec=prec, rows=torch.from_numpy(rows).cuda())
+    assert np.abs(sr.cpu().numpy().astype(np.float64) - s_o[rows]).max() <= TC_TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
