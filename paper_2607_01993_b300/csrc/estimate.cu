@@ -957,8 +957,8 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
         if (rows == nullptr &&
             (double)(n + 31.0 * k) * (double)k * 8.0 <= 4294967296.0) {
             // all points: each pair once, row and column sums into an FP64 matrix
-            st = tc_exact_sym(X, dtype, n, d, ld, k, metric, prec, sizes, coff, order, maxc, s, a,
-                              b, sc, stream);
+            st = tc_exact_sym(X, dtype, n, d, ld, k, metric, prec, sizes, coff, order, h_sizes, s,
+                              a, b, sc, stream);
         } else {
             st = tc_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, order, nullptr,
                           n, maxc, rows, nrows, s, a, b, sc, stream);

@@ -50,11 +50,12 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
                      float *a, float *b, Scratch &sc, cudaStream_t stream);
 // Exact silhouette of all n points on the tensor cores with each unordered
 // pair evaluated once (Euclidean / cosine, the tc_sweep precisions, d <= 64).
-// coff / order from cluster_sort; max_cluster = the largest |Cj|.
+// coff / order / h_sizes from cluster_sort.
 silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                          int32_t k, int metric, int prec, const int64_t *sizes,
-                         const int64_t *coff, const int32_t *order, int64_t max_cluster,
-                         float *s, float *a, float *b, Scratch &sc, cudaStream_t stream);
+                         const int64_t *coff, const int32_t *order,
+                         const std::vector<int64_t> &h_sizes, float *s, float *a, float *b,
+                         Scratch &sc, cudaStream_t stream);
 // 1 if a bounded wait in the tensor-core sweep gave up since the last call
 // (and clears it), 0 if not, -1 on a CUDA error.  Synchronous.
 int tc_take_error();

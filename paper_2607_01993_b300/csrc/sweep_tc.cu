@@ -713,6 +713,108 @@ k_own_direct(const float *__restrict__ a_hi, const float *__restrict__ a_lo,
         if (pos[r] < nrows && acc[r] != 0.0) atomicAdd(&w_own[pos[r]], acc[r]);
 }
 
+// Own-cluster pairs of the symmetric exact, each unordered pair once.  Work
+// item (j, I, J), I <= J: the rows of tile I and the columns of tile J of
+// cluster j's padded range [poff[j], poff[j+1]) (tiles of 128 * RPT points).
+// Row sums of d go to W[row * k + j]; off the diagonal the column sums (over
+// the tile's rows, weighted by the row weight, 0 for padding) go to
+// W[col * k + j] through a warp transpose-reduce.  Distances directly in FP32
+// from the FP32 layout yf, as the row-streaming own pass does.
+struct OwnItem {
+    int32_t j, I, J, pad_;
+};
+
+template <int METRIC, int KD>
+__global__ void __launch_bounds__(128)
+k_own_sym(const float *__restrict__ yf, const float2 *__restrict__ ywn,
+          const int64_t *__restrict__ poff, const OwnItem *__restrict__ items, int k,
+          double *__restrict__ W) {
+    constexpr int RPT = (KD == 32) ? 2 : 1;
+    constexpr int T = 128 * RPT, BN = 64, CB = 8, NW = 4;
+    __shared__ __align__(16) float sh_y[BN * KD];      // negated columns
+    __shared__ float2 sh_w[BN];                        // (weight, squared norm)
+    __shared__ float sh_col[NW][BN];
+    const OwnItem it = items[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = poff[it.j], end = poff[it.j + 1];
+    const bool diag = it.I == it.J;
+    float2 x[RPT][KD / 2];
+    float rw[RPT], zx[RPT], accr[RPT];
+    int64_t pos[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        pos[r] = base + (int64_t)it.I * T + threadIdx.x + r * 128;
+        const bool valid = pos[r] < end;
+        const float2 wn = valid ? ywn[pos[r]] : make_float2(0.f, 0.f);
+        rw[r] = wn.x;
+        zx[r] = (METRIC == SILH_COSINE && valid && wn.y == 0.f) ? 0.5f : 0.f;
+        accr[r] = 0.f;
+#pragma unroll
+        for (int c = 0; c < KD / 2; ++c)
+            x[r][c] = valid ? make_float2(yf[pos[r] * KD + 2 * c], yf[pos[r] * KD + 2 * c + 1])
+                            : make_float2(0.f, 0.f);
+    }
+    const int64_t cs_ = base + (int64_t)it.J * T, ce = min(cs_ + T, end);
+    for (int64_t cb = cs_; cb < ce; cb += BN) {
+        const int nb = (int)min((int64_t)BN, ce - cb);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nb * (KD / 4); q += 128) {
+            const float4 v = reinterpret_cast<const float4 *>(yf + cb * KD)[q];
+            reinterpret_cast<float4 *>(sh_y)[q] = make_float4(-v.x, -v.y, -v.z, -v.w);
+        }
+        for (int q = threadIdx.x; q < BN; q += 128)
+            sh_w[q] = (q < nb) ? ywn[cb + q] : make_float2(0.f, 0.f);
+        __syncthreads();
+        for (int col0 = 0; col0 < nb; col0 += CB) {
+            float cs[CB];
+#pragma unroll
+            for (int c = 0; c < CB; ++c) {
+                const int col = col0 + c;
+                cs[c] = 0.f;
+                if (col < nb) {
+                    const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * KD);
+                    const float2 wn = sh_w[col];
+                    const float zy = (METRIC == SILH_COSINE && wn.y == 0.f) ? 0.5f : 0.f;
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        float2 b0 = make_float2(0.f, 0.f), b1 = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int q = 0; q < KD / 4; ++q) {
+                            const float4 y = y4[q];
+                            const float2 t0 = __fadd2_rn(x[r][2 * q], make_float2(y.x, y.y));
+                            const float2 t1 = __fadd2_rn(x[r][2 * q + 1], make_float2(y.z, y.w));
+                            b0 = __ffma2_rn(t0, t0, b0);
+                            b1 = __ffma2_rn(t1, t1, b1);
+                        }
+                        const float q2 = (b0.x + b0.y) + (b1.x + b1.y);
+                        const float dist = (METRIC == SILH_EUCLIDEAN) ? sqrt_apx(q2)
+                                                                      : 0.5f * q2 + zx[r] + zy;
+                        accr[r] = fmaf(wn.x, dist, accr[r]);
+                        cs[c] = fmaf(rw[r], dist, cs[c]);
+                    }
+                }
+            }
+            if (!diag) {
+                int mine = 0;
+                const float tot = transpose_reduce<CB>(cs, lane, mine);
+                if ((lane & (32 / CB - 1)) == 0 && col0 + mine < nb) sh_col[warp][col0 + mine] = tot;
+            }
+        }
+        if (!diag) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < nb; q += 128) {
+                float v = 0.f;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) v += sh_col[w][q];
+                if (v != 0.f) atomicAdd(&W[(cb + q) * k + it.j], (double)v);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+        if (pos[r] < end && accr[r] != 0.f) atomicAdd(&W[pos[r] * k + it.j], (double)accr[r]);
+}
+
 // Mean of the m sampled columns (Euclidean centring): per-block partial sums
 // over a fixed slice of columns, then one block adds them in order.
 template <class T>
@@ -1022,9 +1124,9 @@ __global__ void k_padded_meta(const int64_t *__restrict__ offsets, const int64_t
     nrm[i] = wn[i].y;
 }
 
-// s, a, b of every point from its row of W (the cross-cluster sums) and its
-// own-cluster sum, written at the point's original index.
-__global__ void k_tc_sym_finalize(const double *__restrict__ W, const double *__restrict__ w_own,
+// s, a, b of every point from its row of W (the cross-cluster sums, and at
+// its own cluster the own-cluster sum), written at the point's original index.
+__global__ void k_tc_sym_finalize(const double *__restrict__ W,
                                   const int32_t *__restrict__ plab, const int64_t *__restrict__ outi,
                                   const int64_t *__restrict__ sizes, int64_t mp_max, int k,
                                   float *__restrict__ s_out, float *__restrict__ a_out,
@@ -1040,7 +1142,7 @@ __global__ void k_tc_sym_finalize(const double *__restrict__ W, const double *__
         if (j != own) bm.add(w[j], (double)sizes[j]);
     const double bmin = bm.value();
     const int64_t nc = sizes[own];
-    const double a = (nc > 1) ? w_own[i] / (double)(nc - 1) : 0.0;
+    const double a = (nc > 1) ? w[own] / (double)(nc - 1) : 0.0;    // own-cluster sum
     const double mx = fmax(a, bmin);
     s_out[o] = (float)((nc > 1 && mx > 0.0) ? (bmin - a) / mx : 0.0);
     if (a_out) a_out[o] = (float)a;
@@ -1088,17 +1190,27 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
                       const int64_t *a_out, int64_t nrows, const float *y_full, const float2 *y_wn,
                       const int64_t *poff, const int64_t *sizes, int k, float tau,
                       int64_t max_cluster_cols, double *w_own, float *s, float *a, float *b,
-                      double *W = nullptr) {
+                      double *W = nullptr, const OwnItem *own_items = nullptr,
+                      int64_t n_own_items = 0) {
     using C = TcCfg<KD, SPLIT, BF>;
-    constexpr int64_t kChunk = 2048;
-    const int64_t nchunk = std::max<int64_t>(1, (max_cluster_cols + 31 + kChunk - 1) / kChunk);
-    cudaError_t e0 = cudaMemsetAsync(w_own, 0, sizeof(double) * (size_t)nrows, stream);
-    if (e0 != cudaSuccess) return e0;
-    // the own-cluster pass reads FP32 rows: hi + lo (TF32 operands) or the FP32
-    // copy (BF16 operands, and the symmetric layout whose rows are the columns)
-    k_own_direct<METRIC, KD, BF || SYM><<<dim3((unsigned)((nrows + 255) / 256), (unsigned)nchunk), 128, 0, stream>>>(
-        a_hi, a_lo, a_norm, a_lab, nrows, y_full, y_wn, poff, k, kChunk, w_own);
-    count_launches(1);
+    if (SYM) {
+        // own-cluster pairs once each, into W at the own cluster
+        if (n_own_items > 0) {
+            k_own_sym<METRIC, KD><<<(unsigned)n_own_items, 128, 0, stream>>>(y_full, y_wn, poff,
+                                                                             own_items, k, W);
+            count_launches(1);
+        }
+    } else {
+        constexpr int64_t kChunk = 2048;
+        const int64_t nchunk = std::max<int64_t>(1, (max_cluster_cols + 31 + kChunk - 1) / kChunk);
+        cudaError_t e0 = cudaMemsetAsync(w_own, 0, sizeof(double) * (size_t)nrows, stream);
+        if (e0 != cudaSuccess) return e0;
+        // the own-cluster pass reads FP32 rows: hi + lo (TF32 operands) or the
+        // FP32 copy (BF16 operands)
+        k_own_direct<METRIC, KD, BF><<<dim3((unsigned)((nrows + 255) / 256), (unsigned)nchunk), 128, 0, stream>>>(
+            a_hi, a_lo, a_norm, a_lab, nrows, y_full, y_wn, poff, k, kChunk, w_own);
+        count_launches(1);
+    }
     auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF, SYM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
@@ -1244,12 +1356,13 @@ done:
 // once (the SYM sweep).  Points are laid out cluster-major and padded per
 // cluster to multiples of 32 (the column layout of tc_sweep, weights 1), and
 // that one layout is both the row and the column operand.  coff / order: the
-// cluster offsets and the cluster-sorted element ids; max_cluster: the largest
-// cluster.  Needs (n + 31 k) * k doubles of scratch for the sums.
+// cluster offsets and the cluster-sorted element ids; h_sizes: the cluster
+// sizes on the host.  Needs (n + 31 k) * k doubles of scratch for the sums.
 silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                          int32_t k, int metric, int prec, const int64_t *sizes,
-                         const int64_t *coff, const int32_t *order, int64_t max_cluster,
-                         float *s, float *a, float *b, Scratch &sc, cudaStream_t stream) {
+                         const int64_t *coff, const int32_t *order,
+                         const std::vector<int64_t> &h_sizes, float *s, float *a, float *b,
+                         Scratch &sc, cudaStream_t stream) {
     silh_status st = SILH_OK;
     const int KD = d <= 32 ? 32 : 64;
     const bool split = prec == SILH_PREC_3XTF32 || prec == SILH_PREC_BF16X3;
@@ -1261,8 +1374,10 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     int dev = 0, nsm = 0;
     int64_t *poff = nullptr, *outi = nullptr;
     int32_t *plab = nullptr;
-    double *w_own = nullptr, *W = nullptr, *mpart = nullptr;
+    double *W = nullptr, *mpart = nullptr;
     float *mu = nullptr, *yf = nullptr, *rn = nullptr;
+    OwnItem *own_items = nullptr;
+    std::vector<OwnItem> h_items;
     uint8_t *yhi = nullptr, *ylo = nullptr;
     float2 *ywn = nullptr;
     CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
@@ -1272,7 +1387,6 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     SILH_CK(sc.alloc(&outi, (size_t)mp_max));
     SILH_CK(sc.alloc(&plab, (size_t)mp_max));
     SILH_CK(sc.alloc(&rn, (size_t)mp_max));
-    SILH_CK(sc.alloc(&w_own, (size_t)mp_max));
     SILH_CK(sc.alloc(&W, (size_t)mp_max * k));
     SILH_CK(sc.alloc(&mpart, (size_t)mean_blocks * d));
     SILH_CK(sc.alloc(&mu, (size_t)d));
@@ -1281,6 +1395,20 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     SILH_CK(sc.alloc(&ylo, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&ywn, (size_t)mp_max));
     SILH_CK(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)mp_max * k, stream));
+    {   // own-cluster tile pairs (I <= J) over each cluster's padded range
+        const int64_t T = (KD == 32) ? 256 : 128;
+        for (int32_t j = 0; j < k; ++j) {
+            const int64_t len = (h_sizes[j] + 31) & ~int64_t(31);
+            const int64_t nt = (len + T - 1) / T;
+            for (int64_t I = 0; I < nt; ++I)
+                for (int64_t J = I; J < nt; ++J) h_items.push_back({j, (int32_t)I, (int32_t)J, 0});
+        }
+        if (!h_items.empty()) {
+            SILH_CK(sc.alloc(&own_items, h_items.size()));
+            SILH_CK(cudaMemcpyAsync(own_items, h_items.data(), sizeof(OwnItem) * h_items.size(),
+                                    cudaMemcpyHostToDevice, stream));
+        }
+    }
     k_col_poff<<<1, 1024, 0, stream>>>(coff, k, poff);
     count_launches(1);
     if (metric == SILH_EUCLIDEAN) {
@@ -1322,7 +1450,8 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     if (metric == MET && KD == KDV && split == SP && bf == BFV) {                              \
         SILH_CK((launch_tc<MET, KDV, SP, BFV, true>(                                            \
             nsm, stream, m_ahi, m_alo, m_bhi, m_blo, yf, nullptr, rn, plab, outi, mp_max, yf,  \
-            ywn, poff, sizes, k, tau, max_cluster, w_own, nullptr, nullptr, nullptr, W)));     \
+            ywn, poff, sizes, k, tau, 0, nullptr, nullptr, nullptr, nullptr, W, own_items,     \
+            (int64_t)h_items.size())));                                                         \
     }
 #define SILH_TC_SYM_CASES(MET, KDV)             \
     SILH_TC_SYM_CASE(MET, KDV, true, false)     \
@@ -1335,7 +1464,7 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     SILH_TC_SYM_CASES(SILH_COSINE, 64)
 #undef SILH_TC_SYM_CASES
 #undef SILH_TC_SYM_CASE
-    k_tc_sym_finalize<<<ceil_div_i(mp_max, 256), 256, 0, stream>>>(W, w_own, plab, outi, sizes,
+    k_tc_sym_finalize<<<ceil_div_i(mp_max, 256), 256, 0, stream>>>(W, plab, outi, sizes,
                                                                    mp_max, k, s, a, b);
     count_launches(1);
     SILH_CK(cudaGetLastError());
