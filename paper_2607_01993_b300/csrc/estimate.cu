@@ -610,10 +610,12 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
     int lp[RPT];
     float zx[RPT];
     int64_t prow[RPT];
+    float rv[RPT];                     // 1 for a row of the input, 0 past n
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         const int64_t p = I * T + threadIdx.x + r * kThreads;
         prow[r] = p;
+        rv[r] = p < n ? 1.f : 0.f;
         const bool v = p < n;
         lp[r] = v ? lab_s[p] : -1;
         zx[r] = (METRIC == SILH_COSINE && v) ? zY[p] : 0.f;
@@ -671,9 +673,8 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
                         for (int r = 0; r < RPT; ++r) {
                             float dd = pair_dist<METRIC, D, NA>(x[r], ax[r], y4, ya4);
                             if (METRIC == SILH_COSINE) dd += zx[r] + sh_z[col];
-                            dd = (prow[r] < n) ? dd : 0.f;
-                            accr[r] += dd;
-                            cs[c] += dd;
+                            accr[r] += dd;                  // flushed only for rows < n
+                            cs[c] = fmaf(rv[r], dd, cs[c]); // rows past n add nothing
                         }
                     }
                 }
