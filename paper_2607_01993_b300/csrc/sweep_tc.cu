@@ -54,22 +54,30 @@ __device__ int g_tc_error = 0;    // set when a bounded wait gives up
 
 // KD: padded FP32 row length (32 or 64); BF: BF16 operands (one 128-byte K
 // block of 64 elements) instead of TF32 (KD / 32 blocks of 32 elements).
-template <int KD, bool SPLIT, bool BF = false>
+// WIDE: 128-column tiles (one MMA covers N = 128, so each read of the 128-row
+// A tile from shared memory serves twice the columns) with one accumulator
+// per slot where two would not fit in tensor memory; otherwise 64-column
+// tiles, two accumulators per slot.
+template <int KD, bool SPLIT, bool BF = false, bool WIDE = false>
 struct TcCfg {
     static constexpr int KB = BF ? 1 : KD / 32;                 // 128-byte K blocks
     static constexpr int KSTEPS = BF ? KD / 16 : 4;             // 32-byte MMA K steps per block
     static constexpr int KELEM = BF ? 64 : 32;                  // elements per 128-byte row
     static constexpr int PARTS = SPLIT ? 2 : 1;                 // hi (+ lo)
     static constexpr int SLOTS = (KB == 1) ? 4 : 2;             // row tiles per CTA pass
+    static constexpr int TN = WIDE ? 128 : kTileN;              // columns per tile
+    static constexpr int NACC = (SLOTS * 2 * TN <= 512) ? 2 : 1;  // accumulators per slot
     static constexpr int A_SLOT = PARTS * KB * kTileM * 128;
     static constexpr int A_BYTES = SLOTS * A_SLOT;
-    static constexpr int B_BYTES = PARTS * KB * kTileN * 128;   // one stage
-    static constexpr int STAGES = (KB == 1) ? (SPLIT ? 4 : 8) : (SPLIT ? 2 : 4);
-    static_assert(SMEM_CHECK(SLOTS * PARTS * KB * kTileM * 128 + STAGES * PARTS * KB * kTileN * 128),
-                  "dynamic shared memory over budget");
+    static constexpr int B_BYTES = PARTS * KB * TN * 128;       // one stage
+    static constexpr int STAGES_FIT = (199 * 1024 - A_BYTES) / B_BYTES;
+    static constexpr int STAGES = WIDE ? (STAGES_FIT < 8 ? STAGES_FIT : 8)
+                                       : ((KB == 1) ? (SPLIT ? 4 : 8) : (SPLIT ? 2 : 4));
+    static_assert(STAGES >= 2, "fewer than two B stages fit");
+    static_assert(SMEM_CHECK(A_BYTES + STAGES * B_BYTES), "dynamic shared memory over budget");
     static constexpr int SMEM = 1024 + A_BYTES + STAGES * B_BYTES;
     static constexpr int THREADS = 64 + 128 * SLOTS;            // TMA, MMA, epilogue groups
-    static constexpr uint32_t TMEM_COLS = SLOTS * 2 * kTileN;   // two accumulators per slot
+    static constexpr uint32_t TMEM_COLS = SLOTS * NACC * TN;
 };
 
 // Named barrier (1 + group) over one epilogue group's 128 threads that also
@@ -197,8 +205,8 @@ __device__ __forceinline__ float half_chunk_sym(const uint32_t (&r)[16], const f
 // cluster pairs, which the direct pass covers).  Row sums per cluster and the
 // column sums (per column, over the warp's rows, which share one cluster) are
 // added to W (FP64, position x cluster); a separate pass forms s, a, b.
-template <int METRIC, int KD, bool SPLIT, bool BF, bool SYM = false>
-__global__ void __launch_bounds__(TcCfg<KD, SPLIT, BF>::THREADS, 1)
+template <int METRIC, int KD, bool SPLIT, bool BF, bool SYM = false, bool WIDE = false>
+__global__ void __launch_bounds__(TcCfg<KD, SPLIT, BF, WIDE>::THREADS, 1)
 k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CUtensorMap m_alo,
            const __grid_constant__ CUtensorMap m_bhi, const __grid_constant__ CUtensorMap m_blo,
            const float *__restrict__ a_hi, const float *__restrict__ a_lo,
@@ -209,15 +217,16 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
            const double *__restrict__ w_own, float *__restrict__ s_out,
            float *__restrict__ a_out_v, float *__restrict__ b_out_v,
            double *__restrict__ W = nullptr) {
-    using C = TcCfg<KD, SPLIT, BF>;
+    using C = TcCfg<KD, SPLIT, BF, WIDE>;
+    constexpr int TN = C::TN;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_full[C::STAGES], bar_empty[C::STAGES];
-    __shared__ uint64_t bar_afull, bar_aempty, bar_accf[C::SLOTS][2], bar_acce[C::SLOTS][2];
+    __shared__ uint64_t bar_afull, bar_aempty, bar_accf[C::SLOTS][C::NACC], bar_acce[C::SLOTS][C::NACC];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     // (w, |y|^2) of the current tile's columns, two columns per float4 as
     // (w_2i, w_2i+1, n_2i, n_2i+1) so that the epilogue reads lane pairs
-    __shared__ __align__(16) float4 sh_wn[C::SLOTS][2][kTileN / 2];
+    __shared__ __align__(16) float4 sh_wn[C::SLOTS][2][TN / 2];
 
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -228,7 +237,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     const int64_t ntiles = (nrows + kTileM - 1) / kTileM;
     const int64_t ngroups = (ntiles + C::SLOTS - 1) / C::SLOTS;
     const int64_t mp = poff[k];                       // padded column count
-    const int64_t nct = (mp + kTileN - 1) / kTileN;
+    const int64_t nct = (mp + TN - 1) / TN;
     // Row group of this CTA's it-th round: blockIdx.x + it * gridDim.x, except
     // that SYM (whose groups shrink with their index) reverses odd rounds so
     // that the CTAs' totals even out; -1 when the round has no group for it,
@@ -240,7 +249,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
         return rg < ngroups ? rg : -1;
     };
     auto ct_first = [&](int64_t rg) -> int64_t {
-        return SYM ? (rg * C::SLOTS * kTileM) / kTileN : 0;
+        return SYM ? (rg * C::SLOTS * kTileM) / TN : 0;
     };
 
     if (threadIdx.x == 0) {
@@ -251,7 +260,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
         mbar_init(&bar_afull, 1);
         mbar_init(&bar_aempty, 1);
         for (int g = 0; g < C::SLOTS; ++g)
-            for (int a = 0; a < 2; ++a) {
+            for (int a = 0; a < C::NACC; ++a) {
                 mbar_init(&bar_accf[g][a], 1);
                 mbar_init(&bar_acce[g][a], 4);
             }
@@ -302,12 +311,12 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     uint8_t *dst = sB + stage * C::B_BYTES;
                     mbar_expect_tx(&bar_full[stage], C::B_BYTES);
                     for (int kb = 0; kb < C::KB; ++kb) {
-                        tma_load_2d(&m_bhi, &bar_full[stage], dst + kb * kTileN * 128,
-                                    kb * C::KELEM, (int)(ct * kTileN));
+                        tma_load_2d(&m_bhi, &bar_full[stage], dst + kb * TN * 128,
+                                    kb * C::KELEM, (int)(ct * TN));
                         if (SPLIT)
                             tma_load_2d(&m_blo, &bar_full[stage],
-                                        dst + (C::KB + kb) * kTileN * 128, kb * C::KELEM,
-                                        (int)(ct * kTileN));
+                                        dst + (C::KB + kb) * TN * 128, kb * C::KELEM,
+                                        (int)(ct * TN));
                     }
                     if (++stage == C::STAGES) {
                         stage = 0;
@@ -320,7 +329,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = BF ? idesc_bf16(kTileM, kTileN) : idesc_tf32(kTileM, kTileN);
+            constexpr uint32_t idesc = BF ? idesc_bf16(kTileM, TN) : idesc_tf32(kTileM, TN);
             const uint64_t adesc0 = sw128_kmajor_desc(smem_u32(sA));
             const uint64_t bdesc0 = sw128_kmajor_desc(smem_u32(sB));
             int stage = 0;
@@ -351,7 +360,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             break;
                         }
                         fence_after_sync();
-                        const uint32_t d_tmem = tmem + (uint32_t)(g * 2 + acc) * kTileN;
+                        const uint32_t d_tmem = tmem + (uint32_t)(g * C::NACC + acc) * TN;
                         const uint64_t ad = adesc0 + (uint64_t)((g * C::A_SLOT) >> 4);
 #pragma unroll
                         for (int kb = 0; kb < C::KB; ++kb) {
@@ -359,12 +368,12 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             for (int ks = 0; ks < C::KSTEPS; ++ks) {
                                 const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;
                                 const uint64_t ahi = ad + (uint64_t)((kb * kTileM * 128 + ks * 32) >> 4);
-                                const uint64_t bhi = bd + (uint64_t)((kb * kTileN * 128 + ks * 32) >> 4);
+                                const uint64_t bhi = bd + (uint64_t)((kb * TN * 128 + ks * 32) >> 4);
                                 if (SPLIT) {
                                     const uint64_t alo =
                                         ad + (uint64_t)(((C::KB + kb) * kTileM * 128 + ks * 32) >> 4);
                                     const uint64_t blo =
-                                        bd + (uint64_t)(((C::KB + kb) * kTileN * 128 + ks * 32) >> 4);
+                                        bd + (uint64_t)(((C::KB + kb) * TN * 128 + ks * 32) >> 4);
                                     if (BF) {
                                         mma_bf16(d_tmem, alo, bhi, idesc, first);
                                         mma_bf16(d_tmem, ahi, blo, idesc, 1);
@@ -391,7 +400,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         stage = 0;
                         phase ^= 1u;
                     }
-                    acc ^= 1u;
+                    acc = (acc + 1 == (uint32_t)C::NACC) ? 0u : acc + 1;
                     if (acc == 0) acc_phase ^= 1u;
                 }
                 mma_commit(&bar_aempty);
@@ -431,20 +440,20 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             const float rw = (SYM && valid) ? y_wn[pos].x : 0.f;
             const int64_t ct0 = ct_first(rg);
             int j = 0;
-            while (SYM && j < k && poff[j + 1] <= ct0 * kTileN) ++j;
+            while (SYM && j < k && poff[j + 1] <= ct0 * TN) ++j;
             int64_t pbnd = (j < k) ? poff[j + 1] : LLONG_MAX;
             double accd = 0.0;
             RatioMin bmin;
             float accf = 0.f;                         // current cluster, this tile
             bool dead = false;
             // (weight, |y|^2) of this thread's column, fetched one tile ahead
-            const int64_t c_first = ct0 * kTileN + et;
-            float2 wn_next = (et < kTileN && c_first < mp) ? y_wn[c_first] : make_float2(0.f, 0.f);
+            const int64_t c_first = ct0 * TN + et;
+            float2 wn_next = (et < TN && c_first < mp) ? y_wn[c_first] : make_float2(0.f, 0.f);
             for (int64_t ct = ct0; ct < nct; ++ct) {
                 const float2 wn_cur = wn_next;
-                const int64_t cn = (ct + 1) * kTileN + et;
-                if (et < kTileN) wn_next = (cn < mp) ? y_wn[cn] : make_float2(0.f, 0.f);
-                if (et < kTileN) {
+                const int64_t cn = (ct + 1) * TN + et;
+                if (et < TN) wn_next = (cn < mp) ? y_wn[cn] : make_float2(0.f, 0.f);
+                if (et < TN) {
                     float *f = reinterpret_cast<float *>(&sh_wn[g][buf][et >> 1]);
                     f[et & 1] = wn_cur.x;
                     f[2 + (et & 1)] = wn_cur.y;
@@ -456,7 +465,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     break;
                 }
                 fence_after_sync();
-                const uint32_t tcol = tmem + tlane + (uint32_t)(g * 2 + acc) * kTileN;
+                const uint32_t tcol = tmem + tlane + (uint32_t)(g * C::NACC + acc) * TN;
                 // The tile's 64 accumulator columns are read in four 16-column
                 // halves; each half's load is issued before the previous half's
                 // arithmetic, so the TMEM latency overlaps it.
@@ -464,8 +473,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 __syncwarp();
                 tmem_ld16_issue(tcol, ra);
 #pragma unroll
-                for (int ch = 0; ch < kTileN / 32; ++ch) {
-                    const int64_t c0 = ct * kTileN + ch * 32;
+                for (int ch = 0; ch < TN / 32; ++ch) {
+                    const int64_t c0 = ct * TN + ch * 32;
                     // clusters that end here (empty ones included) are complete;
                     // the own cluster's sum comes from the direct pass (w_own)
                     while (j < k && c0 == pbnd) {
@@ -498,7 +507,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         else half_chunk<METRIC>(ra, wn4, xn, tau, part, flag);
                     }
                     tmem_wait_16(rb);                     // second half
-                    if (ch + 1 < kTileN / 32) {
+                    if (ch + 1 < TN / 32) {
                         __syncwarp();
                         tmem_ld16_issue(tcol + (ch + 1) * 32, ra);
                     }
@@ -547,7 +556,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 fence_before_sync();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar_acce[g][acc]);
-                acc ^= 1u;
+                acc = (acc + 1 == (uint32_t)C::NACC) ? 0u : acc + 1;
                 if (acc == 0) acc_phase ^= 1u;
                 buf ^= 1;
                 accd += (double)accf;                    // FP64 fold once per tile
@@ -557,34 +566,34 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             if (SYM) {                                // row side of the last cluster reached
                 accd += (double)accf;
                 if (j < k && accd != 0.0 && rw != 0.f) atomicAdd(&W[pos * k + j], accd);
-                continue;
-            }
-            // clusters after the last processed chunk (the current one and empty ones)
-            while (j < k) {
-                accd += (double)accf;
-                accf = 0.f;
-                if (j != own) bmin.add(accd, (double)sizes[j]);
-                accd = 0.0;
-                ++j;
-            }
-            const double wown = (valid && own >= 0) ? w_own[pos] : 0.0;
-            if (valid) {
-                const int64_t o = a_out[pos];
-                float sv, av, bv;
-                if (own < 0 || own >= k) {
-                    sv = av = bv = NAN;
-                } else {
-                    const int64_t nc = sizes[own];
-                    const double a = (nc > 1) ? wown / (double)(nc - 1) : 0.0;
-                    const double b = bmin.value();
-                    const double mx = fmax(a, b);
-                    sv = (float)((nc > 1 && mx > 0.0) ? (b - a) / mx : 0.0);
-                    av = (float)a;
-                    bv = (float)b;
+            } else {
+                // clusters after the last processed chunk (the current one and empty ones)
+                while (j < k) {
+                    accd += (double)accf;
+                    accf = 0.f;
+                    if (j != own) bmin.add(accd, (double)sizes[j]);
+                    accd = 0.0;
+                    ++j;
                 }
-                s_out[o] = sv;
-                if (a_out_v) a_out_v[o] = av;
-                if (b_out_v) b_out_v[o] = bv;
+                const double wown = (valid && own >= 0) ? w_own[pos] : 0.0;
+                if (valid) {
+                    const int64_t o = a_out[pos];
+                    float sv, av, bv;
+                    if (own < 0 || own >= k) {
+                        sv = av = bv = NAN;
+                    } else {
+                        const int64_t nc = sizes[own];
+                        const double a = (nc > 1) ? wown / (double)(nc - 1) : 0.0;
+                        const double b = bmin.value();
+                        const double mx = fmax(a, b);
+                        sv = (float)((nc > 1 && mx > 0.0) ? (b - a) / mx : 0.0);
+                        av = (float)a;
+                        bv = (float)b;
+                    }
+                    s_out[o] = sv;
+                    if (a_out_v) a_out_v[o] = av;
+                    if (b_out_v) b_out_v[o] = bv;
+                }
             }
         }
     }
@@ -1183,6 +1192,11 @@ bool make_map(CUtensorMap *map, const void *ptr, int KD, int64_t rows, int box_r
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 128-column tiles wherever the A operand is one 128-byte K block (split TF32
+// at d <= 32 and every BF16 mode); 64-column tiles for two-block TF32 rows.
+constexpr bool kWideTiles = true;
+constexpr bool wide_tiles(int KD, bool BF) { return kWideTiles && (BF || KD == 32); }
+
 template <int METRIC, int KD, bool SPLIT, bool BF, bool SYM = false>
 cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, const CUtensorMap &alo,
                       const CUtensorMap &bhi, const CUtensorMap &blo, const float *a_hi,
@@ -1192,7 +1206,8 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
                       int64_t max_cluster_cols, double *w_own, float *s, float *a, float *b,
                       double *W = nullptr, const OwnItem *own_items = nullptr,
                       int64_t n_own_items = 0) {
-    using C = TcCfg<KD, SPLIT, BF>;
+    constexpr bool WIDE = wide_tiles(KD, BF);
+    using C = TcCfg<KD, SPLIT, BF, WIDE>;
     if (SYM) {
         // own-cluster pairs once each, into W at the own cluster
         if (n_own_items > 0) {
@@ -1211,7 +1226,7 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
             a_hi, a_lo, a_norm, a_lab, nrows, y_full, y_wn, poff, k, kChunk, w_own);
         count_launches(1);
     }
-    auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF, SYM>;
+    auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF, SYM, WIDE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     const int64_t groups = ((nrows + kTileM - 1) / kTileM + C::SLOTS - 1) / C::SLOTS;
@@ -1323,8 +1338,8 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     SILH_CK(cudaGetLastError());
     SILH_REQ(make_map(&m_ahi, rhi, KD, nrows, kTileM, bf) &&
                  make_map(&m_alo, rlo, KD, nrows, kTileM, bf) &&
-                 make_map(&m_bhi, yhi, KD, mp_max, kTileN, bf) &&
-                 make_map(&m_blo, ylo, KD, mp_max, kTileN, bf),
+                 make_map(&m_bhi, yhi, KD, mp_max, wide_tiles(KD, bf) ? 128 : kTileN, bf) &&
+                 make_map(&m_blo, ylo, KD, mp_max, wide_tiles(KD, bf) ? 128 : kTileN, bf),
              "tensor map encoding failed");
     SILH_CK(cudaGetDevice(&dev));
     SILH_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -1441,8 +1456,8 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     SILH_CK(cudaGetLastError());
     SILH_REQ(make_map(&m_ahi, yhi, KD, mp_max, kTileM, bf) &&
                  make_map(&m_alo, ylo, KD, mp_max, kTileM, bf) &&
-                 make_map(&m_bhi, yhi, KD, mp_max, kTileN, bf) &&
-                 make_map(&m_blo, ylo, KD, mp_max, kTileN, bf),
+                 make_map(&m_bhi, yhi, KD, mp_max, wide_tiles(KD, bf) ? 128 : kTileN, bf) &&
+                 make_map(&m_blo, ylo, KD, mp_max, wide_tiles(KD, bf) ? 128 : kTileN, bf),
              "tensor map encoding failed");
     SILH_CK(cudaGetDevice(&dev));
     SILH_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
