@@ -426,6 +426,31 @@ def run_batching(args):
     ms_separate = timed(separate, max(1, args.steps // 2))
     same = all(torch.equal(a, b) for a, b in zip(outs, sep_outs)) if variant == -1 else None
     maxdiff = max((a - b).abs().max().item() for a, b in zip(outs, sep_outs))
+    del g
+
+    # the same clusterings on the tensor cores (split TF32, Euclidean): one
+    # captured graph of the batched call against one silh_estimate per clustering
+    tc_prec = "3xtf32"
+    tc_outs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in items]
+    silh.silh_estimate_batched(Xt, items, "euclidean", outs=tc_outs, prec=tc_prec)
+    torch.cuda.synchronize()
+    gt = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gt):
+        silh.silh_estimate_batched(Xt, items, "euclidean", outs=tc_outs, prec=tc_prec)
+    gt.replay()
+    torch.cuda.synchronize()
+    ms_tc = timed(gt.replay, args.steps)
+    del gt
+    tc_sep = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in items]
+
+    def separate_tc():
+        for (lt, smp), k, o in zip(items, ks, tc_sep):
+            silh.silh_estimate(Xt, lt, k, smp, "euclidean", prec=tc_prec, out=o)
+
+    separate_tc()
+    ms_tc_sep = timed(separate_tc, max(1, args.steps // 2))
+    tc_same = all(torch.equal(a, b) for a, b in zip(tc_outs, tc_sep))
+    tc_vs_fp32 = max((a - b).abs().max().item() for a, b in zip(tc_outs, outs))
     pairs = float(n) * sum(smp.size for _, smp in items)
     line = {"metric": "batched PPS silhouette points/s (Phase 2, all clusterings)",
             "value": round(len(items) * n / (ms_batched * 1e-3), 1), "unit": "points/s",
@@ -434,10 +459,17 @@ def run_batching(args):
             "separate_ms": round(ms_separate, 3), "speedup_vs_separate": round(ms_separate / ms_batched, 3),
             "pairs_per_s": round(pairs / (ms_batched * 1e-3), 1), "variant": variant,
             "autotune_ms": tune_ms, "labels_and_phase1_s_all": round(t_phase1, 3),
-            "max_abs_diff_vs_separate": maxdiff,
+            "same_as_separate": same, "max_abs_diff_vs_separate": maxdiff,
+            "tensor_cores_3xtf32": {"batched_ms": round(ms_tc, 3),
+                                    "separate_ms": round(ms_tc_sep, 3),
+                                    "speedup_vs_separate": round(ms_tc_sep / ms_tc, 3),
+                                    "pairs_per_s": round(pairs / (ms_tc * 1e-3), 1),
+                                    "same_as_separate": tc_same,
+                                    "max_abs_diff_vs_fp32": tc_vs_fp32},
             "config": {"workload": f"batching: n={n}, d=16 FP32, {len(items)} clusterings k=2..{ks[-1]} "
-                                   f"(nearest random data-row centres), t=128, Euclidean, FP32 CUDA cores",
-                       "graph": "CUDA graph of one persistent launch"}}
+                                   f"(nearest random data-row centres), t=128, Euclidean; FP32 CUDA "
+                                   f"cores (autotuned tile), and tensor cores (split TF32)",
+                       "graph": "CUDA graph of the batched call"}}
     print(json.dumps(line))
 
 

@@ -1062,6 +1062,10 @@ extern "C" silh_status silh_estimate_batched(const void *X, silh_dtype dtype, in
         b.total_tiles = tiles;
         b.total_cols = cols;
     }
+    if (tc_eligible(metric, prec, d)) {
+        st = tc_sweep_batched(X, dtype, n, d, ld, metric, prec, items, order, stream);
+        goto done;
+    }
     SILH_CK(sc.alloc(&next_work, 1));
     for (BatchParams &b : parts) {
         SILH_CK(sc.alloc(&Y, (size_t)b.total_cols * D));

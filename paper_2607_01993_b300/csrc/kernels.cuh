@@ -48,6 +48,14 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
                      const int64_t *offsets, const int32_t *col_idx, const double *col_p, int64_t m,
                      int64_t max_cluster_cols, const int64_t *rows, int64_t nrows, float *s,
                      float *a, float *b, Scratch &sc, cudaStream_t stream);
+// Phase 2 of many clusterings of X (all rows each) on the tensor cores: per
+// clustering the operands of tc_sweep, then one persistent sweep over every
+// (clustering, row group); the results equal tc_sweep's bit for bit.  order:
+// the items in launch order (largest first).  Batches beyond the operand
+// budget are split into several launches.
+silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                             int metric, int prec, const silh_batch_item *items,
+                             const std::vector<int32_t> &order, cudaStream_t stream);
 // Exact silhouette of all n points on the tensor cores with each unordered
 // pair evaluated once (Euclidean / cosine, the tc_sweep precisions, d <= 64).
 // coff / order / h_sizes from cluster_sort.

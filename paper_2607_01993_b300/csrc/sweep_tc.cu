@@ -31,8 +31,10 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -205,7 +207,46 @@ __device__ __forceinline__ float half_chunk_sym(const uint32_t (&r)[16], const f
 // cluster pairs, which the direct pass covers).  Row sums per cluster and the
 // column sums (per column, over the warp's rows, which share one cluster) are
 // added to W (FP64, position x cluster); a separate pass forms s, a, b.
-template <int METRIC, int KD, bool SPLIT, bool BF, bool SYM = false, bool WIDE = false>
+//
+// BATCH (many clusterings of one dataset in one launch): clustering b has its
+// own cluster-sorted row operand, rows [arow, arow + nrows) of the shared row
+// buffers (zero padded to whole row groups), its own padded column range from
+// column ccol (a multiple of the tile width, zero padded to whole tiles), its
+// padded cluster offsets at poff + pbase, its cluster sizes and its output.
+// Work items are (clustering, row group), numbered clustering by clustering
+// from work_base; each is swept exactly as the single-clustering kernel sweeps
+// that row group, so a batched result equals the single call's bit for bit.
+struct TcItem {
+    int64_t work_base;
+    int64_t arow;
+    int64_t ccol;
+    int64_t nrows;
+    int64_t pbase;
+    const int64_t *sizes;
+    float *s_out;
+    int32_t k;
+    int32_t pad_;
+};
+constexpr int kMaxTcBatch = 256;
+// Device memory of one batched launch's operands; a batch that needs more is
+// split into several launches (a single clustering always fits one).
+constexpr size_t kTcBatchBytes = size_t(16) << 30;
+template <bool BATCH>
+struct TcBatchArg {            // one clustering: everything is in the kernel arguments
+    int32_t unused;
+};
+template <>
+struct TcBatchArg<true> {
+    int32_t nitems;
+    int64_t total_work;
+    TcItem items[kMaxTcBatch];
+};
+
+__device__ __forceinline__ int64_t bt_total_work(const TcBatchArg<false> &) { return 0; }
+__device__ __forceinline__ int64_t bt_total_work(const TcBatchArg<true> &b) { return b.total_work; }
+
+template <int METRIC, int KD, bool SPLIT, bool BF, bool SYM = false, bool WIDE = false,
+          bool BATCH = false>
 __global__ void __launch_bounds__(TcCfg<KD, SPLIT, BF, WIDE>::THREADS, 1)
 k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CUtensorMap m_alo,
            const __grid_constant__ CUtensorMap m_bhi, const __grid_constant__ CUtensorMap m_blo,
@@ -215,8 +256,9 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
            const float2 *__restrict__ y_wn, const int64_t *__restrict__ poff,
            const int64_t *__restrict__ sizes, int k, float tau,
            const double *__restrict__ w_own, float *__restrict__ s_out,
-           float *__restrict__ a_out_v, float *__restrict__ b_out_v,
-           double *__restrict__ W = nullptr) {
+           float *__restrict__ a_out_v, float *__restrict__ b_out_v, double *__restrict__ W,
+           const __grid_constant__ TcBatchArg<BATCH> bt) {
+    static_assert(!(BATCH && SYM), "the symmetric exact sweep is not batched");
     using C = TcCfg<KD, SPLIT, BF, WIDE>;
     constexpr int TN = C::TN;
     extern __shared__ uint8_t smem_raw[];
@@ -234,10 +276,50 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     uint8_t *sB = sm + C::A_BYTES;      // [stage][part][kb][128 cols][128 B]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ntiles = (nrows + kTileM - 1) / kTileM;
-    const int64_t ngroups = (ntiles + C::SLOTS - 1) / C::SLOTS;
-    const int64_t mp = poff[k];                       // padded column count
-    const int64_t nct = (mp + TN - 1) / TN;
+    const int64_t ngroups = BATCH ? bt_total_work(bt)
+                                  : ((nrows + kTileM - 1) / kTileM + C::SLOTS - 1) / C::SLOTS;
+    // Work item w as (clustering, row group): its row group rg, the first row
+    // (arow) and column (ccol) of its clustering in the operands, the row
+    // count, padded cluster offsets, sizes, cluster count, output, and the
+    // padded column count mp with its column-tile count nct.
+    struct View {
+        int64_t rg, arow, ccol, nrows, mp, nct;
+        const int64_t *poff, *sizes;
+        float *s_out;
+        int k;
+    };
+    auto view_of = [&](int64_t w) -> View {
+        View v;
+        if constexpr (BATCH) {
+            int lo = 0, hi = bt.nitems - 1;           // last clustering with work_base <= w
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (bt.items[mid].work_base <= w) lo = mid;
+                else hi = mid - 1;
+            }
+            const TcItem &it = bt.items[lo];
+            v.rg = w - it.work_base;
+            v.arow = it.arow;
+            v.ccol = it.ccol;
+            v.nrows = it.nrows;
+            v.poff = poff + it.pbase;
+            v.sizes = it.sizes;
+            v.s_out = it.s_out;
+            v.k = it.k;
+        } else {
+            v.rg = w;
+            v.arow = 0;
+            v.ccol = 0;
+            v.nrows = nrows;
+            v.poff = poff;
+            v.sizes = sizes;
+            v.s_out = s_out;
+            v.k = k;
+        }
+        v.mp = v.poff[v.k];
+        v.nct = (v.mp + TN - 1) / TN;
+        return v;
+    };
     // Row group of this CTA's it-th round: blockIdx.x + it * gridDim.x, except
     // that SYM (whose groups shrink with their index) reverses odd rounds so
     // that the CTAs' totals even out; -1 when the round has no group for it,
@@ -285,16 +367,18 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             uint32_t phase = 0;
             int64_t idx = 0;
             for (int64_t it = 0; !abort_flag; ++it) {
-                const int64_t rg = group_of(it);
-                if (rg == -2) break;
-                if (rg < 0) continue;
+                const int64_t w = group_of(it);
+                if (w == -2) break;
+                if (w < 0) continue;
+                const View v = view_of(w);
+                const int64_t rg = v.rg;
                 if (idx > 0 && !mbar_wait(&bar_aempty, (uint32_t)((idx - 1) & 1), kWaitNs)) {
                     abort_flag = 1;
                     break;
                 }
                 mbar_expect_tx(&bar_afull, C::A_BYTES);
                 for (int g = 0; g < C::SLOTS; ++g) {
-                    const int y = (int)((rg * C::SLOTS + g) * kTileM);
+                    const int y = (int)(v.arow + (rg * C::SLOTS + g) * kTileM);
                     uint8_t *a = sA + g * C::A_SLOT;
                     for (int kb = 0; kb < C::KB; ++kb) {
                         tma_load_2d(&m_ahi, &bar_afull, a + kb * kTileM * 128, kb * C::KELEM, y);
@@ -303,7 +387,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                                         kb * C::KELEM, y);
                     }
                 }
-                for (int64_t ct = ct_first(rg); ct < nct; ++ct) {
+                for (int64_t ct = ct_first(rg); ct < v.nct; ++ct) {
                     if (!mbar_wait(&bar_empty[stage], phase ^ 1u, kWaitNs)) {
                         abort_flag = 1;
                         break;
@@ -312,11 +396,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     mbar_expect_tx(&bar_full[stage], C::B_BYTES);
                     for (int kb = 0; kb < C::KB; ++kb) {
                         tma_load_2d(&m_bhi, &bar_full[stage], dst + kb * TN * 128,
-                                    kb * C::KELEM, (int)(ct * TN));
+                                    kb * C::KELEM, (int)(v.ccol + ct * TN));
                         if (SPLIT)
                             tma_load_2d(&m_blo, &bar_full[stage],
                                         dst + (C::KB + kb) * TN * 128, kb * C::KELEM,
-                                        (int)(ct * TN));
+                                        (int)(v.ccol + ct * TN));
                     }
                     if (++stage == C::STAGES) {
                         stage = 0;
@@ -336,14 +420,16 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             uint32_t phase = 0, acc = 0, acc_phase = 0;
             int64_t idx = 0;
             for (int64_t it = 0; !abort_flag; ++it) {
-                const int64_t rg = group_of(it);
-                if (rg == -2) break;
-                if (rg < 0) continue;
+                const int64_t w = group_of(it);
+                if (w == -2) break;
+                if (w < 0) continue;
+                const View v = view_of(w);
+                const int64_t rg = v.rg;
                 if (!mbar_wait(&bar_afull, (uint32_t)(idx & 1), kWaitNs)) {
                     abort_flag = 1;
                     break;
                 }
-                for (int64_t ct = ct_first(rg); ct < nct; ++ct) {
+                for (int64_t ct = ct_first(rg); ct < v.nct; ++ct) {
                     if (!mbar_wait(&bar_full[stage], phase, kWaitNs)) {
                         abort_flag = 1;
                         break;
@@ -422,37 +508,45 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
         uint32_t acc = 0, acc_phase = 0;
         int buf = 0;
         for (int64_t it = 0;; ++it) {
-            const int64_t rg = group_of(it);
-            if (rg == -2) break;
-            if (rg < 0) continue;
-            const int64_t pos = (rg * C::SLOTS + g) * kTileM + r_local;
-            const bool valid = pos < nrows;
-            const int own = valid ? a_lab[pos] : -1;
-            const float xn = valid ? a_norm[pos] : 0.f;
-            const float *xh = a_hi + (valid ? pos : 0) * KD;
+            const int64_t w = group_of(it);
+            if (w == -2) break;
+            if (w < 0) continue;
+            const View v = view_of(w);
+            const int64_t rg = v.rg;
+            const int64_t mp = v.mp;
+            const int64_t nct = v.nct;
+            const int64_t *vpoff = v.poff;
+            const int vk = v.k;
+            const int64_t pos = (rg * C::SLOTS + g) * kTileM + r_local;   // within the clustering
+            const bool valid = pos < v.nrows;
+            const int64_t apos = v.arow + pos;                            // row of the operands
+            const int own = valid ? a_lab[apos] : -1;
+            const float xn = valid ? a_norm[apos] : 0.f;
+            const float *xh = a_hi + (valid ? apos : 0) * KD;
             // FP32 rows for the direct recompute: hi + lo for TF32 operands, the
             // FP32 copy (a_hi) for BF16 operands and for the symmetric layout
             constexpr bool kFull = BF || SYM;
-            const float *xl = kFull ? xh : a_lo + (valid ? pos : 0) * KD;
+            const float *xl = kFull ? xh : a_lo + (valid ? apos : 0) * KD;
             // SYM: this warp's 32-row block starts at wblk; rows are the padded
             // columns, so a row's weight (1 point / 0 padding) is its column weight
             const int64_t wblk = (rg * C::SLOTS + g) * kTileM + 32 * q;
             const float rw = (SYM && valid) ? y_wn[pos].x : 0.f;
             const int64_t ct0 = ct_first(rg);
             int j = 0;
-            while (SYM && j < k && poff[j + 1] <= ct0 * TN) ++j;
-            int64_t pbnd = (j < k) ? poff[j + 1] : LLONG_MAX;
+            while (SYM && j < vk && vpoff[j + 1] <= ct0 * TN) ++j;
+            int64_t pbnd = (j < vk) ? vpoff[j + 1] : LLONG_MAX;
             double accd = 0.0;
             RatioMin bmin;
             float accf = 0.f;                         // current cluster, this tile
             bool dead = false;
             // (weight, |y|^2) of this thread's column, fetched one tile ahead
+            const float2 *ywn = y_wn + v.ccol;
             const int64_t c_first = ct0 * TN + et;
-            float2 wn_next = (et < TN && c_first < mp) ? y_wn[c_first] : make_float2(0.f, 0.f);
+            float2 wn_next = (et < TN && c_first < mp) ? ywn[c_first] : make_float2(0.f, 0.f);
             for (int64_t ct = ct0; ct < nct; ++ct) {
                 const float2 wn_cur = wn_next;
                 const int64_t cn = (ct + 1) * TN + et;
-                if (et < TN) wn_next = (cn < mp) ? y_wn[cn] : make_float2(0.f, 0.f);
+                if (et < TN) wn_next = (cn < mp) ? ywn[cn] : make_float2(0.f, 0.f);
                 if (et < TN) {
                     float *f = reinterpret_cast<float *>(&sh_wn[g][buf][et >> 1]);
                     f[et & 1] = wn_cur.x;
@@ -477,19 +571,19 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     const int64_t c0 = ct * TN + ch * 32;
                     // clusters that end here (empty ones included) are complete;
                     // the own cluster's sum comes from the direct pass (w_own)
-                    while (j < k && c0 == pbnd) {
+                    while (j < vk && c0 == pbnd) {
                         accd += (double)accf;
                         accf = 0.f;
                         if (SYM) {
                             if (accd != 0.0 && rw != 0.f) atomicAdd(&W[pos * k + j], accd);
                         } else if (j != own) {
-                            bmin.add(accd, (double)sizes[j]);
+                            bmin.add(accd, (double)v.sizes[j]);
                         }
                         accd = 0.0;
                         ++j;
-                        pbnd = (j < k) ? poff[j + 1] : LLONG_MAX;
+                        pbnd = (j < vk) ? vpoff[j + 1] : LLONG_MAX;
                     }
-                    const bool live = j < k;              // else padding beyond the last cluster
+                    const bool live = j < vk;             // else padding beyond the last cluster
                     const bool mine = live && (j == own); // own-cluster pairs: skipped here
                     // SYM: own is uniform over the warp (one cluster per 32-row block)
                     const bool skip = SYM ? (!live || mine || c0 <= wblk)
@@ -531,7 +625,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             const float *f = reinterpret_cast<const float *>(
                                 &sh_wn[g][buf][ch * 16 + (i >> 1)]);
                             const float2 wn = make_float2(f[i & 1], f[2 + (i & 1)]);
-                            const float *yc = y_full + (c0 + i) * KD;
+                            const float *yc = y_full + (v.ccol + c0 + i) * KD;
                             float dist;
                             if (METRIC == SILH_EUCLIDEAN) {
                                 const float s2 = xn + wn.y;
@@ -544,10 +638,10 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             }
                             part = fmaf(wn.x, dist, part);
                             if (SYM) {                // column side of this pair
-                                float v = dist * rw;
+                                float cv = dist * rw;
 #pragma unroll
-                                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                                if (lane == 0) atomicAdd(&W[(c0 + i) * k + own], (double)v);
+                                for (int o = 16; o > 0; o >>= 1) cv += __shfl_xor_sync(0xffffffffu, cv, o);
+                                if (lane == 0) atomicAdd(&W[(c0 + i) * k + own], (double)cv);
                             }
                         }
                     }
@@ -568,21 +662,21 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 if (j < k && accd != 0.0 && rw != 0.f) atomicAdd(&W[pos * k + j], accd);
             } else {
                 // clusters after the last processed chunk (the current one and empty ones)
-                while (j < k) {
+                while (j < vk) {
                     accd += (double)accf;
                     accf = 0.f;
-                    if (j != own) bmin.add(accd, (double)sizes[j]);
+                    if (j != own) bmin.add(accd, (double)v.sizes[j]);
                     accd = 0.0;
                     ++j;
                 }
-                const double wown = (valid && own >= 0) ? w_own[pos] : 0.0;
+                const double wown = (valid && own >= 0) ? w_own[apos] : 0.0;
                 if (valid) {
-                    const int64_t o = a_out[pos];
+                    const int64_t o = a_out[apos];
                     float sv, av, bv;
-                    if (own < 0 || own >= k) {
+                    if (own < 0 || own >= vk) {
                         sv = av = bv = NAN;
                     } else {
-                        const int64_t nc = sizes[own];
+                        const int64_t nc = v.sizes[own];
                         const double a = (nc > 1) ? wown / (double)(nc - 1) : 0.0;
                         const double b = bmin.value();
                         const double mx = fmax(a, b);
@@ -590,7 +684,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         av = (float)a;
                         bv = (float)b;
                     }
-                    s_out[o] = sv;
+                    v.s_out[o] = sv;
                     if (a_out_v) a_out_v[o] = av;
                     if (b_out_v) b_out_v[o] = bv;
                 }
@@ -977,17 +1071,23 @@ __device__ __forceinline__ void store_split(float v, int64_t row, int c, int KD,
 // Row operand in sorted order: hi/lo split (zero padded), the FP32 row when
 // the operands are BF16 (full, KD columns; the direct recompute reads it),
 // squared norm (Euclidean) or unit scaling (cosine), label, output index.
+// Positions nrows .. nrows_pad - 1 get zero hi/lo rows (the tail of a row
+// group that the tile loads read).
 template <class T, bool BF>
 __global__ void k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int64_t n,
                                  const int32_t *__restrict__ labels, const int64_t *__restrict__ rows,
-                                 const int64_t *__restrict__ perm, int64_t nrows, int KD, int k,
-                                 int metric, const float *__restrict__ mu, void *__restrict__ hi,
-                                 void *__restrict__ lo, float *__restrict__ full,
-                                 float *__restrict__ nrm, int32_t *__restrict__ lab,
-                                 int64_t *__restrict__ outi) {
+                                 const int64_t *__restrict__ perm, int64_t nrows, int64_t nrows_pad,
+                                 int KD, int k, int metric, const float *__restrict__ mu,
+                                 void *__restrict__ hi, void *__restrict__ lo,
+                                 float *__restrict__ full, float *__restrict__ nrm,
+                                 int32_t *__restrict__ lab, int64_t *__restrict__ outi) {
     const int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
-    if (p >= nrows) return;
+    if (p >= nrows_pad) return;
+    if (p >= nrows) {
+        for (int c = lane; c < (BF ? 64 : KD); c += 32) store_split<BF>(0.f, p, c, KD, hi, lo);
+        return;
+    }
     const int64_t r = perm[p];
     const int64_t e = rows ? rows[r] : r;
     const bool ok = e >= 0 && e < n;
@@ -1197,6 +1297,25 @@ bool make_map(CUtensorMap *map, const void *ptr, int KD, int64_t rows, int box_r
 constexpr bool kWideTiles = true;
 constexpr bool wide_tiles(int KD, bool BF) { return kWideTiles && (BF || KD == 32); }
 
+// Own-cluster pass of the row-streaming sweep: W_own of every sorted row is
+// zeroed, then set to the direct FP32 sums over its own cluster's columns.
+template <int METRIC, int KD, bool BF>
+cudaError_t launch_own(cudaStream_t stream, const float *a_hi, const float *a_lo,
+                       const float *a_norm, const int32_t *a_lab, int64_t nrows,
+                       const float *y_full, const float2 *y_wn, const int64_t *poff, int k,
+                       int64_t max_cluster_cols, double *w_own) {
+    constexpr int64_t kChunk = 2048;
+    const int64_t nchunk = std::max<int64_t>(1, (max_cluster_cols + 31 + kChunk - 1) / kChunk);
+    cudaError_t e = cudaMemsetAsync(w_own, 0, sizeof(double) * (size_t)nrows, stream);
+    if (e != cudaSuccess) return e;
+    // the own-cluster pass reads FP32 rows: hi + lo (TF32 operands) or the
+    // FP32 copy (BF16 operands)
+    k_own_direct<METRIC, KD, BF><<<dim3((unsigned)((nrows + 255) / 256), (unsigned)nchunk), 128, 0, stream>>>(
+        a_hi, a_lo, a_norm, a_lab, nrows, y_full, y_wn, poff, k, kChunk, w_own);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 template <int METRIC, int KD, bool SPLIT, bool BF, bool SYM = false>
 cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, const CUtensorMap &alo,
                       const CUtensorMap &bhi, const CUtensorMap &blo, const float *a_hi,
@@ -1216,15 +1335,9 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
             count_launches(1);
         }
     } else {
-        constexpr int64_t kChunk = 2048;
-        const int64_t nchunk = std::max<int64_t>(1, (max_cluster_cols + 31 + kChunk - 1) / kChunk);
-        cudaError_t e0 = cudaMemsetAsync(w_own, 0, sizeof(double) * (size_t)nrows, stream);
+        cudaError_t e0 = launch_own<METRIC, KD, BF>(stream, a_hi, a_lo, a_norm, a_lab, nrows, y_full,
+                                                    y_wn, poff, k, max_cluster_cols, w_own);
         if (e0 != cudaSuccess) return e0;
-        // the own-cluster pass reads FP32 rows: hi + lo (TF32 operands) or the
-        // FP32 copy (BF16 operands)
-        k_own_direct<METRIC, KD, BF><<<dim3((unsigned)((nrows + 255) / 256), (unsigned)nchunk), 128, 0, stream>>>(
-            a_hi, a_lo, a_norm, a_lab, nrows, y_full, y_wn, poff, k, kChunk, w_own);
-        count_launches(1);
     }
     auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF, SYM, WIDE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
@@ -1233,9 +1346,117 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
     const int grid = (int)std::min<int64_t>(groups, nsm);
     kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_norm, a_lab,
                                                 a_out, nrows, y_full, y_wn, poff, sizes, k, tau,
-                                                w_own, s, a, b, W);
+                                                w_own, s, a, b, W, TcBatchArg<false>{});
     count_launches(1);
     return cudaGetLastError();
+}
+
+// One persistent sweep over the (clustering, row group) work items of a batch;
+// the row and column operands, weights, offsets and W_own of all its
+// clusterings live in shared buffers (bases in bt).
+template <int METRIC, int KD, bool SPLIT, bool BF>
+cudaError_t launch_tc_batched(int nsm, cudaStream_t stream, const CUtensorMap &ahi,
+                              const CUtensorMap &alo, const CUtensorMap &bhi,
+                              const CUtensorMap &blo, const float *a_hi, const float *a_lo,
+                              const float *a_norm, const int32_t *a_lab, const int64_t *a_out,
+                              const float *y_full, const float2 *y_wn, const int64_t *poff,
+                              float tau, const double *w_own, const TcBatchArg<true> &bt) {
+    constexpr bool WIDE = wide_tiles(KD, BF);
+    using C = TcCfg<KD, SPLIT, BF, WIDE>;
+    auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF, false, WIDE, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>(bt.total_work, nsm);
+    kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_norm, a_lab,
+                                                a_out, 0, y_full, y_wn, poff, nullptr, 0, tau,
+                                                w_own, nullptr, nullptr, nullptr, nullptr, bt);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Operands of one clustering in the tensor-core layouts, written into
+// caller-provided device buffers: the listed rows sorted by cluster (hi/lo
+// split, the FP32 copy for BF16 operands, norms, labels, output indices;
+// nrows_pad rows, the tail zero) and the cluster-major sample columns padded
+// per cluster to multiples of 32 (FP32 copy, hi/lo split, weight and norm,
+// padded offsets; mp_pad columns, the tail zero with weight 0).
+struct TcOps {
+    uint8_t *rhi, *rlo;
+    float *rfull, *rn;
+    int32_t *lab;
+    int64_t *outi;
+    float *yf;
+    uint8_t *yhi, *ylo;
+    float2 *ywn;
+    int64_t *poff;
+};
+
+silh_status tc_prepare(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                       const int32_t *labels, int32_t k, int metric, int KD, bool bf,
+                       const int64_t *offsets, const int32_t *col_idx, const double *col_p,
+                       int64_t m, const int64_t *rows, int64_t nrows, int64_t nrows_pad,
+                       int64_t mp_pad, const TcOps &o, cudaStream_t stream) {
+    silh_status st = SILH_OK;
+    Scratch sc(stream);                          // temporaries, released on return
+    const int tile = (k <= 512) ? 1024 : 8192;
+    const int ntiles = (int)std::max<int64_t>(1, (nrows + tile - 1) / tile);
+    const size_t hsmem = sizeof(int32_t) * (size_t)(k + 1);
+    const int mean_blocks = 128;
+    int32_t *counts = nullptr;
+    int64_t *tbase = nullptr, *tot = nullptr, *boff = nullptr, *perm = nullptr;
+    double *mpart = nullptr;
+    float *mu = nullptr;
+    SILH_CK(sc.alloc(&counts, (size_t)(k + 1) * ntiles));
+    SILH_CK(sc.alloc(&tbase, (size_t)(k + 1) * ntiles));
+    SILH_CK(sc.alloc(&tot, (size_t)k + 1));
+    SILH_CK(sc.alloc(&boff, (size_t)k + 2));
+    SILH_CK(sc.alloc(&perm, (size_t)nrows));
+    SILH_CK(sc.alloc(&mpart, (size_t)mean_blocks * d));
+    SILH_CK(sc.alloc(&mu, (size_t)d));
+    if (hsmem > 48 * 1024) {
+        SILH_CK(cudaFuncSetAttribute(k_key_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)hsmem));
+        SILH_CK(cudaFuncSetAttribute(k_key_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)hsmem));
+    }
+    k_key_hist<<<ntiles, 32, hsmem, stream>>>(labels, rows, nrows, n, k, tile, ntiles, counts);
+    k_key_scan<<<k + 1, 256, 0, stream>>>(counts, ntiles, tbase, tot);
+    k_key_offsets<<<1, 1024, 0, stream>>>(tot, k + 1, boff);
+    k_key_scatter<<<ntiles, 32, hsmem, stream>>>(labels, rows, nrows, n, k, tile, ntiles, tbase,
+                                                  boff, perm);
+    k_col_poff<<<1, 1024, 0, stream>>>(offsets, k, o.poff);
+    count_launches(5);
+    if (metric == SILH_EUCLIDEAN) {
+        // distances are shift invariant: centre rows and columns on the sample mean
+        const int per = (int)((m + mean_blocks - 1) / mean_blocks);
+        if (dtype == SILH_F32)
+            k_col_mean_partial<float><<<mean_blocks, 128, 0, stream>>>((const float *)X, d, ld,
+                                                                       col_idx, m, per, mpart);
+        else
+            k_col_mean_partial<__nv_bfloat16><<<mean_blocks, 128, 0, stream>>>(
+                (const __nv_bfloat16 *)X, d, ld, col_idx, m, per, mpart);
+        k_col_mean_final<<<1, 128, 0, stream>>>(mpart, mean_blocks, d, m, mu);
+        count_launches(2);
+    } else {
+        mu = nullptr;
+    }
+#define SILH_TC_GATHER(T, BFV)                                                                  \
+    k_gather_rows_tc<T, BFV><<<ceil_div_i(nrows_pad, 8), 256, 0, stream>>>(                    \
+        (const T *)X, d, ld, n, labels, rows, perm, nrows, nrows_pad, KD, k, metric, mu, o.rhi, \
+        o.rlo, o.rfull, o.rn, o.lab, o.outi);                                                   \
+    k_gather_cols_tc<T, BFV><<<ceil_div_i(mp_pad, 8), 256, 0, stream>>>(                       \
+        (const T *)X, d, ld, col_idx, col_p, offsets, o.poff, k, mp_pad, KD, metric, mu, o.yf,  \
+        o.yhi, o.ylo, o.ywn);
+    if (dtype == SILH_F32) {
+        if (bf) { SILH_TC_GATHER(float, true) } else { SILH_TC_GATHER(float, false) }
+    } else {
+        if (bf) { SILH_TC_GATHER(__nv_bfloat16, true) } else { SILH_TC_GATHER(__nv_bfloat16, false) }
+    }
+#undef SILH_TC_GATHER
+    count_launches(2);
+    SILH_CK(cudaGetLastError());
+done:
+    return st;
 }
 
 }  // namespace
@@ -1258,88 +1479,32 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     const bool bf = prec == SILH_PREC_BF16 || prec == SILH_PREC_BF16X3;
     const int KE = bf ? 64 : KD;                  // operand row length (128 B per K block)
     const size_t ebytes = bf ? 2 : 4;
-    const int tile = (k <= 512) ? 1024 : 8192;
-    const int ntiles = (int)std::max<int64_t>(1, (nrows + tile - 1) / tile);
-    const size_t hsmem = sizeof(int32_t) * (size_t)(k + 1);
     const int64_t mp_max = m + 31 * (int64_t)k;   // padded columns, upper bound
     int dev = 0, nsm = 0;
-    int32_t *counts = nullptr, *lab = nullptr;
-    int64_t *tbase = nullptr, *tot = nullptr, *boff = nullptr, *perm = nullptr, *outi = nullptr;
-    int64_t *poff = nullptr;
-    double *w_own = nullptr, *mpart = nullptr;
-    float *mu = nullptr;
-    const int mean_blocks = 128;
-    uint8_t *rhi = nullptr, *rlo = nullptr, *yhi = nullptr, *ylo = nullptr;
-    float *rfull = nullptr, *rn = nullptr, *yf = nullptr;
-    float2 *ywn = nullptr;
+    double *w_own = nullptr;
+    TcOps o = {};
     CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
-    const float tau = (metric == SILH_EUCLIDEAN) ? 0.25f : 0.25f;
+    const float tau = 0.25f;
 
-    SILH_CK(sc.alloc(&counts, (size_t)(k + 1) * ntiles));
-    SILH_CK(sc.alloc(&tbase, (size_t)(k + 1) * ntiles));
-    SILH_CK(sc.alloc(&tot, (size_t)k + 1));
-    SILH_CK(sc.alloc(&boff, (size_t)k + 2));
-    SILH_CK(sc.alloc(&perm, (size_t)nrows));
-    SILH_CK(sc.alloc(&outi, (size_t)nrows));
-    SILH_CK(sc.alloc(&lab, (size_t)nrows));
-    SILH_CK(sc.alloc(&rhi, (size_t)nrows * KE * ebytes));
-    SILH_CK(sc.alloc(&rlo, (size_t)nrows * KE * ebytes));
-    if (bf) SILH_CK(sc.alloc(&rfull, (size_t)nrows * KD));
-    SILH_CK(sc.alloc(&rn, (size_t)nrows));
-    SILH_CK(sc.alloc(&poff, (size_t)k + 1));
+    SILH_CK(sc.alloc(&o.outi, (size_t)nrows));
+    SILH_CK(sc.alloc(&o.lab, (size_t)nrows));
+    SILH_CK(sc.alloc(&o.rhi, (size_t)nrows * KE * ebytes));
+    SILH_CK(sc.alloc(&o.rlo, (size_t)nrows * KE * ebytes));
+    if (bf) SILH_CK(sc.alloc(&o.rfull, (size_t)nrows * KD));
+    SILH_CK(sc.alloc(&o.rn, (size_t)nrows));
+    SILH_CK(sc.alloc(&o.poff, (size_t)k + 1));
     SILH_CK(sc.alloc(&w_own, (size_t)nrows));
-    SILH_CK(sc.alloc(&mpart, (size_t)mean_blocks * d));
-    SILH_CK(sc.alloc(&mu, (size_t)d));
-    SILH_CK(sc.alloc(&yf, (size_t)mp_max * KD));
-    SILH_CK(sc.alloc(&yhi, (size_t)mp_max * KE * ebytes));
-    SILH_CK(sc.alloc(&ylo, (size_t)mp_max * KE * ebytes));
-    SILH_CK(sc.alloc(&ywn, (size_t)mp_max));
-    if (hsmem > 48 * 1024) {
-        SILH_CK(cudaFuncSetAttribute(k_key_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)hsmem));
-        SILH_CK(cudaFuncSetAttribute(k_key_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)hsmem));
-    }
-    k_key_hist<<<ntiles, 32, hsmem, stream>>>(labels, rows, nrows, n, k, tile, ntiles, counts);
-    k_key_scan<<<k + 1, 256, 0, stream>>>(counts, ntiles, tbase, tot);
-    k_key_offsets<<<1, 1024, 0, stream>>>(tot, k + 1, boff);
-    k_key_scatter<<<ntiles, 32, hsmem, stream>>>(labels, rows, nrows, n, k, tile, ntiles, tbase,
-                                                  boff, perm);
-    k_col_poff<<<1, 1024, 0, stream>>>(offsets, k, poff);
-    count_launches(5);
-    if (metric == SILH_EUCLIDEAN) {
-        // distances are shift invariant: centre rows and columns on the sample mean
-        const int per = (int)((m + mean_blocks - 1) / mean_blocks);
-        if (dtype == SILH_F32)
-            k_col_mean_partial<float><<<mean_blocks, 128, 0, stream>>>((const float *)X, d, ld,
-                                                                       col_idx, m, per, mpart);
-        else
-            k_col_mean_partial<__nv_bfloat16><<<mean_blocks, 128, 0, stream>>>(
-                (const __nv_bfloat16 *)X, d, ld, col_idx, m, per, mpart);
-        k_col_mean_final<<<1, 128, 0, stream>>>(mpart, mean_blocks, d, m, mu);
-        count_launches(2);
-    } else {
-        mu = nullptr;
-    }
-#define SILH_TC_GATHER(T, BFV)                                                                  \
-    k_gather_rows_tc<T, BFV><<<ceil_div_i(nrows, 8), 256, 0, stream>>>(                        \
-        (const T *)X, d, ld, n, labels, rows, perm, nrows, KD, k, metric, mu, rhi, rlo, rfull, rn, \
-        lab, outi);                                                                             \
-    k_gather_cols_tc<T, BFV><<<ceil_div_i(mp_max, 8), 256, 0, stream>>>(                       \
-        (const T *)X, d, ld, col_idx, col_p, offsets, poff, k, mp_max, KD, metric, mu, yf, yhi,  \
-        ylo, ywn);
-    if (dtype == SILH_F32) {
-        if (bf) { SILH_TC_GATHER(float, true) } else { SILH_TC_GATHER(float, false) }
-    } else {
-        if (bf) { SILH_TC_GATHER(__nv_bfloat16, true) } else { SILH_TC_GATHER(__nv_bfloat16, false) }
-    }
-#undef SILH_TC_GATHER
-    count_launches(2);
-    SILH_CK(cudaGetLastError());
-    SILH_REQ(make_map(&m_ahi, rhi, KD, nrows, kTileM, bf) &&
-                 make_map(&m_alo, rlo, KD, nrows, kTileM, bf) &&
-                 make_map(&m_bhi, yhi, KD, mp_max, wide_tiles(KD, bf) ? 128 : kTileN, bf) &&
-                 make_map(&m_blo, ylo, KD, mp_max, wide_tiles(KD, bf) ? 128 : kTileN, bf),
+    SILH_CK(sc.alloc(&o.yf, (size_t)mp_max * KD));
+    SILH_CK(sc.alloc(&o.yhi, (size_t)mp_max * KE * ebytes));
+    SILH_CK(sc.alloc(&o.ylo, (size_t)mp_max * KE * ebytes));
+    SILH_CK(sc.alloc(&o.ywn, (size_t)mp_max));
+    st = tc_prepare(X, dtype, n, d, ld, labels, k, metric, KD, bf, offsets, col_idx, col_p, m,
+                    rows, nrows, nrows, mp_max, o, stream);
+    if (st != SILH_OK) goto done;
+    SILH_REQ(make_map(&m_ahi, o.rhi, KD, nrows, kTileM, bf) &&
+                 make_map(&m_alo, o.rlo, KD, nrows, kTileM, bf) &&
+                 make_map(&m_bhi, o.yhi, KD, mp_max, wide_tiles(KD, bf) ? 128 : kTileN, bf) &&
+                 make_map(&m_blo, o.ylo, KD, mp_max, wide_tiles(KD, bf) ? 128 : kTileN, bf),
              "tensor map encoding failed");
     SILH_CK(cudaGetDevice(&dev));
     SILH_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -1348,9 +1513,9 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
 #define SILH_TC_CASE(MET, KDV, SP, BFV)                                                        \
     if (metric == MET && KD == KDV && split == SP && bf == BFV) {                              \
         SILH_CK((launch_tc<MET, KDV, SP, BFV>(                                                  \
-            nsm, stream, m_ahi, m_alo, m_bhi, m_blo, BFV ? rfull : (const float *)rhi,         \
-            BFV ? nullptr : (const float *)rlo, rn, lab, outi, nrows, yf, ywn, poff, sizes, k, \
-            tau, max_cluster_cols, w_own, s, a, b)));                                         \
+            nsm, stream, m_ahi, m_alo, m_bhi, m_blo, BFV ? o.rfull : (const float *)o.rhi,     \
+            BFV ? nullptr : (const float *)o.rlo, o.rn, o.lab, o.outi, nrows, o.yf, o.ywn,      \
+            o.poff, sizes, k, tau, max_cluster_cols, w_own, s, a, b)));                         \
     }
 #define SILH_TC_CASES(MET, KDV)             \
     SILH_TC_CASE(MET, KDV, true, false)     \
@@ -1363,6 +1528,148 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     SILH_TC_CASES(SILH_COSINE, 64)
 #undef SILH_TC_CASES
 #undef SILH_TC_CASE
+done:
+    return st;
+}
+
+silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                             int metric, int prec, const silh_batch_item *items,
+                             const std::vector<int32_t> &order, cudaStream_t stream) {
+    silh_status st = SILH_OK;
+    const int KD = d <= 32 ? 32 : 64;
+    const bool split = prec == SILH_PREC_3XTF32 || prec == SILH_PREC_BF16X3;
+    const bool bf = prec == SILH_PREC_BF16 || prec == SILH_PREC_BF16X3;
+    const int KE = bf ? 64 : KD;
+    const size_t ebytes = bf ? 2 : 4;
+    const int slots = (bf || KD == 32) ? 4 : 2;   // row tiles per row group (TcCfg::SLOTS)
+    const int64_t group_rows = (int64_t)slots * kTileM;
+    const int64_t rows_pad = (n + 4 * kTileM - 1) / (4 * kTileM) * (4 * kTileM);
+    const int64_t work_per_item = (n + group_rows - 1) / group_rows;
+    const size_t row_bytes = 2 * KE * ebytes + (bf ? KD * 4 : 0) + 4 + 4 + 8 + 8;
+    const size_t col_bytes = KD * 4 + 2 * KE * ebytes + 8;
+    const float tau = 0.25f;
+    int dev = 0, nsm = 0;
+    auto cols_of = [&](int32_t i) -> int64_t {     // padded column count, whole 128-column tiles
+        const silh_sample *S = items[i].sample;
+        return (S->size + 31 * (int64_t)S->k + 127) / 128 * 128;
+    };
+    auto bytes_of = [&](int32_t i) -> size_t {
+        return (size_t)rows_pad * row_bytes + (size_t)cols_of(i) * col_bytes +
+               8 * (size_t)(items[i].sample->k + 1);
+    };
+    SILH_CK(cudaGetDevice(&dev));
+    SILH_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    for (size_t i0 = 0; i0 < order.size();) {
+        // as many clusterings as fit the group budget (at least one)
+        size_t i1 = i0, bytes = 0;
+        while (i1 < order.size() && i1 - i0 < (size_t)kMaxTcBatch) {
+            const size_t b = bytes_of(order[i1]);
+            if (i1 > i0 && bytes + b > kTcBatchBytes) break;
+            bytes += b;
+            ++i1;
+        }
+        const int nb = (int)(i1 - i0);
+        int64_t cols_total = 0, poff_total = 0;
+        for (size_t i = i0; i < i1; ++i) {
+            cols_total += cols_of(order[i]);
+            poff_total += items[order[i]].sample->k + 1;
+        }
+        const int64_t rows_total = rows_pad * nb;
+        Scratch gs(stream);                       // this group's operands
+        TcOps g = {};
+        double *w_own = nullptr;
+        CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
+        TcBatchArg<true> bt;
+        std::memset(&bt, 0, sizeof(bt));
+        bt.nitems = nb;
+        bt.total_work = work_per_item * nb;
+        SILH_CK(gs.alloc(&g.outi, (size_t)rows_total));
+        SILH_CK(gs.alloc(&g.lab, (size_t)rows_total));
+        SILH_CK(gs.alloc(&g.rhi, (size_t)rows_total * KE * ebytes));
+        SILH_CK(gs.alloc(&g.rlo, (size_t)rows_total * KE * ebytes));
+        if (bf) SILH_CK(gs.alloc(&g.rfull, (size_t)rows_total * KD));
+        SILH_CK(gs.alloc(&g.rn, (size_t)rows_total));
+        SILH_CK(gs.alloc(&w_own, (size_t)rows_total));
+        SILH_CK(gs.alloc(&g.poff, (size_t)poff_total));
+        SILH_CK(gs.alloc(&g.yf, (size_t)cols_total * KD));
+        SILH_CK(gs.alloc(&g.yhi, (size_t)cols_total * KE * ebytes));
+        SILH_CK(gs.alloc(&g.ylo, (size_t)cols_total * KE * ebytes));
+        SILH_CK(gs.alloc(&g.ywn, (size_t)cols_total));
+        {
+            int64_t ccol = 0, pbase = 0;
+            for (int c = 0; c < nb; ++c) {
+                const silh_batch_item &src = items[order[i0 + c]];
+                const silh_sample *S = src.sample;
+                const int64_t arow = rows_pad * c, mp_pad = cols_of(order[i0 + c]);
+                TcOps o = g;
+                o.rhi = g.rhi + arow * KE * ebytes;
+                o.rlo = g.rlo + arow * KE * ebytes;
+                o.rfull = bf ? g.rfull + arow * KD : nullptr;
+                o.rn = g.rn + arow;
+                o.lab = g.lab + arow;
+                o.outi = g.outi + arow;
+                o.yf = g.yf + ccol * KD;
+                o.yhi = g.yhi + ccol * KE * ebytes;
+                o.ylo = g.ylo + ccol * KE * ebytes;
+                o.ywn = g.ywn + ccol;
+                o.poff = g.poff + pbase;
+                st = tc_prepare(X, dtype, n, d, ld, src.labels, S->k, metric, KD, bf, S->offsets,
+                                S->idx, S->p, S->size, nullptr, n, rows_pad, mp_pad, o, stream);
+                if (st != SILH_OK) goto done;
+                const float *rows32 = bf ? o.rfull : (const float *)o.rhi;
+                const float *lo32 = bf ? nullptr : (const float *)o.rlo;
+#define SILH_TC_OWN(MET, KDV, BFV)                                                              \
+                if (metric == MET && KD == KDV && bf == BFV)                                    \
+                    SILH_CK((launch_own<MET, KDV, BFV>(stream, rows32, lo32, o.rn, o.lab, n, o.yf, \
+                                                       o.ywn, o.poff, S->k, S->size,            \
+                                                       w_own + arow)));
+                SILH_TC_OWN(SILH_EUCLIDEAN, 32, false)
+                SILH_TC_OWN(SILH_EUCLIDEAN, 32, true)
+                SILH_TC_OWN(SILH_EUCLIDEAN, 64, false)
+                SILH_TC_OWN(SILH_EUCLIDEAN, 64, true)
+                SILH_TC_OWN(SILH_COSINE, 32, false)
+                SILH_TC_OWN(SILH_COSINE, 32, true)
+                SILH_TC_OWN(SILH_COSINE, 64, false)
+                SILH_TC_OWN(SILH_COSINE, 64, true)
+#undef SILH_TC_OWN
+                TcItem &it = bt.items[c];
+                it.work_base = work_per_item * c;
+                it.arow = arow;
+                it.ccol = ccol;
+                it.nrows = n;
+                it.pbase = pbase;
+                it.sizes = S->sizes;
+                it.s_out = src.s_hat;
+                it.k = S->k;
+                ccol += mp_pad;
+                pbase += S->k + 1;
+            }
+        }
+        SILH_REQ(make_map(&m_ahi, g.rhi, KD, rows_total, kTileM, bf) &&
+                     make_map(&m_alo, g.rlo, KD, rows_total, kTileM, bf) &&
+                     make_map(&m_bhi, g.yhi, KD, cols_total, wide_tiles(KD, bf) ? 128 : kTileN, bf) &&
+                     make_map(&m_blo, g.ylo, KD, cols_total, wide_tiles(KD, bf) ? 128 : kTileN, bf),
+                 "tensor map encoding failed");
+#define SILH_TC_BCASE(MET, KDV, SP, BFV)                                                       \
+        if (metric == MET && KD == KDV && split == SP && bf == BFV) {                          \
+            SILH_CK((launch_tc_batched<MET, KDV, SP, BFV>(                                      \
+                nsm, stream, m_ahi, m_alo, m_bhi, m_blo,                                        \
+                BFV ? g.rfull : (const float *)g.rhi, BFV ? nullptr : (const float *)g.rlo,     \
+                g.rn, g.lab, g.outi, g.yf, g.ywn, g.poff, tau, w_own, bt)));                   \
+        }
+#define SILH_TC_BCASES(MET, KDV)             \
+        SILH_TC_BCASE(MET, KDV, true, false)     \
+        SILH_TC_BCASE(MET, KDV, false, false)    \
+        SILH_TC_BCASE(MET, KDV, true, true)      \
+        SILH_TC_BCASE(MET, KDV, false, true)
+        SILH_TC_BCASES(SILH_EUCLIDEAN, 32)
+        SILH_TC_BCASES(SILH_EUCLIDEAN, 64)
+        SILH_TC_BCASES(SILH_COSINE, 32)
+        SILH_TC_BCASES(SILH_COSINE, 64)
+#undef SILH_TC_BCASES
+#undef SILH_TC_BCASE
+        i0 = i1;
+    }
 done:
     return st;
 }

@@ -277,12 +277,17 @@ def pipe_rates(stream=None):
 BATCH_VARIANTS = 4   # tile shapes of the batched sweep (see include/silh.h)
 
 
-def silh_estimate_batched(X, items, metric="euclidean", variant=-1, outs=None, stream=None):
+def silh_estimate_batched(X, items, metric="euclidean", variant=-1, outs=None, stream=None,
+                          prec="fp32"):
     """Phase 2 for many clusterings of X in one persistent launch.
 
     items: list of (labels, sample) pairs (int32 CUDA labels, Sample from
     silh_sample_pps on those labels).  Returns one FP32 s_hat tensor per item.
-    Asynchronous and graph-capturable when outs are preallocated.
+    prec "fp32" runs the CUDA-core sweep (variant picks its tile shape);
+    "tf32" / "3xtf32" / "bf16" / "bf16x3" with the Euclidean or cosine
+    distance and d <= 64 run the tensor-core sweep, each item equal to
+    silh_estimate with that prec.  Asynchronous and graph-capturable when outs
+    are preallocated.
     """
     lib = load()
     dt, n, d, ld = _data(X)
@@ -297,7 +302,7 @@ def silh_estimate_batched(X, items, metric="euclidean", variant=-1, outs=None, s
         arr[i].labels = _labels(labels).data_ptr()
         arr[i].sample = ctypes.pointer(st)
         arr[i].s_hat = out.data_ptr()
-    _check(lib.silh_estimate_batched(_ptr(X), dt, n, d, ld, METRICS[metric], PRECS["fp32"],
+    _check(lib.silh_estimate_batched(_ptr(X), dt, n, d, ld, METRICS[metric], PRECS[prec],
                                      len(items), arr, int(variant), _stream(stream)))
     return outs
 

@@ -110,3 +110,93 @@ def test_batched_other_metrics(metric):
     for (lt, smp), k, out in zip(items, [3, 7], outs):
         ref = silh.silh_estimate(Xt, lt, k, smp, metric, prec="fp32")
         assert torch.equal(out, ref)
+
+
+# ---------------------------------------------------------------- tensor cores
+# With prec tf32 / 3xtf32 / bf16 / bf16x3 (Euclidean or cosine, d <= 64) the
+# batched call runs one persistent tensor-core sweep over every (clustering,
+# row group); each clustering is swept exactly as silh_estimate sweeps it, so
+# the results are equal bit for bit, and within the per-precision bound of the
+# oracle.
+TC_TOL = {"3xtf32": S_TOL, "tf32": 2e-3, "bf16x3": 2e-5, "bf16": 5e-3}
+TC_PRECS = ["3xtf32", "tf32", "bf16x3", "bf16"]
+
+
+def _items(Xt, ks, labels, metric, t=64.0):
+    items = []
+    for c, (k, lab) in enumerate(zip(ks, labels)):
+        lt = torch.from_numpy(lab).cuda()
+        items.append((lt, silh.silh_sample_pps(Xt, lt, k, metric, t=t, seed=5, clustering_id=c)))
+    return items
+
+
+@pytest.mark.parametrize("prec", TC_PRECS)
+@pytest.mark.parametrize("metric", ["euclidean", "cosine"])
+def test_batched_tensor_cores_equal_single_sweeps(batch, metric, prec):
+    X, Xt, ks, labels, items = batch
+    if metric != "euclidean":
+        items = _items(Xt, ks, labels, metric)
+    outs = silh.silh_estimate_batched(Xt, items, metric, prec=prec)
+    for (lt, smp), k, out in zip(items, ks, outs):
+        ref = silh.silh_estimate(Xt, lt, k, smp, metric, prec=prec)
+        assert torch.equal(out, ref)
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
+@pytest.mark.parametrize("metric", ["euclidean", "cosine"])
+def test_batched_tensor_cores_match_oracle(batch, metric, prec):
+    X, Xt, ks, labels, items = batch
+    items = _items(Xt, ks, labels, metric)
+    outs = silh.silh_estimate_batched(Xt, items, metric, prec=prec)
+    Xh = X.astype(np.float64)
+    rows = synth.seeded_rows(X.shape[0], 150, seed=4)
+    for c in (0, 3, 5):
+        os_ = oracle.sample_pps(Xh, labels[c], ks[c], metric, t=64.0, seed=5, cid=c)
+        s_o, _, _ = oracle.estimate(Xh, labels[c], ks[c], metric, os_.offsets, os_.idx,
+                                    os_.ps, rows=rows)
+        got = outs[c][torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+        assert np.abs(got - s_o).max() <= TC_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "tf32", "bf16"])
+def test_batched_tensor_cores_two_block_rows_bf16_data(prec):
+    # d = 50: two 128-byte K blocks for TF32 operands (two row tiles per group);
+    # BF16 storage; n = 7001 leaves a ragged last row group
+    ks = [2, 6, 11]
+    X, labels = _dataset(7001, 50, 42, ks)
+    Xt = torch.from_numpy(X).cuda().to(torch.bfloat16)
+    items = _items(Xt, ks, labels, "euclidean", t=48.0)
+    outs = silh.silh_estimate_batched(Xt, items, "euclidean", prec=prec)
+    for (lt, smp), k, out in zip(items, ks, outs):
+        assert torch.equal(out, silh.silh_estimate(Xt, lt, k, smp, "euclidean", prec=prec))
+
+
+def test_batched_tensor_cores_more_items_than_one_launch():
+    # 300 clusterings: more than one launch's item table holds
+    rng = np.random.default_rng(43)
+    ks = [int(v) for v in rng.integers(2, 7, size=300)]
+    X, _, _ = synth.gaussian_mixture(2500, 8, 6, seed=43, sigma=1.0)
+    labels = [synth.nearest_centre_labels(X, k, seed=500 + i) for i, k in enumerate(ks)]
+    Xt = torch.from_numpy(X).cuda()
+    items = _items(Xt, ks, labels, "cosine", t=24.0)
+    outs = silh.silh_estimate_batched(Xt, items, "cosine", prec="3xtf32")
+    for (lt, smp), k, out in zip(items, ks, outs):
+        assert torch.equal(out, silh.silh_estimate(Xt, lt, k, smp, "cosine", prec="3xtf32"))
+
+
+def test_batched_tensor_cores_graph_capture_and_replay(batch):
+    X, Xt, ks, labels, items = batch
+    outs = [torch.empty(X.shape[0], dtype=torch.float32, device="cuda") for _ in items]
+    silh.silh_estimate_batched(Xt, items, "euclidean", outs=outs, prec="3xtf32")
+    torch.cuda.synchronize()
+    ref = [o.clone() for o in outs]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        silh.silh_estimate_batched(Xt, items, "euclidean", outs=outs, prec="3xtf32")
+    for _ in range(2):
+        for o in outs:
+            o.fill_(7.0)
+        g.replay()
+        torch.cuda.synchronize()
+        for a, b in zip(outs, ref):
+            assert torch.equal(a, b)
