@@ -188,13 +188,22 @@ typedef struct silh_batch_item {
 
 /* Phase 2 of Algorithm 1 for many clusterings of the same data X in one
  * persistent launch (the work items are (clustering, row tile) pairs, taken
- * round-robin by CTAs sized to fill the GPU).  Same arithmetic and results as
- * silh_estimate with SILH_PREC_FP32 on each item, all rows.  variant selects
- * the tile shape (rows per thread x columns per stage: 0 = 1x32, 1 = 1x64,
- * 2 = 2x32, 3 = 2x64; -1 = default) -- the choice an autotuner makes by
- * timing.  Asynchronous and free of host synchronisation, so the call can be
- * captured in a CUDA graph; items are passed to the kernels as launch
- * parameters, 256 per launch.  Errors: SILH_EINVAL for bad arguments. */
+ * round-robin by CTAs sized to fill the GPU), all rows of every item.
+ * prec SILH_PREC_FP32 (or a tensor-core mode the metric or d rules out): CUDA
+ * cores, the arithmetic and results of silh_estimate with SILH_PREC_FP32 on
+ * each item; variant selects the tile shape (rows per thread x columns per
+ * stage: 0 = 1x32, 1 = 1x64, 2 = 2x32, 3 = 2x64; -1 = default) -- the choice
+ * an autotuner makes by timing.  prec TF32 / 3XTF32 / BF16 / BF16X3 with the
+ * Euclidean or cosine distance and d <= 64: tensor cores; each item first gets
+ * the operands of the single-clustering tensor-core sweep (rows sorted by its
+ * clusters, its padded sample columns, its own-cluster sums), then one
+ * persistent sweep covers every (clustering, row group), and each result
+ * equals silh_estimate with that prec bit for bit; variant is ignored.
+ * Operands above 16 GiB per launch are split over several launches.
+ * Asynchronous and free of host synchronisation, so the call can be captured
+ * in a CUDA graph; items are passed to the kernels as launch parameters, 256
+ * per launch.  Errors: SILH_EINVAL for bad arguments, SILH_ENOMEM when the
+ * scratch cannot be allocated. */
 silh_status silh_estimate_batched(const void *X, silh_dtype dtype, int64_t n, int32_t d,
                                   int64_t ld, silh_metric metric, silh_prec prec, int32_t nitems,
                                   const silh_batch_item *items, int32_t variant, void *stream);

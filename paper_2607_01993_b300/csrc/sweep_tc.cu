@@ -103,28 +103,36 @@ __device__ __forceinline__ float sqrt_apx(float x) {
     return r;
 }
 
-// Distance of a row (global; TF32 operands: x = hi + lo exactly, BF16
-// operands: xh is the FP32 row and xl is unused) to a column (y, global),
-// directly from the coordinates in FP32: the rare close pairs the epilogue
-// flags.
-template <int METRIC, int KD, bool BF>
-__device__ __noinline__ float direct_dist(const float *__restrict__ xh, const float *__restrict__ xl,
-                                          const float *__restrict__ y) {
+// Lane-interleaved FP32 copy of a row operand (the direct recompute of close
+// pairs reads it): rows in blocks of 32 (one epilogue warp), element c of row r
+// at il[(r / 32) * 32 KD + (c / 4) * 128 + (r % 32) * 4 + c % 4], so a warp
+// reading one row's four elements at a time, every lane the same row, or every
+// lane its own row, touches consecutive bytes.  For TF32 operands the values
+// are hi + lo.
+// Distance of the lane's row (xr: its first element in the interleaved copy)
+// to a column (y, global, KD elements) over the first dq groups of four
+// coordinates (the rest are zero in both), directly in FP32.
+template <int METRIC, int KD>
+__device__ __noinline__ float direct_dist(const float *__restrict__ xr, const float *__restrict__ y,
+                                          int dq) {
     const float4 *y4 = reinterpret_cast<const float4 *>(y);
-    const float4 *h4 = reinterpret_cast<const float4 *>(xh);
-    const float4 *l4 = reinterpret_cast<const float4 *>(xl);
     float a0 = 0.f, a1 = 0.f;
 #pragma unroll 4
-    for (int q = 0; q < KD / 4; ++q) {
-        const float4 v = __ldg(y4 + q), h = __ldg(h4 + q);
-        const float4 l = BF ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(l4 + q);
-        const float t0 = (h.x + l.x) - v.x, t1 = (h.y + l.y) - v.y;
-        const float t2 = (h.z + l.z) - v.z, t3 = (h.w + l.w) - v.w;
+    for (int q = 0; q < dq; ++q) {
+        const float4 v = __ldg(y4 + q);
+        const float4 h = __ldg(reinterpret_cast<const float4 *>(xr + q * 128));
+        const float t0 = h.x - v.x, t1 = h.y - v.y;
+        const float t2 = h.z - v.z, t3 = h.w - v.w;
         a0 = fmaf(t0, t0, a0); a1 = fmaf(t1, t1, a1);
         a0 = fmaf(t2, t2, a0); a1 = fmaf(t3, t3, a1);
     }
     const float s = a0 + a1;
-    return METRIC == SILH_EUCLIDEAN ? sqrtf(s) : 0.5f * s;
+    return METRIC == SILH_EUCLIDEAN ? sqrt_apx(s) : 0.5f * s;
+}
+
+// Position of element c of row r in the lane-interleaved row copy.
+__device__ __forceinline__ int64_t il_index(int64_t r, int c, int KD) {
+    return (r >> 5) * (int64_t)(KD * 32) + (c >> 2) * 128 + (r & 31) * 4 + (c & 3);
 }
 
 // Fast-path epilogue of 16 accumulator columns (inner products r) of one row,
@@ -251,10 +259,12 @@ __global__ void __launch_bounds__(TcCfg<KD, SPLIT, BF, WIDE>::THREADS, 1)
 k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CUtensorMap m_alo,
            const __grid_constant__ CUtensorMap m_bhi, const __grid_constant__ CUtensorMap m_blo,
            const float *__restrict__ a_hi, const float *__restrict__ a_lo,
+           const float *__restrict__ a_il,
            const float *__restrict__ a_norm, const int32_t *__restrict__ a_lab,
            const int64_t *__restrict__ a_out, int64_t nrows, const float *__restrict__ y_full,
+           const float *__restrict__ y_il,
            const float2 *__restrict__ y_wn, const int64_t *__restrict__ poff,
-           const int64_t *__restrict__ sizes, int k, float tau,
+           const int64_t *__restrict__ sizes, int k, float tau, int dq,
            const double *__restrict__ w_own, float *__restrict__ s_out,
            float *__restrict__ a_out_v, float *__restrict__ b_out_v, double *__restrict__ W,
            const __grid_constant__ TcBatchArg<BATCH> bt) {
@@ -522,11 +532,10 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             const int64_t apos = v.arow + pos;                            // row of the operands
             const int own = valid ? a_lab[apos] : -1;
             const float xn = valid ? a_norm[apos] : 0.f;
-            const float *xh = a_hi + (valid ? apos : 0) * KD;
-            // FP32 rows for the direct recompute: hi + lo for TF32 operands, the
-            // FP32 copy (a_hi) for BF16 operands and for the symmetric layout
-            constexpr bool kFull = BF || SYM;
-            const float *xl = kFull ? xh : a_lo + (valid ? apos : 0) * KD;
+            // the warp's block of 32 rows in the lane-interleaved FP32 copy (for
+            // the direct recompute; a warp past the last row never recomputes)
+            const int64_t blk0 = pos - lane;
+            const float *xblk = a_il + il_index(v.arow + (blk0 < v.nrows ? blk0 : 0), 0, KD);
             // SYM: this warp's 32-row block starts at wblk; rows are the padded
             // columns, so a row's weight (1 point / 0 padding) is its column weight
             const int64_t wblk = (rg * C::SLOTS + g) * kTileM + 32 * q;
@@ -614,9 +623,57 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         atomicAdd(&W[(c0 + col0) * k + own], (double)cs0);
                         atomicAdd(&W[(c0 + 16 + col1) * k + own], (double)cs1);
                     }
-                    if (redo) {
-                        // a lane has a close pair here: redo the chunk column by column,
-                        // recomputing the flagged pairs directly from the coordinates
+                    // Columns per lane where rows are 32 elements or two row slots share
+                    // the register file; elsewhere the rows keep their lanes.
+                    constexpr bool kColRedo = KD == 32 || C::SLOTS == 2;
+                    if (redo && kColRedo) {
+                        // A lane has a close pair in this chunk: the warp evaluates the
+                        // chunk's 32 x 32 pairs directly from the coordinates in FP32.
+                        // Lane c takes column c and the 32 rows pass by: each step loads
+                        // one row's four coordinates as a broadcast and the 32 columns'
+                        // four as one coalesced run (both copies lane-interleaved and
+                        // L1-resident), so every pair is an independent FMA chain over
+                        // the d real coordinates; a butterfly gives each row's sum of
+                        // w d to its own lane.
+                        const float *ycl = y_il + il_index(v.ccol + c0, 0, KD) + 4 * lane;
+                        const float *fw = reinterpret_cast<const float *>(
+                            &sh_wn[g][buf][ch * 16 + (lane >> 1)]);
+                        const float wc = fw[lane & 1], nyc = fw[2 + (lane & 1)];
+                        float colsum = 0.f;
+                        part = 0.f;
+#pragma unroll 2
+                        for (int r = 0; r < 32; ++r) {
+                            const float *xr = xblk + 4 * r;
+                            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                            for (int q = 0; q < KD / 4; ++q) {
+                                if (q < dq) {
+                                    const float4 h = __ldg(reinterpret_cast<const float4 *>(xr + 128 * q));
+                                    const float4 y = __ldg(reinterpret_cast<const float4 *>(ycl + 128 * q));
+                                    const float t0 = h.x - y.x, t1 = h.y - y.y;
+                                    const float t2 = h.z - y.z, t3 = h.w - y.w;
+                                    a0 = fmaf(t0, t0, a0); a1 = fmaf(t1, t1, a1);
+                                    a0 = fmaf(t2, t2, a0); a1 = fmaf(t3, t3, a1);
+                                }
+                            }
+                            float dist;
+                            if (METRIC == SILH_EUCLIDEAN) {
+                                dist = sqrt_apx(a0 + a1);
+                            } else {     // a zero vector is at distance 1 from everything
+                                const float nxr = __shfl_sync(0xffffffffu, xn, r);
+                                dist = (nxr == 0.f || nyc == 0.f) ? 1.f : 0.5f * (a0 + a1);
+                            }
+                            if (SYM) colsum = fmaf(__shfl_sync(0xffffffffu, rw, r), dist, colsum);
+                            float rs = wc * dist;
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+                            if (lane == r) part = rs;
+                        }
+                        if (SYM) atomicAdd(&W[(c0 + lane) * k + own], (double)colsum);
+                    } else if (redo) {
+                        // the same chunk column by column, each lane its own row; the
+                        // flagged pairs directly from the coordinates
+                        const float *xr = xblk + 4 * lane;
                         part = 0.f;
 #pragma unroll 1
                         for (int i = 0; i < 32; ++i) {
@@ -630,11 +687,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             if (METRIC == SILH_EUCLIDEAN) {
                                 const float s2 = xn + wn.y;
                                 const float d2 = fmaf(-2.f, dot, s2);
-                                dist = (d2 < tau * s2) ? direct_dist<METRIC, KD, kFull>(xh, xl, yc)
+                                dist = (d2 < tau * s2) ? direct_dist<METRIC, KD>(xr, yc, dq)
                                                        : sqrt_apx(d2);
                             } else {
                                 dist = 1.f - dot;
-                                if (dist < tau) dist = direct_dist<METRIC, KD, kFull>(xh, xl, yc);
+                                if (dist < tau) dist = direct_dist<METRIC, KD>(xr, yc, dq);
                             }
                             part = fmaf(wn.x, dist, part);
                             if (SYM) {                // column side of this pair
@@ -1069,8 +1126,9 @@ __device__ __forceinline__ void store_split(float v, int64_t row, int c, int KD,
 }
 
 // Row operand in sorted order: hi/lo split (zero padded), the FP32 row when
-// the operands are BF16 (full, KD columns; the direct recompute reads it),
-// squared norm (Euclidean) or unit scaling (cosine), label, output index.
+// the operands are BF16 (full, KD columns; the own-cluster pass reads it),
+// the lane-interleaved FP32 copy (il; the direct recompute reads it), squared
+// norm (Euclidean) or unit scaling (cosine), label, output index.
 // Positions nrows .. nrows_pad - 1 get zero hi/lo rows (the tail of a row
 // group that the tile loads read).
 template <class T, bool BF>
@@ -1079,13 +1137,17 @@ __global__ void k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int
                                  const int64_t *__restrict__ perm, int64_t nrows, int64_t nrows_pad,
                                  int KD, int k, int metric, const float *__restrict__ mu,
                                  void *__restrict__ hi, void *__restrict__ lo,
-                                 float *__restrict__ full, float *__restrict__ nrm,
-                                 int32_t *__restrict__ lab, int64_t *__restrict__ outi) {
+                                 float *__restrict__ full, float *__restrict__ il,
+                                 float *__restrict__ nrm, int32_t *__restrict__ lab,
+                                 int64_t *__restrict__ outi) {
     const int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (p >= nrows_pad) return;
     if (p >= nrows) {
-        for (int c = lane; c < (BF ? 64 : KD); c += 32) store_split<BF>(0.f, p, c, KD, hi, lo);
+        for (int c = lane; c < (BF ? 64 : KD); c += 32) {
+            store_split<BF>(0.f, p, c, KD, hi, lo);
+            if (c < KD) il[il_index(p, c, KD)] = 0.f;
+        }
         return;
     }
     const int64_t r = perm[p];
@@ -1109,6 +1171,7 @@ __global__ void k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int
         if (mu != nullptr && c < d) v = v - mu[c];
         store_split<BF>(v, p, c, KD, hi, lo);
         if (BF && c < KD) full[p * KD + c] = v;
+        if (c < KD) il[il_index(p, c, KD)] = v;
         ss = fmaf(v, v, ss);
     }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
@@ -1146,8 +1209,10 @@ __global__ void k_col_poff(const int64_t *__restrict__ offsets, int k, int64_t *
 }
 
 // Column operand in the padded layout (one warp per padded column): full FP32
-// copy, hi/lo split, (weight, squared norm).  Padding columns are zero with
-// weight 0.  Source column of sampled position t is idx[t] (idx == nullptr: t).
+// copy, hi/lo split, (weight, squared norm), and when il is given the
+// lane-interleaved FP32 copy (the symmetric exact, whose rows are these
+// columns).  Padding columns are zero with weight 0.  Source column of sampled
+// position t is idx[t] (idx == nullptr: t).
 template <class T, bool BF>
 __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
                                  const int32_t *__restrict__ idx, const double *__restrict__ p,
@@ -1155,7 +1220,7 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
                                  const int64_t *__restrict__ poff, int k, int64_t mp_max, int KD,
                                  int metric, const float *__restrict__ mu, float *__restrict__ full,
                                  void *__restrict__ hi, void *__restrict__ lo,
-                                 float2 *__restrict__ wn) {
+                                 float2 *__restrict__ wn, float *__restrict__ il) {
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (i >= mp_max) return;
@@ -1174,6 +1239,7 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
     if (t < 0) {
         for (int c = lane; c < KE; c += 32) {
             if (c < KD) full[i * KD + c] = 0.f;
+            if (il != nullptr && c < KD) il[il_index(i, c, KD)] = 0.f;
             store_split<BF>(0.f, i, c, KD, hi, lo);
         }
         if (lane == 0) wn[i] = make_float2(0.f, 0.f);
@@ -1195,6 +1261,7 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
         float v = (c < d) ? to_f32<T>(x[c]) * scale : 0.f;
         if (mu != nullptr && c < d) v = v - mu[c];
         if (c < KD) full[i * KD + c] = v;
+        if (il != nullptr && c < KD) il[il_index(i, c, KD)] = v;
         store_split<BF>(v, i, c, KD, hi, lo);
         ss = fmaf(v, v, ss);
     }
@@ -1319,9 +1386,10 @@ cudaError_t launch_own(cudaStream_t stream, const float *a_hi, const float *a_lo
 template <int METRIC, int KD, bool SPLIT, bool BF, bool SYM = false>
 cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, const CUtensorMap &alo,
                       const CUtensorMap &bhi, const CUtensorMap &blo, const float *a_hi,
-                      const float *a_lo, const float *a_norm, const int32_t *a_lab,
-                      const int64_t *a_out, int64_t nrows, const float *y_full, const float2 *y_wn,
-                      const int64_t *poff, const int64_t *sizes, int k, float tau,
+                      const float *a_lo, const float *a_il, const float *a_norm,
+                      const int32_t *a_lab, const int64_t *a_out, int64_t nrows,
+                      const float *y_full, const float *y_il, const float2 *y_wn,
+                      const int64_t *poff, const int64_t *sizes, int k, float tau, int dq,
                       int64_t max_cluster_cols, double *w_own, float *s, float *a, float *b,
                       double *W = nullptr, const OwnItem *own_items = nullptr,
                       int64_t n_own_items = 0) {
@@ -1344,9 +1412,10 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
     if (e != cudaSuccess) return e;
     const int64_t groups = ((nrows + kTileM - 1) / kTileM + C::SLOTS - 1) / C::SLOTS;
     const int grid = (int)std::min<int64_t>(groups, nsm);
-    kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_norm, a_lab,
-                                                a_out, nrows, y_full, y_wn, poff, sizes, k, tau,
-                                                w_own, s, a, b, W, TcBatchArg<false>{});
+    kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_il, a_norm,
+                                                a_lab, a_out, nrows, y_full, y_il, y_wn, poff,
+                                                sizes, k, tau, dq, w_own, s, a, b, W,
+                                                TcBatchArg<false>{});
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1358,34 +1427,40 @@ template <int METRIC, int KD, bool SPLIT, bool BF>
 cudaError_t launch_tc_batched(int nsm, cudaStream_t stream, const CUtensorMap &ahi,
                               const CUtensorMap &alo, const CUtensorMap &bhi,
                               const CUtensorMap &blo, const float *a_hi, const float *a_lo,
-                              const float *a_norm, const int32_t *a_lab, const int64_t *a_out,
-                              const float *y_full, const float2 *y_wn, const int64_t *poff,
-                              float tau, const double *w_own, const TcBatchArg<true> &bt) {
+                              const float *a_il, const float *a_norm, const int32_t *a_lab,
+                              const int64_t *a_out,
+                              const float *y_full, const float *y_il, const float2 *y_wn,
+                              const int64_t *poff,
+                              float tau, int dq, const double *w_own,
+                              const TcBatchArg<true> &bt) {
     constexpr bool WIDE = wide_tiles(KD, BF);
     using C = TcCfg<KD, SPLIT, BF, WIDE>;
     auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF, false, WIDE, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(bt.total_work, nsm);
-    kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_norm, a_lab,
-                                                a_out, 0, y_full, y_wn, poff, nullptr, 0, tau,
-                                                w_own, nullptr, nullptr, nullptr, nullptr, bt);
+    kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_il, a_norm,
+                                                a_lab, a_out, 0, y_full, y_il, y_wn, poff, nullptr,
+                                                0, tau, dq, w_own, nullptr, nullptr, nullptr,
+                                                nullptr, bt);
     count_launches(1);
     return cudaGetLastError();
 }
 
 // Operands of one clustering in the tensor-core layouts, written into
 // caller-provided device buffers: the listed rows sorted by cluster (hi/lo
-// split, the FP32 copy for BF16 operands, norms, labels, output indices;
+// split, the FP32 copy for BF16 operands, the lane-interleaved FP32 copy (whole
+// blocks of 32 rows), norms, labels, output indices;
 // nrows_pad rows, the tail zero) and the cluster-major sample columns padded
-// per cluster to multiples of 32 (FP32 copy, hi/lo split, weight and norm,
-// padded offsets; mp_pad columns, the tail zero with weight 0).
+// per cluster to multiples of 32 (FP32 copy, lane-interleaved FP32 copy,
+// hi/lo split, weight and norm, padded offsets; mp_pad columns, the tail zero
+// with weight 0).
 struct TcOps {
     uint8_t *rhi, *rlo;
-    float *rfull, *rn;
+    float *rfull, *ril, *rn;
     int32_t *lab;
     int64_t *outi;
-    float *yf;
+    float *yf, *yil;
     uint8_t *yhi, *ylo;
     float2 *ywn;
     int64_t *poff;
@@ -1440,13 +1515,19 @@ silh_status tc_prepare(const void *X, silh_dtype dtype, int64_t n, int32_t d, in
     } else {
         mu = nullptr;
     }
+    if (nrows_pad % 32 != 0)     // rows of the last block past nrows_pad are read, as zeros
+        SILH_CK(cudaMemsetAsync(o.ril + (nrows_pad / 32) * 32 * KD, 0, sizeof(float) * 32 * KD,
+                                stream));
+    if (mp_pad % 32 != 0)        // and so are columns of the last block past mp_pad
+        SILH_CK(cudaMemsetAsync(o.yil + (mp_pad / 32) * 32 * KD, 0, sizeof(float) * 32 * KD,
+                                stream));
 #define SILH_TC_GATHER(T, BFV)                                                                  \
     k_gather_rows_tc<T, BFV><<<ceil_div_i(nrows_pad, 8), 256, 0, stream>>>(                    \
         (const T *)X, d, ld, n, labels, rows, perm, nrows, nrows_pad, KD, k, metric, mu, o.rhi, \
-        o.rlo, o.rfull, o.rn, o.lab, o.outi);                                                   \
+        o.rlo, o.rfull, o.ril, o.rn, o.lab, o.outi);                                            \
     k_gather_cols_tc<T, BFV><<<ceil_div_i(mp_pad, 8), 256, 0, stream>>>(                       \
         (const T *)X, d, ld, col_idx, col_p, offsets, o.poff, k, mp_pad, KD, metric, mu, o.yf,  \
-        o.yhi, o.ylo, o.ywn);
+        o.yhi, o.ylo, o.ywn, o.yil);
     if (dtype == SILH_F32) {
         if (bf) { SILH_TC_GATHER(float, true) } else { SILH_TC_GATHER(float, false) }
     } else {
@@ -1491,10 +1572,12 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     SILH_CK(sc.alloc(&o.rhi, (size_t)nrows * KE * ebytes));
     SILH_CK(sc.alloc(&o.rlo, (size_t)nrows * KE * ebytes));
     if (bf) SILH_CK(sc.alloc(&o.rfull, (size_t)nrows * KD));
+    SILH_CK(sc.alloc(&o.ril, (size_t)((nrows + 31) & ~int64_t(31)) * KD));
     SILH_CK(sc.alloc(&o.rn, (size_t)nrows));
     SILH_CK(sc.alloc(&o.poff, (size_t)k + 1));
     SILH_CK(sc.alloc(&w_own, (size_t)nrows));
     SILH_CK(sc.alloc(&o.yf, (size_t)mp_max * KD));
+    SILH_CK(sc.alloc(&o.yil, (size_t)((mp_max + 31) & ~int64_t(31)) * KD));
     SILH_CK(sc.alloc(&o.yhi, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&o.ylo, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&o.ywn, (size_t)mp_max));
@@ -1514,8 +1597,8 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     if (metric == MET && KD == KDV && split == SP && bf == BFV) {                              \
         SILH_CK((launch_tc<MET, KDV, SP, BFV>(                                                  \
             nsm, stream, m_ahi, m_alo, m_bhi, m_blo, BFV ? o.rfull : (const float *)o.rhi,     \
-            BFV ? nullptr : (const float *)o.rlo, o.rn, o.lab, o.outi, nrows, o.yf, o.ywn,      \
-            o.poff, sizes, k, tau, max_cluster_cols, w_own, s, a, b)));                         \
+            BFV ? nullptr : (const float *)o.rlo, o.ril, o.rn, o.lab, o.outi, nrows, o.yf,      \
+            o.yil, o.ywn, o.poff, sizes, k, tau, (d + 3) / 4, max_cluster_cols, w_own, s, a, b))); \
     }
 #define SILH_TC_CASES(MET, KDV)             \
     SILH_TC_CASE(MET, KDV, true, false)     \
@@ -1545,8 +1628,8 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
     const int64_t group_rows = (int64_t)slots * kTileM;
     const int64_t rows_pad = (n + 4 * kTileM - 1) / (4 * kTileM) * (4 * kTileM);
     const int64_t work_per_item = (n + group_rows - 1) / group_rows;
-    const size_t row_bytes = 2 * KE * ebytes + (bf ? KD * 4 : 0) + 4 + 4 + 8 + 8;
-    const size_t col_bytes = KD * 4 + 2 * KE * ebytes + 8;
+    const size_t row_bytes = 2 * KE * ebytes + (bf ? KD * 4 : 0) + KD * 4 + 4 + 4 + 8 + 8;
+    const size_t col_bytes = 2 * KD * 4 + 2 * KE * ebytes + 8;
     const float tau = 0.25f;
     int dev = 0, nsm = 0;
     auto cols_of = [&](int32_t i) -> int64_t {     // padded column count, whole 128-column tiles
@@ -1588,10 +1671,12 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
         SILH_CK(gs.alloc(&g.rhi, (size_t)rows_total * KE * ebytes));
         SILH_CK(gs.alloc(&g.rlo, (size_t)rows_total * KE * ebytes));
         if (bf) SILH_CK(gs.alloc(&g.rfull, (size_t)rows_total * KD));
+        SILH_CK(gs.alloc(&g.ril, (size_t)rows_total * KD));
         SILH_CK(gs.alloc(&g.rn, (size_t)rows_total));
         SILH_CK(gs.alloc(&w_own, (size_t)rows_total));
         SILH_CK(gs.alloc(&g.poff, (size_t)poff_total));
         SILH_CK(gs.alloc(&g.yf, (size_t)cols_total * KD));
+        SILH_CK(gs.alloc(&g.yil, (size_t)cols_total * KD));
         SILH_CK(gs.alloc(&g.yhi, (size_t)cols_total * KE * ebytes));
         SILH_CK(gs.alloc(&g.ylo, (size_t)cols_total * KE * ebytes));
         SILH_CK(gs.alloc(&g.ywn, (size_t)cols_total));
@@ -1605,10 +1690,12 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
                 o.rhi = g.rhi + arow * KE * ebytes;
                 o.rlo = g.rlo + arow * KE * ebytes;
                 o.rfull = bf ? g.rfull + arow * KD : nullptr;
+                o.ril = g.ril + arow * KD;
                 o.rn = g.rn + arow;
                 o.lab = g.lab + arow;
                 o.outi = g.outi + arow;
                 o.yf = g.yf + ccol * KD;
+                o.yil = g.yil + ccol * KD;
                 o.yhi = g.yhi + ccol * KE * ebytes;
                 o.ylo = g.ylo + ccol * KE * ebytes;
                 o.ywn = g.ywn + ccol;
@@ -1655,7 +1742,8 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
             SILH_CK((launch_tc_batched<MET, KDV, SP, BFV>(                                      \
                 nsm, stream, m_ahi, m_alo, m_bhi, m_blo,                                        \
                 BFV ? g.rfull : (const float *)g.rhi, BFV ? nullptr : (const float *)g.rlo,     \
-                g.rn, g.lab, g.outi, g.yf, g.ywn, g.poff, tau, w_own, bt)));                   \
+                g.ril, g.rn, g.lab, g.outi, g.yf, g.yil, g.ywn, g.poff, tau, (d + 3) / 4, w_own, \
+                bt)));                                                                          \
         }
 #define SILH_TC_BCASES(MET, KDV)             \
         SILH_TC_BCASE(MET, KDV, true, false)     \
@@ -1697,7 +1785,7 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     int64_t *poff = nullptr, *outi = nullptr;
     int32_t *plab = nullptr;
     double *W = nullptr, *mpart = nullptr;
-    float *mu = nullptr, *yf = nullptr, *rn = nullptr;
+    float *mu = nullptr, *yf = nullptr, *yil = nullptr, *rn = nullptr;
     OwnItem *own_items = nullptr;
     std::vector<OwnItem> h_items;
     uint8_t *yhi = nullptr, *ylo = nullptr;
@@ -1713,6 +1801,7 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     SILH_CK(sc.alloc(&mpart, (size_t)mean_blocks * d));
     SILH_CK(sc.alloc(&mu, (size_t)d));
     SILH_CK(sc.alloc(&yf, (size_t)mp_max * KD));
+    SILH_CK(sc.alloc(&yil, (size_t)((mp_max + 31) & ~int64_t(31)) * KD));
     SILH_CK(sc.alloc(&yhi, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&ylo, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&ywn, (size_t)mp_max));
@@ -1747,10 +1836,12 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     } else {
         mu = nullptr;
     }
+    if (mp_max % 32 != 0)        // positions of the last block past mp_max are read, as zeros
+        SILH_CK(cudaMemsetAsync(yil + (mp_max / 32) * 32 * KD, 0, sizeof(float) * 32 * KD, stream));
 #define SILH_TC_GATHER_SYM(T, BFV)                                                              \
     k_gather_cols_tc<T, BFV><<<ceil_div_i(mp_max, 8), 256, 0, stream>>>(                       \
         (const T *)X, d, ld, order, nullptr, coff, poff, k, mp_max, KD, metric, mu, yf, yhi,    \
-        ylo, ywn);
+        ylo, ywn, yil);
     if (dtype == SILH_F32) {
         if (bf) { SILH_TC_GATHER_SYM(float, true) } else { SILH_TC_GATHER_SYM(float, false) }
     } else {
@@ -1771,8 +1862,9 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
 #define SILH_TC_SYM_CASE(MET, KDV, SP, BFV)                                                    \
     if (metric == MET && KD == KDV && split == SP && bf == BFV) {                              \
         SILH_CK((launch_tc<MET, KDV, SP, BFV, true>(                                            \
-            nsm, stream, m_ahi, m_alo, m_bhi, m_blo, yf, nullptr, rn, plab, outi, mp_max, yf,  \
-            ywn, poff, sizes, k, tau, 0, nullptr, nullptr, nullptr, nullptr, W, own_items,     \
+            nsm, stream, m_ahi, m_alo, m_bhi, m_blo, yf, nullptr, yil, rn, plab, outi, mp_max, yf, \
+            yil, ywn, poff, sizes, k, tau, (d + 3) / 4, 0, nullptr, nullptr, nullptr, nullptr, W, \
+            own_items,                                                                          \
             (int64_t)h_items.size())));                                                         \
     }
 #define SILH_TC_SYM_CASES(MET, KDV)             \
