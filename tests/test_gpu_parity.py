@@ -272,11 +272,23 @@ def _tc_case(name):
         X, lab, _ = synth.gaussian_mixture(12000, 50, 8, seed=9, sizes=synth.zipf_sizes(12000, 8),
                                            sigma_range=(0.5, 3))
         return X, lab, 8, dict(t=96.0, m0=None, seed=9)
+    if name in ("voronoi", "voronoi_wide"):
+        # Nearest-centre labels cut each mixture component into several clusters,
+        # so many pairs across clusters are close against |x|^2 + |y|^2: most
+        # column chunks take the direct FP32 recompute (d = 16: one column per
+        # lane over 4 of 8 coordinate groups; d = 50: the two-slot TF32 form and,
+        # for BF16 operands, each lane its own row).  Two zero rows meet it too.
+        d, n, comps, k, seed = (16, 9000, 6, 40, 11) if name == "voronoi" else (50, 6000, 4, 24, 13)
+        X, _, _ = synth.gaussian_mixture(n, d, comps, seed=seed, sigma=1.5)
+        X = X.copy()
+        X[[5, 777]] = 0.0
+        lab = synth.nearest_centre_labels(X, k, seed=seed + 1)
+        return X, lab, k, dict(t=48.0, m0=None, seed=seed)
     return _case(name)
 
 
 @pytest.mark.parametrize("prec", TC_PRECS)
-@pytest.mark.parametrize("case", ["tiny", "ragged", "multitile", "wide"])
+@pytest.mark.parametrize("case", ["tiny", "ragged", "multitile", "wide", "voronoi", "voronoi_wide"])
 @pytest.mark.parametrize("metric", ["euclidean", "cosine"])
 def test_tensor_core_estimate_matches_oracle(case, metric, prec):
     X, lab, k, kw = _tc_case(case)
@@ -302,7 +314,7 @@ def test_tensor_core_estimate_matches_oracle(case, metric, prec):
 
 
 @pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
-@pytest.mark.parametrize("case", ["tiny", "ragged", "wide"])
+@pytest.mark.parametrize("case", ["tiny", "ragged", "wide", "voronoi", "voronoi_wide"])
 @pytest.mark.parametrize("metric", ["euclidean", "cosine"])
 def test_tensor_core_exact_matches_oracle(case, metric, prec):
     X, lab, k, _ = _tc_case(case)
