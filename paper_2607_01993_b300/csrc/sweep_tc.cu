@@ -60,13 +60,20 @@ __device__ int g_tc_error = 0;    // set when a bounded wait gives up
 // A tile from shared memory serves twice the columns) with one accumulator
 // per slot where two would not fit in tensor memory; otherwise 64-column
 // tiles, two accumulators per slot.
+// Row tiles a CTA sweeps at once (each with its own epilogue warpgroup and
+// accumulators): four where a row is one 128-byte K block (BF16 operands, or
+// TF32 rows of 32 elements), two for two-block TF32 rows.  (Two slots for
+// one-block rows, with deeper B staging and two accumulators per slot, were
+// slower: fewer epilogue warps per column tile.)
+constexpr int tc_slots(int KD, bool BF) { return (BF || KD == 32) ? 4 : 2; }
+
 template <int KD, bool SPLIT, bool BF = false, bool WIDE = false>
 struct TcCfg {
     static constexpr int KB = BF ? 1 : KD / 32;                 // 128-byte K blocks
     static constexpr int KSTEPS = BF ? KD / 16 : 4;             // 32-byte MMA K steps per block
     static constexpr int KELEM = BF ? 64 : 32;                  // elements per 128-byte row
     static constexpr int PARTS = SPLIT ? 2 : 1;                 // hi (+ lo)
-    static constexpr int SLOTS = (KB == 1) ? 4 : 2;             // row tiles per CTA pass
+    static constexpr int SLOTS = tc_slots(KD, BF);              // row tiles per CTA pass
     static constexpr int TN = WIDE ? 128 : kTileN;              // columns per tile
     static constexpr int NACC = (SLOTS * 2 * TN <= 512) ? 2 : 1;  // accumulators per slot
     static constexpr int A_SLOT = PARTS * KB * kTileM * 128;
@@ -1624,7 +1631,7 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
     const bool bf = prec == SILH_PREC_BF16 || prec == SILH_PREC_BF16X3;
     const int KE = bf ? 64 : KD;
     const size_t ebytes = bf ? 2 : 4;
-    const int slots = (bf || KD == 32) ? 4 : 2;   // row tiles per row group (TcCfg::SLOTS)
+    const int slots = tc_slots(KD, bf);           // row tiles per row group (TcCfg::SLOTS)
     const int64_t group_rows = (int64_t)slots * kTileM;
     const int64_t rows_pad = (n + 4 * kTileM - 1) / (4 * kTileM) * (4 * kTileM);
     const int64_t work_per_item = (n + group_rows - 1) / group_rows;
