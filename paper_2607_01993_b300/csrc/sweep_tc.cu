@@ -65,7 +65,15 @@ __device__ int g_tc_error = 0;    // set when a bounded wait gives up
 // TF32 rows of 32 elements), two for two-block TF32 rows.  (Two slots for
 // one-block rows, with deeper B staging and two accumulators per slot, were
 // slower: fewer epilogue warps per column tile.)
-constexpr int tc_slots(int KD, bool BF) { return (BF || KD == 32) ? 4 : 2; }
+__host__ __device__ constexpr int tc_slots(int KD, bool BF) { return (BF || KD == 32) ? 4 : 2; }
+
+// Close-pair recompute form: rows of 32 elements evaluate a flagged chunk's
+// 32 x 32 pairs with one column per lane, from lane-interleaved FP32 copies of
+// rows and columns; 64-element rows recompute only the flagged pairs, each lane
+// its own row from the row-major operands (there, typically one lane of a chunk
+// is flagged, and a whole row-major row is two cache lines where its
+// interleaved form is sixteen).
+__host__ __device__ constexpr bool tc_col_redo(int KD) { return KD == 32; }
 
 template <int KD, bool SPLIT, bool BF = false, bool WIDE = false>
 struct TcCfg {
@@ -116,25 +124,28 @@ __device__ __forceinline__ float sqrt_apx(float x) {
 // reading one row's four elements at a time, every lane the same row, or every
 // lane its own row, touches consecutive bytes.  For TF32 operands the values
 // are hi + lo.
-// Distance of the lane's row (xr: its first element in the interleaved copy)
-// to a column (y, global, KD elements) over the first dq groups of four
-// coordinates (the rest are zero in both), directly in FP32.
-template <int METRIC, int KD>
-__device__ __noinline__ float direct_dist(const float *__restrict__ xr, const float *__restrict__ y,
-                                          int dq) {
+// Distance of a row (row-major; TF32 operands: x = hi + lo exactly, BF16
+// operands and the symmetric layout: xh is the FP32 row and xl is unused) to a
+// column (y, global), directly from the coordinates in FP32.
+template <int METRIC, int KD, bool FULL>
+__device__ __noinline__ float direct_dist_rows(const float *__restrict__ xh,
+                                               const float *__restrict__ xl,
+                                               const float *__restrict__ y) {
     const float4 *y4 = reinterpret_cast<const float4 *>(y);
+    const float4 *h4 = reinterpret_cast<const float4 *>(xh);
+    const float4 *l4 = reinterpret_cast<const float4 *>(xl);
     float a0 = 0.f, a1 = 0.f;
 #pragma unroll 4
-    for (int q = 0; q < dq; ++q) {
-        const float4 v = __ldg(y4 + q);
-        const float4 h = __ldg(reinterpret_cast<const float4 *>(xr + q * 128));
-        const float t0 = h.x - v.x, t1 = h.y - v.y;
-        const float t2 = h.z - v.z, t3 = h.w - v.w;
+    for (int q = 0; q < KD / 4; ++q) {
+        const float4 v = __ldg(y4 + q), h = __ldg(h4 + q);
+        const float4 l = FULL ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(l4 + q);
+        const float t0 = (h.x + l.x) - v.x, t1 = (h.y + l.y) - v.y;
+        const float t2 = (h.z + l.z) - v.z, t3 = (h.w + l.w) - v.w;
         a0 = fmaf(t0, t0, a0); a1 = fmaf(t1, t1, a1);
         a0 = fmaf(t2, t2, a0); a1 = fmaf(t3, t3, a1);
     }
     const float s = a0 + a1;
-    return METRIC == SILH_EUCLIDEAN ? sqrt_apx(s) : 0.5f * s;
+    return METRIC == SILH_EUCLIDEAN ? sqrtf(s) : 0.5f * s;
 }
 
 // Position of element c of row r in the lane-interleaved row copy.
@@ -278,6 +289,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     static_assert(!(BATCH && SYM), "the symmetric exact sweep is not batched");
     using C = TcCfg<KD, SPLIT, BF, WIDE>;
     constexpr int TN = C::TN;
+    constexpr bool kColRedo = tc_col_redo(KD);
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_full[C::STAGES], bar_empty[C::STAGES];
     __shared__ uint64_t bar_afull, bar_aempty, bar_accf[C::SLOTS][C::NACC], bar_acce[C::SLOTS][C::NACC];
@@ -542,7 +554,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             // the warp's block of 32 rows in the lane-interleaved FP32 copy (for
             // the direct recompute; a warp past the last row never recomputes)
             const int64_t blk0 = pos - lane;
-            const float *xblk = a_il + il_index(v.arow + (blk0 < v.nrows ? blk0 : 0), 0, KD);
+            const float *xblk =
+                kColRedo ? a_il + il_index(v.arow + (blk0 < v.nrows ? blk0 : 0), 0, KD) : nullptr;
             // SYM: this warp's 32-row block starts at wblk; rows are the padded
             // columns, so a row's weight (1 point / 0 padding) is its column weight
             const int64_t wblk = (rg * C::SLOTS + g) * kTileM + 32 * q;
@@ -630,9 +643,6 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         atomicAdd(&W[(c0 + col0) * k + own], (double)cs0);
                         atomicAdd(&W[(c0 + 16 + col1) * k + own], (double)cs1);
                     }
-                    // Columns per lane where rows are 32 elements or two row slots share
-                    // the register file; elsewhere the rows keep their lanes.
-                    constexpr bool kColRedo = KD == 32 || C::SLOTS == 2;
                     if (redo && kColRedo) {
                         // A lane has a close pair in this chunk: the warp evaluates the
                         // chunk's 32 x 32 pairs directly from the coordinates in FP32.
@@ -680,7 +690,9 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     } else if (redo) {
                         // the same chunk column by column, each lane its own row; the
                         // flagged pairs directly from the coordinates
-                        const float *xr = xblk + 4 * lane;
+                        const float *xh = a_hi + (valid ? apos : 0) * KD;
+                        constexpr bool kFull = BF || SYM;
+                        const float *xl = kFull ? xh : a_lo + (valid ? apos : 0) * KD;
                         part = 0.f;
 #pragma unroll 1
                         for (int i = 0; i < 32; ++i) {
@@ -694,11 +706,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             if (METRIC == SILH_EUCLIDEAN) {
                                 const float s2 = xn + wn.y;
                                 const float d2 = fmaf(-2.f, dot, s2);
-                                dist = (d2 < tau * s2) ? direct_dist<METRIC, KD>(xr, yc, dq)
+                                dist = (d2 < tau * s2) ? direct_dist_rows<METRIC, KD, kFull>(xh, xl, yc)
                                                        : sqrt_apx(d2);
                             } else {
                                 dist = 1.f - dot;
-                                if (dist < tau) dist = direct_dist<METRIC, KD>(xr, yc, dq);
+                                if (dist < tau) dist = direct_dist_rows<METRIC, KD, kFull>(xh, xl, yc);
                             }
                             part = fmaf(wn.x, dist, part);
                             if (SYM) {                // column side of this pair
@@ -1134,7 +1146,8 @@ __device__ __forceinline__ void store_split(float v, int64_t row, int c, int KD,
 
 // Row operand in sorted order: hi/lo split (zero padded), the FP32 row when
 // the operands are BF16 (full, KD columns; the own-cluster pass reads it),
-// the lane-interleaved FP32 copy (il; the direct recompute reads it), squared
+// the lane-interleaved FP32 copy (il, when given; the direct recompute of
+// 32-element rows reads it), squared
 // norm (Euclidean) or unit scaling (cosine), label, output index.
 // Positions nrows .. nrows_pad - 1 get zero hi/lo rows (the tail of a row
 // group that the tile loads read).
@@ -1153,7 +1166,7 @@ __global__ void k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int
     if (p >= nrows) {
         for (int c = lane; c < (BF ? 64 : KD); c += 32) {
             store_split<BF>(0.f, p, c, KD, hi, lo);
-            if (c < KD) il[il_index(p, c, KD)] = 0.f;
+            if (il != nullptr && c < KD) il[il_index(p, c, KD)] = 0.f;
         }
         return;
     }
@@ -1178,7 +1191,7 @@ __global__ void k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int
         if (mu != nullptr && c < d) v = v - mu[c];
         store_split<BF>(v, p, c, KD, hi, lo);
         if (BF && c < KD) full[p * KD + c] = v;
-        if (c < KD) il[il_index(p, c, KD)] = v;
+        if (il != nullptr && c < KD) il[il_index(p, c, KD)] = v;
         ss = fmaf(v, v, ss);
     }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
@@ -1522,10 +1535,10 @@ silh_status tc_prepare(const void *X, silh_dtype dtype, int64_t n, int32_t d, in
     } else {
         mu = nullptr;
     }
-    if (nrows_pad % 32 != 0)     // rows of the last block past nrows_pad are read, as zeros
-        SILH_CK(cudaMemsetAsync(o.ril + (nrows_pad / 32) * 32 * KD, 0, sizeof(float) * 32 * KD,
-                                stream));
-    if (mp_pad % 32 != 0)        // and so are columns of the last block past mp_pad
+    if (o.ril != nullptr && nrows_pad % 32 != 0)   // rows of the last block past nrows_pad
+        SILH_CK(cudaMemsetAsync(o.ril + (nrows_pad / 32) * 32 * KD, 0,   // are read, as zeros
+                                sizeof(float) * 32 * KD, stream));
+    if (o.yil != nullptr && mp_pad % 32 != 0)      // and so are columns past mp_pad
         SILH_CK(cudaMemsetAsync(o.yil + (mp_pad / 32) * 32 * KD, 0, sizeof(float) * 32 * KD,
                                 stream));
 #define SILH_TC_GATHER(T, BFV)                                                                  \
@@ -1579,12 +1592,12 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     SILH_CK(sc.alloc(&o.rhi, (size_t)nrows * KE * ebytes));
     SILH_CK(sc.alloc(&o.rlo, (size_t)nrows * KE * ebytes));
     if (bf) SILH_CK(sc.alloc(&o.rfull, (size_t)nrows * KD));
-    SILH_CK(sc.alloc(&o.ril, (size_t)((nrows + 31) & ~int64_t(31)) * KD));
+    if (tc_col_redo(KD)) SILH_CK(sc.alloc(&o.ril, (size_t)((nrows + 31) & ~int64_t(31)) * KD));
     SILH_CK(sc.alloc(&o.rn, (size_t)nrows));
     SILH_CK(sc.alloc(&o.poff, (size_t)k + 1));
     SILH_CK(sc.alloc(&w_own, (size_t)nrows));
     SILH_CK(sc.alloc(&o.yf, (size_t)mp_max * KD));
-    SILH_CK(sc.alloc(&o.yil, (size_t)((mp_max + 31) & ~int64_t(31)) * KD));
+    if (tc_col_redo(KD)) SILH_CK(sc.alloc(&o.yil, (size_t)((mp_max + 31) & ~int64_t(31)) * KD));
     SILH_CK(sc.alloc(&o.yhi, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&o.ylo, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&o.ywn, (size_t)mp_max));
@@ -1635,8 +1648,9 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
     const int64_t group_rows = (int64_t)slots * kTileM;
     const int64_t rows_pad = (n + 4 * kTileM - 1) / (4 * kTileM) * (4 * kTileM);
     const int64_t work_per_item = (n + group_rows - 1) / group_rows;
-    const size_t row_bytes = 2 * KE * ebytes + (bf ? KD * 4 : 0) + KD * 4 + 4 + 4 + 8 + 8;
-    const size_t col_bytes = 2 * KD * 4 + 2 * KE * ebytes + 8;
+    const size_t il_bytes = tc_col_redo(KD) ? KD * 4 : 0;    // interleaved copies
+    const size_t row_bytes = 2 * KE * ebytes + (bf ? KD * 4 : 0) + il_bytes + 4 + 4 + 8 + 8;
+    const size_t col_bytes = KD * 4 + il_bytes + 2 * KE * ebytes + 8;
     const float tau = 0.25f;
     int dev = 0, nsm = 0;
     auto cols_of = [&](int32_t i) -> int64_t {     // padded column count, whole 128-column tiles
@@ -1678,12 +1692,12 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
         SILH_CK(gs.alloc(&g.rhi, (size_t)rows_total * KE * ebytes));
         SILH_CK(gs.alloc(&g.rlo, (size_t)rows_total * KE * ebytes));
         if (bf) SILH_CK(gs.alloc(&g.rfull, (size_t)rows_total * KD));
-        SILH_CK(gs.alloc(&g.ril, (size_t)rows_total * KD));
+        if (tc_col_redo(KD)) SILH_CK(gs.alloc(&g.ril, (size_t)rows_total * KD));
         SILH_CK(gs.alloc(&g.rn, (size_t)rows_total));
         SILH_CK(gs.alloc(&w_own, (size_t)rows_total));
         SILH_CK(gs.alloc(&g.poff, (size_t)poff_total));
         SILH_CK(gs.alloc(&g.yf, (size_t)cols_total * KD));
-        SILH_CK(gs.alloc(&g.yil, (size_t)cols_total * KD));
+        if (tc_col_redo(KD)) SILH_CK(gs.alloc(&g.yil, (size_t)cols_total * KD));
         SILH_CK(gs.alloc(&g.yhi, (size_t)cols_total * KE * ebytes));
         SILH_CK(gs.alloc(&g.ylo, (size_t)cols_total * KE * ebytes));
         SILH_CK(gs.alloc(&g.ywn, (size_t)cols_total));
@@ -1697,12 +1711,12 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
                 o.rhi = g.rhi + arow * KE * ebytes;
                 o.rlo = g.rlo + arow * KE * ebytes;
                 o.rfull = bf ? g.rfull + arow * KD : nullptr;
-                o.ril = g.ril + arow * KD;
+                o.ril = g.ril ? g.ril + arow * KD : nullptr;
                 o.rn = g.rn + arow;
                 o.lab = g.lab + arow;
                 o.outi = g.outi + arow;
                 o.yf = g.yf + ccol * KD;
-                o.yil = g.yil + ccol * KD;
+                o.yil = g.yil ? g.yil + ccol * KD : nullptr;
                 o.yhi = g.yhi + ccol * KE * ebytes;
                 o.ylo = g.ylo + ccol * KE * ebytes;
                 o.ywn = g.ywn + ccol;
@@ -1808,7 +1822,7 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     SILH_CK(sc.alloc(&mpart, (size_t)mean_blocks * d));
     SILH_CK(sc.alloc(&mu, (size_t)d));
     SILH_CK(sc.alloc(&yf, (size_t)mp_max * KD));
-    SILH_CK(sc.alloc(&yil, (size_t)((mp_max + 31) & ~int64_t(31)) * KD));
+    if (tc_col_redo(KD)) SILH_CK(sc.alloc(&yil, (size_t)((mp_max + 31) & ~int64_t(31)) * KD));
     SILH_CK(sc.alloc(&yhi, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&ylo, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&ywn, (size_t)mp_max));
@@ -1843,8 +1857,9 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     } else {
         mu = nullptr;
     }
-    if (mp_max % 32 != 0)        // positions of the last block past mp_max are read, as zeros
-        SILH_CK(cudaMemsetAsync(yil + (mp_max / 32) * 32 * KD, 0, sizeof(float) * 32 * KD, stream));
+    if (yil != nullptr && mp_max % 32 != 0)   // positions of the last block past mp_max are
+        SILH_CK(cudaMemsetAsync(yil + (mp_max / 32) * 32 * KD, 0,   // read, as zeros
+                                sizeof(float) * 32 * KD, stream));
 #define SILH_TC_GATHER_SYM(T, BFV)                                                              \
     k_gather_cols_tc<T, BFV><<<ceil_div_i(mp_max, 8), 256, 0, stream>>>(                       \
         (const T *)X, d, ld, order, nullptr, coff, poff, k, mp_max, KD, metric, mu, yf, yhi,    \
