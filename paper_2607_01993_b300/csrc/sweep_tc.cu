@@ -28,6 +28,10 @@
 //
 // Rows are processed in cluster-sorted order so that a warp's rows share their
 // own cluster and the recompute branch rarely diverges.
+//
+// Many clusterings of one dataset run as one persistent launch (BATCH): each
+// gets its own sorted rows and padded columns in shared buffers, and the
+// kernel's work items become (clustering, row group) pairs.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -118,12 +122,6 @@ __device__ __forceinline__ float sqrt_apx(float x) {
     return r;
 }
 
-// Lane-interleaved FP32 copy of a row operand (the direct recompute of close
-// pairs reads it): rows in blocks of 32 (one epilogue warp), element c of row r
-// at il[(r / 32) * 32 KD + (c / 4) * 128 + (r % 32) * 4 + c % 4], so a warp
-// reading one row's four elements at a time, every lane the same row, or every
-// lane its own row, touches consecutive bytes.  For TF32 operands the values
-// are hi + lo.
 // Distance of a row (row-major; TF32 operands: x = hi + lo exactly, BF16
 // operands and the symmetric layout: xh is the FP32 row and xl is unused) to a
 // column (y, global), directly from the coordinates in FP32.
@@ -148,7 +146,13 @@ __device__ __noinline__ float direct_dist_rows(const float *__restrict__ xh,
     return METRIC == SILH_EUCLIDEAN ? sqrtf(s) : 0.5f * s;
 }
 
-// Position of element c of row r in the lane-interleaved row copy.
+// Lane-interleaved FP32 copy of a row or column operand (the dense close-pair
+// recompute of 32-element rows reads it): rows in blocks of 32 (one epilogue
+// warp), element c of row r at
+//   il[(r / 32) * 32 KD + (c / 4) * 128 + (r % 32) * 4 + c % 4],
+// so a warp reading four elements of one row (every lane the same row) or of
+// its 32 rows (every lane its own) touches consecutive bytes.  For TF32
+// operands the values are hi + lo.  il_index gives that position.
 __device__ __forceinline__ int64_t il_index(int64_t r, int c, int KD) {
     return (r >> 5) * (int64_t)(KD * 32) + (c >> 2) * 128 + (r & 31) * 4 + (c & 3);
 }
@@ -1147,8 +1151,8 @@ __device__ __forceinline__ void store_split(float v, int64_t row, int c, int KD,
 // Row operand in sorted order: hi/lo split (zero padded), the FP32 row when
 // the operands are BF16 (full, KD columns; the own-cluster pass reads it),
 // the lane-interleaved FP32 copy (il, when given; the direct recompute of
-// 32-element rows reads it), squared
-// norm (Euclidean) or unit scaling (cosine), label, output index.
+// 32-element rows reads it), squared norm (Euclidean) or unit scaling
+// (cosine), label, output index.
 // Positions nrows .. nrows_pad - 1 get zero hi/lo rows (the tail of a row
 // group that the tile loads read).
 template <class T, bool BF>
