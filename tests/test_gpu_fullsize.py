@@ -122,13 +122,19 @@ def test_batching_workload_sampled_parity():
         items.append((lt, silh.silh_sample_pps(Xt, lt, k, "euclidean", t=128.0, seed=7,
                                                clustering_id=k - 2)))
     outs = silh.silh_estimate_batched(Xt, items, "euclidean")
+    # the same launch on the tensor cores (split TF32): the data put many close
+    # pairs in neighbouring clusters, so the direct FP32 recompute carries much
+    # of the accuracy; held to the same bound
+    outs_tc = silh.silh_estimate_batched(Xt, items, "euclidean", prec="3xtf32")
     Xh = X.astype(np.float64)
     rows = synth.seeded_rows(X.shape[0], 100, seed=21)
-    for k, lab, (lt, smp), out in zip(ks, labs, items, outs):
+    rows_t = torch.from_numpy(rows).cuda()
+    for k, lab, (lt, smp), out, out_tc in zip(ks, labs, items, outs, outs_tc):
         sizes = np.bincount(lab, minlength=k)
         assert sizes.min() >= 1
         os_ = oracle.sample_pps(Xh, lab, k, "euclidean", t=128.0, seed=7, cid=k - 2)
         assert_same_sample(smp, os_, k, 7, k - 2)
         s_o, _, _ = oracle.estimate(Xh, lab, k, "euclidean", os_.offsets, os_.idx, os_.ps,
                                     rows=rows)
-        _assert_close(out[torch.from_numpy(rows).cuda()], s_o)
+        _assert_close(out[rows_t], s_o)
+        _assert_close(out_tc[rows_t], s_o)
