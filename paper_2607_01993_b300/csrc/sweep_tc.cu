@@ -289,6 +289,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
            const int64_t *__restrict__ sizes, int k, float tau, int dq,
            const double *__restrict__ w_own, float *__restrict__ s_out,
            float *__restrict__ a_out_v, float *__restrict__ b_out_v, double *__restrict__ W,
+           const int4 *__restrict__ sym_work, int64_t n_sym_work,
            const __grid_constant__ TcBatchArg<BATCH> bt) {
     static_assert(!(BATCH && SYM), "the symmetric exact sweep is not batched");
     using C = TcCfg<KD, SPLIT, BF, WIDE>;
@@ -310,13 +311,16 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ngroups = BATCH ? bt_total_work(bt)
+                          : SYM   ? n_sym_work
                                   : ((nrows + kTileM - 1) / kTileM + C::SLOTS - 1) / C::SLOTS;
     // Work item w as (clustering, row group): its row group rg, the first row
     // (arow) and column (ccol) of its clustering in the operands, the row
-    // count, padded cluster offsets, sizes, cluster count, output, and the
-    // padded column count mp with its column-tile count nct.
+    // count, padded cluster offsets, sizes, cluster count, output, the padded
+    // column count mp with its column-tile count nct, and the column tiles
+    // [ct_b, ct_e) the item sweeps: all of them, or for SYM one segment of the
+    // row group's triangle (sym_work[w] = (row group, first tile, end tile)).
     struct View {
-        int64_t rg, arow, ccol, nrows, mp, nct;
+        int64_t rg, arow, ccol, nrows, mp, nct, ct_b, ct_e;
         const int64_t *poff, *sizes;
         float *s_out;
         int k;
@@ -351,20 +355,23 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
         }
         v.mp = v.poff[v.k];
         v.nct = (v.mp + TN - 1) / TN;
+        v.ct_b = 0;
+        v.ct_e = v.nct;
+        if constexpr (SYM) {
+            const int4 e = sym_work[w];
+            v.rg = e.x;
+            v.ct_b = e.y;
+            v.ct_e = e.z;
+        }
         return v;
     };
-    // Row group of this CTA's it-th round: blockIdx.x + it * gridDim.x, except
-    // that SYM (whose groups shrink with their index) reverses odd rounds so
-    // that the CTAs' totals even out; -1 when the round has no group for it,
-    // -2 past the last round.  Its column tiles start at ct_first(rg).
+    // Work item of this CTA's it-th round: blockIdx.x + it * gridDim.x; -1
+    // when the round has none for it, -2 past the last round.
     auto group_of = [&](int64_t it) -> int64_t {
         const int64_t base = it * gridDim.x;
         if (base >= ngroups) return -2;
-        const int64_t rg = (SYM && (it & 1)) ? base + gridDim.x - 1 - blockIdx.x : base + blockIdx.x;
-        return rg < ngroups ? rg : -1;
-    };
-    auto ct_first = [&](int64_t rg) -> int64_t {
-        return SYM ? (rg * C::SLOTS * kTileM) / TN : 0;
+        const int64_t w = base + blockIdx.x;
+        return w < ngroups ? w : -1;
     };
 
     if (threadIdx.x == 0) {
@@ -420,7 +427,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                                         kb * C::KELEM, y);
                     }
                 }
-                for (int64_t ct = ct_first(rg); ct < v.nct; ++ct) {
+                for (int64_t ct = v.ct_b; ct < v.ct_e; ++ct) {
                     if (!mbar_wait(&bar_empty[stage], phase ^ 1u, kWaitNs)) {
                         abort_flag = 1;
                         break;
@@ -462,7 +469,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     abort_flag = 1;
                     break;
                 }
-                for (int64_t ct = ct_first(rg); ct < v.nct; ++ct) {
+                for (int64_t ct = v.ct_b; ct < v.ct_e; ++ct) {
                     if (!mbar_wait(&bar_full[stage], phase, kWaitNs)) {
                         abort_flag = 1;
                         break;
@@ -547,7 +554,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             const View v = view_of(w);
             const int64_t rg = v.rg;
             const int64_t mp = v.mp;
-            const int64_t nct = v.nct;
+            const int64_t ct_end = v.ct_e;
             const int64_t *vpoff = v.poff;
             const int vk = v.k;
             const int64_t pos = (rg * C::SLOTS + g) * kTileM + r_local;   // within the clustering
@@ -564,9 +571,17 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             // columns, so a row's weight (1 point / 0 padding) is its column weight
             const int64_t wblk = (rg * C::SLOTS + g) * kTileM + 32 * q;
             const float rw = (SYM && valid) ? y_wn[pos].x : 0.f;
-            const int64_t ct0 = ct_first(rg);
+            const int64_t ct0 = v.ct_b;
             int j = 0;
-            while (SYM && j < vk && vpoff[j + 1] <= ct0 * TN) ++j;
+            if (SYM) {                                // first cluster ending after column ct0 TN
+                int lo = 0, hi = vk;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (vpoff[mid + 1] <= ct0 * TN) lo = mid + 1;
+                    else hi = mid;
+                }
+                j = lo;
+            }
             int64_t pbnd = (j < vk) ? vpoff[j + 1] : LLONG_MAX;
             double accd = 0.0;
             RatioMin bmin;
@@ -576,7 +591,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             const float2 *ywn = y_wn + v.ccol;
             const int64_t c_first = ct0 * TN + et;
             float2 wn_next = (et < TN && c_first < mp) ? ywn[c_first] : make_float2(0.f, 0.f);
-            for (int64_t ct = ct0; ct < nct; ++ct) {
+            for (int64_t ct = ct0; ct < ct_end; ++ct) {
                 const float2 wn_cur = wn_next;
                 const int64_t cn = (ct + 1) * TN + et;
                 if (et < TN) wn_next = (cn < mp) ? ywn[cn] : make_float2(0.f, 0.f);
@@ -1416,7 +1431,8 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
                       const int64_t *poff, const int64_t *sizes, int k, float tau, int dq,
                       int64_t max_cluster_cols, double *w_own, float *s, float *a, float *b,
                       double *W = nullptr, const OwnItem *own_items = nullptr,
-                      int64_t n_own_items = 0) {
+                      int64_t n_own_items = 0, const int4 *sym_work = nullptr,
+                      int64_t n_sym_work = 0) {
     constexpr bool WIDE = wide_tiles(KD, BF);
     using C = TcCfg<KD, SPLIT, BF, WIDE>;
     if (SYM) {
@@ -1434,12 +1450,14 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
     auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF, SYM, WIDE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    const int64_t groups = ((nrows + kTileM - 1) / kTileM + C::SLOTS - 1) / C::SLOTS;
+    const int64_t groups = SYM ? n_sym_work
+                               : ((nrows + kTileM - 1) / kTileM + C::SLOTS - 1) / C::SLOTS;
+    if (groups == 0) return cudaSuccess;
     const int grid = (int)std::min<int64_t>(groups, nsm);
     kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_il, a_norm,
                                                 a_lab, a_out, nrows, y_full, y_il, y_wn, poff,
-                                                sizes, k, tau, dq, w_own, s, a, b, W,
-                                                TcBatchArg<false>{});
+                                                sizes, k, tau, dq, w_own, s, a, b, W, sym_work,
+                                                n_sym_work, TcBatchArg<false>{});
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1466,7 +1484,7 @@ cudaError_t launch_tc_batched(int nsm, cudaStream_t stream, const CUtensorMap &a
     kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_il, a_norm,
                                                 a_lab, a_out, 0, y_full, y_il, y_wn, poff, nullptr,
                                                 0, tau, dq, w_own, nullptr, nullptr, nullptr,
-                                                nullptr, bt);
+                                                nullptr, nullptr, 0, bt);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1813,6 +1831,8 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     float *mu = nullptr, *yf = nullptr, *yil = nullptr, *rn = nullptr;
     OwnItem *own_items = nullptr;
     std::vector<OwnItem> h_items;
+    int4 *sym_work = nullptr;
+    std::vector<int4> h_work;
     uint8_t *yhi = nullptr, *ylo = nullptr;
     float2 *ywn = nullptr;
     CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
@@ -1885,13 +1905,35 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
              "tensor map encoding failed");
     SILH_CK(cudaGetDevice(&dev));
     SILH_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    {   // The symmetric sweep's work: each row group takes the column tiles from
+        // its own first row on (a triangle), cut into segments of about equal
+        // length, so that the CTAs' totals even out; segments of one row group
+        // add their row sums to W like the column sums.
+        const int64_t TN = wide_tiles(KD, bf) ? 128 : kTileN;
+        const int64_t slots = tc_slots(KD, bf);
+        const int64_t step = slots * kTileM / TN;   // column tiles per row group on the diagonal
+        int64_t mp = 0;
+        for (int32_t j = 0; j < k; ++j) mp += (h_sizes[j] + 31) & ~int64_t(31);
+        const int64_t nct = (mp + TN - 1) / TN;
+        const int64_t ngroups = ((mp_max + kTileM - 1) / kTileM + slots - 1) / slots;
+        int64_t total = 0;
+        for (int64_t rg = 0; rg < ngroups && rg * step < nct; ++rg) total += nct - rg * step;
+        const int64_t seg = std::max<int64_t>(8, (total + 8 * (int64_t)nsm - 1) / (8 * (int64_t)nsm));
+        for (int64_t rg = 0; rg < ngroups; ++rg)
+            for (int64_t c = rg * step; c < nct; c += seg)
+                h_work.push_back(make_int4((int)rg, (int)c, (int)std::min(c + seg, nct), 0));
+        if (!h_work.empty()) {
+            SILH_CK(sc.alloc(&sym_work, h_work.size()));
+            SILH_CK(cudaMemcpyAsync(sym_work, h_work.data(), sizeof(int4) * h_work.size(),
+                                    cudaMemcpyHostToDevice, stream));
+        }
+    }
 #define SILH_TC_SYM_CASE(MET, KDV, SP, BFV)                                                    \
     if (metric == MET && KD == KDV && split == SP && bf == BFV) {                              \
         SILH_CK((launch_tc<MET, KDV, SP, BFV, true>(                                            \
             nsm, stream, m_ahi, m_alo, m_bhi, m_blo, yf, nullptr, yil, rn, plab, outi, mp_max, yf, \
             yil, ywn, poff, sizes, k, tau, (d + 3) / 4, 0, nullptr, nullptr, nullptr, nullptr, W, \
-            own_items,                                                                          \
-            (int64_t)h_items.size())));                                                         \
+            own_items, (int64_t)h_items.size(), sym_work, (int64_t)h_work.size())));            \
     }
 #define SILH_TC_SYM_CASES(MET, KDV)             \
     SILH_TC_SYM_CASE(MET, KDV, true, false)     \
