@@ -231,12 +231,14 @@ __device__ __forceinline__ float half_chunk_sym(const uint32_t (&r)[16], const f
 //
 // SYM (the exact silhouette over all points, rows = columns in the padded
 // layout): each unordered pair is evaluated once.  A row group streams only
-// the column tiles from its own first row on; a warp's 32-row block takes a
-// 32-column chunk only when the chunk lies entirely after the block (blocks
-// are 32-aligned and never straddle clusters, so the diagonal blocks are own
-// cluster pairs, which the direct pass covers).  Row sums per cluster and the
-// column sums (per column, over the warp's rows, which share one cluster) are
-// added to W (FP64, position x cluster); a separate pass forms s, a, b.
+// the column tiles from its own first row on, split into work items of about
+// equal length (sym_work: row group, first tile, end tile); a warp's 32-row
+// block takes a 32-column chunk only when the chunk lies entirely after the
+// block (blocks are 32-aligned and never straddle clusters, so the diagonal
+// blocks are own cluster pairs, which the direct pass covers).  Row sums per
+// cluster and the column sums (per column, over the warp's rows, which share
+// one cluster) are added to W (FP64, position x cluster); a separate pass forms
+// s, a, b.
 //
 // BATCH (many clusterings of one dataset in one launch): clustering b has its
 // own cluster-sorted row operand, rows [arow, arow + nrows) of the shared row
