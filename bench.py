@@ -696,10 +696,12 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     peaks, peak_kind = _peaks()
     w = WORKLOAD
-    config = {"workload": f"large: n={w['n']}, d={w['d']} FP32, k={w['k']} Zipf(1.1) Gaussian "
-                          f"mixture; t={int(w['t'])}, delta={w['delta']}; 4 metrics; exact on "
-                          f"{w['exact_rows']}-row subset",
-              "n": w["n"], "d": w["d"], "k": w["k"], "t": w["t"],
+    n_run = int(w["n"] * args.scale)                 # as make_workload draws it
+    rows_run = min(int(w["exact_rows"] * args.scale), n_run)
+    config = {"workload": f"large: n={n_run}, d={w['d']} FP32, k={w['k']} Zipf(1.1) Gaussian "
+                          f"mixture; t={int(w['t'])}, delta={w['delta']}; {len(METRICS)} metrics; "
+                          f"exact on {rows_run}-row subset",
+              "n": n_run, "d": w["d"], "k": w["k"], "t": w["t"],
               "metrics": list(METRICS), "precision": {m: PREC[m] for m in METRICS}, "l2": "flushed (256 MB write) between timed steps",
               "parallelism": f"replicas x{world}"}
 

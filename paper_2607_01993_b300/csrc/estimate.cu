@@ -72,6 +72,18 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return r;
 }
 
+// Register / shared-memory slot layout of the coordinates.  Canberra stores
+// each group of four coordinates as (c0, c2, c1, c3), so that the two-lane
+// registers hold (c0, c2) and (c1, c3): the terms of the pairs (c0, c1) and
+// (c2, c3), which share one reciprocal each, then sit in the same lane of two
+// registers, and the pair fractions of both pairs are single packed
+// instructions.  Other metrics keep the natural order.  The map is its own
+// inverse: slot s holds coordinate canb_slot<METRIC>(s).
+template <int METRIC>
+__device__ __forceinline__ int canb_slot(int s) {
+    return METRIC == SILH_CANBERRA ? (s & ~3) | ((s & 1) << 1) | ((s >> 1) & 1) : s;
+}
+
 // Distance of one row (registers, coordinate pairs) to one column (shared
 // memory, float4 of NEGATED coordinates, so x - y is one packed add).
 // Euclidean: sqrt(sum (x - y)^2).  Manhattan: sum |x - y|.  Cosine: rows and
@@ -83,15 +95,13 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // is staged) so that an all-zero coordinate pair (including padding)
 // contributes 0 and d1 d2 stays a normal float.  ax holds |x| when the caller
 // keeps it in registers (NA = D / 2), else NA = 1 and |x| is formed here.
-// The differences and sums of coordinate pairs are packed two-lane FP32
-// operations (one instruction for two coordinates), as are the Euclidean,
-// cosine and Manhattan accumulations: the sweep is issue-bound, and packing
-// halves the issue slots of the element-wise part.
+// Everything but the reciprocals is packed two-lane FP32 (one instruction for
+// two coordinates, or for two Canberra pairs in the (c0, c2, c1, c3) slot
+// order): the sweep is issue-bound, and packing halves the issue slots.
 template <int METRIC, int D, int NA>
 __device__ __forceinline__ float pair_dist(const float2 (&x)[D / 2], const float2 (&ax)[NA],
                                            const float4 *__restrict__ ny4,
                                            const float4 *__restrict__ ya4) {
-    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
     float2 sq0 = make_float2(0.f, 0.f), sq1 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < D / 4; ++q) {
@@ -114,18 +124,23 @@ __device__ __forceinline__ float pair_dist(const float2 (&x)[D / 2], const float
                 a0 = make_float2(fabsf(x[2 * q].x), fabsf(x[2 * q].y));
                 a1 = make_float2(fabsf(x[2 * q + 1].x), fabsf(x[2 * q + 1].y));
             }
+            // slots (c0, c2) and (c1, c3): t0 = (n0, n2), t1 = (n1, n3) are the
+            // numerators |x - y|, d0 = (d0, d2), d1 = (d1, d3) the denominators
             const float2 d0 = __fadd2_rn(a0, make_float2(ya.x, ya.y));   // |x| + (|y| + 1e-18)
             const float2 d1 = __fadd2_rn(a1, make_float2(ya.z, ya.w));
-            const float num0 = fmaf(fabsf(t0.y), d0.x, fabsf(t0.x) * d0.y);
-            const float num1 = fmaf(fabsf(t1.y), d1.x, fabsf(t1.x) * d1.y);
-            acc0 = fmaf(num0, rcp_approx(d0.x * d0.y), acc0);
-            acc1 = fmaf(num1, rcp_approx(d1.x * d1.y), acc1);
+            const float2 n0 = make_float2(fabsf(t0.x), fabsf(t0.y));
+            const float2 n1 = make_float2(fabsf(t1.x), fabsf(t1.y));
+            // pairs (c0, c1) and (c2, c3): (n0 d1 + n1 d0) / (d0 d1) in each lane
+            const float2 num = __ffma2_rn(n0, d1, __fmul2_rn(n1, d0));
+            const float2 den = __fmul2_rn(d0, d1);
+            const float2 r = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+            if (q & 1) sq1 = __ffma2_rn(num, r, sq1);
+            else sq0 = __ffma2_rn(num, r, sq0);
         }
     }
     if (METRIC == SILH_EUCLIDEAN) return sqrt_approx((sq0.x + sq0.y) + (sq1.x + sq1.y));
     if (METRIC == SILH_COSINE) return 0.5f * ((sq0.x + sq0.y) + (sq1.x + sq1.y));
-    if (METRIC == SILH_MANHATTAN) return (sq0.x + sq0.y) + (sq1.x + sq1.y);
-    return (acc0 + acc1) + (acc2 + acc3);
+    return (sq0.x + sq0.y) + (sq1.x + sq1.y);     // Manhattan, Canberra
 }
 
 // Whether a row tile keeps |x| in registers for Canberra (register budget).
@@ -135,13 +150,14 @@ struct RowAbs {
 };
 
 // Stage nq float4 of column coordinates as their negation (and, for Canberra,
-// |y| + 1e-18 beside them).
+// |y| + 1e-18 beside them), in the slot order of canb_slot.
 template <int METRIC>
 __device__ __forceinline__ void stage_columns(const float4 *__restrict__ src, int nq,
                                               float *__restrict__ sh_ny, float *__restrict__ sh_ya,
                                               int tid, int nthreads) {
     for (int q = tid; q < nq; q += nthreads) {
-        const float4 v = src[q];
+        float4 v = src[q];
+        if (METRIC == SILH_CANBERRA) v = make_float4(v.x, v.z, v.y, v.w);   // slot order
         reinterpret_cast<float4 *>(sh_ny)[q] = make_float4(-v.x, -v.y, -v.z, -v.w);
         if (METRIC == SILH_CANBERRA)
             reinterpret_cast<float4 *>(sh_ya)[q] =
@@ -189,8 +205,9 @@ __device__ __forceinline__ void sweep_rows(
 #pragma unroll
         for (int c = 0; c < D; c += 2) {
             const bool ok = e >= 0 && e < n;
-            x[r][c / 2].x = (ok && c < d) ? to_f32<T>(X[e * ld + c]) : 0.f;
-            x[r][c / 2].y = (ok && c + 1 < d) ? to_f32<T>(X[e * ld + c + 1]) : 0.f;
+            const int c0 = canb_slot<METRIC>(c), c1 = canb_slot<METRIC>(c + 1);
+            x[r][c / 2].x = (ok && c0 < d) ? to_f32<T>(X[e * ld + c0]) : 0.f;
+            x[r][c / 2].y = (ok && c1 < d) ? to_f32<T>(X[e * ld + c1]) : 0.f;
             sc = fmaf(x[r][c / 2].x, x[r][c / 2].x, sc);
             sc = fmaf(x[r][c / 2].y, x[r][c / 2].y, sc);
         }
@@ -621,7 +638,9 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
         zx[r] = (METRIC == SILH_COSINE && v) ? zY[p] : 0.f;
 #pragma unroll
         for (int c = 0; c < D / 2; ++c)
-            x[r][c] = v ? make_float2(Y[p * D + 2 * c], Y[p * D + 2 * c + 1]) : make_float2(0.f, 0.f);
+            x[r][c] = v ? make_float2(Y[p * D + canb_slot<METRIC>(2 * c)],
+                                      Y[p * D + canb_slot<METRIC>(2 * c + 1)])
+                        : make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < NA; ++c) ax[r][c] = make_float2(fabsf(x[r][c].x), fabsf(x[r][c].y));
     }
