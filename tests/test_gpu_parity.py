@@ -194,6 +194,29 @@ def test_uniform_variant_matches_oracle():
     assert_same_sample(gs, os_, k, 9, 0)
 
 
+@pytest.mark.parametrize("metric", METRICS)
+def test_empty_initial_sample_matches_oracle(metric):
+    """Clusters larger than t with an empty initial sample (m0 = 1e-3): the
+    device must take the gamma = 1/|Cj| branch of the oracle, giving the same
+    sample (probabilities min(1, t/|Cj|)) and the same estimate."""
+    X, lab, k, _ = _case("ragged")
+    if metric == "canberra":
+        X = synth.abs_shift(X)
+    Xt, lt = _to_dev(X, lab)
+    Xh = _host_values(Xt)
+    gs = silh.silh_sample_pps(Xt, lt, k, metric, t=40.0, m0=1e-3, seed=11, clustering_id=3)
+    os_ = oracle.sample_pps(Xh, lab, k, metric, t=40.0, m0=1e-3, seed=11, cid=3)
+    assert not os_.in_f0.any()
+    sizes = np.bincount(lab, minlength=k)
+    big = sizes[lab] > 40.0
+    assert big.sum() > 4000
+    np.testing.assert_allclose(os_.p[big], 40.0 / sizes[lab][big], rtol=2.0 ** -52, atol=0)
+    assert assert_same_sample(gs, os_, k, 11, 3, metric, lab) == 0
+    s, a, b = silh.silh_estimate(Xt, lt, k, gs, metric, want_ab=True)
+    s_o, a_o, b_o = oracle.estimate(Xh, lab, k, metric, os_.offsets, os_.idx, os_.ps)
+    _assert_close(s, s_o, a, a_o, b, b_o)
+
+
 def test_invalid_clusterings_raise():
     X, lab, k, _ = _case("tiny")
     Xt, lt = _to_dev(X, lab)

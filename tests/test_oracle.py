@@ -210,6 +210,53 @@ def test_f0_size_is_binomial():
         assert abs(z) < 4.5
 
 
+@pytest.mark.parametrize("k,delta", [(2, 0.01), (5, 0.2)])
+def test_default_m0_is_two_ln_5k_over_delta(k, delta):
+    # With m0 left to its default, Algorithm 1 draws the initial sample F0_j
+    # with probability min(1, (2/|Cj|) ln(5k/delta)), so summed over the k
+    # clusters E|F0| = sum_j |Cj| min(1, 2 ln(5k/delta)/|Cj|), with the binomial
+    # variance.  A z-test over many seeds separates this from the MapReduce
+    # round's ln(2k/delta) (z > 8 at these sizes), a dropped delta or factor 2.
+    n = 200 * k
+    X, lab = _blobs(n, 2, k, seed=20 + k)
+    sizes = np.bincount(lab, minlength=k)
+    t, R = 20.0, 300
+    assert (sizes > t).all()          # every cluster draws an initial sample
+    q = np.minimum(1.0, 2.0 * math.log(5.0 * k / delta) / sizes)
+    mu, var = float((sizes * q).sum()), float((sizes * q * (1 - q)).sum())
+    tot = np.array([oracle.sample_pps(X, lab, k, "euclidean", t=t, m0=None, delta=delta,
+                                      seed=5000 + r).in_f0.sum() for r in range(R)])
+    z = (tot.mean() - mu) / math.sqrt(var / R)
+    assert abs(z) < 4.5, z
+    # the alternative readings sit far outside that band
+    for m_alt in (2.0 * math.log(2.0 * k / delta), 2.0 * math.log(5.0 * k),
+                  math.log(5.0 * k / delta)):
+        q_alt = np.minimum(1.0, m_alt / sizes)
+        assert abs(float((sizes * q_alt).sum()) - mu) > 8 * math.sqrt(var / R)
+
+
+def test_empty_initial_sample_gives_uniform_probabilities():
+    # Clusters larger than t whose initial Poisson sample is empty (m0 tiny):
+    # the maximum over F0_j ranges over no element, so gamma_e = 1/|Cj| (the
+    # first term of Algorithm 1's maximum alone) and p_e = min(1, t/|Cj|) --
+    # the probabilities of the uniform variant of Sec. 4.1.3, and the same draw.
+    X, lab = _blobs(900, 3, 3, seed=12, sigma=2.0)
+    k, t = 3, 30.0
+    sizes = np.bincount(lab, minlength=k)
+    assert (sizes > t).all()
+    smp = oracle.sample_pps(X, lab, k, "manhattan", t=t, m0=1e-3, seed=6)
+    assert not smp.in_f0.any()
+    uni = oracle.sample_pps(X, lab, k, "manhattan", t=t, seed=6, uniform=True)
+    for j in range(k):
+        m = lab == j
+        assert (smp.gamma[m] == 1.0 / sizes[j]).all()
+        np.testing.assert_allclose(smp.p[m], t / sizes[j], rtol=2.0 ** -52, atol=0)
+        np.testing.assert_allclose(uni.p[m], t / sizes[j], rtol=2.0 ** -52, atol=0)
+    np.testing.assert_array_equal(smp.in_f, uni.in_f)
+    # and the sample is the Poisson draw of those probabilities on stream 1
+    np.testing.assert_array_equal(smp.in_f, oracle.poisson_draw(6, 1, 0, t / sizes[lab]))
+
+
 def test_poisson_draw_frequency():
     probs = np.array([0.0, 0.05, 0.3, 0.5, 0.9, 1.0])
     R = 4000
