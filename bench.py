@@ -118,22 +118,26 @@ class ClockSampler:
 
 # ------------------------------------------------------------ CPU oracle
 
-def cpu_oracle_sample(X, lab, rows_exact, k, t, delta, budget_s=20.0):
-    """Time the FP64 oracle on a bounded sample of one step and extrapolate.
+def cpu_oracle_sample(X, lab, rows_exact, k, t, delta, m2=16384, m3=2048):
+    """Time the FP64 oracle on one bounded sample of the step, as it stands.
 
-    Per metric: full Phase 1 (all n), Phase 2 on m2 rows, exact on m3 rows of
-    the exact sub-dataset.  Returns (extrapolated step seconds, description).
+    Per metric: Phase 1 on all n (the sample needs it), Phase 2 on m2 seeded
+    rows, exact on m3 rows of the exact sub-dataset -- the step's legs with
+    fewer rows.  Returns a dict: measured wall seconds, the Phase-2 rows it
+    estimated (4 m2, the points of the sample), the measured points/s, the
+    full-step time extrapolated linearly in rows (context only), and a
+    description.
     """
-    import oracle
     n = X.shape[0]
     Xd = X.astype(np.float64)
     Xc = synth.abs_shift(X).astype(np.float64)
     Xs, ls = Xd[rows_exact], lab[rows_exact]
     Xsc = Xc[rows_exact]
-    m2, m3 = min(8192, n), min(1024, len(rows_exact))
+    m2, m3 = min(m2, n), min(m3, len(rows_exact))
     r2 = synth.seeded_rows(n, m2, seed=7)
     r3 = synth.seeded_rows(len(rows_exact), m3, seed=8)
-    total = 0.0
+    import oracle
+    measured = extrap = 0.0
     parts = []
     for metric in METRICS:
         Xm, Xsm = (Xc, Xsc) if metric == "canberra" else (Xd, Xs)
@@ -144,14 +148,18 @@ def cpu_oracle_sample(X, lab, rows_exact, k, t, delta, budget_s=20.0):
         t2 = time.perf_counter()
         oracle.exact(Xsm, ls, k, metric, rows=r3)
         t3 = time.perf_counter()
-        step = (t1 - t0) + (t2 - t1) * n / m2 + (t3 - t2) * len(rows_exact) / m3
-        total += step
-        parts.append(f"{metric}: phase1 {t1 - t0:.2f}s full, phase2 {m2} rows {t2 - t1:.2f}s, "
-                     f"exact {m3} rows {t3 - t2:.2f}s")
-    desc = (f"FP64 oracle (C, OpenMP) on n={n}: Phase 1 in full, Phase 2 on {m2} seeded rows, "
-            f"exact on {m3} of {len(rows_exact)} rows, per metric; Phase 2 and exact extrapolated "
-            f"linearly in rows to the full step. " + "; ".join(parts))
-    return total, desc
+        measured += t3 - t0
+        extrap += (t1 - t0) + (t2 - t1) * n / m2 + (t3 - t2) * len(rows_exact) / m3
+        parts.append(f"{metric}: phase1 {t1 - t0:.2f}s, phase2 {t2 - t1:.2f}s, "
+                     f"exact {t3 - t2:.2f}s")
+    points = len(METRICS) * m2
+    desc = (f"FP64 oracle (C, OpenMP) on n={n}, per metric: Phase 1 on all n, Phase 2 on {m2} "
+            f"seeded rows, exact on {m3} of the {len(rows_exact)} subset rows; points = the "
+            f"{points} Phase-2 estimates, time = all three legs, measured (nothing extrapolated); "
+            + "; ".join(parts))
+    return {"seconds": measured, "points": points, "points_per_s": points / measured,
+            "extrapolated_full_step_s": extrap,
+            "extrapolated_points_per_s": len(METRICS) * n / extrap, "sample": desc}
 
 
 # --------------------------------------------------------- multi-process
@@ -349,27 +357,45 @@ def _profiled_traffic(kernel_key):
 def roofline(res, peaks, peak_kind):
     """Dominant kernel: the Phase-2 sweep of the metric with the longest leg.
 
-    Algorithmic FP32-pipe work per pair (d = 32 coordinates): euclidean 2d
-    (sub, fma) + sqrt, cosine d (fma), manhattan 2d (sub, add), canberra 4d + 1
-    (per coordinate x - y and |x| + |y|; per coordinate pair n1 d2, + n2 d1,
-    d1 d2 and the FMA of num / den into the sum; plus the weight FMA) with d/2
-    reciprocals on the MUFU pipe; the reported unit is FP32 lane-operations.
+    Algorithmic FP32-pipe work per pair, the counts of the method (d = 32
+    coordinates): euclidean 2d (sub, fma) + sqrt, cosine d (fma), manhattan
+    2d + 1 (sub, |.|-add per coordinate, the weight FMA), canberra 3d + 1 (per
+    coordinate x - y, |x| + |y| and the quotient's multiply, plus the weight
+    FMA) with d reciprocals, one per coordinate, on the MUFU pipe.  frac is
+    that work over the FP32 lane peak.  The Canberra sweep itself executes
+    4d + 1 lane-operations and d/2 reciprocals per pair (two coordinate terms
+    share one reciprocal: n1/d1 + n2/d2 = (n1 d2 + n2 d1)/(d1 d2)); those
+    counts, and the pair rate against the bound that one reciprocal per
+    coordinate would set, are reported under their own keys.
     """
     d = res["d"]
     per_pair = {"euclidean": 2 * d + 2, "cosine": d + 3, "manhattan": 2 * d + 1,
-                "canberra": 4 * d + 1}
+                "canberra": 3 * d + 1}
     mean_p2 = {m: float(np.mean(res["legs"][m]["phase2"])) for m in METRICS}
     dom = max(mean_p2, key=mean_p2.get)
     S = res["info"]["sample_size"][dom]
-    ops = res["n"] * S * per_pair[dom]
+    pairs = res["n"] * S
+    ops = pairs * per_pair[dom]
     achieved = ops / (mean_p2[dom] * 1e-3) / 1e9          # Gop/s
     clock = peaks.get("sm_max_mhz", 2032.0)
     peak = 148 * 128 * clock * 1e6 / 1e9                   # FP32 lanes x clock
     traffic = _profiled_traffic(f"k_sweep_{dom}") if res["n"] == WORKLOAD["n"] else None
-    return dom, {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
-                 "unit": "Gop/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                 "kernel": f"k_sweep ({dom}, Phase 2)",
-                 "peak_source": f"148 SMs x 128 FP32 lanes x {clock:.0f} MHz ({peak_kind} clock)"}
+    out = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
+           "unit": "Gop/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+           "kernel": f"k_sweep ({dom}, Phase 2)",
+           "work": f"n |S| ({per_pair[dom]} FP32 lane-ops per pair, the method's count)",
+           "peak_source": f"148 SMs x 128 FP32 lanes x {clock:.0f} MHz ({peak_kind} clock)"}
+    if dom == "canberra":
+        impl = pairs * (4 * d + 1) / (mean_p2[dom] * 1e-3) / 1e9
+        pair_rate = pairs / (mean_p2[dom] * 1e-3)
+        mufu_bound = 148 * 16 * clock * 1e6 / d            # one reciprocal per coordinate
+        out["impl_lane_ops_per_pair"] = 4 * d + 1
+        out["impl_achieved"] = round(impl, 1)
+        out["impl_frac"] = round(impl / peak, 4)
+        out["pairs_per_s"] = round(pair_rate, 1)
+        out["naive_reciprocal_bound_pairs_per_s"] = round(mufu_bound, 1)
+        out["vs_naive_reciprocal_bound"] = round(pair_rate / mufu_bound, 4)
+    return dom, out
 
 
 def run_batching(args):
@@ -710,19 +736,22 @@ def main():
             return
         X, lab, rows = make_workload(seed=1, scale=args.scale)
         import oracle
-        ts = []
-        desc = ""
-        for _ in range(args.steps):
-            t_step, desc = cpu_oracle_sample(X, lab, rows, w["k"], w["t"], w["delta"])
-            ts.append(t_step)
-        t_mean = float(np.mean(ts))
-        value = len(METRICS) * X.shape[0] / t_mean
+        for _ in range(min(args.warmup, 1)):          # builds / pages in the oracle
+            cpu_oracle_sample(X, lab, rows, w["k"], w["t"], w["delta"], m2=1024, m3=256)
+        runs = [cpu_oracle_sample(X, lab, rows, w["k"], w["t"], w["delta"])
+                for _ in range(args.steps)]
+        secs = float(np.sum([r["seconds"] for r in runs]))
+        value = float(np.sum([r["points"] for r in runs])) / secs
         line = {"impl": "reference", "metric": "PPS silhouette points/s", "value": value,
                 "unit": "points/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": t_mean * 1e3, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config,
+                "points_per_step": runs[0]["points"],
+                "extrapolated_full_step_points_per_s": float(np.mean(
+                    [r["extrapolated_points_per_s"] for r in runs])),
                 "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.nthreads(),
-                                 "kind": "oracle", "sample": desc},
+                                 "kind": "oracle", "sample": runs[0]["sample"]},
                 "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -757,11 +786,13 @@ def main():
         line["cosine_collapsed"] = res["info"]["cosine_collapsed"]
     if not args.no_cpu_baseline and world == 1:
         import oracle
-        t_cpu, desc = cpu_oracle_sample(res["X"], res["lab"], res["rows"], res["k"], WORKLOAD["t"],
-                                        WORKLOAD["delta"])
-        line["cpu_baseline"] = {"value": round(len(METRICS) * res["n"] / t_cpu, 1),
-                                "unit": "points/s",
-                                "cores": oracle.nthreads(), "kind": "oracle", "sample": desc}
+        cpu = cpu_oracle_sample(res["X"], res["lab"], res["rows"], res["k"], WORKLOAD["t"],
+                                WORKLOAD["delta"])
+        line["cpu_baseline"] = {"value": round(cpu["points_per_s"], 1), "unit": "points/s",
+                                "cores": oracle.nthreads(), "kind": "oracle",
+                                "sample": cpu["sample"],
+                                "extrapolated_full_step_points_per_s":
+                                    round(cpu["extrapolated_points_per_s"], 1)}
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -159,19 +159,29 @@ silh_status silh_estimate_cosine_collapsed(const void *X, silh_dtype dtype, int6
  * allocate device memory while they run -- a host framework that has already
  * reserved all of the device's memory for its own allocator, a latency-bound
  * loop that cannot take an allocation (or its failure) in the middle of a
- * stream, or code running inside an allocator or driver callback.  Arguments,
- * results and errors are those of silh_estimate, which it matches exactly; the
- * caller still provides every input and output buffer.
+ * stream, or code running inside an allocator or driver callback.  Arguments
+ * and errors are those of silh_estimate; the caller still provides every input
+ * and output buffer.
+ * Precision: distances are always evaluated in FP32 on the CUDA cores, whatever
+ * prec says (any valid mode is accepted).  The results equal silh_estimate
+ * with SILH_PREC_FP32 bit for bit; where silh_estimate would run a tensor-core
+ * mode (Euclidean or cosine, d <= 64) they are the more accurate FP32 values,
+ * within that mode's tolerance of its results, not equal to them.
  * Scratch: a fixed array in the library's device image (every GPU that loads
  * libsilh holds it until the process exits) sized for |S| <=
  * SILH_NOALLOC_MAX_COLUMNS sampled columns and |S| x D <= SILH_NOALLOC_MAX_FLOATS
  * (D = d rounded up to 8, 16, 32, 64 or 128); larger samples are rejected with
- * SILH_ECAPACITY before any work is enqueued.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress, no allocation); make that
- * first call before any stream capture.  All calls share the array and it keeps
- * the last call's contents; each call rewrites everything it reads, so nothing
- * needs clearing, but calls whose work overlaps on the GPU race on it and must
- * be ordered by the caller.  Asynchronous. */
+ * SILH_ECAPACITY before any work is enqueued.  With lazy module loading (the
+ * CUDA default) the first call on a device loads this part of the library's
+ * device code and maps the 8.5 MiB array; that first call can fail with
+ * SILH_ECUDA if the device has no memory left, so make it during
+ * initialisation, before reserving the device's memory and before any stream
+ * capture.  Every call looks the array's address up again (no allocation).
+ * All calls share the array and it keeps the last call's contents; each call
+ * rewrites everything it reads (and resets the two words it reduces into),
+ * so nothing needs clearing by the caller, but calls whose work overlaps on
+ * the GPU race on it and must be ordered by the caller.
+ * Asynchronous. */
 silh_status silh_estimate_noalloc(const void *X, silh_dtype dtype, int64_t n, int32_t d,
                                   int64_t ld, const int32_t *labels, int32_t k,
                                   silh_metric metric, silh_prec prec, const silh_sample *S,
@@ -242,6 +252,17 @@ silh_status silh_global(const float *s, int64_t n, double *out, void *stream);
  * multi-stream caller treats SILH_ETIMEOUT as "some call since the last check".
  * Synchronising. */
 silh_status silh_stream_status(void *stream);
+
+/* Self-test of the bounded-wait error path; no counterpart in the paper.  One
+ * kernel of one thread initialises an mbarrier expecting one arrival and waits
+ * for it with the limit timeout_ns (1 us .. 1 s): with arrive != 0 the thread
+ * arrives first and the wait succeeds; with arrive == 0 nothing ever arrives,
+ * the wait gives up after the limit and records the failure in the word that
+ * silh_stream_status reads, exactly as the tensor-core sweep's waits do.  No
+ * TMA copy, MMA or tensor memory is involved, so nothing is left in flight and
+ * the context stays usable.  Asynchronous.  Errors: SILH_EINVAL for a limit
+ * outside the range. */
+silh_status silh_wait_selftest(int32_t arrive, uint64_t timeout_ns, void *stream);
 
 /* Lemma 1: t = ceil((3c/eps^2) ln(5 n k / delta)) with c = 18.  Host-only. */
 double silh_t_from_eps(double eps, double delta, int64_t n, int32_t k);

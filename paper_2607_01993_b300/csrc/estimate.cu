@@ -27,12 +27,123 @@ int padded_dim(int d) {
 
 namespace {
 
+// ------------------------------------------------ Canberra at any scale
+// A Canberra term |x_c - y_c| / (|x_c| + |y_c|) (Sec. 5.1.1) does not change
+// when both coordinates are multiplied by the same factor.  The sweeps multiply
+// every coordinate by one power of two, 2^-E with 2^E above the data's largest
+// magnitude (exact, except below FP32's normal range), so every scaled
+// magnitude is below 1 (at most 4 for data above 2^125) and the pair fraction
+// (n1 d2 + n2 d1) / (d1 d2) cannot overflow, whatever the data's scale.  Each
+// staged |y| carries +2^-63, which makes a 0/0 term 0 and keeps d1 d2 >= 2^-126,
+// a normal FP32 number; the guard is below 2^-24 of every denominator whose
+// coordinates are zero or at least 2^-39 in scaled magnitude.  A point with a
+// nonzero coordinate below that ("tiny") has its pairs evaluated term by term
+// from the unscaled values instead (canb_direct).
+constexpr float kCanbGuard = 0x1p-63f;
+constexpr float kCanbTiny = 0x1p-39f;
+
+// 2^-E for the largest magnitude, range[0] (bits of a non-negative float;
+// non-negative floats order like their bit patterns): range[0] 2^-E lands in
+// [1/2, 1).
+__host__ __device__ __forceinline__ float canb_scale_of(unsigned b) {
+    if (b == 0u) return 1.0f;
+    const int e = (int)(b >> 23);
+    const int field = 253 - e < 1 ? 1 : (253 - e > 253 ? 253 : 253 - e);
+    const unsigned bits = (unsigned)field << 23;
+    float f;
+    memcpy(&f, &bits, sizeof f);
+    return f;
+}
+
+__device__ __forceinline__ float canb_scale(const unsigned *__restrict__ range) {
+    return canb_scale_of(range ? range[0] : 0u);
+}
+
+// Whether any nonzero coordinate of the data is tiny at that scale: the
+// smallest nonzero magnitude, range[1], times the scale is below 2^-39 (when
+// the data have no nonzero value range[1] holds a sentinel near FLT_MAX).
+__host__ __device__ __forceinline__ bool canb_tiny_of(unsigned min_bits, float scale) {
+    float mn;
+    memcpy(&mn, &min_bits, sizeof mn);
+    return mn * scale < kCanbTiny;
+}
+
+__device__ __forceinline__ bool canb_tiny_data(const unsigned *__restrict__ range, float scale) {
+    return range != nullptr && canb_tiny_of(range[1], scale);
+}
+
+__device__ __forceinline__ bool canb_is_tiny(float v, float scale) {
+    return v != 0.f && fabsf(v * scale) < kCanbTiny;
+}
+
+// Canberra distance of one pair term by term from the unscaled coordinates
+// (the path for points with tiny coordinates): each term's two coordinates are
+// multiplied by a power of two that brings the larger magnitude into
+// [2^-49, 2^64] (exact for the larger; the smaller only loses bits that are
+// below FP32 resolution of the term), then |x - y| / (|x| + |y|) by the
+// approximate reciprocal and one Newton step; a 0/0 term is 0.
+__device__ __forceinline__ float rcp_nr(float den) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(den));
+    return r;
+}
+
+template <class T>
+__device__ __forceinline__ float canb_direct(const T *__restrict__ x, const float *__restrict__ y,
+                                             int d) {
+    float acc = 0.f;
+    for (int c = 0; c < d; ++c) {
+        const float xv = to_f32<T>(x[c]), yv = y[c];
+        const float m = fmaxf(fabsf(xv), fabsf(yv));
+        const float sc = m > 0x1p64f ? 0x1p-64f
+                         : (m < 0x1p-100f ? 0x1p100f : (m < 0x1p-64f ? 0x1p64f : 1.0f));
+        const float xs = xv * sc, ys = yv * sc;
+        const float num = fabsf(xs - ys), den = fabsf(xs) + fabsf(ys);
+        if (den > 0.f) {
+            const float r = rcp_nr(den);
+            float q = num * r;
+            q = fmaf(r, fmaf(-q, den, num), q);
+            acc += q;
+        }
+    }
+    return acc;
+}
+
+// Largest and smallest nonzero |x| over the n x d data, as the bits of
+// non-negative floats: range[0] (atomicMax, starts at 0) and range[1]
+// (atomicMin, starts at a sentinel near FLT_MAX).  NaN is skipped.
+template <class T>
+__global__ void k_range(const T *__restrict__ X, int64_t n, int d, int64_t ld,
+                        unsigned *__restrict__ range) {
+    float mx = 0.f, mn = FLT_MAX;
+    const int64_t total = n * (int64_t)d;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / d;
+        const int c = (int)(i - r * d);
+        const float a = fabsf(to_f32<T>(X[r * ld + c]));
+        mx = fmaxf(mx, a);
+        if (a > 0.f) mn = fminf(mn, a);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (mx > 0.f) atomicMax(&range[0], __float_as_uint(mx));
+        if (mn < FLT_MAX) atomicMin(&range[1], __float_as_uint(mn));
+    }
+}
+
 // ------------------------------------------------------------- gather
 
+// zY: cosine, 0.5 wY for a zero column (below); Canberra, 1 for a column with a
+// tiny coordinate at the data's scale (*crange), else 0.
 template <class T>
 __global__ void k_gather(const T *__restrict__ X, int d, int64_t ld, const int32_t *__restrict__ idx,
                          const double *__restrict__ p, int64_t m, int D, int metric,
-                         float *__restrict__ Y, float *__restrict__ wY, float *__restrict__ zY) {
+                         const unsigned *__restrict__ crange, float *__restrict__ Y,
+                         float *__restrict__ wY, float *__restrict__ zY) {
     int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
     if (i >= m) return;
@@ -48,13 +159,20 @@ __global__ void k_gather(const T *__restrict__ X, int d, int64_t ld, const int32
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         scale = s > 0.f ? rsqrtf(s) : 0.0f;
     }
-    for (int c = lane; c < D; c += 32) Y[i * D + c] = (c < d) ? to_f32<T>(x[c]) * scale : 0.0f;
+    const float cs = (metric == SILH_CANBERRA) ? canb_scale(crange) : 1.0f;
+    bool tiny = false;
+    for (int c = lane; c < D; c += 32) {
+        const float v = (c < d) ? to_f32<T>(x[c]) : 0.0f;
+        if (metric == SILH_CANBERRA) tiny = tiny || canb_is_tiny(v, cs);
+        Y[i * D + c] = v * scale;
+    }
+    tiny = __any_sync(0xffffffffu, tiny);
     if (lane == 0) {
         float w = p ? (float)(1.0 / p[i]) : 1.0f;
         wY[i] = w;
         // cosine: a zero column is at distance 1 from everything; the unit-vector
         // form 0.5 |x - y|^2 gives 0.5 for it, so it carries +0.5 w here.
-        zY[i] = (metric == SILH_COSINE && scale == 0.0f) ? 0.5f * w : 0.0f;
+        zY[i] = (metric == SILH_COSINE && scale == 0.0f) ? 0.5f * w : (tiny ? 1.0f : 0.0f);
     }
 }
 
@@ -91,9 +209,10 @@ __device__ __forceinline__ int canb_slot(int s) {
 // (equal for unit vectors, and free of the cancellation of 1 - <x,y> for
 // nearly parallel pairs).  Canberra: terms |x - y| / (|x| + |y|) taken two at a
 // time as (n1 d2 + n2 d1)/(d1 d2) so that one reciprocal serves two
-// coordinates; each denominator carries +1e-18 (added to |y| when the column
-// is staged) so that an all-zero coordinate pair (including padding)
-// contributes 0 and d1 d2 stays a normal float.  ax holds |x| when the caller
+// coordinates, on coordinates scaled by the data's power-of-two scale; each
+// denominator carries +2^-63 (added to |y| when the column is staged) so that
+// an all-zero coordinate pair (including padding) contributes 0 and d1 d2
+// stays a normal float (see "Canberra at any scale").  ax holds |x| when the caller
 // keeps it in registers (NA = D / 2), else NA = 1 and |x| is formed here.
 // Everything but the reciprocals is packed two-lane FP32 (one instruction for
 // two coordinates, or for two Canberra pairs in the (c0, c2, c1, c3) slot
@@ -126,7 +245,7 @@ __device__ __forceinline__ float pair_dist(const float2 (&x)[D / 2], const float
             }
             // slots (c0, c2) and (c1, c3): t0 = (n0, n2), t1 = (n1, n3) are the
             // numerators |x - y|, d0 = (d0, d2), d1 = (d1, d3) the denominators
-            const float2 d0 = __fadd2_rn(a0, make_float2(ya.x, ya.y));   // |x| + (|y| + 1e-18)
+            const float2 d0 = __fadd2_rn(a0, make_float2(ya.x, ya.y));   // |x| + (|y| + 2^-63)
             const float2 d1 = __fadd2_rn(a1, make_float2(ya.z, ya.w));
             const float2 n0 = make_float2(fabsf(t0.x), fabsf(t0.y));
             const float2 n1 = make_float2(fabsf(t1.x), fabsf(t1.y));
@@ -150,19 +269,21 @@ struct RowAbs {
 };
 
 // Stage nq float4 of column coordinates as their negation (and, for Canberra,
-// |y| + 1e-18 beside them), in the slot order of canb_slot.
+// scaled by cscale, with |y| + 2^-63 beside them), in the slot order of
+// canb_slot.
 template <int METRIC>
 __device__ __forceinline__ void stage_columns(const float4 *__restrict__ src, int nq,
                                               float *__restrict__ sh_ny, float *__restrict__ sh_ya,
-                                              int tid, int nthreads) {
+                                              int tid, int nthreads, float cscale) {
     for (int q = tid; q < nq; q += nthreads) {
         float4 v = src[q];
-        if (METRIC == SILH_CANBERRA) v = make_float4(v.x, v.z, v.y, v.w);   // slot order
+        if (METRIC == SILH_CANBERRA)                                          // slot order
+            v = make_float4(v.x * cscale, v.z * cscale, v.y * cscale, v.w * cscale);
         reinterpret_cast<float4 *>(sh_ny)[q] = make_float4(-v.x, -v.y, -v.z, -v.w);
         if (METRIC == SILH_CANBERRA)
             reinterpret_cast<float4 *>(sh_ya)[q] =
-                make_float4(fabsf(v.x) + 1e-18f, fabsf(v.y) + 1e-18f, fabsf(v.z) + 1e-18f,
-                            fabsf(v.w) + 1e-18f);
+                make_float4(fabsf(v.x) + kCanbGuard, fabsf(v.y) + kCanbGuard,
+                            fabsf(v.z) + kCanbGuard, fabsf(v.w) + kCanbGuard);
     }
 }
 
@@ -171,13 +292,14 @@ constexpr int kThreads = 128;
 // One CTA's tile of BM = 128 RPT rows [r0, r0 + BM) against the whole
 // cluster-major column operand (Y, wY, zY, offsets): W_hat_j for every cluster
 // and the silhouette of Eq. 8.  Shared by the single and the batched sweeps.
-template <class T, int METRIC, int D, int RPT, int BN>
+template <class T, int METRIC, int D, int RPT, int BN, bool CHECK_TINY = true>
 __device__ __forceinline__ void sweep_rows(
         int64_t r0, const T *__restrict__ X, int d, int64_t ld, int64_t n,
         const int32_t *__restrict__ labels, int k, const int64_t *__restrict__ sizes,
         const int64_t *__restrict__ offsets, const float *__restrict__ Y,
         const float *__restrict__ wY, const float *__restrict__ zY,
-        const int64_t *__restrict__ rows, int64_t nrows, float *__restrict__ s_out,
+        const unsigned *__restrict__ crange, const int64_t *__restrict__ rows, int64_t nrows,
+        float *__restrict__ s_out,
         float *__restrict__ a_out, float *__restrict__ b_out,
         double *__restrict__ wown_out = nullptr, double *__restrict__ wsep_out = nullptr) {
     __shared__ __align__(16) float sh_y[BN * D];
@@ -192,10 +314,19 @@ __device__ __forceinline__ void sweep_rows(
     double wown[RPT];
     RatioMin bmin[RPT];
     double wsep[RPT];   // sum of W_hat_j over clusters j > own (separation numerator)
+    bool rslow[RPT];    // Canberra: the row has a tiny coordinate
+    const float cscale = (METRIC == SILH_CANBERRA) ? canb_scale(crange) : 1.0f;
+    // Canberra: some coordinate of the data is tiny at that scale (uniform); only
+    // then are rows and columns checked and flagged pairs evaluated directly
+    // (CHECK_TINY = false: the caller has established that no coordinate is)
+    const bool tiny_data =
+        METRIC == SILH_CANBERRA && CHECK_TINY && canb_tiny_data(crange, cscale);
+    int any_slow = 0;
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         int64_t rr = r0 + threadIdx.x + r * kThreads;
         int64_t e = (rr < nrows) ? (rows ? rows[rr] : rr) : -1;
+        rslow[r] = false;
         own[r] = -1;
         if (e >= 0 && e < n) {
             int l = labels[e];
@@ -208,6 +339,13 @@ __device__ __forceinline__ void sweep_rows(
             const int c0 = canb_slot<METRIC>(c), c1 = canb_slot<METRIC>(c + 1);
             x[r][c / 2].x = (ok && c0 < d) ? to_f32<T>(X[e * ld + c0]) : 0.f;
             x[r][c / 2].y = (ok && c1 < d) ? to_f32<T>(X[e * ld + c1]) : 0.f;
+            if (METRIC == SILH_CANBERRA) {
+                if (tiny_data)
+                    rslow[r] = rslow[r] || canb_is_tiny(x[r][c / 2].x, cscale) ||
+                               canb_is_tiny(x[r][c / 2].y, cscale);
+                x[r][c / 2].x *= cscale;
+                x[r][c / 2].y *= cscale;
+            }
             sc = fmaf(x[r][c / 2].x, x[r][c / 2].x, sc);
             sc = fmaf(x[r][c / 2].y, x[r][c / 2].y, sc);
         }
@@ -227,7 +365,10 @@ __device__ __forceinline__ void sweep_rows(
         wown[r] = 0.0;
         bmin[r] = RatioMin();
         wsep[r] = 0.0;
+        any_slow |= rslow[r] ? 1 : 0;
     }
+    // Canberra: whether any row of the CTA has a tiny coordinate (uniform)
+    if (tiny_data) any_slow = __syncthreads_or(any_slow);
     for (int j = 0; j < k; ++j) {
         int64_t cs = offsets[j], ce = offsets[j + 1];
         double accd[RPT];
@@ -237,27 +378,48 @@ __device__ __forceinline__ void sweep_rows(
             int nb = (int)min((int64_t)BN, ce - cb);
             __syncthreads();
             stage_columns<METRIC>(reinterpret_cast<const float4 *>(Y + cb * D), nb * (D / 4), sh_y,
-                                  sh_ya, threadIdx.x, kThreads);
+                                  sh_ya, threadIdx.x, kThreads, cscale);
+            int chunk_slow = 0;
             for (int q = threadIdx.x; q < BN; q += kThreads) {
                 sh_w[q] = (q < nb) ? wY[cb + q] : 0.f;
+                // cosine: the zero-column term; Canberra: the tiny-column flag
                 if (METRIC == SILH_COSINE) sh_z[q] = (q < nb) ? zY[cb + q] : 0.f;
+                if (tiny_data && q < nb && zY[cb + q] != 0.f) chunk_slow = 1;
             }
-            __syncthreads();
+            if (tiny_data) chunk_slow = __syncthreads_or(chunk_slow | any_slow);
+            else __syncthreads();
             float accf[RPT];
             float accz = 0.f, accw = 0.f;
 #pragma unroll
             for (int r = 0; r < RPT; ++r) accf[r] = 0.f;
-            for (int col = 0; col < nb; ++col) {
-                const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * D);
-                const float4 *ya4 = reinterpret_cast<const float4 *>(sh_ya + col * D);
-                float w = sh_w[col];
-                if (METRIC == SILH_COSINE) {
-                    accz += sh_z[col];
-                    accw += w;
-                }
+            if (METRIC == SILH_CANBERRA && chunk_slow) {
+                // a tiny row or column in the CTA's rows or this chunk: every
+                // pair of the chunk term by term from the unscaled coordinates
+                for (int col = 0; col < nb; ++col) {
+                    const float w = sh_w[col];
 #pragma unroll
-                for (int r = 0; r < RPT; ++r)
-                    accf[r] = fmaf(w, pair_dist<METRIC, D, NA>(x[r], ax[r], y4, ya4), accf[r]);
+                    for (int r = 0; r < RPT; ++r) {
+                        const int64_t rr = r0 + threadIdx.x + r * kThreads;
+                        const int64_t e = (rr < nrows) ? (rows ? rows[rr] : rr) : -1;
+                        const float dd = (e >= 0 && e < n)
+                                             ? canb_direct<T>(X + e * ld, Y + (cb + col) * D, d)
+                                             : 0.f;
+                        accf[r] = fmaf(w, dd, accf[r]);
+                    }
+                }
+            } else {
+                for (int col = 0; col < nb; ++col) {
+                    const float4 *y4 = reinterpret_cast<const float4 *>(sh_y + col * D);
+                    const float4 *ya4 = reinterpret_cast<const float4 *>(sh_ya + col * D);
+                    float w = sh_w[col];
+                    if (METRIC == SILH_COSINE) {
+                        accz += sh_z[col];
+                        accw += w;
+                    }
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r)
+                        accf[r] = fmaf(w, pair_dist<METRIC, D, NA>(x[r], ax[r], y4, ya4), accf[r]);
+                }
             }
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
@@ -303,10 +465,11 @@ k_sweep_cohsep(const T *__restrict__ X, int d, int64_t ld, int64_t n,
                const int32_t *__restrict__ labels, int k, const int64_t *__restrict__ sizes,
                const int64_t *__restrict__ offsets, const float *__restrict__ Y,
                const float *__restrict__ wY, const float *__restrict__ zY,
-               double *__restrict__ wown, double *__restrict__ wsep) {
+               const unsigned *__restrict__ crange, double *__restrict__ wown,
+               double *__restrict__ wsep) {
     sweep_rows<T, METRIC, D, RPT, BN>((int64_t)blockIdx.x * kThreads * RPT, X, d, ld, n, labels, k,
-                                      sizes, offsets, Y, wY, zY, nullptr, n, nullptr, nullptr,
-                                      nullptr, wown, wsep);
+                                      sizes, offsets, Y, wY, zY, crange, nullptr, n, nullptr,
+                                      nullptr, nullptr, wown, wsep);
 }
 
 // Coh = (1/2) sum wown / sum_j C(|Cj|,2), Sep = sum wsep / sum_{j1<j2} |Cj1||Cj2|
@@ -344,28 +507,35 @@ __global__ void k_cohsep_final(const double *__restrict__ wown, const double *__
     }
 }
 
-template <class T, int METRIC, int D, int RPT, int BN>
+// TINY selects the instantiation for Canberra data with (true) or without
+// (false) tiny coordinates; both are launched, and the one that does not match
+// the data (read from crange) returns at once, so the common case runs a
+// kernel without the direct-evaluation path.  Other metrics: TINY = false.
+template <class T, int METRIC, int D, int RPT, int BN, bool TINY>
 __global__ void __launch_bounds__(kThreads)
 k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__restrict__ labels,
         int k, const int64_t *__restrict__ sizes, const int64_t *__restrict__ offsets,
         const float *__restrict__ Y, const float *__restrict__ wY, const float *__restrict__ zY,
-        const int64_t *__restrict__ rows, int64_t nrows, float *__restrict__ s_out,
-        float *__restrict__ a_out, float *__restrict__ b_out) {
-    sweep_rows<T, METRIC, D, RPT, BN>((int64_t)blockIdx.x * kThreads * RPT, X, d, ld, n, labels, k,
-                                      sizes, offsets, Y, wY, zY, rows, nrows, s_out, a_out, b_out);
+        const unsigned *__restrict__ crange, const int64_t *__restrict__ rows, int64_t nrows,
+        float *__restrict__ s_out, float *__restrict__ a_out, float *__restrict__ b_out) {
+    if (METRIC == SILH_CANBERRA && canb_tiny_data(crange, canb_scale(crange)) != TINY) return;
+    sweep_rows<T, METRIC, D, RPT, BN, TINY>((int64_t)blockIdx.x * kThreads * RPT, X, d, ld, n, labels, k,
+                                      sizes, offsets, Y, wY, zY, crange, rows, nrows, s_out, a_out,
+                                      b_out);
 }
 
 template <class T, int METRIC>
 void launch_cohsep_d(int D, cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
                      const int32_t *labels, int k, const int64_t *sizes, const int64_t *offsets,
-                     const float *Y, const float *wY, const float *zY, double *wown, double *wsep) {
+                     const float *Y, const float *wY, const float *zY, const unsigned *crange,
+                     double *wown, double *wsep) {
     const int grid1 = (int)((n + kThreads - 1) / kThreads), grid2 = (int)((n + 2 * kThreads - 1) / (2 * kThreads));
     switch (D) {
-        case 8: k_sweep_cohsep<T, METRIC, 8, 2, 64><<<grid2, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, wown, wsep); break;
-        case 16: k_sweep_cohsep<T, METRIC, 16, 2, 64><<<grid2, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, wown, wsep); break;
-        case 32: k_sweep_cohsep<T, METRIC, 32, 2, 64><<<grid2, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, wown, wsep); break;
-        case 64: k_sweep_cohsep<T, METRIC, 64, 1, 32><<<grid1, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, wown, wsep); break;
-        default: k_sweep_cohsep<T, METRIC, 128, 1, 32><<<grid1, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, wown, wsep); break;
+        case 8: k_sweep_cohsep<T, METRIC, 8, 2, 64><<<grid2, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, wown, wsep); break;
+        case 16: k_sweep_cohsep<T, METRIC, 16, 2, 64><<<grid2, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, wown, wsep); break;
+        case 32: k_sweep_cohsep<T, METRIC, 32, 2, 64><<<grid2, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, wown, wsep); break;
+        case 64: k_sweep_cohsep<T, METRIC, 64, 1, 32><<<grid1, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, wown, wsep); break;
+        default: k_sweep_cohsep<T, METRIC, 128, 1, 32><<<grid1, kThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, wown, wsep); break;
     }
     count_launches(1);
 }
@@ -404,7 +574,8 @@ template <class T, int METRIC, int D, int RPT, int BN>
 __global__ void __launch_bounds__(kThreads)
 k_sweep_batched(const __grid_constant__ BatchParams bp, const T *__restrict__ X, int d, int64_t ld,
                 int64_t n, const float *__restrict__ Y, const float *__restrict__ wY,
-                const float *__restrict__ zY, unsigned long long *__restrict__ next_work) {
+                const float *__restrict__ zY, const unsigned *__restrict__ crange,
+                unsigned long long *__restrict__ next_work) {
     __shared__ int64_t sh_work;
     for (;;) {
         // dynamic schedule: claim the next work item (items are ordered by cost, largest first)
@@ -422,7 +593,7 @@ k_sweep_batched(const __grid_constant__ BatchParams bp, const T *__restrict__ X,
         const int64_t rt = w - it.tile_base;
         sweep_rows<T, METRIC, D, RPT, BN>(rt * kThreads * RPT, X, d, ld, n, it.labels, it.k,
                                           it.sizes, it.offsets, Y + it.col_base * D,
-                                          wY + it.col_base, zY + it.col_base, nullptr, n,
+                                          wY + it.col_base, zY + it.col_base, crange, nullptr, n,
                                           it.s_out, nullptr, nullptr);
     }
 }
@@ -430,7 +601,8 @@ k_sweep_batched(const __grid_constant__ BatchParams bp, const T *__restrict__ X,
 // Concatenated column operand of all items (one warp per column).
 template <class T>
 __global__ void k_gather_batched(const __grid_constant__ BatchParams bp, const T *__restrict__ X,
-                                 int d, int64_t ld, int D, int metric, float *__restrict__ Y,
+                                 int d, int64_t ld, int D, int metric,
+                                 const unsigned *__restrict__ crange, float *__restrict__ Y,
                                  float *__restrict__ wY, float *__restrict__ zY) {
     const int64_t g = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
@@ -453,18 +625,26 @@ __global__ void k_gather_batched(const __grid_constant__ BatchParams bp, const T
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
         scale = sq > 0.f ? rsqrtf(sq) : 0.0f;
     }
-    for (int c = lane; c < D; c += 32) Y[g * D + c] = (c < d) ? to_f32<T>(x[c]) * scale : 0.0f;
+    const float cs = (metric == SILH_CANBERRA) ? canb_scale(crange) : 1.0f;
+    bool tiny = false;
+    for (int c = lane; c < D; c += 32) {
+        const float v = (c < d) ? to_f32<T>(x[c]) : 0.0f;
+        if (metric == SILH_CANBERRA) tiny = tiny || canb_is_tiny(v, cs);
+        Y[g * D + c] = v * scale;
+    }
+    tiny = __any_sync(0xffffffffu, tiny);
     if (lane == 0) {
         const float w = (float)(1.0 / it.p[i]);
         wY[g] = w;
-        zY[g] = (metric == SILH_COSINE && scale == 0.0f) ? 0.5f * w : 0.0f;
+        zY[g] = (metric == SILH_COSINE && scale == 0.0f) ? 0.5f * w : (tiny ? 1.0f : 0.0f);
     }
 }
 
 template <class T, int METRIC, int D, int RPT, int BN>
 cudaError_t launch_batched_v(const BatchParams &bp, cudaStream_t stream, const T *X, int d,
                              int64_t ld, int64_t n, const float *Y, const float *wY,
-                             const float *zY, unsigned long long *next_work) {
+                             const float *zY, const unsigned *crange,
+                             unsigned long long *next_work) {
     auto kern = k_sweep_batched<T, METRIC, D, RPT, BN>;
     int dev = 0, nsm = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -475,7 +655,7 @@ cudaError_t launch_batched_v(const BatchParams &bp, cudaStream_t stream, const T
     e = cudaMemsetAsync(next_work, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)std::max<int64_t>(grid, 1), kThreads, 0, stream>>>(bp, X, d, ld, n, Y, wY, zY,
-                                                                       next_work);
+                                                                       crange, next_work);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -486,27 +666,27 @@ constexpr int kBatchVariants = 4;
 template <class T, int METRIC, int D>
 cudaError_t launch_batched(int variant, const BatchParams &bp, cudaStream_t stream, const T *X,
                            int d, int64_t ld, int64_t n, const float *Y, const float *wY,
-                           const float *zY, unsigned long long *nw) {
+                           const float *zY, const unsigned *crange, unsigned long long *nw) {
     if (variant < 0) variant = (D <= 32) ? 3 : 0;     // as the single sweep: (2, 64) / (1, 32)
     switch (variant) {
-        case 0: return launch_batched_v<T, METRIC, D, 1, 32>(bp, stream, X, d, ld, n, Y, wY, zY, nw);
-        case 1: return launch_batched_v<T, METRIC, D, 1, 64>(bp, stream, X, d, ld, n, Y, wY, zY, nw);
-        case 2: return launch_batched_v<T, METRIC, D, 2, 32>(bp, stream, X, d, ld, n, Y, wY, zY, nw);
+        case 0: return launch_batched_v<T, METRIC, D, 1, 32>(bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
+        case 1: return launch_batched_v<T, METRIC, D, 1, 64>(bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
+        case 2: return launch_batched_v<T, METRIC, D, 2, 32>(bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
         default: return launch_batched_v<T, METRIC, D, 2, (D >= 128 ? 32 : 64)>(bp, stream, X, d, ld,
-                                                                               n, Y, wY, zY, nw);
+                                                                               n, Y, wY, zY, crange, nw);
     }
 }
 
 template <class T, int METRIC>
 cudaError_t launch_batched_d(int D, int variant, const BatchParams &bp, cudaStream_t stream,
                              const T *X, int d, int64_t ld, int64_t n, const float *Y,
-                             const float *wY, const float *zY, unsigned long long *nw) {
+                             const float *wY, const float *zY, const unsigned *crange, unsigned long long *nw) {
     switch (D) {
-        case 8: return launch_batched<T, METRIC, 8>(variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
-        case 16: return launch_batched<T, METRIC, 16>(variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
-        case 32: return launch_batched<T, METRIC, 32>(variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
-        case 64: return launch_batched<T, METRIC, 64>(variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
-        default: return launch_batched<T, METRIC, 128>(variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+        case 8: return launch_batched<T, METRIC, 8>(variant, bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
+        case 16: return launch_batched<T, METRIC, 16>(variant, bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
+        case 32: return launch_batched<T, METRIC, 32>(variant, bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
+        case 64: return launch_batched<T, METRIC, 64>(variant, bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
+        default: return launch_batched<T, METRIC, 128>(variant, bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
     }
 }
 
@@ -514,40 +694,46 @@ template <class T>
 cudaError_t launch_batched_m(int metric, int D, int variant, const BatchParams &bp,
                              cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
                              const float *Y, const float *wY, const float *zY,
-                             unsigned long long *nw) {
+                             const unsigned *crange, unsigned long long *nw) {
     switch (metric) {
         case SILH_EUCLIDEAN:
-            return launch_batched_d<T, SILH_EUCLIDEAN>(D, variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+            return launch_batched_d<T, SILH_EUCLIDEAN>(D, variant, bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
         case SILH_COSINE:
-            return launch_batched_d<T, SILH_COSINE>(D, variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+            return launch_batched_d<T, SILH_COSINE>(D, variant, bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
         case SILH_MANHATTAN:
-            return launch_batched_d<T, SILH_MANHATTAN>(D, variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+            return launch_batched_d<T, SILH_MANHATTAN>(D, variant, bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
         default:
-            return launch_batched_d<T, SILH_CANBERRA>(D, variant, bp, stream, X, d, ld, n, Y, wY, zY, nw);
+            return launch_batched_d<T, SILH_CANBERRA>(D, variant, bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
     }
 }
 
 template <class T, int METRIC, int D>
 void launch_sweep(cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
                   const int32_t *labels, int k, const int64_t *sizes, const int64_t *offsets,
-                  const float *Y, const float *wY, const float *zY, const int64_t *rows,
-                  int64_t nrows, float *s, float *a, float *b) {
+                  const float *Y, const float *wY, const float *zY, const unsigned *crange,
+                  const int64_t *rows, int64_t nrows, float *s, float *a, float *b) {
     constexpr int RPT = (D <= 32) ? 2 : 1;
     constexpr int BN = (D <= 32) ? 64 : 32;
     int grid = (int)((nrows + kThreads * RPT - 1) / (kThreads * RPT));
-    k_sweep<T, METRIC, D, RPT, BN><<<grid, kThreads, 0, stream>>>(
-        X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, rows, nrows, s, a, b); count_launches(1);
+    k_sweep<T, METRIC, D, RPT, BN, false><<<grid, kThreads, 0, stream>>>(
+        X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, rows, nrows, s, a, b);
+    count_launches(1);
+    if (METRIC == SILH_CANBERRA) {
+        k_sweep<T, METRIC, D, RPT, BN, METRIC == SILH_CANBERRA><<<grid, kThreads, 0, stream>>>(
+            X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, rows, nrows, s, a, b);
+        count_launches(1);
+    }
 }
 
 template <class T, int METRIC>
 void launch_sweep_d(int D, cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
                     const int32_t *labels, int k, const int64_t *sizes, const int64_t *offsets,
-                    const float *Y, const float *wY, const float *zY, const int64_t *rows,
-                    int64_t nrows, float *s, float *a, float *b) {
+                    const float *Y, const float *wY, const float *zY, const unsigned *crange,
+                    const int64_t *rows, int64_t nrows, float *s, float *a, float *b) {
 #define SILH_SWEEP_D(DD)                                                                      \
     case DD:                                                                                  \
         launch_sweep<T, METRIC, DD>(stream, X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, \
-                                    rows, nrows, s, a, b);                                    \
+                                    crange, rows, nrows, s, a, b);                          \
         break;
     switch (D) {
         SILH_SWEEP_D(8)
@@ -564,23 +750,24 @@ template <class T>
 void launch_sweep_m(int metric, int D, cudaStream_t stream, const T *X, int d, int64_t ld,
                     int64_t n, const int32_t *labels, int k, const int64_t *sizes,
                     const int64_t *offsets, const float *Y, const float *wY, const float *zY,
-                    const int64_t *rows, int64_t nrows, float *s, float *a, float *b) {
+                    const unsigned *crange, const int64_t *rows, int64_t nrows, float *s, float *a,
+                    float *b) {
     switch (metric) {
         case SILH_EUCLIDEAN:
             launch_sweep_d<T, SILH_EUCLIDEAN>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
-                                              Y, wY, zY, rows, nrows, s, a, b);
+                                              Y, wY, zY, crange, rows, nrows, s, a, b);
             break;
         case SILH_COSINE:
             launch_sweep_d<T, SILH_COSINE>(D, stream, X, d, ld, n, labels, k, sizes, offsets, Y,
-                                           wY, zY, rows, nrows, s, a, b);
+                                           wY, zY, crange, rows, nrows, s, a, b);
             break;
         case SILH_MANHATTAN:
             launch_sweep_d<T, SILH_MANHATTAN>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
-                                              Y, wY, zY, rows, nrows, s, a, b);
+                                              Y, wY, zY, crange, rows, nrows, s, a, b);
             break;
         default:
             launch_sweep_d<T, SILH_CANBERRA>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
-                                             Y, wY, zY, rows, nrows, s, a, b);
+                                             Y, wY, zY, crange, rows, nrows, s, a, b);
             break;
     }
 }
@@ -596,11 +783,11 @@ void launch_sweep_m(int metric, int D, cudaStream_t stream, const T *X, int d, i
 // for the row's cluster (reduced over the CTA's rows with warp shuffles and
 // shared memory).  Both land in the n x k FP64 weight matrix W with atomic
 // adds (so results are reproducible to rounding order, not bitwise).
-template <int METRIC, int D, int RPT>
+template <int METRIC, int D, int RPT, bool TINY>
 __global__ void __launch_bounds__(kThreads)
 k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
             const int32_t *__restrict__ lab_s, int64_t n, int k, int64_t ntiles,
-            double *__restrict__ W) {
+            const unsigned *__restrict__ crange, double *__restrict__ W) {
     constexpr int T = kThreads * RPT;
     constexpr int BN = (D >= 128) ? 32 : 64;   // static shared memory stays under 48 KB
     constexpr int NW = kThreads / 32;
@@ -628,6 +815,12 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
     float zx[RPT];
     int64_t prow[RPT];
     float rv[RPT];                     // 1 for a row of the input, 0 past n
+    const float cscale = (METRIC == SILH_CANBERRA) ? canb_scale(crange) : 1.0f;
+    // Canberra with some coordinate of the data tiny at that scale (the host
+    // picks this instantiation from crange): rows and columns are checked and
+    // flagged chunks evaluated directly
+    constexpr bool tiny_data = METRIC == SILH_CANBERRA && TINY;
+    int any_slow = 0;
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         const int64_t p = I * T + threadIdx.x + r * kThreads;
@@ -636,14 +829,16 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
         const bool v = p < n;
         lp[r] = v ? lab_s[p] : -1;
         zx[r] = (METRIC == SILH_COSINE && v) ? zY[p] : 0.f;
+        if (tiny_data && v && zY[p] != 0.f) any_slow = 1;    // a tiny row
 #pragma unroll
         for (int c = 0; c < D / 2; ++c)
-            x[r][c] = v ? make_float2(Y[p * D + canb_slot<METRIC>(2 * c)],
-                                      Y[p * D + canb_slot<METRIC>(2 * c + 1)])
+            x[r][c] = v ? make_float2(Y[p * D + canb_slot<METRIC>(2 * c)] * cscale,
+                                      Y[p * D + canb_slot<METRIC>(2 * c + 1)] * cscale)
                         : make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < NA; ++c) ax[r][c] = make_float2(fabsf(x[r][c].x), fabsf(x[r][c].y));
     }
+    if (tiny_data) any_slow = __syncthreads_or(any_slow);
     const int64_t rlast = min(I * T + T, n) - 1;
     const int cI0 = lab_s[I * T], cI1 = lab_s[rlast];
     const int64_t c_begin = J * T, c_end = min(J * T + T, n);
@@ -655,13 +850,20 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
         const int nb = (int)min((int64_t)BN, c_end - cb);
         __syncthreads();
         stage_columns<METRIC>(reinterpret_cast<const float4 *>(Y + cb * D), nb * (D / 4), sh_y,
-                              sh_ya, threadIdx.x, kThreads);
+                              sh_ya, threadIdx.x, kThreads, cscale);
+        int chunk_slow = 0;
         for (int q = threadIdx.x; q < BN; q += kThreads) {
             sh_lab[q] = (q < nb) ? lab_s[cb + q] : -1;
             sh_z[q] = (METRIC == SILH_COSINE && q < nb) ? zY[cb + q] : 0.f;
+            // Canberra: a column with a tiny coordinate
+            if (tiny_data && q < nb && zY[cb + q] != 0.f) chunk_slow = 1;
         }
-        __syncthreads();
-        if (!diag && cI0 == cI1) {
+        if (tiny_data) chunk_slow = __syncthreads_or(chunk_slow | any_slow);
+        else __syncthreads();
+        // Canberra with a tiny row in the CTA or a tiny column in this chunk
+        // takes the per-column branch, every pair term by term (canb_direct).
+        const bool direct = METRIC == SILH_CANBERRA && chunk_slow;
+        if (!diag && cI0 == cI1 && !direct) {
             // One row cluster: the column sums are reduced across the warp CB
             // columns at a time (transpose-reduce: 16 shuffles for 16 columns,
             // 6 for 4; Canberra's larger body takes 4 to stay in the
@@ -721,7 +923,12 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
                 float dr[RPT];
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
-                    float dd = pair_dist<METRIC, D, NA>(x[r], ax[r], y4, ya4);
+                    float dd;
+                    if (METRIC == SILH_CANBERRA && direct)
+                        dd = prow[r] < n ? canb_direct<float>(Y + prow[r] * D, Y + (cb + col) * D, D)
+                                         : 0.f;
+                    else
+                        dd = pair_dist<METRIC, D, NA>(x[r], ax[r], y4, ya4);
                     if (METRIC == SILH_COSINE) dd += zx[r] + sh_z[col];
                     dr[r] = (prow[r] < n) ? dd : 0.f;
                     accr[r] += dr[r];
@@ -738,7 +945,7 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
                 }
             }
         }
-        if (!diag && cI0 == cI1) {
+        if (!diag && cI0 == cI1 && !direct) {
             __syncthreads();
             for (int q = threadIdx.x; q < nb; q += kThreads) {
                 float v = 0.f;
@@ -786,24 +993,30 @@ __global__ void k_sorted_labels(const int32_t *__restrict__ labels, const int32_
 
 template <int METRIC, int D>
 void launch_exact_sym(cudaStream_t stream, const float *Y, const float *zY, const int32_t *lab_s,
-                      int64_t n, int k, double *W) {
+                      int64_t n, int k, const unsigned *crange, bool tiny, double *W) {
     constexpr int RPT = (D <= 32) ? 2 : 1;
     constexpr int T = kThreads * RPT;
     const int64_t nt = (n + T - 1) / T;
     const int64_t nblk = nt * (nt + 1) / 2;
-    k_exact_sym<METRIC, D, RPT><<<(unsigned)nblk, kThreads, 0, stream>>>(Y, zY, lab_s, n, k, nt, W);
+    if (METRIC == SILH_CANBERRA && tiny)
+        k_exact_sym<METRIC, D, RPT, METRIC == SILH_CANBERRA><<<(unsigned)nblk, kThreads, 0, stream>>>(
+            Y, zY, lab_s, n, k, nt, crange, W);
+    else
+        k_exact_sym<METRIC, D, RPT, false><<<(unsigned)nblk, kThreads, 0, stream>>>(
+            Y, zY, lab_s, n, k, nt, crange, W);
     count_launches(1);
 }
 
 template <int METRIC>
 void launch_exact_sym_d(int D, cudaStream_t stream, const float *Y, const float *zY,
-                        const int32_t *lab_s, int64_t n, int k, double *W) {
+                        const int32_t *lab_s, int64_t n, int k, const unsigned *crange, bool tiny,
+                        double *W) {
     switch (D) {
-        case 8: launch_exact_sym<METRIC, 8>(stream, Y, zY, lab_s, n, k, W); break;
-        case 16: launch_exact_sym<METRIC, 16>(stream, Y, zY, lab_s, n, k, W); break;
-        case 32: launch_exact_sym<METRIC, 32>(stream, Y, zY, lab_s, n, k, W); break;
-        case 64: launch_exact_sym<METRIC, 64>(stream, Y, zY, lab_s, n, k, W); break;
-        default: launch_exact_sym<METRIC, 128>(stream, Y, zY, lab_s, n, k, W); break;
+        case 8: launch_exact_sym<METRIC, 8>(stream, Y, zY, lab_s, n, k, crange, tiny, W); break;
+        case 16: launch_exact_sym<METRIC, 16>(stream, Y, zY, lab_s, n, k, crange, tiny, W); break;
+        case 32: launch_exact_sym<METRIC, 32>(stream, Y, zY, lab_s, n, k, crange, tiny, W); break;
+        case 64: launch_exact_sym<METRIC, 64>(stream, Y, zY, lab_s, n, k, crange, tiny, W); break;
+        default: launch_exact_sym<METRIC, 128>(stream, Y, zY, lab_s, n, k, crange, tiny, W); break;
     }
 }
 
@@ -842,18 +1055,37 @@ __global__ void k_sum_final(const double *__restrict__ part, int np, int64_t n,
 
 }  // namespace
 
+silh_status canberra_range(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                           unsigned *range, cudaStream_t stream) {
+    silh_status st = SILH_OK;
+    int grid = ceil_div_i(std::max<int64_t>(n * (int64_t)d, 1), 256 * 8);
+    grid = std::min(grid, 148 * 8);
+    SILH_CK(cudaMemsetAsync(range, 0, sizeof(unsigned), stream));
+    SILH_CK(cudaMemsetAsync(range + 1, 0x7F, sizeof(unsigned), stream));   // 0x7F7F7F7F
+    if (dtype == SILH_F32)
+        k_range<float><<<grid, 256, 0, stream>>>((const float *)X, n, d, ld, range);
+    else
+        k_range<__nv_bfloat16><<<grid, 256, 0, stream>>>((const __nv_bfloat16 *)X, n, d, ld, range);
+    count_launches(1);
+    SILH_CK(cudaGetLastError());
+done:
+    return st;
+}
+
 silh_status gather_columns(const void *X, silh_dtype dtype, int32_t d, int64_t ld,
                            const int32_t *idx, const double *p, int64_t m, int D, int metric,
-                           float *Y, float *wY, float *zY, cudaStream_t stream) {
+                           const unsigned *crange, float *Y, float *wY, float *zY,
+                           cudaStream_t stream) {
     silh_status st = SILH_OK;
     if (m > 0) {
         int grid = ceil_div_i(m, 8);
         if (dtype == SILH_F32)
             k_gather<float><<<grid, 256, 0, stream>>>((const float *)X, d, ld, idx, p, m, D,
-                                                      metric, Y, wY, zY);
+                                                      metric, crange, Y, wY, zY);
         else
             k_gather<__nv_bfloat16><<<grid, 256, 0, stream>>>((const __nv_bfloat16 *)X, d, ld,
-                                                              idx, p, m, D, metric, Y, wY, zY);
+                                                              idx, p, m, D, metric, crange, Y, wY,
+                                                              zY);
         count_launches(1);
     }
     SILH_CK(cudaGetLastError());
@@ -864,19 +1096,20 @@ done:
 silh_status phase2_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                          const int32_t *labels, int32_t k, int metric, int prec,
                          const int64_t *sizes, const int64_t *offsets, const float *Y,
-                         const float *wY, const float *zY, int64_t m, int D, const int64_t *rows,
-                         int64_t nrows, float *s, float *a, float *b, cudaStream_t stream) {
+                         const float *wY, const float *zY, const unsigned *crange, int64_t m, int D,
+                         const int64_t *rows, int64_t nrows, float *s, float *a, float *b,
+                         cudaStream_t stream) {
     silh_status st = SILH_OK;
     (void)prec;
     (void)m;
     if (nrows > 0) {
         if (dtype == SILH_F32)
             launch_sweep_m<float>(metric, D, stream, (const float *)X, d, ld, n, labels, k, sizes,
-                                  offsets, Y, wY, zY, rows, nrows, s, a, b);
+                                  offsets, Y, wY, zY, crange, rows, nrows, s, a, b);
         else
             launch_sweep_m<__nv_bfloat16>(metric, D, stream, (const __nv_bfloat16 *)X, d, ld, n,
-                                          labels, k, sizes, offsets, Y, wY, zY, rows, nrows, s,
-                                          a, b);
+                                          labels, k, sizes, offsets, Y, wY, zY, crange, rows, nrows,
+                                          s, a, b);
     }
     SILH_CK(cudaGetLastError());
 done:
@@ -914,6 +1147,7 @@ extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n,
     int D = padded_dim(d);
     Scratch sc(stream);
     float *Y = nullptr, *wY = nullptr, *zY = nullptr;
+    unsigned *crange = nullptr;
     int64_t m = 0;
     SILH_REQ(S && S->k == k && S->sizes && S->offsets, "sample missing or k mismatch");
     m = S->size;
@@ -937,10 +1171,15 @@ extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n,
     SILH_CK(sc.alloc(&Y, (size_t)m * D));
     SILH_CK(sc.alloc(&wY, (size_t)m));
     SILH_CK(sc.alloc(&zY, (size_t)m));
-    st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, Y, wY, zY, stream);
+    if (metric == SILH_CANBERRA) {
+        SILH_CK(sc.alloc(&crange, 2));
+        st = canberra_range(X, dtype, n, d, ld, crange, stream);
+        if (st != SILH_OK) goto done;
+    }
+    st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, crange, Y, wY, zY, stream);
     if (st != SILH_OK) goto done;
     st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, S->sizes, S->offsets, Y, wY, zY,
-                      m, D, rows, nrows, s_hat, a_hat, b_hat, stream);
+                      crange, m, D, rows, nrows, s_hat, a_hat, b_hat, stream);
 done:
     return st;
 }
@@ -959,6 +1198,9 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     int64_t *sizes = nullptr, *coff = nullptr;
     int32_t *order = nullptr, *lab_s = nullptr;
     double *W = nullptr;
+    unsigned *crange = nullptr;
+    unsigned h_range[2] = {0u, 0u};
+    bool tiny = false;
     float *Y = nullptr, *wY = nullptr, *zY = nullptr;
     SILH_REQ(s, "s is null");
     SILH_DEVPTR(s, "s");
@@ -970,8 +1212,16 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     SILH_CK(cudaGetDevice(&dev));
     ensure_pool_retains(dev);
     SILH_CK(sc.alloc(&sizes, (size_t)k));
+    if (metric == SILH_CANBERRA) {
+        // the data range, read back under cluster_sort's synchronisation
+        SILH_CK(sc.alloc(&crange, 2));
+        st = canberra_range(X, dtype, n, d, ld, crange, stream);
+        if (st != SILH_OK) goto done;
+        SILH_CK(cudaMemcpyAsync(h_range, crange, sizeof(h_range), cudaMemcpyDeviceToHost, stream));
+    }
     st = cluster_sort(labels, n, k, sc, stream, sizes, &coff, &order, h_sizes, h_coff);
     if (st != SILH_OK) goto done;
+    tiny = metric == SILH_CANBERRA && canb_tiny_of(h_range[1], canb_scale_of(h_range[0]));
     if (nrows > 0 && tc_eligible(metric, prec, d)) {
         const int64_t maxc = *std::max_element(h_sizes.begin(), h_sizes.end());
         if (rows == nullptr &&
@@ -988,7 +1238,7 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     SILH_CK(sc.alloc(&Y, (size_t)n * D));
     SILH_CK(sc.alloc(&wY, (size_t)n));
     SILH_CK(sc.alloc(&zY, (size_t)n));
-    st = gather_columns(X, dtype, d, ld, order, nullptr, n, D, metric, Y, wY, zY, stream);
+    st = gather_columns(X, dtype, d, ld, order, nullptr, n, D, metric, crange, Y, wY, zY, stream);
     if (st != SILH_OK) goto done;
     if (rows == nullptr && (double)n * (double)k * 8.0 <= 2147483648.0) {
         // all rows: the symmetric sweep evaluates each pair once
@@ -998,10 +1248,10 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
         k_sorted_labels<<<ceil_div_i(n, 256), 256, 0, stream>>>(labels, order, n, lab_s);
         count_launches(1);
         switch (metric) {
-            case SILH_EUCLIDEAN: launch_exact_sym_d<SILH_EUCLIDEAN>(D, stream, Y, zY, lab_s, n, k, W); break;
-            case SILH_COSINE: launch_exact_sym_d<SILH_COSINE>(D, stream, Y, zY, lab_s, n, k, W); break;
-            case SILH_MANHATTAN: launch_exact_sym_d<SILH_MANHATTAN>(D, stream, Y, zY, lab_s, n, k, W); break;
-            default: launch_exact_sym_d<SILH_CANBERRA>(D, stream, Y, zY, lab_s, n, k, W); break;
+            case SILH_EUCLIDEAN: launch_exact_sym_d<SILH_EUCLIDEAN>(D, stream, Y, zY, lab_s, n, k, crange, tiny, W); break;
+            case SILH_COSINE: launch_exact_sym_d<SILH_COSINE>(D, stream, Y, zY, lab_s, n, k, crange, tiny, W); break;
+            case SILH_MANHATTAN: launch_exact_sym_d<SILH_MANHATTAN>(D, stream, Y, zY, lab_s, n, k, crange, tiny, W); break;
+            default: launch_exact_sym_d<SILH_CANBERRA>(D, stream, Y, zY, lab_s, n, k, crange, tiny, W); break;
         }
         k_exact_finalize<<<ceil_div_i(n, 256), 256, 0, stream>>>(W, lab_s, order, sizes, n, k, s, a,
                                                                  b);
@@ -1009,8 +1259,8 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
         SILH_CK(cudaGetLastError());
         goto done;
     }
-    st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, Y, wY, zY, n, D,
-                      rows, nrows, s, a, b, stream);
+    st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, Y, wY, zY, crange, n,
+                      D, rows, nrows, s, a, b, stream);
 done:
     return st;
 }
@@ -1026,6 +1276,7 @@ extern "C" silh_status silh_estimate_batched(const void *X, silh_dtype dtype, in
     Scratch sc(stream);
     float *Y = nullptr, *wY = nullptr, *zY = nullptr;
     unsigned long long *next_work = nullptr;
+    unsigned *crange = nullptr;
     std::vector<BatchParams> parts;
     std::vector<int32_t> order;
     SILH_REQ(X && items, "null pointer argument");
@@ -1086,23 +1337,28 @@ extern "C" silh_status silh_estimate_batched(const void *X, silh_dtype dtype, in
         goto done;
     }
     SILH_CK(sc.alloc(&next_work, 1));
+    if (metric == SILH_CANBERRA) {
+        SILH_CK(sc.alloc(&crange, 2));
+        st = canberra_range(X, dtype, n, d, ld, crange, stream);
+        if (st != SILH_OK) goto done;
+    }
     for (BatchParams &b : parts) {
         SILH_CK(sc.alloc(&Y, (size_t)b.total_cols * D));
         SILH_CK(sc.alloc(&wY, (size_t)b.total_cols));
         SILH_CK(sc.alloc(&zY, (size_t)b.total_cols));
         if (dtype == SILH_F32) {
             k_gather_batched<float><<<ceil_div_i(b.total_cols, 8), 256, 0, stream>>>(
-                b, (const float *)X, d, ld, D, metric, Y, wY, zY);
+                b, (const float *)X, d, ld, D, metric, crange, Y, wY, zY);
             count_launches(1);
             SILH_CK(launch_batched_m<float>(metric, D, variant, b, stream, (const float *)X, d, ld,
-                                            n, Y, wY, zY, next_work));
+                                            n, Y, wY, zY, crange, next_work));
         } else {
             k_gather_batched<__nv_bfloat16><<<ceil_div_i(b.total_cols, 8), 256, 0, stream>>>(
-                b, (const __nv_bfloat16 *)X, d, ld, D, metric, Y, wY, zY);
+                b, (const __nv_bfloat16 *)X, d, ld, D, metric, crange, Y, wY, zY);
             count_launches(1);
             SILH_CK(launch_batched_m<__nv_bfloat16>(metric, D, variant, b, stream,
                                                     (const __nv_bfloat16 *)X, d, ld, n, Y, wY,
-                                                    zY, next_work));
+                                                    zY, crange, next_work));
         }
     }
 done:
@@ -1119,6 +1375,7 @@ extern "C" silh_status silh_cohsep(const void *X, silh_dtype dtype, int64_t n, i
     Scratch sc(stream);
     float *Y = nullptr, *wY = nullptr, *zY = nullptr;
     double *wown = nullptr, *wsep = nullptr;
+    unsigned *crange = nullptr;
     int64_t m = 0;
     SILH_REQ(S && S->k == k && S->sizes && S->offsets && out, "sample or output missing");
     m = S->size;
@@ -1130,22 +1387,27 @@ extern "C" silh_status silh_cohsep(const void *X, silh_dtype dtype, int64_t n, i
     SILH_CK(sc.alloc(&zY, (size_t)m));
     SILH_CK(sc.alloc(&wown, (size_t)n));
     SILH_CK(sc.alloc(&wsep, (size_t)n));
-    st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, Y, wY, zY, stream);
+    if (metric == SILH_CANBERRA) {
+        SILH_CK(sc.alloc(&crange, 2));
+        st = canberra_range(X, dtype, n, d, ld, crange, stream);
+        if (st != SILH_OK) goto done;
+    }
+    st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, crange, Y, wY, zY, stream);
     if (st != SILH_OK) goto done;
     if (dtype == SILH_F32) {
         switch (metric) {
-            case SILH_EUCLIDEAN: launch_cohsep_d<float, SILH_EUCLIDEAN>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
-            case SILH_COSINE: launch_cohsep_d<float, SILH_COSINE>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
-            case SILH_MANHATTAN: launch_cohsep_d<float, SILH_MANHATTAN>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
-            default: launch_cohsep_d<float, SILH_CANBERRA>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
+            case SILH_EUCLIDEAN: launch_cohsep_d<float, SILH_EUCLIDEAN>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, crange, wown, wsep); break;
+            case SILH_COSINE: launch_cohsep_d<float, SILH_COSINE>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, crange, wown, wsep); break;
+            case SILH_MANHATTAN: launch_cohsep_d<float, SILH_MANHATTAN>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, crange, wown, wsep); break;
+            default: launch_cohsep_d<float, SILH_CANBERRA>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, crange, wown, wsep); break;
         }
     } else {
         const __nv_bfloat16 *Xb = (const __nv_bfloat16 *)X;
         switch (metric) {
-            case SILH_EUCLIDEAN: launch_cohsep_d<__nv_bfloat16, SILH_EUCLIDEAN>(D, stream, Xb, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
-            case SILH_COSINE: launch_cohsep_d<__nv_bfloat16, SILH_COSINE>(D, stream, Xb, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
-            case SILH_MANHATTAN: launch_cohsep_d<__nv_bfloat16, SILH_MANHATTAN>(D, stream, Xb, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
-            default: launch_cohsep_d<__nv_bfloat16, SILH_CANBERRA>(D, stream, Xb, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, wown, wsep); break;
+            case SILH_EUCLIDEAN: launch_cohsep_d<__nv_bfloat16, SILH_EUCLIDEAN>(D, stream, Xb, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, crange, wown, wsep); break;
+            case SILH_COSINE: launch_cohsep_d<__nv_bfloat16, SILH_COSINE>(D, stream, Xb, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, crange, wown, wsep); break;
+            case SILH_MANHATTAN: launch_cohsep_d<__nv_bfloat16, SILH_MANHATTAN>(D, stream, Xb, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, crange, wown, wsep); break;
+            default: launch_cohsep_d<__nv_bfloat16, SILH_CANBERRA>(D, stream, Xb, d, ld, n, labels, k, S->sizes, S->offsets, Y, wY, zY, crange, wown, wsep); break;
         }
     }
     k_cohsep_final<<<1, 256, 0, stream>>>(wown, wsep, n, S->sizes, k, out);
@@ -1162,6 +1424,15 @@ extern "C" silh_status silh_stream_status(void *stream_) {
     e = tc_take_error();
     if (e < 0) st = fail(SILH_ECUDA, "reading the device error word failed");
     else if (e > 0) st = fail(SILH_ETIMEOUT, "a bounded device wait gave up");
+done:
+    return st;
+}
+
+extern "C" silh_status silh_wait_selftest(int32_t arrive, uint64_t timeout_ns, void *stream_) {
+    silh_status st = SILH_OK;
+    SILH_REQ(timeout_ns >= 1000 && timeout_ns <= 1000000000ull,
+             "timeout_ns must be in [1 us, 1 s]");
+    st = tc_wait_selftest(arrive != 0, timeout_ns, (cudaStream_t)stream_);
 done:
     return st;
 }

@@ -13,12 +13,17 @@
 // The scratch array lives in this library's device image: every GPU that loads
 // the library holds it until the process exits.  Every call shares it.  The
 // gather kernel rewrites every element a call reads (all m x D entries of the
-// column operand, including padding, and all m weights), so nothing needs to be
-// cleared between calls; two calls whose work overlaps on the GPU (different
+// column operand, including padding, and all m weights), and a Canberra call
+// resets the two words of its data range before it reduces into them, so nothing
+// carries over between calls; two calls whose work overlaps on the GPU (different
 // streams, no ordering between them) race on the array and must be serialised
 // by the caller.
-#include <mutex>
-
+//
+// Precision: the column scratch holds the FP32 operand of the CUDA-core sweep,
+// so every call evaluates distances in FP32 on the CUDA cores, whatever prec
+// asks for.  The results equal silh_estimate with SILH_PREC_FP32 bit for bit;
+// for a tensor-core precision they are the more accurate FP32 values, not that
+// mode's.
 #include "kernels.cuh"
 
 namespace silh {
@@ -27,27 +32,29 @@ namespace {
 constexpr int64_t kNoAllocMaxColumns = SILH_NOALLOC_MAX_COLUMNS;  // include/silh.h
 constexpr int64_t kNoAllocMaxFloats = SILH_NOALLOC_MAX_FLOATS;
 
-// Column operand Y (m x D), then wY (m) and zY (m).
-static __device__ __align__(256) float g_noalloc_scratch[kNoAllocMaxFloats + 2 * kNoAllocMaxColumns];
-
-std::mutex g_noalloc_mu;
-float *g_noalloc_ptr[64] = {nullptr};
+// Column operand Y (m x D), then wY (m), zY (m) and one 256-byte slot whose
+// first two words hold the Canberra sweep's data range (largest and smallest
+// nonzero magnitude).
+static __device__ __align__(256) float
+    g_noalloc_scratch[kNoAllocMaxFloats + 2 * kNoAllocMaxColumns + 64];
 
 // Device address of the scratch array for the current device.  The array's
 // name is only a host-side stand-in in host code; the address must come from
-// cudaGetSymbolAddress with the device current.  Done once per device.
-silh_status noalloc_scratch(int dev, float **out) {
-    if (dev < 0 || dev >= 64) return fail(SILH_EINVAL, "device ordinal %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (g_noalloc_ptr[dev] == nullptr) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess)
-            return fail(SILH_ECUDA, "cudaGetSymbolAddress(no-alloc scratch) failed: %s",
-                        cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = static_cast<float *>(p);
+// cudaGetSymbolAddress with the device current.  It is looked up on every call
+// (no allocation, a table lookup once the module is loaded), so a cached address
+// can never outlive a device reset or a re-created context.
+silh_status noalloc_scratch(float **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SILH_ECUDA,
+                    "cudaGetSymbolAddress(no-alloc scratch) failed: %s (the first call on a "
+                    "device loads the library's device code and maps the %.1f MiB scratch; "
+                    "make it before reserving the device's memory)",
+                    cudaGetErrorString(e), sizeof(g_noalloc_scratch) / 1048576.0);
     }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<float *>(p);
     return SILH_OK;
 }
 
@@ -64,10 +71,10 @@ extern "C" silh_status silh_estimate_noalloc(const void *X, silh_dtype dtype, in
                                              float *b_hat, void *stream_) {
     cudaStream_t stream = (cudaStream_t)stream_;
     silh_status st = SILH_OK;
-    int dev = 0;
     int D = 0;
     int64_t m = 0;
     float *base = nullptr, *Y = nullptr, *wY = nullptr, *zY = nullptr;
+    unsigned *crange = nullptr;
 
     SILH_REQ(X && labels, "null pointer argument");
     SILH_REQ(n >= 2 && n < (int64_t(1) << 31), "n must be in [2, 2^31)");
@@ -97,16 +104,20 @@ extern "C" silh_status silh_estimate_noalloc(const void *X, silh_dtype dtype, in
     }
     if (rows == nullptr) nrows = n;
     SILH_REQ(nrows >= 0, "nrows < 0");
-    SILH_CK(cudaGetDevice(&dev));
-    st = noalloc_scratch(dev, &base);
+    st = noalloc_scratch(&base);
     if (st != SILH_OK) goto done;
     Y = base;
     wY = base + kNoAllocMaxFloats;
     zY = wY + kNoAllocMaxColumns;
-    st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, Y, wY, zY, stream);
+    if (metric == SILH_CANBERRA) {
+        crange = reinterpret_cast<unsigned *>(zY + kNoAllocMaxColumns);
+        st = canberra_range(X, dtype, n, d, ld, crange, stream);
+        if (st != SILH_OK) goto done;
+    }
+    st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, crange, Y, wY, zY, stream);
     if (st != SILH_OK) goto done;
-    st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, S->sizes, S->offsets, Y, wY, zY,
-                      m, D, rows, nrows, s_hat, a_hat, b_hat, stream);
+    st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, SILH_PREC_FP32, S->sizes, S->offsets,
+                      Y, wY, zY, crange, m, D, rows, nrows, s_hat, a_hat, b_hat, stream);
 done:
     return st;
 }

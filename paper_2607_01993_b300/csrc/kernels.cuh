@@ -23,20 +23,31 @@ silh_status cluster_sort(const int32_t *labels, int64_t n, int k, Scratch &sc,
 cudaError_t scan_flags(const int32_t *flags, int64_t n, int64_t *out, int64_t *d_total,
                        Scratch &sc, cudaStream_t stream);
 
+// Largest and smallest nonzero |x| over the n x d data, for the Canberra
+// sweeps' power-of-two scale and their test for tiny coordinates:
+// crange[0..1] (device, two words) receive the bits of those non-negative floats.
+silh_status canberra_range(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                           unsigned *crange, cudaStream_t stream);
+
 // Rows of the Phase-2 column operand: Y[i, :] = X[idx[i], :] for i < m, padded
 // with zeros to D columns; cosine rows are scaled to unit norm.  wY[i] = 1/p[i]
-// (or 1 when p == nullptr); zY[i] = 0.5 wY[i] for a zero cosine column, else 0.
+// (or 1 when p == nullptr); zY[i] = 0.5 wY[i] for a zero cosine column, 1 for a
+// Canberra column with a coordinate that is tiny at the scale of crange (from
+// canberra_range; read only for Canberra), else 0.
 silh_status gather_columns(const void *X, silh_dtype dtype, int32_t d, int64_t ld,
                            const int32_t *idx, const double *p, int64_t m, int D, int metric,
-                           float *Y, float *wY, float *zY, cudaStream_t stream);
+                           const unsigned *crange, float *Y, float *wY, float *zY,
+                           cudaStream_t stream);
 
 // Phase-2 sweep: for every listed row, W_hat_j over the cluster-major column
-// operand (Y, wY, offsets) and the silhouette of Eq. 8.
+// operand (Y, wY, offsets) and the silhouette of Eq. 8 (crange as for
+// gather_columns).
 silh_status phase2_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                          const int32_t *labels, int32_t k, int metric, int prec,
                          const int64_t *sizes, const int64_t *offsets, const float *Y,
-                         const float *wY, const float *zY, int64_t m, int D, const int64_t *rows,
-                         int64_t nrows, float *s, float *a, float *b, cudaStream_t stream);
+                         const float *wY, const float *zY, const unsigned *crange, int64_t m, int D,
+                         const int64_t *rows, int64_t nrows, float *s, float *a, float *b,
+                         cudaStream_t stream);
 
 // Padded row width of the column operand for a given d.
 int padded_dim(int d);
@@ -67,5 +78,9 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
 // 1 if a bounded wait in the tensor-core sweep gave up since the last call
 // (and clears it), 0 if not, -1 on a CUDA error.  Synchronous.
 int tc_take_error();
+// One-thread kernel that waits (bounded) on an mbarrier that is either
+// satisfied first (arrive != 0) or never (arrive == 0), and records a wait that
+// gives up in the same error word as the tensor-core sweep.
+silh_status tc_wait_selftest(int arrive, uint64_t timeout_ns, cudaStream_t stream);
 
 }  // namespace silh

@@ -347,7 +347,18 @@ __global__ void k_dist_f0_df(const T *__restrict__ X, int d, int64_t ld,
                     } else {                            // Canberra
                         float ds, de;
                         two_sum(fabsf(xv), fabsf(yv), ds, de);   // |x| + |y| exactly
-                        if (ds > 0.f) {
+                        if (!(ds >= 0x1p-100f && ds <= 0x1p+100f)) {
+                            // magnitudes outside the range the FP32 reciprocal and
+                            // residual steps keep exact (or a zero pair): the
+                            // term in FP64, from the coordinates themselves
+                            if (ds != 0.f) {
+                                const double xd = xv, yd = yv;
+                                const double q = fabs(xd - yd) / (fabs(xd) + fabs(yd));
+                                const float qh = (float)q;
+                                df_acc(hi[g], lo[g], qh);
+                                lo[g] = __fadd_rn(lo[g], (float)(q - (double)qh));
+                            }
+                        } else {
                             const float rc = rcp_apx(ds);
                             const float q0 = __fmul_rn(s, rc);
                             float rr = __fmaf_rn(-q0, ds, s);     // residual of s / ds

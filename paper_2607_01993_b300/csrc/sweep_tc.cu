@@ -300,6 +300,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_full[C::STAGES], bar_empty[C::STAGES];
     __shared__ uint64_t bar_afull, bar_aempty, bar_accf[C::SLOTS][C::NACC], bar_acce[C::SLOTS][C::NACC];
+    __shared__ uint64_t bar_drain;      // the MMA issuer's last commit, after an abort
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     // (w, |y|^2) of the current tile's columns, two columns per float4 as
@@ -383,6 +384,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
         }
         mbar_init(&bar_afull, 1);
         mbar_init(&bar_aempty, 1);
+        mbar_init(&bar_drain, 1);
         for (int g = 0; g < C::SLOTS; ++g)
             for (int a = 0; a < C::NACC; ++a) {
                 mbar_init(&bar_accf[g][a], 1);
@@ -395,6 +397,12 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = tmem_base;
+    // TMA loads the producer thread has issued: per B stage whether one was and
+    // the phase parity it completes, and the same for the A tile (drained on abort)
+    uint32_t ld_issued = 0, ld_parity = 0;
+    bool a_issued = false;
+    uint32_t a_parity = 0;
+    static_assert(C::STAGES <= 32, "stage masks are 32-bit");
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -419,6 +427,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     break;
                 }
                 mbar_expect_tx(&bar_afull, C::A_BYTES);
+                a_issued = true;
+                a_parity = (uint32_t)(idx & 1);
                 for (int g = 0; g < C::SLOTS; ++g) {
                     const int y = (int)(v.arow + (rg * C::SLOTS + g) * kTileM);
                     uint8_t *a = sA + g * C::A_SLOT;
@@ -436,6 +446,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     }
                     uint8_t *dst = sB + stage * C::B_BYTES;
                     mbar_expect_tx(&bar_full[stage], C::B_BYTES);
+                    ld_issued |= 1u << stage;
+                    ld_parity = (ld_parity & ~(1u << stage)) | (phase << stage);
                     for (int kb = 0; kb < C::KB; ++kb) {
                         tma_load_2d(&m_bhi, &bar_full[stage], dst + kb * TN * 128,
                                     kb * C::KELEM, (int)(v.ccol + ct * TN));
@@ -791,6 +803,22 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     if (threadIdx.x == 0 && abort_flag) atomicExch(&g_tc_error, 1);
     fence_before_sync();
     __syncthreads();
+    if (abort_flag) {
+        // A wait gave up: before shared and tensor memory are released, wait
+        // (bounded) for every TMA load the producer issued and for the MMAs the
+        // issuer issued (one more commit tracks all of them).
+        if (warp == 0 && lane == 0) {
+            for (int st = 0; st < C::STAGES; ++st)
+                if ((ld_issued >> st) & 1u)
+                    mbar_wait(&bar_full[st], (ld_parity >> st) & 1u, kWaitNs);
+            if (a_issued) mbar_wait(&bar_afull, a_parity, kWaitNs);
+        } else if (warp == 1 && lane == 0) {
+            mma_commit(&bar_drain);
+            mbar_wait(&bar_drain, 0u, kWaitNs);
+        }
+        fence_before_sync();
+        __syncthreads();
+    }
     if (warp == 1) {
         __syncwarp();
         tmem_dealloc(tmem, C::TMEM_COLS);
@@ -1950,6 +1978,32 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
 #undef SILH_TC_SYM_CASE
     k_tc_sym_finalize<<<ceil_div_i(mp_max, 256), 256, 0, stream>>>(W, plab, outi, sizes,
                                                                    mp_max, k, s, a, b);
+    count_launches(1);
+    SILH_CK(cudaGetLastError());
+done:
+    return st;
+}
+
+namespace {
+
+// Self-test of the bounded-wait error path (one thread, one mbarrier, no TMA and
+// no tensor memory): waits for phase 0 of a barrier with one expected arrival,
+// after arriving on it first when arrive != 0 (the wait then succeeds at once),
+// else with nothing that ever arrives (the wait runs out after timeout_ns).  A
+// wait that gives up is recorded exactly as the sweep records it.
+__global__ void k_wait_selftest(int arrive, uint64_t timeout_ns) {
+    __shared__ uint64_t bar;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (arrive) mbar_arrive(&bar);
+    if (!mbar_wait(&bar, 0u, timeout_ns)) atomicExch(&g_tc_error, 1);
+}
+
+}  // namespace
+
+silh_status tc_wait_selftest(int arrive, uint64_t timeout_ns, cudaStream_t stream) {
+    silh_status st = SILH_OK;
+    k_wait_selftest<<<1, 1, 0, stream>>>(arrive, timeout_ns);
     count_launches(1);
     SILH_CK(cudaGetLastError());
 done:

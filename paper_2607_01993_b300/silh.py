@@ -27,7 +27,7 @@ SILH_ECAPACITY = -4
 EXPORTS = ("silh_sample_pps", "silh_estimate", "silh_exact", "silh_global", "silh_t_from_eps",
            "silh_last_error", "silh_version", "silh_kernel_launches", "silh_estimate_noalloc",
            "silh_stream_status", "silh_estimate_batched", "silh_cohsep",
-           "silh_estimate_cosine_collapsed", "silh_pipe_rates")
+           "silh_estimate_cosine_collapsed", "silh_pipe_rates", "silh_wait_selftest")
 SILH_NOALLOC_MAX_COLUMNS = 65536
 SILH_NOALLOC_MAX_FLOATS = 2097152
 
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH):
     lib.silh_cohsep.restype = ctypes.c_int
     lib.silh_stream_status.argtypes = [vp]
     lib.silh_stream_status.restype = ctypes.c_int
+    lib.silh_wait_selftest.argtypes = [i32, ctypes.c_uint64, vp]
+    lib.silh_wait_selftest.restype = ctypes.c_int
     lib.silh_kernel_launches.argtypes = []
     lib.silh_kernel_launches.restype = ctypes.c_uint64
     _lib = lib
@@ -355,6 +357,12 @@ def silh_stream_status(stream=None):
     """Synchronise the stream; raise SilhError(SILH_ETIMEOUT) if a bounded device
     wait gave up since the previous check."""
     _check(load().silh_stream_status(_stream(stream)))
+
+
+def wait_selftest(arrive: bool, timeout_ns: int = 1_000_000, stream=None):
+    """Launch the bounded-wait self-test kernel (asynchronous); read the outcome
+    with silh_stream_status."""
+    _check(load().silh_wait_selftest(1 if arrive else 0, int(timeout_ns), _stream(stream)))
 
 
 def kernel_launches() -> int:

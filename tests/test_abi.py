@@ -68,4 +68,8 @@ def test_argument_validation_without_device(lib):
     assert rc == -1
     rc = lib.silh_global(None, 10, None, None)
     assert rc == -1
+    # the wait self-test refuses a limit outside [1 us, 1 s] before launching
+    lib.silh_wait_selftest.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p]
+    assert lib.silh_wait_selftest(0, 0, None) == -1
+    assert lib.silh_wait_selftest(0, 2_000_000_000, None) == -1
     assert lib.silh_version().startswith(b"silh")

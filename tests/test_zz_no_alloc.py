@@ -7,8 +7,13 @@ the middle of a stream, code running inside an allocator callback.  For them
 silh_estimate_noalloc runs Phase 2 with its scratch in a fixed device array of
 the library.  These tests call it through the C ABI and compare it with the
 allocating silh_estimate, on two calls in a row, within the tolerance the other
-parity tests use.  The file is named to be collected last.
+parity tests use, check that a call takes no memory from the device's
+stream-ordered pool and leaves free device memory unchanged, and check the
+documented precision rule (FP32 on CUDA cores whatever mode is asked for).
+The file is named to be collected last.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -62,6 +67,70 @@ def test_noalloc_row_subset_and_oracle():
     s_o, _, _ = oracle.estimate(Xh, lab, 4, "manhattan", os_.offsets, os_.idx, os_.ps,
                                 rows=rows.cpu().numpy())
     assert np.abs(got.cpu().numpy() - s_o).max() <= S_TOL
+
+
+def test_noalloc_runs_fp32_whatever_the_precision():
+    # A tensor-core precision is accepted but the distances stay FP32 on the CUDA
+    # cores: equal to silh_estimate(prec="fp32") bit for bit, and within the FP32
+    # tolerance of the oracle, while silh_estimate(prec="bf16") itself is not.
+    X, l = _data(20000, 24, 8, seed=35)
+    smp = silh.silh_sample_pps(X, l, 8, "euclidean", t=96.0, seed=5)
+    ref = silh.silh_estimate(X, l, 8, smp, "euclidean", prec="fp32")
+    for prec in ("3xtf32", "bf16", "bf16x3", "tf32"):
+        got = silh.silh_estimate_noalloc(X, l, 8, smp, "euclidean", prec=prec)
+        assert torch.equal(got, ref), prec
+    rows = torch.arange(0, 20000, 13, dtype=torch.int64, device="cuda")
+    Xh = X.cpu().numpy().astype(np.float64)
+    lab = l.cpu().numpy()
+    off = smp.offsets.cpu().numpy()
+    idx = smp.idx[: smp.size].cpu().numpy().astype(np.int64)
+    ps = smp.p[: smp.size].cpu().numpy()
+    s_o, _, _ = oracle.estimate(Xh, lab, 8, "euclidean", off, idx, ps, rows=rows.cpu().numpy())
+    got = silh.silh_estimate_noalloc(X, l, 8, smp, "euclidean", prec="3xtf32", rows=rows)
+    assert np.abs(got.cpu().numpy() - s_o).max() <= S_TOL
+
+
+def _cudart():
+    for name in ("libcudart.so.13", "libcudart.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("libcudart not found by the dynamic loader")
+
+
+def test_noalloc_takes_no_device_memory_during_a_call():
+    # The property the entry point exists for: with its outputs in place, a call
+    # neither draws on the device's stream-ordered pool (whose high-water mark is
+    # reset just before) nor changes the free device memory.
+    rt = _cudart()
+    X, l = _data(30000, 16, 12, seed=36)
+    smp = silh.silh_sample_pps(X, l, 12, "canberra", t=64.0, seed=6)
+    out = torch.empty(30000, dtype=torch.float32, device="cuda")
+    silh.silh_estimate_noalloc(X, l, 12, smp, "canberra", out=out)      # loads, maps
+    torch.cuda.synchronize()
+    dev = torch.cuda.current_device()
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    USED_CURRENT, USED_HIGH = 7, 8          # cudaMemPoolAttr values
+    used0, high, zero = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(0)
+    assert rt.cudaMemPoolGetAttribute(pool, USED_CURRENT, ctypes.byref(used0)) == 0
+    assert rt.cudaMemPoolSetAttribute(pool, USED_HIGH, ctypes.byref(zero)) == 0
+    free0, total = ctypes.c_size_t(), ctypes.c_size_t()
+    assert rt.cudaMemGetInfo(ctypes.byref(free0), ctypes.byref(total)) == 0
+    silh.silh_estimate_noalloc(X, l, 12, smp, "canberra", out=out)
+    torch.cuda.synchronize()
+    free1 = ctypes.c_size_t()
+    assert rt.cudaMemGetInfo(ctypes.byref(free1), ctypes.byref(total)) == 0
+    assert rt.cudaMemPoolGetAttribute(pool, USED_HIGH, ctypes.byref(high)) == 0
+    assert high.value <= used0.value, (high.value, used0.value)
+    assert free1.value == free0.value
+    # the allocating entry point, by contrast, does draw on the pool
+    assert rt.cudaMemPoolSetAttribute(pool, USED_HIGH, ctypes.byref(zero)) == 0
+    silh.silh_estimate(X, l, 12, smp, "canberra", out=out)
+    torch.cuda.synchronize()
+    assert rt.cudaMemPoolGetAttribute(pool, USED_HIGH, ctypes.byref(high)) == 0
+    assert high.value > used0.value
 
 
 def test_noalloc_rejects_samples_beyond_its_scratch():
