@@ -602,13 +602,16 @@ def run_peaks(args):
     print(json.dumps(line))
 
 
-def run_serving(args):
+def run_serving(args, emit=True):
     """Serving workload: Poisson streams of silhouette requests over 64 resident
     datasets (n log-uniform 5k-2M, d in {8,16,64,128}, FP32/BF16), k uniform
     2-100 (nearest random centres), metric uniform over the four, t = 64.
-    Reports the specified 2000 req/s stream (with queue growth), the measured
-    one-at-a-time capacity, and p50/p99 latency at ~80% of it, continuous
-    batching (8 slots) against one request at a time."""
+    The server (8 slots, each request one asynchronous chain on its stream)
+    against one request at a time with the plain synchronising calls, both in
+    FP32 on CUDA cores.  Reports the capacity of each (back to back on the
+    load-test requests), p50/p99 latency of each at ~80% of the plain path's
+    capacity under the same Poisson arrivals, and the specified 2000 req/s
+    stream (with queue growth)."""
     import torch
     from paper_2607_01993_b300 import serve, silh
     torch.cuda.set_device(0)
@@ -627,56 +630,95 @@ def run_serving(args):
         torch.cuda.synchronize()
         return reqs
 
-    def stream_run(reqs, rate, slots):
-        gaps = rng.exponential(1.0 / rate, size=len(reqs)) if rate else np.zeros(len(reqs))
+    def arrivals(count, rate):
+        return np.cumsum(rng.exponential(1.0 / rate, size=count)) if rate else np.zeros(count)
+
+    def summary(lat_ms, count, t0, t1, rate, slots, extra):
+        d = {"requests": count, "offered_req_s": rate, "slots": slots,
+             "achieved_req_s": round(count / (t1 - t0), 2),
+             "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+             "p99_ms": round(float(np.percentile(lat_ms, 99)), 3)}
+        d.update(extra)
+        return d
+
+    def served(reqs, rate, slots):
+        due = arrivals(len(reqs), rate)
         srv = serve.SilhServer(datasets, slots=slots)
         t0 = time.perf_counter()
-        futs, due, max_q = [], t0, 0
-        for r, gap in zip(reqs, gaps):
-            due += gap
-            delay = due - time.perf_counter()
+        futs, max_q = [], 0
+        for r, a in zip(reqs, due):
+            delay = t0 + a - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            futs.append(srv.submit(serve.Request(**r, arrival=due)))
+            futs.append(srv.submit(serve.Request(**r, arrival=t0 + a)))
             max_q = max(max_q, len(srv._queue))
-        res = [f.result(timeout=600) for f in futs]
+        res = [f.result(timeout=900) for f in futs]
         t1 = time.perf_counter()
         srv.close()
         lat = np.array([x.latency_s for x in res]) * 1e3
-        return {"requests": len(res), "offered_req_s": rate, "slots": slots,
-                "achieved_req_s": round(len(res) / (t1 - t0), 2),
-                "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                "max_queue": max_q, "peak_running": srv.peak_running}, res
+        return summary(lat, len(res), t0, t1, rate, slots,
+                       {"max_queue": max_q, "peak_running": srv.peak_running,
+                        "redone_capacity": srv.redone}), res
+
+    def one_at_a_time(reqs, rate, prec):
+        """Requests in arrival order, each with the plain synchronising calls
+        once the previous one has finished (a queue of one server)."""
+        due = arrivals(len(reqs), rate)
+        t0 = time.perf_counter()
+        lat, res = [], []
+        for r, a in zip(reqs, due):
+            delay = t0 + a - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            out = serve.run_one_at_a_time(datasets, [serve.Request(**r, arrival=t0 + a)],
+                                          prec=prec)[0]
+            lat.append(out.latency_s * 1e3)
+            res.append(out)
+        t1 = time.perf_counter()
+        return summary(np.array(lat), len(res), t0, t1, rate, 1,
+                       {"precision": prec}), res
 
     warm = make_requests(8, 10_000)
-    stream_run(warm, 0, 4)                                      # warm-up (compiles, pools)
+    served(warm, 0, 4)                                          # warm-up (compiles, pools)
+    one_at_a_time(warm, 0, "fp32")
     # capacity measured on the very requests of the load test (service times
     # vary by two orders of magnitude between requests, so a separate
-    # calibration set would misstate it): back to back, one at a time, and
-    # back to back with 8 slots (the saturation throughput)
+    # calibration set would misstate it)
     load = make_requests(args.serve_load, 40_000)
-    one, _ = stream_run(load, 0, 1)
-    capacity = one["achieved_req_s"]
-    saturated, _ = stream_run(load, 0, 8)
+    plain_cap, res_alone = one_at_a_time(load, 0, "fp32")
+    sat, res_sat = served(load, 0, 8)
+    capacity = plain_cap["achieved_req_s"]
+    rate = 0.8 * capacity
+    at80_served, res_b = served(load, rate, 8)
+    at80_plain, _ = one_at_a_time(load, rate, "fp32")
     spec_reqs = make_requests(args.serve_spec, 30_000)
-    specified, _ = stream_run(spec_reqs, 2000.0, 8)
-    at80_batched, res_b = stream_run(load, 0.8 * capacity, 8)
-    at80_single, res_s = stream_run(load, 0.8 * capacity, 1)
-    same = all(a.s_global == b.s_global for a, b in zip(res_b, res_s))
-    line = {"metric": "serving req/s at ~80% of one-at-a-time capacity (continuous batching)",
-            "value": at80_batched["achieved_req_s"], "unit": "req/s", "n_gpus": 1,
-            "higher_is_better": True, "dtype": "f32/bf16 data, split-TF32 or FP32 arithmetic",
-            "data": "synthetic", "p50_ms": at80_batched["p50_ms"], "p99_ms": at80_batched["p99_ms"],
-            "one_at_a_time_at_same_load": at80_single,
-            "batched_at_80pct": at80_batched, "capacity_one_at_a_time_req_s": capacity,
-            "saturation_8_slots_req_s": saturated["achieved_req_s"],
-            "specified_stream_2000_req_s": specified,
-            "results_identical_batched_vs_one_at_a_time": same,
+    specified, _ = served(spec_reqs, 2000.0, 8)
+    # the server's results equal the same requests run alone, bit for bit
+    same = all(a.s_global == b.s_global and a.sample_size == b.sample_size
+               for a, b in zip(res_b, res_alone)) and \
+        all(a.s_global == b.s_global for a, b in zip(res_sat, res_alone))
+    out = {"capacity_req_s": {"server_8_slots": sat["achieved_req_s"],
+                              "one_at_a_time_plain_fp32": plain_cap["achieved_req_s"]},
+           "capacity_vs_plain_fp32": round(sat["achieved_req_s"] / capacity, 3),
+           "at_80pct_of_plain_capacity": {"offered_req_s": round(rate, 2),
+                                          "server": at80_served, "plain_fp32": at80_plain},
+           "specified_stream_2000_req_s": specified,
+           "results_identical_served_vs_alone": same,
+           "precision": "FP32 on CUDA cores for every request, server and baselines (on these "
+                        "nearest-centre clusterings the tensor-core sweep recomputes many close "
+                        "pairs and is the slower path)"}
+    line = {"metric": "serving req/s (continuous batching) at ~80% of the plain one-at-a-time "
+                      "FP32 capacity, with p50/p99 latency",
+            "value": at80_served["achieved_req_s"], "unit": "req/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32/bf16 data, FP32 arithmetic",
+            "data": "synthetic", "p50_ms": at80_served["p50_ms"], "p99_ms": at80_served["p99_ms"],
+            **out,
             "config": {"workload": "serving: 64 resident datasets, n log-uniform 5k-2M, "
                                    "d in {8,16,64,128}, FP32/BF16; k ~ U{2..100}; 4 metrics; t=64",
-                       "datasets": len(datasets)}}
-    print(json.dumps(line))
+                       "datasets": len(datasets), "load_requests": len(load)}}
+    if emit:
+        print(json.dumps(line))
+    return line
 
 
 def main():

@@ -131,6 +131,42 @@ silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n, int32_t d,
                           const silh_sample *S, const int64_t *rows, int64_t nrows,
                           float *s_hat, float *a_hat, float *b_hat, void *stream);
 
+/* Phase 1 of Algorithm 1, as silh_sample_pps, with no host synchronisation: the
+ * whole phase is enqueued on stream and the call returns at once, so a request
+ * (this call, silh_estimate_async, silh_global) is one asynchronous chain and
+ * several can run at once on different streams.  Same arguments, arithmetic
+ * and sample as silh_sample_pps; in addition
+ *   d_size    device int64: receives |S| (0 after any error);
+ *   d_status  device int32: receives SILH_OK, SILH_EINVAL (a label outside
+ *             [0, k) or an empty cluster), or SILH_ECAPACITY (|S| > out->cap,
+ *             or initial samples beyond the planned capacity, below 1e-15 in
+ *             probability); after an error the sample is written as an empty
+ *             one (offsets all 0), so a following silh_estimate_async stays in
+ *             bounds, and the caller may redo the request with
+ *             silh_sample_pps.
+ * out->cap bounds |S| (cap = n is always enough); out->size is not written.
+ * Sizes, offsets and the plan of the initial-sample distance matrices are
+ * computed on the device; their scratch is sized from n, k and m0 (n (m0 +
+ * 8 sqrt(m0) + 16) FP64 entries for the matrices) and released in stream
+ * order.  Errors returned by the call itself: invalid arguments (SILH_EINVAL)
+ * and scratch allocation (SILH_ENOMEM), before anything is enqueued. */
+silh_status silh_sample_pps_async(const void *X, silh_dtype dtype, int64_t n, int32_t d,
+                                  int64_t ld, const int32_t *labels, int32_t k, silh_metric metric,
+                                  double t, double m0, double delta, uint64_t seed,
+                                  uint32_t clustering_id, int32_t uniform, silh_sample *out,
+                                  int64_t *d_size, int32_t *d_status, void *stream);
+
+/* silh_estimate for a sample whose size |S| is known only on the device
+ * (*d_size, device int64, from silh_sample_pps_async); S->cap bounds it and sizes
+ * the scratch, S->size is ignored.  Results equal silh_estimate's on the same
+ * sample bit for bit.  Asynchronous, nothing waits for the device.  Errors: as
+ * silh_estimate, and SILH_EINVAL for a null d_size. */
+silh_status silh_estimate_async(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                                const int32_t *labels, int32_t k, silh_metric metric,
+                                silh_prec prec, const silh_sample *S, const int64_t *d_size,
+                                const int64_t *rows, int64_t nrows, float *s_hat, float *a_hat,
+                                float *b_hat, void *stream);
+
 /* Phase 2 of Algorithm 1 (Eq. 8) for the cosine distance in O(n k d): with unit
  * vectors d_cos = 1 - <x^, y^> = 0.5 |x^ - y^|^2 (the cosine distance of
  * Sec. 5.1.1, read as in the exact definition), and the weighted sum over a

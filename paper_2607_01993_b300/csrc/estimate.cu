@@ -143,10 +143,11 @@ template <class T>
 __global__ void k_gather(const T *__restrict__ X, int d, int64_t ld, const int32_t *__restrict__ idx,
                          const double *__restrict__ p, int64_t m, int D, int metric,
                          const unsigned *__restrict__ crange, float *__restrict__ Y,
-                         float *__restrict__ wY, float *__restrict__ zY) {
+                         float *__restrict__ wY, float *__restrict__ zY,
+                         const int64_t *__restrict__ d_m) {
     int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
-    if (i >= m) return;
+    if (i >= m || (d_m != nullptr && i >= *d_m)) return;
     int64_t e = idx ? idx[i] : i;
     const T *x = X + e * ld;
     float scale = 1.0f;
@@ -1075,17 +1076,17 @@ done:
 silh_status gather_columns(const void *X, silh_dtype dtype, int32_t d, int64_t ld,
                            const int32_t *idx, const double *p, int64_t m, int D, int metric,
                            const unsigned *crange, float *Y, float *wY, float *zY,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, const int64_t *d_m) {
     silh_status st = SILH_OK;
     if (m > 0) {
         int grid = ceil_div_i(m, 8);
         if (dtype == SILH_F32)
             k_gather<float><<<grid, 256, 0, stream>>>((const float *)X, d, ld, idx, p, m, D,
-                                                      metric, crange, Y, wY, zY);
+                                                      metric, crange, Y, wY, zY, d_m);
         else
             k_gather<__nv_bfloat16><<<grid, 256, 0, stream>>>((const __nv_bfloat16 *)X, d, ld,
                                                               idx, p, m, D, metric, crange, Y, wY,
-                                                              zY);
+                                                              zY, d_m);
         count_launches(1);
     }
     SILH_CK(cudaGetLastError());
@@ -1135,12 +1136,14 @@ static silh_status check_data_args(const void *X, silh_dtype dtype, int64_t n, i
     return SILH_OK;
 }
 
-extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n, int32_t d,
-                                     int64_t ld, const int32_t *labels, int32_t k,
-                                     silh_metric metric, silh_prec prec, const silh_sample *S,
-                                     const int64_t *rows, int64_t nrows, float *s_hat,
-                                     float *a_hat, float *b_hat, void *stream_) {
-    cudaStream_t stream = (cudaStream_t)stream_;
+// Phase 2 for a sample of m columns (S->size), or, when d_m is given, of *d_m
+// columns with m = S->cap bounding it (scratch sized for m; the kernels read
+// the actual size from the device).
+static silh_status estimate_impl(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
+                                 const int32_t *labels, int32_t k, silh_metric metric,
+                                 silh_prec prec, const silh_sample *S, const int64_t *d_m,
+                                 const int64_t *rows, int64_t nrows, float *s_hat, float *a_hat,
+                                 float *b_hat, cudaStream_t stream) {
     silh_status st = check_data_args(X, dtype, n, d, ld, labels, k, metric, prec);
     if (st != SILH_OK) return st;
     int dev = 0;
@@ -1150,7 +1153,7 @@ extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n,
     unsigned *crange = nullptr;
     int64_t m = 0;
     SILH_REQ(S && S->k == k && S->sizes && S->offsets, "sample missing or k mismatch");
-    m = S->size;
+    m = d_m ? S->cap : S->size;
     SILH_REQ(m >= 0 && m <= S->cap && (m == 0 || (S->idx && S->p)), "bad sample size");
     SILH_REQ(s_hat, "s_hat is null");
     SILH_REQ(sample_accessible(S), "sample arrays are not device-accessible memory");
@@ -1158,6 +1161,7 @@ extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n,
     SILH_DEVPTR_OPT(a_hat, "a_hat");
     SILH_DEVPTR_OPT(b_hat, "b_hat");
     SILH_DEVPTR_OPT(rows, "rows");
+    SILH_DEVPTR_OPT(d_m, "d_size");
     if (rows == nullptr) nrows = n;
     SILH_REQ(nrows >= 0, "nrows < 0");
     SILH_CK(cudaGetDevice(&dev));
@@ -1165,7 +1169,7 @@ extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n,
     if (m > 0 && nrows > 0 && tc_eligible(metric, prec, d)) {
         // a cluster holds at most all m sampled columns
         st = tc_sweep(X, dtype, n, d, ld, labels, k, metric, prec, S->sizes, S->offsets, S->idx,
-                      S->p, m, m, rows, nrows, s_hat, a_hat, b_hat, sc, stream);
+                      S->p, m, m, rows, nrows, s_hat, a_hat, b_hat, sc, stream, d_m);
         goto done;
     }
     SILH_CK(sc.alloc(&Y, (size_t)m * D));
@@ -1176,12 +1180,33 @@ extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n,
         st = canberra_range(X, dtype, n, d, ld, crange, stream);
         if (st != SILH_OK) goto done;
     }
-    st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, crange, Y, wY, zY, stream);
+    st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, crange, Y, wY, zY, stream,
+                        d_m);
     if (st != SILH_OK) goto done;
     st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, S->sizes, S->offsets, Y, wY, zY,
                       crange, m, D, rows, nrows, s_hat, a_hat, b_hat, stream);
 done:
     return st;
+}
+
+extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n, int32_t d,
+                                     int64_t ld, const int32_t *labels, int32_t k,
+                                     silh_metric metric, silh_prec prec, const silh_sample *S,
+                                     const int64_t *rows, int64_t nrows, float *s_hat,
+                                     float *a_hat, float *b_hat, void *stream_) {
+    return estimate_impl(X, dtype, n, d, ld, labels, k, metric, prec, S, nullptr, rows, nrows,
+                         s_hat, a_hat, b_hat, (cudaStream_t)stream_);
+}
+
+extern "C" silh_status silh_estimate_async(const void *X, silh_dtype dtype, int64_t n, int32_t d,
+                                           int64_t ld, const int32_t *labels, int32_t k,
+                                           silh_metric metric, silh_prec prec,
+                                           const silh_sample *S, const int64_t *d_size,
+                                           const int64_t *rows, int64_t nrows, float *s_hat,
+                                           float *a_hat, float *b_hat, void *stream_) {
+    if (d_size == nullptr) return fail(SILH_EINVAL, "d_size is null");
+    return estimate_impl(X, dtype, n, d, ld, labels, k, metric, prec, S, d_size, rows, nrows,
+                         s_hat, a_hat, b_hat, (cudaStream_t)stream_);
 }
 
 extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, int32_t d,

@@ -29,7 +29,8 @@ cudaError_t scan_flags(const int32_t *flags, int64_t n, int64_t *out, int64_t *d
 silh_status canberra_range(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                            unsigned *crange, cudaStream_t stream);
 
-// Rows of the Phase-2 column operand: Y[i, :] = X[idx[i], :] for i < m, padded
+// Rows of the Phase-2 column operand: Y[i, :] = X[idx[i], :] for i < m (or
+// i < *d_m <= m when the sample size is given on the device), padded
 // with zeros to D columns; cosine rows are scaled to unit norm.  wY[i] = 1/p[i]
 // (or 1 when p == nullptr); zY[i] = 0.5 wY[i] for a zero cosine column, 1 for a
 // Canberra column with a coordinate that is tiny at the scale of crange (from
@@ -37,7 +38,7 @@ silh_status canberra_range(const void *X, silh_dtype dtype, int64_t n, int32_t d
 silh_status gather_columns(const void *X, silh_dtype dtype, int32_t d, int64_t ld,
                            const int32_t *idx, const double *p, int64_t m, int D, int metric,
                            const unsigned *crange, float *Y, float *wY, float *zY,
-                           cudaStream_t stream);
+                           cudaStream_t stream, const int64_t *d_m = nullptr);
 
 // Phase-2 sweep: for every listed row, W_hat_j over the cluster-major column
 // operand (Y, wY, offsets) and the silhouette of Eq. 8 (crange as for
@@ -58,7 +59,8 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
                      const int32_t *labels, int32_t k, int metric, int prec, const int64_t *sizes,
                      const int64_t *offsets, const int32_t *col_idx, const double *col_p, int64_t m,
                      int64_t max_cluster_cols, const int64_t *rows, int64_t nrows, float *s,
-                     float *a, float *b, Scratch &sc, cudaStream_t stream);
+                     float *a, float *b, Scratch &sc, cudaStream_t stream,
+                     const int64_t *d_m = nullptr);
 // Phase 2 of many clusterings of X (all rows each) on the tensor cores: per
 // clustering the operands of tc_sweep, then one persistent sweep over every
 // (clustering, row group); the results equal tc_sweep's bit for bit.  order:

@@ -108,6 +108,99 @@ __global__ void k_scatter(const int32_t *__restrict__ labels, int64_t n, int k, 
     }
 }
 
+// ----------------------------------------------- asynchronous Phase 1
+// The asynchronous entry point sizes everything on the device: a status word
+// (SILH_OK or an error) gates every later kernel, which returns at once when it
+// is set, so an invalid clustering or an exhausted capacity never leads to an
+// out-of-range access; the sample is then written as an empty one.
+
+__device__ __forceinline__ bool gated(const int32_t *status) {
+    return status != nullptr && *status != SILH_OK;
+}
+
+// coff[j] = exclusive prefix of the sizes (one block); an invalid label seen by
+// the histogram (*bad) or an empty cluster sets *status = SILH_EINVAL.
+__global__ void k_coff_async(const int64_t *__restrict__ sizes, int k,
+                             const int32_t *__restrict__ bad, int64_t *__restrict__ coff,
+                             int32_t *__restrict__ status) {
+    __shared__ int64_t sh[1024];
+    __shared__ int empty;
+    if (threadIdx.x == 0) empty = 0;
+    __syncthreads();
+    const int per = (k + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(lo + per, k);
+    int64_t s = 0;
+    for (int j = lo; j < hi; ++j) {
+        s += sizes[j];
+        if (sizes[j] == 0) empty = 1;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int64_t v = (threadIdx.x >= (unsigned)off) ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = sh[threadIdx.x] - s;
+    for (int j = lo; j < hi; ++j) {
+        coff[j] = run;
+        run += sizes[j];
+    }
+    if (threadIdx.x == 1023) coff[k] = sh[1023];
+    if (threadIdx.x == 0 && (*bad != 0 || empty)) *status = SILH_EINVAL;
+}
+
+// Plan of the member x F0 distance matrices on the device (one block): doff[j] =
+// exclusive prefix of |Cj| |F0_j| and item_base[j] = exclusive prefix of the
+// 128-member chunks of the clusters with a non-empty F0; a total beyond the
+// matrix capacity sets *status = SILH_ECAPACITY.
+__global__ void k_plan_f0(const int64_t *__restrict__ coff, const int64_t *__restrict__ f0off,
+                          int k, int64_t dcap, int64_t *__restrict__ doff,
+                          int64_t *__restrict__ item_base, int32_t *__restrict__ status) {
+    __shared__ int64_t shd[1024], shi[1024];
+    if (gated(status)) return;
+    const int per = (k + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(lo + per, k);
+    int64_t sd = 0, si = 0;
+    for (int j = lo; j < hi; ++j) {
+        const int64_t nc = coff[j + 1] - coff[j], nf = f0off[j + 1] - f0off[j];
+        sd += nc * nf;
+        si += nf > 0 ? (nc + 127) / 128 : 0;
+    }
+    shd[threadIdx.x] = sd;
+    shi[threadIdx.x] = si;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int64_t vd = (threadIdx.x >= (unsigned)off) ? shd[threadIdx.x - off] : 0;
+        const int64_t vi = (threadIdx.x >= (unsigned)off) ? shi[threadIdx.x - off] : 0;
+        __syncthreads();
+        shd[threadIdx.x] += vd;
+        shi[threadIdx.x] += vi;
+        __syncthreads();
+    }
+    int64_t rd = shd[threadIdx.x] - sd, ri = shi[threadIdx.x] - si;
+    for (int j = lo; j < hi; ++j) {
+        const int64_t nc = coff[j + 1] - coff[j], nf = f0off[j + 1] - f0off[j];
+        doff[j] = rd;
+        item_base[j] = ri;
+        rd += nc * nf;
+        ri += nf > 0 ? (nc + 127) / 128 : 0;
+    }
+    if (threadIdx.x == 1023) {
+        doff[k] = shd[1023];
+        item_base[k] = shi[1023];
+        if (shd[1023] > dcap) *status = SILH_ECAPACITY;
+    }
+}
+
+// |S| to *d_size, or SILH_ECAPACITY when it exceeds the caller's capacity.
+__global__ void k_finish_size(const int64_t *__restrict__ total, int64_t cap,
+                              int64_t *__restrict__ d_size, int32_t *__restrict__ status) {
+    if (*status == SILH_OK && *total > cap) *status = SILH_ECAPACITY;
+    *d_size = (*status == SILH_OK) ? *total : 0;
+}
+
 // ------------------------------------------------------------------- scan
 
 constexpr int kScanThreads = 256;
@@ -179,9 +272,10 @@ __global__ void k_scan_down(const int32_t *__restrict__ f, int64_t n,
 // Initial Poisson sample F0 (stream 0) for clusters with |Cj| > t.
 __global__ void k_draw_f0(const int32_t *__restrict__ order, const int32_t *__restrict__ labels,
                           const int64_t *__restrict__ sizes, int64_t n, double t, double m0,
-                          uint64_t seed, uint64_t cid, int32_t *__restrict__ flag0) {
+                          uint64_t seed, uint64_t cid, int32_t *__restrict__ flag0,
+                          const int32_t *__restrict__ status = nullptr) {
     int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= n) return;
+    if (pos >= n || gated(status)) return;
     int32_t e = order[pos];
     int64_t nc = sizes[labels[e]];
     int32_t f = 0;
@@ -195,20 +289,27 @@ __global__ void k_draw_f0(const int32_t *__restrict__ order, const int32_t *__re
 
 __global__ void k_compact(const int32_t *__restrict__ flag, const int64_t *__restrict__ pos_of,
                           const int32_t *__restrict__ order, int64_t n, int32_t *__restrict__ ids,
-                          const double *__restrict__ pv, double *__restrict__ pout) {
+                          const double *__restrict__ pv, double *__restrict__ pout,
+                          const int32_t *__restrict__ status = nullptr) {
     int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= n || !flag[pos]) return;
+    if (pos >= n || gated(status) || !flag[pos]) return;
     int64_t o = pos_of[pos];
     ids[o] = order[pos];
     if (pout) pout[o] = pv[pos];
 }
 
-// off[j] = pos_of[coff[j]] (j < k), off[k] = total.
+// off[j] = pos_of[coff[j]] (j < k), off[k] = total; all zero (an empty sample)
+// when the status word is set.
 __global__ void k_seg_offsets(const int64_t *__restrict__ pos_of, const int64_t *__restrict__ coff,
                               int k, int64_t n, const int64_t *__restrict__ total,
-                              int64_t *__restrict__ off) {
+                              int64_t *__restrict__ off,
+                              const int32_t *__restrict__ status = nullptr) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j > k) return;
+    if (gated(status)) {
+        off[j] = 0;
+        return;
+    }
     off[j] = (j == k || coff[j] >= n) ? *total : pos_of[coff[j]];
 }
 
@@ -260,17 +361,39 @@ __device__ __forceinline__ float sqrt_apx(float x) {
 // arithmetic.  D_j[f, i] = d(member i, F0_j[f]), one thread per member, F0
 // rows staged in shared memory kF0Group at a time; work item w covers members
 // [chunk*128, chunk*128+128) of cluster item_cluster[w].
+// Work items from item_cluster / item_chunk (planned on the host), or, when
+// item_cluster is null, from item_base[k + 1] (planned on the device: block b is
+// chunk b - item_base[j] of the last cluster j with item_base[j] <= b; blocks
+// past item_base[k] have none).
 template <class T, int METRIC>
 __global__ void k_dist_f0_df(const T *__restrict__ X, int d, int64_t ld,
                              const int32_t *__restrict__ order, const int64_t *__restrict__ coff,
                              const int32_t *__restrict__ f0_elem, const int64_t *__restrict__ f0off,
                              const int64_t *__restrict__ doff, const int32_t *__restrict__ item_cluster,
-                             const int32_t *__restrict__ item_chunk, double *__restrict__ D) {
+                             const int32_t *__restrict__ item_chunk, double *__restrict__ D,
+                             const int64_t *__restrict__ item_base = nullptr, int k = 0,
+                             const int32_t *__restrict__ status = nullptr) {
     extern __shared__ float sh_yf[];            // kF0Group x d
     __shared__ double sh_inv[kF0Group];         // cosine: 1/|y| of the staged rows (0: zero row)
-    const int j = item_cluster[blockIdx.x];
+    int j;
+    int64_t chunk;
+    if (item_cluster != nullptr) {
+        j = item_cluster[blockIdx.x];
+        chunk = item_chunk[blockIdx.x];
+    } else {
+        const int64_t b = blockIdx.x;
+        if (gated(status) || b >= item_base[k]) return;
+        int lo = 0, hi = k - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (item_base[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        j = lo;
+        chunk = b - item_base[lo];
+    }
     const int64_t c0 = coff[j], nc = coff[j + 1] - c0;
-    const int64_t i = (int64_t)item_chunk[blockIdx.x] * kDistThreads + threadIdx.x;
+    const int64_t i = chunk * kDistThreads + threadIdx.x;
     const bool live = i < nc;
     const int64_t e = live ? order[c0 + i] : 0;
     const int64_t g0 = f0off[j], nf = f0off[j + 1] - g0;
@@ -407,27 +530,35 @@ __global__ void k_dist_f0_df(const T *__restrict__ X, int d, int64_t ld,
 }
 
 // W(e0) = sum over the members of column e0 of D_j, fixed reduction tree.
+// Initial-sample points g = blockIdx.x, blockIdx.x + gridDim.x, ... below nf0
+// (*d_nf0 when given, else gridDim.x: one block per point).
 __global__ void k_w0(const int32_t *__restrict__ f0_elem, const int32_t *__restrict__ labels,
                      const int64_t *__restrict__ coff, const int64_t *__restrict__ f0off,
                      const int64_t *__restrict__ doff, const double *__restrict__ D,
-                     double *__restrict__ W0, double *__restrict__ invW0) {
+                     double *__restrict__ W0, double *__restrict__ invW0,
+                     const int64_t *__restrict__ d_nf0 = nullptr,
+                     const int32_t *__restrict__ status = nullptr) {
     __shared__ double sh[256];
-    int64_t g = blockIdx.x;
-    int j = labels[f0_elem[g]];
-    int64_t nc = coff[j + 1] - coff[j];
-    int64_t f = g - f0off[j];
-    const double *col = D + doff[j] + f * nc;
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < nc; i += 256) s += col[i];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 128; off > 0; off >>= 1) {
-        if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    if (gated(status)) return;
+    const int64_t nf0 = d_nf0 ? *d_nf0 : (int64_t)gridDim.x;
+    for (int64_t g = blockIdx.x; g < nf0; g += gridDim.x) {
+        int j = labels[f0_elem[g]];
+        int64_t nc = coff[j + 1] - coff[j];
+        int64_t f = g - f0off[j];
+        const double *col = D + doff[j] + f * nc;
+        double s = 0.0;
+        for (int64_t i = threadIdx.x; i < nc; i += 256) s += col[i];
         __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        W0[g] = sh[0];
-        invW0[g] = sh[0] > 0.0 ? __ddiv_rn(1.0, sh[0]) : 0.0;   // W = 0: the term d/W is 0
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int off = 128; off > 0; off >>= 1) {
+            if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            W0[g] = sh[0];
+            invW0[g] = sh[0] > 0.0 ? __ddiv_rn(1.0, sh[0]) : 0.0;   // W = 0: the term d/W is 0
+        }
     }
 }
 
@@ -437,9 +568,10 @@ __global__ void k_gamma_draw(const int32_t *__restrict__ order, const int32_t *_
                              const int64_t *__restrict__ f0off, const int64_t *__restrict__ doff,
                              const double *__restrict__ D, const double *__restrict__ invW0, int64_t n,
                              double t, int uniform, uint64_t seed, uint64_t cid,
-                             double *__restrict__ pS, int32_t *__restrict__ flag1) {
+                             double *__restrict__ pS, int32_t *__restrict__ flag1,
+                             const int32_t *__restrict__ status = nullptr) {
     int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= n) return;
+    if (pos >= n || gated(status)) return;
     int32_t e = order[pos];
     int j = labels[e];
     int64_t nc = sizes[j];
@@ -471,26 +603,40 @@ template <class T>
 void launch_dist_f0(int metric, int nitems, size_t smem, cudaStream_t stream, const T *X, int d,
                     int64_t ld, const int32_t *order, const int64_t *coff, const int32_t *f0_elem,
                     const int64_t *f0off, const int64_t *doff, const int32_t *ic,
-                    const int32_t *ik, double *D) {
+                    const int32_t *ik, double *D, const int64_t *item_base = nullptr, int k = 0,
+                    const int32_t *status = nullptr) {
     const size_t smem_f = smem / 2;       // FP32 staging for the double-float kernels
     switch (metric) {
         case SILH_EUCLIDEAN:
             k_dist_f0_df<T, SILH_EUCLIDEAN><<<nitems, kDistThreads, smem_f, stream>>>(
-                X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
+                X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D, item_base, k, status);
             break;
         case SILH_COSINE:
             k_dist_f0_df<T, SILH_COSINE><<<nitems, kDistThreads, smem_f, stream>>>(
-                X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
+                X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D, item_base, k, status);
             break;
         case SILH_MANHATTAN:
             k_dist_f0_df<T, SILH_MANHATTAN><<<nitems, kDistThreads, smem_f, stream>>>(
-                X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
+                X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D, item_base, k, status);
             break;
         default:
             k_dist_f0_df<T, SILH_CANBERRA><<<nitems, kDistThreads, smem_f, stream>>>(
-                X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D); count_launches(1);
+                X, d, ld, order, coff, f0_elem, f0off, doff, ic, ik, D, item_base, k, status);
             break;
     }
+    count_launches(1);
+}
+
+// Shared-memory opt-in of the Phase-1 distance kernels for wide rows.
+template <class T>
+cudaError_t dist_f0_smem_optin(size_t smem_f) {
+    if (smem_f <= 48 * 1024) return cudaSuccess;
+    for (auto f : {k_dist_f0_df<T, 0>, k_dist_f0_df<T, 1>, k_dist_f0_df<T, 2>, k_dist_f0_df<T, 3>}) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_f);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -654,19 +800,11 @@ extern "C" silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t 
         size_t smem = sizeof(double) * kF0Group * (size_t)d;
         SILH_REQ(smem <= 200 * 1024, "d too large for Phase 1 (d <= 3200)");
         if (dtype == SILH_F32) {
-            if (smem / 2 > 48 * 1024)
-                for (auto f : {k_dist_f0_df<float, 0>, k_dist_f0_df<float, 1>,
-                               k_dist_f0_df<float, 2>, k_dist_f0_df<float, 3>})
-                    SILH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(smem / 2)));
+            SILH_CK(dist_f0_smem_optin<float>(smem / 2));
             launch_dist_f0<float>(metric, nitems, smem, stream, (const float *)X, d, ld, order,
                                   coff, f0_elem, f0off, doff, ic, ik, D);
         } else {
-            if (smem / 2 > 48 * 1024)
-                for (auto f : {k_dist_f0_df<__nv_bfloat16, 0>, k_dist_f0_df<__nv_bfloat16, 1>,
-                               k_dist_f0_df<__nv_bfloat16, 2>, k_dist_f0_df<__nv_bfloat16, 3>})
-                    SILH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(smem / 2)));
+            SILH_CK(dist_f0_smem_optin<__nv_bfloat16>(smem / 2));
             launch_dist_f0<__nv_bfloat16>(metric, nitems, smem, stream,
                                           (const __nv_bfloat16 *)X, d, ld, order, coff, f0_elem,
                                           f0off, doff, ic, ik, D);
@@ -691,6 +829,142 @@ extern "C" silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t 
                                                               out->offsets); count_launches(1);
     SILH_CK(cudaGetLastError());
     SILH_CK(cudaStreamSynchronize(stream));
+done:
+    return st;
+}
+
+// Phase 1 with every size kept on the device: the same kernels and arithmetic as
+// silh_sample_pps (so the same sample), planned by device kernels instead of the
+// host, with scratch sized from n, k and m0.  The member x F0 distance matrices
+// get n (m0 + 8 sqrt(m0) + 16) entries: |F0_j| exceeds m0 + 8 sqrt(m0) + 16 with
+// probability below 1e-15 (Poisson tail), and a larger total only sets
+// SILH_ECAPACITY in *d_status.
+extern "C" silh_status silh_sample_pps_async(const void *X, silh_dtype dtype, int64_t n,
+                                             int32_t d, int64_t ld, const int32_t *labels,
+                                             int32_t k, silh_metric metric, double t, double m0,
+                                             double delta, uint64_t seed, uint32_t clustering_id,
+                                             int32_t uniform, silh_sample *out, int64_t *d_size,
+                                             int32_t *d_status, void *stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    silh_status st = SILH_OK;
+    int dev = 0;
+    Scratch sc(stream);
+    int64_t *coff = nullptr, *pos0 = nullptr, *pos1 = nullptr, *tot = nullptr, *f0off = nullptr;
+    int64_t *doff = nullptr, *item_base = nullptr, *tile_base = nullptr;
+    int32_t *order = nullptr, *flag0 = nullptr, *flag1 = nullptr, *f0_elem = nullptr;
+    int32_t *counts = nullptr, *bad = nullptr;
+    double *D = nullptr, *W0 = nullptr, *invW0 = nullptr, *pS = nullptr;
+    int64_t dcap = 0;
+    int nblk = 0, tile = 0, ntiles = 0;
+    size_t hsmem = 0;
+
+    SILH_REQ(X && labels && out && d_size && d_status, "null pointer argument");
+    SILH_REQ(n >= 2 && n < (int64_t(1) << 31), "n must be in [2, 2^31)");
+    SILH_REQ(d >= 1 && ld >= d, "need d >= 1 and ld >= d");
+    SILH_REQ(k >= 2 && k <= SILH_MAX_K, "k must be in [2, %d]", SILH_MAX_K);
+    SILH_REQ(out->k == k && out->sizes && out->offsets && out->idx && out->p && out->cap >= 1,
+             "silh_sample buffers missing, k mismatch or no capacity");
+    SILH_REQ(t > 0.0 && std::isfinite(t), "t must be positive");
+    SILH_REQ(metric >= SILH_EUCLIDEAN && metric <= SILH_CANBERRA, "unknown metric");
+    SILH_REQ(dtype == SILH_F32 || dtype == SILH_BF16, "unknown dtype");
+    SILH_DEVPTR(X, "X");
+    SILH_DEVPTR(labels, "labels");
+    SILH_DEVPTR(out->sizes, "sample sizes");
+    SILH_DEVPTR(out->offsets, "sample offsets");
+    SILH_DEVPTR(out->idx, "sample idx");
+    SILH_DEVPTR(out->p, "sample p");
+    SILH_DEVPTR(d_size, "d_size");
+    SILH_DEVPTR(d_status, "d_status");
+    if (!(m0 > 0.0)) {
+        SILH_REQ(delta > 0.0 && delta < 1.0, "delta must be in (0, 1)");
+        m0 = 2.0 * std::log(5.0 * (double)k / delta);
+    }
+    SILH_REQ((size_t)sizeof(double) * kF0Group * (size_t)d <= 200 * 1024,
+             "d too large for Phase 1 (d <= 3200)");
+    SILH_CK(cudaGetDevice(&dev));
+    ensure_pool_retains(dev);
+    dcap = uniform ? 1 : (int64_t)std::ceil((double)n * (m0 + 8.0 * std::sqrt(m0) + 16.0));
+    tile = (k <= 512) ? 1024 : 8192;
+    ntiles = (int)((n + tile - 1) / tile);
+    hsmem = sizeof(int32_t) * (size_t)k;
+    nblk = ceil_div_i(n, 256);
+    SILH_CK(sc.alloc(&counts, (size_t)k * ntiles));
+    SILH_CK(sc.alloc(&tile_base, (size_t)k * ntiles));
+    SILH_CK(sc.alloc(&bad, 1));
+    SILH_CK(sc.alloc(&coff, (size_t)k + 1));
+    SILH_CK(sc.alloc(&order, (size_t)n));
+    SILH_CK(sc.alloc(&flag0, n));
+    SILH_CK(sc.alloc(&flag1, n));
+    SILH_CK(sc.alloc(&pos0, n));
+    SILH_CK(sc.alloc(&pos1, n));
+    SILH_CK(sc.alloc(&tot, 2));
+    SILH_CK(sc.alloc(&f0off, (size_t)k + 1));
+    SILH_CK(sc.alloc(&doff, (size_t)k + 1));
+    SILH_CK(sc.alloc(&item_base, (size_t)k + 1));
+    SILH_CK(sc.alloc(&pS, n));
+    SILH_CK(sc.alloc(&D, (size_t)dcap));
+    SILH_CK(sc.alloc(&W0, n));
+    SILH_CK(sc.alloc(&invW0, n));
+    SILH_CK(sc.alloc(&f0_elem, n));
+    SILH_CK(cudaMemsetAsync(bad, 0, sizeof(int32_t), stream));
+    SILH_CK(cudaMemsetAsync(d_status, 0, sizeof(int32_t), stream));
+    if (hsmem > 48 * 1024) {
+        SILH_CK(cudaFuncSetAttribute(k_tile_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)hsmem));
+        SILH_CK(cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)hsmem));
+    }
+    // cluster bookkeeping: sizes, offsets (validated on the device), stable order
+    k_tile_hist<<<ntiles, 32 * kHistWarps, hsmem, stream>>>(labels, n, k, tile, ntiles, counts, bad);
+    k_cluster_scan<<<k, 256, 0, stream>>>(counts, ntiles, tile_base, out->sizes);
+    k_coff_async<<<1, 1024, 0, stream>>>(out->sizes, k, bad, coff, d_status);
+    k_scatter<<<ntiles, 32, hsmem, stream>>>(labels, n, k, tile, ntiles, tile_base, coff, order);
+    count_launches(4);
+    SILH_CK(cudaGetLastError());
+    if (!uniform) {
+        // initial sample, its offsets, the device plan of the distance matrices
+        k_draw_f0<<<nblk, 256, 0, stream>>>(order, labels, out->sizes, n, t, m0, seed,
+                                            clustering_id, flag0, d_status);
+        count_launches(1);
+        SILH_CK(scan_flags(flag0, n, pos0, tot, sc, stream));
+        k_seg_offsets<<<ceil_div_i(k + 1, 256), 256, 0, stream>>>(pos0, coff, k, n, tot, f0off,
+                                                                  d_status);
+        k_plan_f0<<<1, 1024, 0, stream>>>(coff, f0off, k, dcap, doff, item_base, d_status);
+        k_compact<<<nblk, 256, 0, stream>>>(flag0, pos0, order, n, f0_elem, nullptr, nullptr,
+                                            d_status);
+        count_launches(3);
+        const size_t smem = sizeof(double) * kF0Group * (size_t)d;
+        const int items_cap = ceil_div_i(n, kDistThreads) + k;
+        if (dtype == SILH_F32) {
+            SILH_CK(dist_f0_smem_optin<float>(smem / 2));
+            launch_dist_f0<float>(metric, items_cap, smem, stream, (const float *)X, d, ld, order,
+                                  coff, f0_elem, f0off, doff, nullptr, nullptr, D, item_base, k,
+                                  d_status);
+        } else {
+            SILH_CK(dist_f0_smem_optin<__nv_bfloat16>(smem / 2));
+            launch_dist_f0<__nv_bfloat16>(metric, items_cap, smem, stream,
+                                          (const __nv_bfloat16 *)X, d, ld, order, coff, f0_elem,
+                                          f0off, doff, nullptr, nullptr, D, item_base, k,
+                                          d_status);
+        }
+        k_w0<<<(int)std::min<int64_t>(n, 148 * 16), 256, 0, stream>>>(
+            f0_elem, labels, coff, f0off, doff, D, W0, invW0, tot, d_status);
+        count_launches(1);
+        SILH_CK(cudaGetLastError());
+    } else {
+        SILH_CK(cudaMemsetAsync(f0off, 0, sizeof(int64_t) * (k + 1), stream));
+    }
+    k_gamma_draw<<<nblk, 256, 0, stream>>>(order, labels, coff, out->sizes, f0off, doff, D, invW0,
+                                           n, t, uniform ? 1 : 0, seed, clustering_id, pS, flag1,
+                                           d_status);
+    count_launches(1);
+    SILH_CK(scan_flags(flag1, n, pos1, tot + 1, sc, stream));
+    k_finish_size<<<1, 1, 0, stream>>>(tot + 1, out->cap, d_size, d_status);
+    k_compact<<<nblk, 256, 0, stream>>>(flag1, pos1, order, n, out->idx, pS, out->p, d_status);
+    k_seg_offsets<<<ceil_div_i(k + 1, 256), 256, 0, stream>>>(pos1, coff, k, n, tot + 1,
+                                                              out->offsets, d_status);
+    count_launches(3);
+    SILH_CK(cudaGetLastError());
 done:
     return st;
 }

@@ -1045,12 +1045,18 @@ k_own_sym(const float *__restrict__ yf, const float2 *__restrict__ ywn,
 
 // Mean of the m sampled columns (Euclidean centring): per-block partial sums
 // over a fixed slice of columns, then one block adds them in order.
+// (m, per_block) come from the host, or, when d_m is given, m = *d_m and
+// per_block = ceil(m / gridDim.x), the host's formula.
 template <class T>
 __global__ void k_col_mean_partial(const T *__restrict__ X, int d, int64_t ld,
                                    const int32_t *__restrict__ idx, int64_t m, int per_block,
-                                   double *__restrict__ part) {
+                                   double *__restrict__ part, const int64_t *__restrict__ d_m) {
     const int c = threadIdx.x;                  // coordinate
     if (c >= d) return;
+    if (d_m != nullptr) {
+        m = *d_m;
+        per_block = (int)((m + gridDim.x - 1) / gridDim.x);
+    }
     const int64_t lo = (int64_t)blockIdx.x * per_block, hi = min(lo + per_block, m);
     double s = 0.0;
     for (int64_t i = lo; i < hi; ++i) {
@@ -1061,12 +1067,13 @@ __global__ void k_col_mean_partial(const T *__restrict__ X, int d, int64_t ld,
 }
 
 __global__ void k_col_mean_final(const double *__restrict__ part, int nb, int d, int64_t m,
-                                 float *__restrict__ mu) {
+                                 float *__restrict__ mu, const int64_t *__restrict__ d_m) {
     const int c = threadIdx.x;
     if (c >= d) return;
+    if (d_m != nullptr) m = *d_m;
     double s = 0.0;
     for (int b = 0; b < nb; ++b) s += part[(int64_t)b * d + c];
-    mu[c] = (float)(s / (double)m);
+    mu[c] = m > 0 ? (float)(s / (double)m) : 0.f;     // an empty sample centres nothing
 }
 
 // --------------------------------------------------------- row ordering
@@ -1542,7 +1549,8 @@ silh_status tc_prepare(const void *X, silh_dtype dtype, int64_t n, int32_t d, in
                        const int32_t *labels, int32_t k, int metric, int KD, bool bf,
                        const int64_t *offsets, const int32_t *col_idx, const double *col_p,
                        int64_t m, const int64_t *rows, int64_t nrows, int64_t nrows_pad,
-                       int64_t mp_pad, const TcOps &o, cudaStream_t stream) {
+                       int64_t mp_pad, const TcOps &o, cudaStream_t stream,
+                       const int64_t *d_m = nullptr) {
     silh_status st = SILH_OK;
     Scratch sc(stream);                          // temporaries, released on return
     const int tile = (k <= 512) ? 1024 : 8192;
@@ -1578,11 +1586,11 @@ silh_status tc_prepare(const void *X, silh_dtype dtype, int64_t n, int32_t d, in
         const int per = (int)((m + mean_blocks - 1) / mean_blocks);
         if (dtype == SILH_F32)
             k_col_mean_partial<float><<<mean_blocks, 128, 0, stream>>>((const float *)X, d, ld,
-                                                                       col_idx, m, per, mpart);
+                                                                       col_idx, m, per, mpart, d_m);
         else
             k_col_mean_partial<__nv_bfloat16><<<mean_blocks, 128, 0, stream>>>(
-                (const __nv_bfloat16 *)X, d, ld, col_idx, m, per, mpart);
-        k_col_mean_final<<<1, 128, 0, stream>>>(mpart, mean_blocks, d, m, mu);
+                (const __nv_bfloat16 *)X, d, ld, col_idx, m, per, mpart, d_m);
+        k_col_mean_final<<<1, 128, 0, stream>>>(mpart, mean_blocks, d, m, mu, d_m);
         count_launches(2);
     } else {
         mu = nullptr;
@@ -1625,7 +1633,7 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
                      const int32_t *labels, int32_t k, int metric, int prec, const int64_t *sizes,
                      const int64_t *offsets, const int32_t *col_idx, const double *col_p, int64_t m,
                      int64_t max_cluster_cols, const int64_t *rows, int64_t nrows, float *s,
-                     float *a, float *b, Scratch &sc, cudaStream_t stream) {
+                     float *a, float *b, Scratch &sc, cudaStream_t stream, const int64_t *d_m) {
     silh_status st = SILH_OK;
     const int KD = d <= 32 ? 32 : 64;
     const bool split = prec == SILH_PREC_3XTF32 || prec == SILH_PREC_BF16X3;
@@ -1654,7 +1662,7 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     SILH_CK(sc.alloc(&o.ylo, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&o.ywn, (size_t)mp_max));
     st = tc_prepare(X, dtype, n, d, ld, labels, k, metric, KD, bf, offsets, col_idx, col_p, m,
-                    rows, nrows, nrows, mp_max, o, stream);
+                    rows, nrows, nrows, mp_max, o, stream, d_m);
     if (st != SILH_OK) goto done;
     SILH_REQ(make_map(&m_ahi, o.rhi, KD, nrows, kTileM, bf) &&
                  make_map(&m_alo, o.rlo, KD, nrows, kTileM, bf) &&
@@ -1902,11 +1910,11 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
         const int per = (int)((n + mean_blocks - 1) / mean_blocks);
         if (dtype == SILH_F32)
             k_col_mean_partial<float><<<mean_blocks, 128, 0, stream>>>((const float *)X, d, ld,
-                                                                       order, n, per, mpart);
+                                                                       order, n, per, mpart, nullptr);
         else
             k_col_mean_partial<__nv_bfloat16><<<mean_blocks, 128, 0, stream>>>(
-                (const __nv_bfloat16 *)X, d, ld, order, n, per, mpart);
-        k_col_mean_final<<<1, 128, 0, stream>>>(mpart, mean_blocks, d, n, mu);
+                (const __nv_bfloat16 *)X, d, ld, order, n, per, mpart, nullptr);
+        k_col_mean_final<<<1, 128, 0, stream>>>(mpart, mean_blocks, d, n, mu, nullptr);
         count_launches(2);
     } else {
         mu = nullptr;

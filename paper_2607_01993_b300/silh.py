@@ -27,7 +27,8 @@ SILH_ECAPACITY = -4
 EXPORTS = ("silh_sample_pps", "silh_estimate", "silh_exact", "silh_global", "silh_t_from_eps",
            "silh_last_error", "silh_version", "silh_kernel_launches", "silh_estimate_noalloc",
            "silh_stream_status", "silh_estimate_batched", "silh_cohsep",
-           "silh_estimate_cosine_collapsed", "silh_pipe_rates", "silh_wait_selftest")
+           "silh_estimate_cosine_collapsed", "silh_pipe_rates", "silh_wait_selftest",
+           "silh_sample_pps_async", "silh_estimate_async")
 SILH_NOALLOC_MAX_COLUMNS = 65536
 SILH_NOALLOC_MAX_FLOATS = 2097152
 
@@ -68,6 +69,11 @@ def load(path: str = LIB_PATH):
     lib.silh_estimate.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32, ctypes.c_int,
                                   ctypes.c_int, ctypes.POINTER(SilhSample), vp, i64, vp, vp, vp, vp]
     lib.silh_estimate.restype = ctypes.c_int
+    lib.silh_sample_pps_async.argtypes = list(lib.silh_sample_pps.argtypes[:-1]) + [vp, vp, vp]
+    lib.silh_sample_pps_async.restype = ctypes.c_int
+    lib.silh_estimate_async.argtypes = (list(lib.silh_estimate.argtypes[:10]) + [vp]
+                                        + list(lib.silh_estimate.argtypes[10:]))
+    lib.silh_estimate_async.restype = ctypes.c_int
     lib.silh_estimate_noalloc.argtypes = list(lib.silh_estimate.argtypes)
     lib.silh_estimate_noalloc.restype = ctypes.c_int
     lib.silh_exact.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32, ctypes.c_int,
@@ -202,6 +208,52 @@ def silh_sample_pps(X, labels, k, metric="euclidean", t=64.0, m0=None, delta=0.0
     _check(rc)
     smp.size = int(st.size)
     return smp
+
+
+def silh_sample_pps_async(X, labels, k, metric="euclidean", t=64.0, m0=None, delta=0.01, seed=0,
+                          clustering_id=0, uniform=False, cap=None, out=None, d_size=None,
+                          d_status=None, stream=None):
+    """Algorithm 1, Phase 1, enqueued without host synchronisation.
+
+    Returns (sample, d_size, d_status): |S| and the status stay on the device
+    (int64 / int32 CUDA tensors) until the caller reads them; sample.size is
+    left at -1.  cap defaults to n (always enough)."""
+    lib = load()
+    dt, n, d, ld = _data(X)
+    labels = _labels(labels)
+    smp = out if out is not None else Sample.empty(k, n if cap is None else cap, X.device)
+    if d_size is None:
+        d_size = torch.empty(1, dtype=torch.int64, device=X.device)
+    if d_status is None:
+        d_status = torch.empty(1, dtype=torch.int32, device=X.device)
+    st = smp.as_struct()
+    _check(lib.silh_sample_pps_async(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric],
+                                     float(t), -1.0 if m0 is None else float(m0), float(delta),
+                                     int(seed), int(clustering_id), 1 if uniform else 0,
+                                     ctypes.byref(st), _ptr(d_size), _ptr(d_status),
+                                     _stream(stream)))
+    smp.size = -1
+    return smp, d_size, d_status
+
+
+def silh_estimate_async(X, labels, k, sample: Sample, d_size, metric="euclidean", prec="fp32",
+                        rows=None, want_ab=False, out=None, stream=None):
+    """Phase 2 for a sample whose size is on the device (d_size, int64 CUDA)."""
+    lib = load()
+    dt, n, d, ld = _data(X)
+    labels = _labels(labels)
+    rows, nr = _rows(rows)
+    nrows = n if rows is None else nr
+    s = _out(out, nrows, X.device)
+    a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    if _empty_rows(rows, nr):
+        return (s, a, b) if want_ab else s
+    st = sample.as_struct()
+    _check(lib.silh_estimate_async(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric],
+                                   PRECS[prec], ctypes.byref(st), _ptr(d_size), _ptr(rows), nr,
+                                   _ptr(s), _ptr(a), _ptr(b), _stream(stream)))
+    return (s, a, b) if want_ab else s
 
 
 def silh_estimate(X, labels, k, sample: Sample, metric="euclidean", prec="fp32", rows=None,
