@@ -10,7 +10,12 @@ delta = 0.01):
     exact silhouette (silh_exact) of a seeded 100k-row sub-dataset -> silh_global.
 value = PPS silhouette points/s = 4 n / step time (exact leg included in the time).
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-extras]
+
+At N = 1 the same line also carries, under "configs", the other workloads at
+bounded repetitions: batching (256 clusterings, one persistent launch vs 256
+calls), precision (n = 4M, d = 64, BF16 storage: time and error per mode) and
+serving (Poisson request streams: p50/p99 and req/s vs one at a time).
 
 Multi-GPU runs are independent replicas (one workload per rank, seeds differ),
 so scaling is weak; value sums the points of all ranks over the max-over-ranks
@@ -398,11 +403,12 @@ def roofline(res, peaks, peak_kind):
     return dom, out
 
 
-def run_batching(args):
+def run_batching(args, emit=True):
     """Batching workload: one dataset (n = 500k, d = 16), 256 clusterings
     (k = 2..257, nearest random data-row centres), t = 128.  Phase 1 per
     clustering; Phase 2 of all clusterings as one graph-captured persistent
-    launch (autotuned tile shape) against 256 separate launches."""
+    launch (tile shape picked by the autotuner, on the tensor cores and on CUDA
+    cores) against 256 separate launches."""
     import torch
     from paper_2607_01993_b300 import autotune, silh
     torch.cuda.set_device(0)
@@ -457,12 +463,16 @@ def run_batching(args):
     # the same clusterings on the tensor cores (split TF32, Euclidean): one
     # captured graph of the batched call against one silh_estimate per clustering
     tc_prec = "3xtf32"
+    tc_variant, tc_tune_ms = autotune.tune_batched(Xt, sub, "euclidean", reps=1, force=True,
+                                                   prec=tc_prec)
     tc_outs = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in items]
-    silh.silh_estimate_batched(Xt, items, "euclidean", outs=tc_outs, prec=tc_prec)
+    silh.silh_estimate_batched(Xt, items, "euclidean", outs=tc_outs, prec=tc_prec,
+                               variant=tc_variant)
     torch.cuda.synchronize()
     gt = torch.cuda.CUDAGraph()
     with torch.cuda.graph(gt):
-        silh.silh_estimate_batched(Xt, items, "euclidean", outs=tc_outs, prec=tc_prec)
+        silh.silh_estimate_batched(Xt, items, "euclidean", outs=tc_outs, prec=tc_prec,
+                                   variant=tc_variant)
     gt.replay()
     torch.cuda.synchronize()
     ms_tc = timed(gt.replay, args.steps)
@@ -475,7 +485,8 @@ def run_batching(args):
 
     separate_tc()
     ms_tc_sep = timed(separate_tc, max(1, args.steps // 2))
-    tc_same = all(torch.equal(a, b) for a, b in zip(tc_outs, tc_sep))
+    tc_same = all(torch.equal(a, b) for a, b in zip(tc_outs, tc_sep)) if tc_variant == 0 else None
+    tc_sep_diff = max((a - b).abs().max().item() for a, b in zip(tc_outs, tc_sep))
     tc_vs_fp32 = max((a - b).abs().max().item() for a, b in zip(tc_outs, outs))
     pairs = float(n) * sum(smp.size for _, smp in items)
     line = {"metric": "batched PPS silhouette points/s (Phase 2, all clusterings)",
@@ -485,6 +496,8 @@ def run_batching(args):
             "batched_ms": round(ms_tc, 3), "separate_ms": round(ms_tc_sep, 3),
             "speedup_vs_separate": round(ms_tc_sep / ms_tc, 3),
             "pairs_per_s": round(pairs / (ms_tc * 1e-3), 1), "same_as_separate": tc_same,
+            "max_abs_diff_vs_separate": tc_sep_diff,
+            "tensor_core_variant": tc_variant, "tensor_core_autotune_ms": tc_tune_ms,
             "max_abs_diff_vs_fp32_cuda_cores": tc_vs_fp32,
             "labels_and_phase1_s_all": round(t_phase1, 3),
             "fp32_cuda_cores": {"batched_ms": round(ms_batched, 3),
@@ -495,12 +508,14 @@ def run_batching(args):
                                 "same_as_separate": same, "max_abs_diff_vs_separate": maxdiff},
             "config": {"workload": f"batching: n={n}, d=16 FP32, {len(items)} clusterings k={ks[0]}..{ks[-1]} "
                                    f"(nearest random data-row centres), t=128, Euclidean; tensor cores "
-                                   f"(split TF32) and FP32 CUDA cores (autotuned tile)",
+                                   f"(split TF32) and FP32 CUDA cores (autotuned tiles)",
                        "graph": "CUDA graph of the batched call"}}
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
 
 
-def run_precision(args):
+def run_precision(args, emit=True):
     """Precision workload: n = 4M, d = 64, k = 64 (Zipf sizes, 10% border
     points), stored BF16 with FP32 masters, t = 128; Euclidean and cosine.
     Phase 1 once per metric; Phase 2 over all rows in every precision mode,
@@ -572,7 +587,32 @@ def run_precision(args):
                                    f"stored BF16 (FP32 masters), t={t}, delta=0.01",
                        "error_rows": len(rows), "l2": "flushed (256 MB write) before each timing"},
             "results": out}
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
+
+
+def run_extras(args):
+    """The other workloads of the benchmark, at bounded repetitions, for the one
+    JSON line of the default run: batching (256 clusterings in one launch vs
+    separate calls), precision (time and error per precision mode at n = 4M)
+    and serving (p50/p99 and req/s against one request at a time)."""
+    import copy
+    ea = copy.copy(args)
+    ea.steps, ea.precision_rows, ea.serve_load, ea.serve_spec = 3, 1000, 120, 200
+    extras = {}
+    for name, fn in (("batching", run_batching), ("precision", run_precision),
+                     ("serving", run_serving)):
+        t0 = time.perf_counter()
+        try:
+            extras[name] = fn(ea, emit=False)
+        except Exception as exc:                 # recorded; the main line still prints
+            extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        extras[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+        import torch
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return extras
 
 
 def run_peaks(args):
@@ -742,6 +782,9 @@ def main():
     ap.add_argument("--clusterings", type=int, default=256)
     ap.add_argument("--k-min", type=int, default=2,
                     help="batching: smallest k (the clusterings take k = k_min, k_min + 1, ...)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="large workload only: skip the batching, precision and serving "
+                         "results that the default run adds to its line")
     ap.add_argument("--serve-spec", type=int, default=400)
     ap.add_argument("--serve-load", type=int, default=200)
     args = ap.parse_args()
@@ -826,6 +869,8 @@ def main():
             "gpu_launches": res["launches"], "clocks": res["clocks"]}
     if "cosine_collapsed" in res["info"]:
         line["cosine_collapsed"] = res["info"]["cosine_collapsed"]
+    if not args.no_extras and world == 1 and args.scale == 1.0 and len(METRICS) == 4:
+        line["configs"] = run_extras(args)
     if not args.no_cpu_baseline and world == 1:
         import oracle
         cpu = cpu_oracle_sample(res["X"], res["lab"], res["rows"], res["k"], WORKLOAD["t"],

@@ -244,7 +244,10 @@ typedef struct silh_batch_item {
  * the operands of the single-clustering tensor-core sweep (rows sorted by its
  * clusters, its padded sample columns, its own-cluster sums), then one
  * persistent sweep covers every (clustering, row group), and each result
- * equals silh_estimate with that prec bit for bit; variant is ignored.
+ * equals silh_estimate with that prec bit for bit; variant 1 selects 64-column
+ * tiles with two accumulators per row tile for TF32 operands of rows of up to
+ * 32 elements (d <= 32), any other value the default 128-column tiles with one
+ * (the choice an autotuner makes by timing; the results do not depend on it).
  * Operands above 16 GiB per launch are split over several launches.
  * Asynchronous and free of host synchronisation, so the call can be captured
  * in a CUDA graph; items are passed to the kernels as launch parameters, 256

@@ -1358,7 +1358,7 @@ extern "C" silh_status silh_estimate_batched(const void *X, silh_dtype dtype, in
         b.total_cols = cols;
     }
     if (tc_eligible(metric, prec, d)) {
-        st = tc_sweep_batched(X, dtype, n, d, ld, metric, prec, items, order, stream);
+        st = tc_sweep_batched(X, dtype, n, d, ld, metric, prec, items, order, variant, stream);
         goto done;
     }
     SILH_CK(sc.alloc(&next_work, 1));

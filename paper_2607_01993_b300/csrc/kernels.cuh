@@ -66,9 +66,12 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
 // (clustering, row group); the results equal tc_sweep's bit for bit.  order:
 // the items in launch order (largest first).  Batches beyond the operand
 // budget are split into several launches.
+// variant 1 selects 64-column tiles for TF32 operands of 32-element rows;
+// any other variant the default 128-column tiles.
 silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                              int metric, int prec, const silh_batch_item *items,
-                             const std::vector<int32_t> &order, cudaStream_t stream);
+                             const std::vector<int32_t> &order, int variant,
+                             cudaStream_t stream);
 // Exact silhouette of all n points on the tensor cores with each unordered
 // pair evaluated once (Euclidean / cosine, the tc_sweep precisions, d <= 64).
 // coff / order / h_sizes from cluster_sort.

@@ -1502,7 +1502,7 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
 // One persistent sweep over the (clustering, row group) work items of a batch;
 // the row and column operands, weights, offsets and W_own of all its
 // clusterings live in shared buffers (bases in bt).
-template <int METRIC, int KD, bool SPLIT, bool BF>
+template <int METRIC, int KD, bool SPLIT, bool BF, bool WIDE>
 cudaError_t launch_tc_batched(int nsm, cudaStream_t stream, const CUtensorMap &ahi,
                               const CUtensorMap &alo, const CUtensorMap &bhi,
                               const CUtensorMap &blo, const float *a_hi, const float *a_lo,
@@ -1512,7 +1512,6 @@ cudaError_t launch_tc_batched(int nsm, cudaStream_t stream, const CUtensorMap &a
                               const int64_t *poff,
                               float tau, int dq, const double *w_own,
                               const TcBatchArg<true> &bt) {
-    constexpr bool WIDE = wide_tiles(KD, BF);
     using C = TcCfg<KD, SPLIT, BF, WIDE>;
     auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF, false, WIDE, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
@@ -1697,11 +1696,15 @@ done:
 
 silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                              int metric, int prec, const silh_batch_item *items,
-                             const std::vector<int32_t> &order, cudaStream_t stream) {
+                             const std::vector<int32_t> &order, int variant,
+                             cudaStream_t stream) {
     silh_status st = SILH_OK;
     const int KD = d <= 32 ? 32 : 64;
     const bool split = prec == SILH_PREC_3XTF32 || prec == SILH_PREC_BF16X3;
     const bool bf = prec == SILH_PREC_BF16 || prec == SILH_PREC_BF16X3;
+    // tile shape: 128-column tiles, one accumulator per slot (variant 0), or,
+    // for TF32 operands of 32-element rows, 64-column tiles with two (variant 1)
+    const bool wide = wide_tiles(KD, bf) && !(variant == 1 && !bf && KD == 32);
     const int KE = bf ? 64 : KD;
     const size_t ebytes = bf ? 2 : 4;
     const int slots = tc_slots(KD, bf);           // row tiles per row group (TcCfg::SLOTS)
@@ -1815,17 +1818,18 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
         }
         SILH_REQ(make_map(&m_ahi, g.rhi, KD, rows_total, kTileM, bf) &&
                      make_map(&m_alo, g.rlo, KD, rows_total, kTileM, bf) &&
-                     make_map(&m_bhi, g.yhi, KD, cols_total, wide_tiles(KD, bf) ? 128 : kTileN, bf) &&
-                     make_map(&m_blo, g.ylo, KD, cols_total, wide_tiles(KD, bf) ? 128 : kTileN, bf),
+                     make_map(&m_bhi, g.yhi, KD, cols_total, wide ? 128 : kTileN, bf) &&
+                     make_map(&m_blo, g.ylo, KD, cols_total, wide ? 128 : kTileN, bf),
                  "tensor map encoding failed");
-#define SILH_TC_BCASE(MET, KDV, SP, BFV)                                                       \
-        if (metric == MET && KD == KDV && split == SP && bf == BFV) {                          \
-            SILH_CK((launch_tc_batched<MET, KDV, SP, BFV>(                                      \
+#define SILH_TC_BCASE_W(MET, KDV, SP, BFV, WV)                                                 \
+        if (metric == MET && KD == KDV && split == SP && bf == BFV && wide == WV) {            \
+            SILH_CK((launch_tc_batched<MET, KDV, SP, BFV, WV>(                                  \
                 nsm, stream, m_ahi, m_alo, m_bhi, m_blo,                                        \
                 BFV ? g.rfull : (const float *)g.rhi, BFV ? nullptr : (const float *)g.rlo,     \
                 g.ril, g.rn, g.lab, g.outi, g.yf, g.yil, g.ywn, g.poff, tau, (d + 3) / 4, w_own, \
                 bt)));                                                                          \
         }
+#define SILH_TC_BCASE(MET, KDV, SP, BFV) SILH_TC_BCASE_W(MET, KDV, SP, BFV, wide_tiles(KDV, BFV))
 #define SILH_TC_BCASES(MET, KDV)             \
         SILH_TC_BCASE(MET, KDV, true, false)     \
         SILH_TC_BCASE(MET, KDV, false, false)    \
@@ -1835,8 +1839,14 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
         SILH_TC_BCASES(SILH_EUCLIDEAN, 64)
         SILH_TC_BCASES(SILH_COSINE, 32)
         SILH_TC_BCASES(SILH_COSINE, 64)
+        // 64-column tiles for TF32 operands of 32-element rows (variant 1)
+        SILH_TC_BCASE_W(SILH_EUCLIDEAN, 32, true, false, false)
+        SILH_TC_BCASE_W(SILH_EUCLIDEAN, 32, false, false, false)
+        SILH_TC_BCASE_W(SILH_COSINE, 32, true, false, false)
+        SILH_TC_BCASE_W(SILH_COSINE, 32, false, false, false)
 #undef SILH_TC_BCASES
 #undef SILH_TC_BCASE
+#undef SILH_TC_BCASE_W
         i0 = i1;
     }
 done:

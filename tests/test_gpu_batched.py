@@ -96,6 +96,33 @@ def test_autotuner_picks_a_variant(batch, tmp_path, monkeypatch):
     assert v2 == v
 
 
+@pytest.mark.parametrize("prec", ["3xtf32", "tf32"])
+@pytest.mark.parametrize("metric", ["euclidean", "cosine"])
+def test_tensor_core_tile_variants_equal_single_calls(batch, prec, metric):
+    # the default tile shape of the batched tensor-core sweep (128 columns, one
+    # accumulator per row tile) gives silh_estimate's results bit for bit; the
+    # 64-column one (two accumulators) folds FP32 partial sums into FP64 every
+    # 64 columns instead of 128, so it agrees to FP32 rounding
+    X, Xt, ks, labels, items = batch
+    want = [silh.silh_estimate(Xt, lt, k, smp, metric, prec=prec)
+            for (lt, smp), k in zip(items, ks)]
+    for v in (0, 1):
+        got = silh.silh_estimate_batched(Xt, items, metric, variant=v, prec=prec)
+        for a, b in zip(got, want):
+            if v == 0:
+                assert torch.equal(a, b), (metric, prec)
+            else:
+                assert (a - b).abs().max().item() <= 1e-6, (metric, prec)
+
+
+def test_autotuner_times_the_tensor_core_variants(batch, tmp_path, monkeypatch):
+    X, Xt, ks, labels, items = batch
+    monkeypatch.setenv("SILH_AUTOTUNE_CACHE", str(tmp_path / "tune_tc.json"))
+    v, times = autotune.tune_batched(Xt, items[:3], "euclidean", reps=1, prec="3xtf32")
+    assert v in (0, 1) and sorted(times) == ["0", "1"]
+    assert autotune.tune_batched(Xt, items[:3], "euclidean", prec="3xtf32")[0] == v
+
+
 @pytest.mark.parametrize("metric", ["cosine", "manhattan", "canberra"])
 def test_batched_other_metrics(metric):
     X, labels = _dataset(8000, 13, 41, [3, 7])
