@@ -576,6 +576,19 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             const int64_t apos = v.arow + pos;                            // row of the operands
             const int own = valid ? a_lab[apos] : -1;
             const float xn = valid ? a_norm[apos] : 0.f;
+            if (!kColRedo && valid) {
+                // the row-form recompute reads this row's FP32 coordinates (hi and,
+                // for TF32 operands, lo): bring them into L2 now, so that a close
+                // pair later in the sweep does not wait on DRAM for them
+                const float *xr = a_hi + apos * KD;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(xr));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(xr + 32));
+                if (!(BF || SYM)) {
+                    const float *lr = a_lo + apos * KD;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(lr));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(lr + 32));
+                }
+            }
             // the warp's block of 32 rows in the lane-interleaved FP32 copy (for
             // the direct recompute; a warp past the last row never recomputes)
             const int64_t blk0 = pos - lane;
@@ -720,6 +733,103 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             if (lane == r) part = rs;
                         }
                         if (SYM) atomicAdd(&W[(c0 + lane) * k + own], (double)colsum);
+                    } else if (redo && !SYM) {
+                        // 64-element rows, close pairs in a few lanes and columns: each
+                        // lane first takes its 32 pairs from the inner products (four
+                        // columns per TMEM load) and only marks the close ones; then
+                        // the warp evaluates the marked pairs together, one pair at a
+                        // time with two coordinates per lane -- the row's and the
+                        // column's loads are coalesced and issued at once, and a
+                        // shuffle sum gives the distance.
+                        uint32_t fm = 0u;
+                        part = 0.f;
+                        uint32_t rr0[16], rr1[16];
+                        __syncwarp();
+                        tmem_ld16_issue(tcol + ch * 32, rr0);
+                        tmem_ld16_issue(tcol + ch * 32 + 16, rr1);
+                        tmem_wait_16(rr0);
+                        tmem_wait_16(rr1);
+#pragma unroll
+                        for (int hh = 0; hh < 8; ++hh) {
+#pragma unroll
+                            for (int ii = 0; ii < 4; ++ii) {
+                                const int i = 4 * hh + ii;
+                                const float dot = __uint_as_float(i < 16 ? rr0[i] : rr1[i - 16]);
+                                const float *f = reinterpret_cast<const float *>(
+                                    &sh_wn[g][buf][ch * 16 + (i >> 1)]);
+                                const float2 wn = make_float2(f[i & 1], f[2 + (i & 1)]);
+                                bool close;
+                                float dist;
+                                if (METRIC == SILH_EUCLIDEAN) {
+                                    const float s2 = xn + wn.y;
+                                    const float d2 = fmaf(-2.f, dot, s2);
+                                    close = d2 < tau * s2;
+                                    dist = sqrt_apx(d2);
+                                } else {
+                                    dist = 1.f - dot;
+                                    close = dist < tau;
+                                }
+                                if (close) fm |= 1u << i;
+                                else part = fmaf(wn.x, dist, part);
+                            }
+                        }
+                        if (mine || !valid) fm = 0u;     // own-cluster sums come from w_own
+                        constexpr bool kFullRows = BF;
+                        // the marked (row, column) pairs in lane order, four per round:
+                        // every round issues the rows' and columns' loads of its four
+                        // pairs before any arithmetic
+                        uint32_t todo = __ballot_sync(0xffffffffu, fm != 0u);
+                        uint32_t m = 0u;
+                        int rl = -1;
+                        while (todo != 0u || m != 0u) {
+                            int pr[4], pc[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                if (m == 0u && todo != 0u) {
+                                    rl = __ffs(todo) - 1;
+                                    todo &= todo - 1u;
+                                    m = __shfl_sync(0xffffffffu, fm, rl);
+                                }
+                                pr[u] = (m != 0u) ? rl : -1;
+                                pc[u] = (m != 0u) ? __ffs(m) - 1 : 0;
+                                if (m != 0u) m &= m - 1u;
+                            }
+                            float x0[4], x1[4], y0[4], y1[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int64_t rp = __shfl_sync(0xffffffffu, apos, pr[u] < 0 ? 0 : pr[u]);
+                                const float *xr = a_hi + rp * KD;
+                                const float *yc = y_full + (v.ccol + c0 + pc[u]) * KD;
+                                x0[u] = xr[lane];
+                                x1[u] = (KD > 32) ? xr[lane + 32] : 0.f;
+                                if (!kFullRows) {          // TF32 operands: x = hi + lo exactly
+                                    const float *xq = a_lo + rp * KD;
+                                    x0[u] += xq[lane];
+                                    if (KD > 32) x1[u] += xq[lane + 32];
+                                }
+                                y0[u] = yc[lane];
+                                y1[u] = (KD > 32) ? yc[lane + 32] : 0.f;
+                            }
+                            float ss[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const float t0 = x0[u] - y0[u], t1 = x1[u] - y1[u];
+                                ss[u] = fmaf(t0, t0, t1 * t1);
+                            }
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                                for (int u = 0; u < 4; ++u)
+                                    ss[u] += __shfl_xor_sync(0xffffffffu, ss[u], o);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                if (lane != pr[u]) continue;
+                                const float dist = (METRIC == SILH_EUCLIDEAN) ? sqrtf(ss[u]) : 0.5f * ss[u];
+                                const float wc = reinterpret_cast<const float *>(
+                                    &sh_wn[g][buf][ch * 16 + (pc[u] >> 1)])[pc[u] & 1];
+                                part = fmaf(wc, dist, part);
+                            }
+                        }
                     } else if (redo) {
                         // the same chunk column by column, each lane its own row; the
                         // flagged pairs directly from the coordinates

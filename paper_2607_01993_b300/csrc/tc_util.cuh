@@ -184,6 +184,18 @@ __device__ __forceinline__ void tmem_wait_16(uint32_t (&r)[16]) {
                  : "memory");
 }
 
+// Four consecutive 32-bit columns of this warp's 32 TMEM lanes (waits for them).
+__device__ __forceinline__ float4 tmem_ld_32x4(uint32_t taddr) {
+    uint32_t r0, r1, r2, r3;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)::"memory");
+    return make_float4(__uint_as_float(r0), __uint_as_float(r1), __uint_as_float(r2),
+                       __uint_as_float(r3));
+}
+
 // One 32-bit column of this warp's 32 TMEM lanes.
 __device__ __forceinline__ float tmem_ld_32x1(uint32_t taddr) {
     uint32_t r;
