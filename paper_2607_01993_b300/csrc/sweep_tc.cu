@@ -78,6 +78,12 @@ __host__ __device__ constexpr int tc_slots(int KD, bool BF) { return (BF || KD =
 // is flagged, and a whole row-major row is two cache lines where its
 // interleaved form is sixteen).
 __host__ __device__ constexpr bool tc_col_redo(int KD) { return KD == 32; }
+// 64-element rows: a chunk whose close pairs average more than this many per
+// marked column is recomputed lane by lane (each lane its row, the marked
+// columns one after another), else pair by pair with the whole warp.  For
+// TF32 operands (a row is hi + lo, two loads per coordinate) the pair-by-pair
+// form measured faster at every density, so the threshold is never reached.
+__host__ __device__ constexpr uint32_t coop_pairs_per_column(bool bf) { return bf ? 12u : 33u; }
 
 template <int KD, bool SPLIT, bool BF = false, bool WIDE = false>
 struct TcCfg {
@@ -775,6 +781,28 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         }
                         if (mine || !valid) fm = 0u;     // own-cluster sums come from w_own
                         constexpr bool kFullRows = BF;
+                        // Dense chunks (many close pairs per marked column): each lane
+                        // evaluates its own marked pairs column by column, the lanes in
+                        // parallel (one direct distance per marked column and lane).
+                        const uint32_t npairs = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(fm));
+                        const uint32_t colmask = __reduce_or_sync(0xffffffffu, fm);
+                        if (npairs > coop_pairs_per_column(BF) * (uint32_t)__popc(colmask)) {
+                            const float *xh = a_hi + apos * KD;
+                            const float *xl = kFullRows ? xh : a_lo + apos * KD;
+                            uint32_t cm = colmask;
+                            while (cm != 0u) {
+                                const int i = __ffs(cm) - 1;
+                                cm &= cm - 1u;
+                                if ((fm >> i) & 1u) {
+                                    const float *yc = y_full + (v.ccol + c0 + i) * KD;
+                                    const float dist = direct_dist_rows<METRIC, KD, kFullRows>(xh, xl, yc);
+                                    const float wc = reinterpret_cast<const float *>(
+                                        &sh_wn[g][buf][ch * 16 + (i >> 1)])[i & 1];
+                                    part = fmaf(wc, dist, part);
+                                }
+                            }
+                            fm = 0u;
+                        }
                         // the marked (row, column) pairs in lane order, four per round:
                         // every round issues the rows' and columns' loads of its four
                         // pairs before any arithmetic
