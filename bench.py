@@ -681,9 +681,9 @@ def run_serving(args, emit=True):
         d.update(extra)
         return d
 
-    def served(reqs, rate, slots):
+    def served(reqs, rate, slots, cosine="per_pair"):
         due = arrivals(len(reqs), rate)
-        srv = serve.SilhServer(datasets, slots=slots)
+        srv = serve.SilhServer(datasets, slots=slots, cosine=cosine)
         t0 = time.perf_counter()
         futs, max_q = [], 0
         for r, a in zip(reqs, due):
@@ -727,6 +727,7 @@ def run_serving(args, emit=True):
     load = make_requests(args.serve_load, 40_000)
     plain_cap, res_alone = one_at_a_time(load, 0, "fp32")
     sat, res_sat = served(load, 0, 8)
+    sat_cc, _ = served(load, 0, 8, cosine="collapsed")
     capacity = plain_cap["achieved_req_s"]
     rate = 0.8 * capacity
     at80_served, res_b = served(load, rate, 8)
@@ -740,6 +741,8 @@ def run_serving(args, emit=True):
     out = {"capacity_req_s": {"server_8_slots": sat["achieved_req_s"],
                               "one_at_a_time_plain_fp32": plain_cap["achieved_req_s"]},
            "capacity_vs_plain_fp32": round(sat["achieved_req_s"] / capacity, 3),
+           "capacity_server_collapsed_cosine_req_s": sat_cc["achieved_req_s"],
+           "capacity_collapsed_cosine_vs_plain_fp32": round(sat_cc["achieved_req_s"] / capacity, 3),
            "at_80pct_of_plain_capacity": {"offered_req_s": round(rate, 2),
                                           "server": at80_served, "plain_fp32": at80_plain},
            "specified_stream_2000_req_s": specified,

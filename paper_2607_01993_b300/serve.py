@@ -100,7 +100,15 @@ class _Flight:
 
 
 class SilhServer:
-    def __init__(self, datasets, slots: int = 4, hbm_budget_bytes: int | None = None):
+    """cosine="collapsed" runs cosine requests' Phase 2 in the O(n k d) form of
+    silh_estimate_cosine_collapsed (the same estimate up to rounding; |ds| within
+    the FP32 bound of the oracle) instead of the per-pair sweep."""
+
+    def __init__(self, datasets, slots: int = 4, hbm_budget_bytes: int | None = None,
+                 cosine: str = "per_pair"):
+        if cosine not in ("per_pair", "collapsed"):
+            raise ValueError("cosine must be 'per_pair' or 'collapsed'")
+        self.cosine = cosine
         self.datasets = datasets                                   # list of 2-D CUDA tensors
         self.device = datasets[0].device
         self.slots = max(1, int(slots))
@@ -182,8 +190,15 @@ class SilhServer:
             fl.smp, fl.d_size, fl.d_status = silh.silh_sample_pps_async(
                 X, req.labels, req.k, req.metric, t=req.t, seed=req.seed,
                 clustering_id=req.clustering_id, cap=cap, stream=stream)
-            fl.s = silh.silh_estimate_async(X, req.labels, req.k, fl.smp, fl.d_size, req.metric,
-                                            prec=prec, stream=stream)
+            if req.metric == "cosine" and self.cosine == "collapsed":
+                # the collapsed form reads the per-cluster lists through the
+                # device offsets only; the host size just has to be consistent
+                fl.smp.size = fl.smp.idx.shape[0]
+                fl.s = silh.silh_estimate_cosine_collapsed(X, req.labels, req.k, fl.smp,
+                                                           stream=stream)
+            else:
+                fl.s = silh.silh_estimate_async(X, req.labels, req.k, fl.smp, fl.d_size,
+                                                req.metric, prec=prec, stream=stream)
             fl.g = silh.silh_global(fl.s, stream=stream)
             host = self._host[fl.slot]
             host[0:1].copy_(fl.g, non_blocking=True)
@@ -202,8 +217,11 @@ class SilhServer:
         with torch.cuda.stream(stream):
             smp = silh.silh_sample_pps(X, req.labels, req.k, req.metric, t=req.t, seed=req.seed,
                                        clustering_id=req.clustering_id, stream=stream)
-            s = silh.silh_estimate(X, req.labels, req.k, smp, req.metric, prec=prec,
-                                   stream=stream)
+            if req.metric == "cosine" and self.cosine == "collapsed":
+                s = silh.silh_estimate_cosine_collapsed(X, req.labels, req.k, smp, stream=stream)
+            else:
+                s = silh.silh_estimate(X, req.labels, req.k, smp, req.metric, prec=prec,
+                                       stream=stream)
             g = silh.silh_global(s, stream=stream).item()
         return g, smp.size, s
 

@@ -83,3 +83,26 @@ def test_served_request_matches_oracle(setup):
                                 rows=rows)
     got = res.s_hat[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
     assert np.abs(got - s_o).max() <= 1e-5
+
+
+def test_collapsed_cosine_server_matches_alone_and_oracle(setup):
+    # cosine requests through the O(n k d) collapsed form: the same result alone
+    # and in the mix, and within the FP32 bound of the oracle
+    host, dev, reqs = setup
+    cos = [dict(r, metric="cosine") for r in reqs[:6]]
+    with serve.SilhServer(dev, slots=1, cosine="collapsed") as srv:
+        alone = [srv.submit(serve.Request(**r)).result(timeout=300) for r in cos]
+    with serve.SilhServer(dev, slots=4, cosine="collapsed") as srv:
+        mixed = [f.result(timeout=300) for f in [srv.submit(serve.Request(**r)) for r in cos]]
+    for a, b in zip(alone, mixed):
+        assert a.s_global == b.s_global and torch.equal(a.s_hat, b.s_hat)
+    r = cos[2]
+    Xh = host[r["dataset"]]
+    lab = r["labels"].cpu().numpy()
+    os_ = oracle.sample_pps(Xh, lab, r["k"], "cosine", t=r["t"], seed=r["seed"],
+                            cid=r["clustering_id"])
+    rows = synth.seeded_rows(Xh.shape[0], 200, seed=6)
+    s_o, _, _ = oracle.estimate(Xh, lab, r["k"], "cosine", os_.offsets, os_.idx, os_.ps,
+                                rows=rows)
+    got = mixed[2].s_hat[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    assert np.abs(got - s_o).max() <= 1e-5
