@@ -107,21 +107,6 @@ struct TcCfg {
     static constexpr uint32_t TMEM_COLS = SLOTS * NACC * TN;
 };
 
-// Named barrier (1 + group) over one epilogue group's 128 threads that also
-// ORs a predicate, so that the whole group takes the same decision to stop.
-__device__ __forceinline__ bool epi_bar_any(int group, bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred pi, po;\n\t"
-        "setp.ne.u32 pi, %2, 0;\n\t"
-        "barrier.red.or.pred po, %1, 128, pi;\n\t"
-        "selp.u32 %0, 1, 0, po;\n\t}"
-        : "=r"(r)
-        : "r"(1 + group), "r"((uint32_t)pred)
-        : "memory");
-    return r != 0;
-}
-
 __device__ __forceinline__ float sqrt_apx(float x) {
     float r;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -266,6 +251,8 @@ struct TcItem {
     int32_t pad_;
 };
 constexpr int kMaxTcBatch = 256;
+// Column tiles of (w, |y|^2) the producer may stage ahead of the epilogue.
+constexpr int kWnRing = 8;
 // Device memory of one batched launch's operands; a batch that needs more is
 // split into several launches (a single clustering always fits one).
 constexpr size_t kTcBatchBytes = size_t(16) << 30;
@@ -293,7 +280,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
            const float *__restrict__ a_norm, const int32_t *__restrict__ a_lab,
            const int64_t *__restrict__ a_out, int64_t nrows, const float *__restrict__ y_full,
            const float *__restrict__ y_il,
-           const float2 *__restrict__ y_wn, const int64_t *__restrict__ poff,
+           const float2 *__restrict__ y_wn, const float4 *__restrict__ y_wn4,
+           const int64_t *__restrict__ poff,
            const int64_t *__restrict__ sizes, int k, float tau, int dq,
            const double *__restrict__ w_own, float *__restrict__ s_out,
            float *__restrict__ a_out_v, float *__restrict__ b_out_v, double *__restrict__ W,
@@ -309,9 +297,12 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     __shared__ uint64_t bar_drain;      // the MMA issuer's last commit, after an abort
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
-    // (w, |y|^2) of the current tile's columns, two columns per float4 as
-    // (w_2i, w_2i+1, n_2i, n_2i+1) so that the epilogue reads lane pairs
-    __shared__ __align__(16) float4 sh_wn[C::SLOTS][2][TN / 2];
+    // (w, |y|^2) of the column tiles in flight: a ring of kWnRing tiles that the
+    // producer fills by bulk copies from y_wn4, two columns per float4 as
+    // (w_2i, w_2i+1, n_2i, n_2i+1) so that the epilogue reads lane pairs; a
+    // slot is refilled once every epilogue warp has released it
+    __shared__ __align__(16) float4 sh_wn[kWnRing][TN / 2];
+    __shared__ uint64_t bar_wnf[kWnRing], bar_wne[kWnRing];
 
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -396,6 +387,10 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 mbar_init(&bar_accf[g][a], 1);
                 mbar_init(&bar_acce[g][a], 4);
             }
+        for (int r = 0; r < kWnRing; ++r) {
+            mbar_init(&bar_wnf[r], 1);
+            mbar_init(&bar_wne[r], 4 * C::SLOTS);
+        }
         abort_flag = 0;
         fence_mbar_init();
     }
@@ -408,7 +403,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     uint32_t ld_issued = 0, ld_parity = 0;
     bool a_issued = false;
     uint32_t a_parity = 0;
-    static_assert(C::STAGES <= 32, "stage masks are 32-bit");
+    uint32_t wn_issued = 0, wn_parity = 0;    // the same for the (w, |y|^2) ring
+    static_assert(C::STAGES <= 32 && kWnRing <= 32, "stage masks are 32-bit");
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -422,6 +418,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             int stage = 0;
             uint32_t phase = 0;
             int64_t idx = 0;
+            uint64_t wt = 0;                      // column tiles staged into the ring so far
             for (int64_t it = 0; !abort_flag; ++it) {
                 const int64_t w = group_of(it);
                 if (w == -2) break;
@@ -466,6 +463,19 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         stage = 0;
                         phase ^= 1u;
                     }
+                    // this tile's (w, |y|^2) into ring slot ws, once every
+                    // epilogue warp has released the tile kWnRing earlier
+                    const int ws = (int)(wt % kWnRing);
+                    const uint32_t wpar = (uint32_t)((wt / kWnRing) & 1);
+                    if (wt >= (uint64_t)kWnRing && !mbar_wait(&bar_wne[ws], wpar ^ 1u, kWaitNs)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    mbar_expect_tx(&bar_wnf[ws], TN * 8);
+                    wn_issued |= 1u << ws;
+                    wn_parity = (wn_parity & ~(1u << ws)) | (wpar << ws);
+                    bulk_load(&sh_wn[ws][0], y_wn4 + (v.ccol + ct * TN) / 2, TN * 8, &bar_wnf[ws]);
+                    ++wt;
                 }
                 ++idx;
             }
@@ -566,7 +576,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
         const int et = threadIdx.x - 64 - 128 * g;
         const uint32_t tlane = (uint32_t)(32 * q) << 16;
         uint32_t acc = 0, acc_phase = 0;
-        int buf = 0;
+        uint64_t wt = 0;                         // column tiles consumed from the ring so far
         for (int64_t it = 0;; ++it) {
             const int64_t w = group_of(it);
             if (w == -2) break;
@@ -620,21 +630,12 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             RatioMin bmin;
             float accf = 0.f;                         // current cluster, this tile
             bool dead = false;
-            // (weight, |y|^2) of this thread's column, fetched one tile ahead
-            const float2 *ywn = y_wn + v.ccol;
-            const int64_t c_first = ct0 * TN + et;
-            float2 wn_next = (et < TN && c_first < mp) ? ywn[c_first] : make_float2(0.f, 0.f);
             for (int64_t ct = ct0; ct < ct_end; ++ct) {
-                const float2 wn_cur = wn_next;
-                const int64_t cn = (ct + 1) * TN + et;
-                if (et < TN) wn_next = (cn < mp) ? ywn[cn] : make_float2(0.f, 0.f);
-                if (et < TN) {
-                    float *f = reinterpret_cast<float *>(&sh_wn[g][buf][et >> 1]);
-                    f[et & 1] = wn_cur.x;
-                    f[2 + (et & 1)] = wn_cur.y;
-                }
-                const bool ok = !abort_flag && mbar_wait(&bar_accf[g][acc], acc_phase, kWaitNs);
-                if (epi_bar_any(g, !ok)) {      // also orders the sh_wn writes before the reads
+                // the tile's accumulator and its (w, |y|^2) in ring slot ws
+                const int ws = (int)(wt % kWnRing);
+                const bool ok = !abort_flag && mbar_wait(&bar_accf[g][acc], acc_phase, kWaitNs) &&
+                                mbar_wait(&bar_wnf[ws], (uint32_t)((wt / kWnRing) & 1), kWaitNs);
+                if (!__all_sync(0xffffffffu, ok)) {     // the warp stops as one
                     abort_flag = 1;
                     dead = true;
                     break;
@@ -669,7 +670,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     // SYM: own is uniform over the warp (one cluster per 32-row block)
                     const bool skip = SYM ? (!live || mine || c0 <= wblk)
                                           : (!live || __all_sync(0xffffffffu, mine));
-                    const float4 *wn4 = &sh_wn[g][buf][ch * 16];
+                    const float4 *wn4 = &sh_wn[ws][ch * 16];
                     float part = 0.f;
                     uint32_t flag = 0;
                     float cs0 = 0.f, cs1 = 0.f;           // SYM: column sums of the two halves
@@ -706,7 +707,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         // w d to its own lane.
                         const float *ycl = y_il + il_index(v.ccol + c0, 0, KD) + 4 * lane;
                         const float *fw = reinterpret_cast<const float *>(
-                            &sh_wn[g][buf][ch * 16 + (lane >> 1)]);
+                            &sh_wn[ws][ch * 16 + (lane >> 1)]);
                         const float wc = fw[lane & 1], nyc = fw[2 + (lane & 1)];
                         float colsum = 0.f;
                         part = 0.f;
@@ -762,7 +763,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                                 const int i = 4 * hh + ii;
                                 const float dot = __uint_as_float(i < 16 ? rr0[i] : rr1[i - 16]);
                                 const float *f = reinterpret_cast<const float *>(
-                                    &sh_wn[g][buf][ch * 16 + (i >> 1)]);
+                                    &sh_wn[ws][ch * 16 + (i >> 1)]);
                                 const float2 wn = make_float2(f[i & 1], f[2 + (i & 1)]);
                                 bool close;
                                 float dist;
@@ -797,7 +798,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                                     const float *yc = y_full + (v.ccol + c0 + i) * KD;
                                     const float dist = direct_dist_rows<METRIC, KD, kFullRows>(xh, xl, yc);
                                     const float wc = reinterpret_cast<const float *>(
-                                        &sh_wn[g][buf][ch * 16 + (i >> 1)])[i & 1];
+                                        &sh_wn[ws][ch * 16 + (i >> 1)])[i & 1];
                                     part = fmaf(wc, dist, part);
                                 }
                             }
@@ -854,7 +855,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                                 if (lane != pr[u]) continue;
                                 const float dist = (METRIC == SILH_EUCLIDEAN) ? sqrtf(ss[u]) : 0.5f * ss[u];
                                 const float wc = reinterpret_cast<const float *>(
-                                    &sh_wn[g][buf][ch * 16 + (pc[u] >> 1)])[pc[u] & 1];
+                                    &sh_wn[ws][ch * 16 + (pc[u] >> 1)])[pc[u] & 1];
                                 part = fmaf(wc, dist, part);
                             }
                         }
@@ -870,7 +871,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             __syncwarp();
                             const float dot = tmem_ld_32x1(tcol + ch * 32 + i);
                             const float *f = reinterpret_cast<const float *>(
-                                &sh_wn[g][buf][ch * 16 + (i >> 1)]);
+                                &sh_wn[ws][ch * 16 + (i >> 1)]);
                             const float2 wn = make_float2(f[i & 1], f[2 + (i & 1)]);
                             const float *yc = y_full + (v.ccol + c0 + i) * KD;
                             float dist;
@@ -896,10 +897,13 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 }
                 fence_before_sync();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&bar_acce[g][acc]);
+                if (lane == 0) {
+                    mbar_arrive(&bar_acce[g][acc]);
+                    mbar_arrive(&bar_wne[ws]);
+                }
                 acc = (acc + 1 == (uint32_t)C::NACC) ? 0u : acc + 1;
                 if (acc == 0) acc_phase ^= 1u;
-                buf ^= 1;
+                ++wt;
                 accd += (double)accf;                    // FP64 fold once per tile
                 accf = 0.f;
             }
@@ -949,6 +953,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             for (int st = 0; st < C::STAGES; ++st)
                 if ((ld_issued >> st) & 1u)
                     mbar_wait(&bar_full[st], (ld_parity >> st) & 1u, kWaitNs);
+            for (int r = 0; r < kWnRing; ++r)
+                if ((wn_issued >> r) & 1u) mbar_wait(&bar_wnf[r], (wn_parity >> r) & 1u, kWaitNs);
             if (a_issued) mbar_wait(&bar_afull, a_parity, kWaitNs);
         } else if (warp == 1 && lane == 0) {
             mma_commit(&bar_drain);
@@ -1434,7 +1440,8 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
                                  const int64_t *__restrict__ poff, int k, int64_t mp_max, int KD,
                                  int metric, const float *__restrict__ mu, float *__restrict__ full,
                                  void *__restrict__ hi, void *__restrict__ lo,
-                                 float2 *__restrict__ wn, float *__restrict__ il) {
+                                 float2 *__restrict__ wn, float *__restrict__ wn4,
+                                 float *__restrict__ il) {
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (i >= mp_max) return;
@@ -1456,7 +1463,10 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
             if (il != nullptr && c < KD) il[il_index(i, c, KD)] = 0.f;
             store_split<BF>(0.f, i, c, KD, hi, lo);
         }
-        if (lane == 0) wn[i] = make_float2(0.f, 0.f);
+        if (lane == 0) {
+            wn[i] = make_float2(0.f, 0.f);
+            if (wn4 != nullptr) wn4[(i >> 1) * 4 + (i & 1)] = wn4[(i >> 1) * 4 + 2 + (i & 1)] = 0.f;
+        }
         return;
     }
     const int64_t e = idx ? idx[t] : t;
@@ -1484,6 +1494,10 @@ __global__ void k_gather_cols_tc(const T *__restrict__ X, int d, int64_t ld,
         const float w = p ? (float)(1.0 / p[t]) : 1.0f;
         // Euclidean: squared norm of the (centred) column; cosine: 1, or 0 for a zero column
         wn[i] = make_float2(w, (metric == SILH_COSINE) ? (s > 0.f ? 1.f : 0.f) : ss);
+        if (wn4 != nullptr) {                    // (w_2i, w_2i+1, n_2i, n_2i+1) per column pair
+            wn4[(i >> 1) * 4 + (i & 1)] = wn[i].x;
+            wn4[(i >> 1) * 4 + 2 + (i & 1)] = wn[i].y;
+        }
     }
 }
 
@@ -1603,6 +1617,7 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
                       const float *a_lo, const float *a_il, const float *a_norm,
                       const int32_t *a_lab, const int64_t *a_out, int64_t nrows,
                       const float *y_full, const float *y_il, const float2 *y_wn,
+                      const float *y_wn4,
                       const int64_t *poff, const int64_t *sizes, int k, float tau, int dq,
                       int64_t max_cluster_cols, double *w_own, float *s, float *a, float *b,
                       double *W = nullptr, const OwnItem *own_items = nullptr,
@@ -1630,7 +1645,8 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
     if (groups == 0) return cudaSuccess;
     const int grid = (int)std::min<int64_t>(groups, nsm);
     kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_il, a_norm,
-                                                a_lab, a_out, nrows, y_full, y_il, y_wn, poff,
+                                                a_lab, a_out, nrows, y_full, y_il, y_wn,
+                                                reinterpret_cast<const float4 *>(y_wn4), poff,
                                                 sizes, k, tau, dq, w_own, s, a, b, W, sym_work,
                                                 n_sym_work, TcBatchArg<false>{});
     count_launches(1);
@@ -1647,7 +1663,7 @@ cudaError_t launch_tc_batched(int nsm, cudaStream_t stream, const CUtensorMap &a
                               const float *a_il, const float *a_norm, const int32_t *a_lab,
                               const int64_t *a_out,
                               const float *y_full, const float *y_il, const float2 *y_wn,
-                              const int64_t *poff,
+                              const float *y_wn4, const int64_t *poff,
                               float tau, int dq, const double *w_own,
                               const TcBatchArg<true> &bt) {
     using C = TcCfg<KD, SPLIT, BF, WIDE>;
@@ -1656,7 +1672,8 @@ cudaError_t launch_tc_batched(int nsm, cudaStream_t stream, const CUtensorMap &a
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(bt.total_work, nsm);
     kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_il, a_norm,
-                                                a_lab, a_out, 0, y_full, y_il, y_wn, poff, nullptr,
+                                                a_lab, a_out, 0, y_full, y_il, y_wn,
+                                                reinterpret_cast<const float4 *>(y_wn4), poff, nullptr,
                                                 0, tau, dq, w_own, nullptr, nullptr, nullptr,
                                                 nullptr, nullptr, 0, bt);
     count_launches(1);
@@ -1679,6 +1696,7 @@ struct TcOps {
     float *yf, *yil;
     uint8_t *yhi, *ylo;
     float2 *ywn;
+    float *ywn4;       // (w, |y|^2) in column pairs, whole 128-column tiles
     int64_t *poff;
 };
 
@@ -1744,7 +1762,7 @@ silh_status tc_prepare(const void *X, silh_dtype dtype, int64_t n, int32_t d, in
         o.rlo, o.rfull, o.ril, o.rn, o.lab, o.outi);                                            \
     k_gather_cols_tc<T, BFV><<<ceil_div_i(mp_pad, 8), 256, 0, stream>>>(                       \
         (const T *)X, d, ld, col_idx, col_p, offsets, o.poff, k, mp_pad, KD, metric, mu, o.yf,  \
-        o.yhi, o.ylo, o.ywn, o.yil);
+        o.yhi, o.ylo, o.ywn, o.ywn4, o.yil);
     if (dtype == SILH_F32) {
         if (bf) { SILH_TC_GATHER(float, true) } else { SILH_TC_GATHER(float, false) }
     } else {
@@ -1778,6 +1796,7 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     const int KE = bf ? 64 : KD;                  // operand row length (128 B per K block)
     const size_t ebytes = bf ? 2 : 4;
     const int64_t mp_max = m + 31 * (int64_t)k;   // padded columns, upper bound
+    const int64_t wn_cols = (mp_max + 127) / 128 * 128;
     int dev = 0, nsm = 0;
     double *w_own = nullptr;
     TcOps o = {};
@@ -1798,6 +1817,9 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     SILH_CK(sc.alloc(&o.yhi, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&o.ylo, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&o.ywn, (size_t)mp_max));
+    // the sweep stages whole 128-column tiles of (w, |y|^2): zeros past mp_max
+    SILH_CK(sc.alloc(&o.ywn4, (size_t)2 * wn_cols));
+    SILH_CK(cudaMemsetAsync(o.ywn4, 0, sizeof(float) * 2 * (size_t)wn_cols, stream));
     st = tc_prepare(X, dtype, n, d, ld, labels, k, metric, KD, bf, offsets, col_idx, col_p, m,
                     rows, nrows, nrows, mp_max, o, stream, d_m);
     if (st != SILH_OK) goto done;
@@ -1815,7 +1837,7 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
         SILH_CK((launch_tc<MET, KDV, SP, BFV>(                                                  \
             nsm, stream, m_ahi, m_alo, m_bhi, m_blo, BFV ? o.rfull : (const float *)o.rhi,     \
             BFV ? nullptr : (const float *)o.rlo, o.ril, o.rn, o.lab, o.outi, nrows, o.yf,      \
-            o.yil, o.ywn, o.poff, sizes, k, tau, (d + 3) / 4, max_cluster_cols, w_own, s, a, b))); \
+            o.yil, o.ywn, o.ywn4, o.poff, sizes, k, tau, (d + 3) / 4, max_cluster_cols, w_own, s, a, b))); \
     }
 #define SILH_TC_CASES(MET, KDV)             \
     SILH_TC_CASE(MET, KDV, true, false)     \
@@ -1902,6 +1924,7 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
         SILH_CK(gs.alloc(&g.yhi, (size_t)cols_total * KE * ebytes));
         SILH_CK(gs.alloc(&g.ylo, (size_t)cols_total * KE * ebytes));
         SILH_CK(gs.alloc(&g.ywn, (size_t)cols_total));
+        SILH_CK(gs.alloc(&g.ywn4, (size_t)2 * cols_total));   // whole tiles, all written
         {
             int64_t ccol = 0, pbase = 0;
             for (int c = 0; c < nb; ++c) {
@@ -1921,6 +1944,7 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
                 o.yhi = g.yhi + ccol * KE * ebytes;
                 o.ylo = g.ylo + ccol * KE * ebytes;
                 o.ywn = g.ywn + ccol;
+                o.ywn4 = g.ywn4 + 2 * ccol;
                 o.poff = g.poff + pbase;
                 st = tc_prepare(X, dtype, n, d, ld, src.labels, S->k, metric, KD, bf, S->offsets,
                                 S->idx, S->p, S->size, nullptr, n, rows_pad, mp_pad, o, stream);
@@ -1964,7 +1988,7 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
             SILH_CK((launch_tc_batched<MET, KDV, SP, BFV, WV>(                                  \
                 nsm, stream, m_ahi, m_alo, m_bhi, m_blo,                                        \
                 BFV ? g.rfull : (const float *)g.rhi, BFV ? nullptr : (const float *)g.rlo,     \
-                g.ril, g.rn, g.lab, g.outi, g.yf, g.yil, g.ywn, g.poff, tau, (d + 3) / 4, w_own, \
+                g.ril, g.rn, g.lab, g.outi, g.yf, g.yil, g.ywn, g.ywn4, g.poff, tau, (d + 3) / 4, w_own, \
                 bt)));                                                                          \
         }
 #define SILH_TC_BCASE(MET, KDV, SP, BFV) SILH_TC_BCASE_W(MET, KDV, SP, BFV, wide_tiles(KDV, BFV))
@@ -2021,6 +2045,8 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     std::vector<int4> h_work;
     uint8_t *yhi = nullptr, *ylo = nullptr;
     float2 *ywn = nullptr;
+    float *ywn4 = nullptr;
+    const int64_t wn_cols = (mp_max + 127) / 128 * 128;
     CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
     const float tau = 0.25f;
 
@@ -2036,6 +2062,8 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     SILH_CK(sc.alloc(&yhi, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&ylo, (size_t)mp_max * KE * ebytes));
     SILH_CK(sc.alloc(&ywn, (size_t)mp_max));
+    SILH_CK(sc.alloc(&ywn4, (size_t)2 * wn_cols));     // whole tiles: zeros past mp_max
+    SILH_CK(cudaMemsetAsync(ywn4, 0, sizeof(float) * 2 * (size_t)wn_cols, stream));
     SILH_CK(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)mp_max * k, stream));
     {   // own-cluster tile pairs (I <= J) over each cluster's padded range
         const int64_t T = (KD == 32) ? 256 : 128;
@@ -2073,7 +2101,7 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
 #define SILH_TC_GATHER_SYM(T, BFV)                                                              \
     k_gather_cols_tc<T, BFV><<<ceil_div_i(mp_max, 8), 256, 0, stream>>>(                       \
         (const T *)X, d, ld, order, nullptr, coff, poff, k, mp_max, KD, metric, mu, yf, yhi,    \
-        ylo, ywn, yil);
+        ylo, ywn, ywn4, yil);
     if (dtype == SILH_F32) {
         if (bf) { SILH_TC_GATHER_SYM(float, true) } else { SILH_TC_GATHER_SYM(float, false) }
     } else {
@@ -2118,7 +2146,7 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     if (metric == MET && KD == KDV && split == SP && bf == BFV) {                              \
         SILH_CK((launch_tc<MET, KDV, SP, BFV, true>(                                            \
             nsm, stream, m_ahi, m_alo, m_bhi, m_blo, yf, nullptr, yil, rn, plab, outi, mp_max, yf, \
-            yil, ywn, poff, sizes, k, tau, (d + 3) / 4, 0, nullptr, nullptr, nullptr, nullptr, W, \
+            yil, ywn, ywn4, poff, sizes, k, tau, (d + 3) / 4, 0, nullptr, nullptr, nullptr, nullptr, W, \
             own_items, (int64_t)h_items.size(), sym_work, (int64_t)h_work.size())));            \
     }
 #define SILH_TC_SYM_CASES(MET, KDV)             \
