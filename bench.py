@@ -380,9 +380,11 @@ def roofline(res, peaks, peak_kind):
     dom = max(mean_p2, key=mean_p2.get)
     S = res["info"]["sample_size"][dom]
     pairs = res["n"] * S
+    clock = peaks.get("sm_max_mhz", 2032.0)
+    if PREC[dom] != "fp32":
+        return dom, roofline_tc(dom, d, pairs, mean_p2[dom], peaks, clock, peak_kind)
     ops = pairs * per_pair[dom]
     achieved = ops / (mean_p2[dom] * 1e-3) / 1e9          # Gop/s
-    clock = peaks.get("sm_max_mhz", 2032.0)
     peak = 148 * 128 * clock * 1e6 / 1e9                   # FP32 lanes x clock
     traffic = _profiled_traffic(f"k_sweep_{dom}") if res["n"] == WORKLOAD["n"] else None
     out = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
@@ -401,6 +403,33 @@ def roofline(res, peaks, peak_kind):
         out["naive_reciprocal_bound_pairs_per_s"] = round(mufu_bound, 1)
         out["vs_naive_reciprocal_bound"] = round(pair_rate / mufu_bound, 4)
     return dom, out
+
+
+def roofline_tc(dom, d, pairs, ms, peaks, clock, peak_kind):
+    """A Phase-2 leg on the tensor cores (only when Manhattan and Canberra are
+    not timed).  Euclidean: one square root per pair on the MUFU pipe (16 per
+    clock per SM) is the bound.  Cosine: the inner products, 2d flops per pair
+    (the method's count; split TF32 executes three MMAs per product, reported
+    as impl_*), against the TF32 dense peak taken as the measured BF16 burst
+    times the nominal TF32 / BF16 ratio (1.1 / 2.25)."""
+    rate = pairs / (ms * 1e-3)
+    if dom == "euclidean":
+        peak = 148 * 16 * clock * 1e6 / 1e9
+        return {"bound": "alu", "achieved": round(rate / 1e9, 1), "peak": round(peak, 1),
+                "unit": "Gop/s", "frac": round(rate / 1e9 / peak, 4), "traffic": None,
+                "kernel": "k_sweep_tc (euclidean, Phase 2, split TF32)",
+                "work": "n |S| square roots (one per pair)",
+                "peak_source": f"148 SMs x 16 MUFU lanes x {clock:.0f} MHz ({peak_kind} clock)"}
+    kd = 32 if d <= 32 else 64
+    peak = peaks.get("bf16_tflops", 1800.0) * 1.1 / 2.25
+    ach = rate * 2 * d / 1e12
+    return {"bound": "tensor", "achieved": round(ach, 2), "peak": round(peak, 1),
+            "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+            "kernel": "k_sweep_tc (cosine, Phase 2, split TF32)",
+            "work": "n |S| x 2d flops (the inner products)",
+            "peak_source": "TF32 dense = measured BF16 burst x 1.1 / 2.25 (nominal ratio)",
+            "impl_achieved": round(rate * 3 * 2 * kd / 1e12, 2),
+            "impl_frac": round(rate * 3 * 2 * kd / 1e12 / peak, 4)}
 
 
 def run_batching(args, emit=True):
