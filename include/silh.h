@@ -122,6 +122,11 @@ silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t n, int32_t 
  *   a_hat = W_hat_C(e)/(|C|-1), b_hat = min_{j != C} W_hat_j(e)/|Cj|,
  *   s_hat = (b_hat - a_hat)/max(a_hat, b_hat)   (Eq. 8); singleton -> 0.
  * Outputs are FP32 arrays of nrows entries; a_hat and b_hat may be NULL.
+ * nb (may be NULL): int32 array of nrows entries, the neighbouring cluster --
+ * the j != C that attains b_hat (the cluster Example 1 names as giving b(e)),
+ * the lowest such j among equal ratios; -1 for a row whose label is invalid.
+ * Where two clusters' ratios differ by less than the arithmetic's error the
+ * choice between them follows the evaluated ratios.
  * Per-cluster sums are carried in FP64 across column tiles.
  * S must describe a sample of this clustering (sizes, offsets, idx, p).
  * Asynchronous.  Errors: SILH_EINVAL for bad sizes/pointers.  A label outside
@@ -129,7 +134,7 @@ silh_status silh_sample_pps(const void *X, silh_dtype dtype, int64_t n, int32_t 
 silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                           const int32_t *labels, int32_t k, silh_metric metric, silh_prec prec,
                           const silh_sample *S, const int64_t *rows, int64_t nrows,
-                          float *s_hat, float *a_hat, float *b_hat, void *stream);
+                          float *s_hat, float *a_hat, float *b_hat, int32_t *nb, void *stream);
 
 /* Phase 1 of Algorithm 1, as silh_sample_pps, with no host synchronisation: the
  * whole phase is enqueued on stream and the call returns at once, so a request
@@ -165,7 +170,7 @@ silh_status silh_estimate_async(const void *X, silh_dtype dtype, int64_t n, int3
                                 const int32_t *labels, int32_t k, silh_metric metric,
                                 silh_prec prec, const silh_sample *S, const int64_t *d_size,
                                 const int64_t *rows, int64_t nrows, float *s_hat, float *a_hat,
-                                float *b_hat, void *stream);
+                                float *b_hat, int32_t *nb, void *stream);
 
 /* Phase 2 of Algorithm 1 (Eq. 8) for the cosine distance in O(n k d): with unit
  * vectors d_cos = 1 - <x^, y^> = 0.5 |x^ - y^|^2 (the cosine distance of
@@ -184,7 +189,7 @@ silh_status silh_estimate_cosine_collapsed(const void *X, silh_dtype dtype, int6
                                            int64_t ld, const int32_t *labels, int32_t k,
                                            const silh_sample *S, const int64_t *rows,
                                            int64_t nrows, float *s_hat, float *a_hat,
-                                           float *b_hat, void *stream);
+                                           float *b_hat, int32_t *nb, void *stream);
 
 /* Limits of silh_estimate_noalloc's fixed scratch (8.5 MiB per device). */
 #define SILH_NOALLOC_MAX_COLUMNS 65536
@@ -222,7 +227,7 @@ silh_status silh_estimate_noalloc(const void *X, silh_dtype dtype, int64_t n, in
                                   int64_t ld, const int32_t *labels, int32_t k,
                                   silh_metric metric, silh_prec prec, const silh_sample *S,
                                   const int64_t *rows, int64_t nrows, float *s_hat, float *a_hat,
-                                  float *b_hat, void *stream);
+                                  float *b_hat, int32_t *nb, void *stream);
 
 /* One clustering of the dataset in a batched call: its labels, its sample set
  * (from silh_sample_pps on these labels) and its FP32 output of n s_hat values. */
@@ -258,12 +263,12 @@ silh_status silh_estimate_batched(const void *X, silh_dtype dtype, int64_t n, in
                                   const silh_batch_item *items, int32_t variant, void *stream);
 
 /* Exact silhouette (Eq. 1-2) of the listed rows against all n elements:
- * Phase 2 with F_Cj = Cj and p = 1.  Synchronising (validates labels).
- * Errors: as silh_sample_pps. */
+ * Phase 2 with F_Cj = Cj and p = 1; nb (may be NULL) as for silh_estimate.
+ * Synchronising (validates labels).  Errors: as silh_sample_pps. */
 silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld,
                        const int32_t *labels, int32_t k, silh_metric metric, silh_prec prec,
                        const int64_t *rows, int64_t nrows, float *s, float *a, float *b,
-                       void *stream);
+                       int32_t *nb, void *stream);
 
 /* Cohesion and separation of the clustering estimated from the Phase-2 weights
  * (the paper's section on other clustering validation measures):

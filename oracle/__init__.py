@@ -64,7 +64,7 @@ def _load():
         lib.orc_cluster_sizes.argtypes = [_i32p, ctypes.c_int64, ctypes.c_int, _i64p]
         lib.orc_cluster_sizes.restype = ctypes.c_int
         lib.orc_exact.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, _i32p, ctypes.c_int,
-                                  ctypes.c_int, _i64p, ctypes.c_int64, _f64p, _f64p, _f64p]
+                                  ctypes.c_int, _i64p, ctypes.c_int64, _f64p, _f64p, _f64p, _i32p]
         lib.orc_exact.restype = ctypes.c_int
         lib.orc_poisson_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                          ctypes.c_int64, _f64p, _u8p]
@@ -79,7 +79,7 @@ def _load():
         lib.orc_build_sample.restype = ctypes.c_int64
         lib.orc_estimate.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, _i32p, ctypes.c_int,
                                      ctypes.c_int, _i64p, _i64p, _f64p, _i64p, ctypes.c_int64,
-                                     _f64p, _f64p, _f64p, _f64p]
+                                     _f64p, _f64p, _f64p, _f64p, _i32p]
         lib.orc_estimate.restype = ctypes.c_int
         lib.orc_cohsep.argtypes = [_f64p, _i32p, ctypes.c_int64, ctypes.c_int, _f64p, _f64p]
         lib.orc_cohsep.restype = ctypes.c_int
@@ -151,18 +151,21 @@ def _rows(rows, n):
     return rows, rows.shape[0]
 
 
-def exact(X, labels, k, metric, rows=None):
-    """Exact s(e), a(e), b(e) (Eq. 1-2) for the listed rows."""
+def exact(X, labels, k, metric, rows=None, want_nb=False):
+    """Exact s(e), a(e), b(e) (Eq. 1-2) for the listed rows (and the
+    neighbouring cluster, the j attaining b, with want_nb)."""
     X = _f64(X)
     labels = np.ascontiguousarray(labels, dtype=np.int32)
     n, d = X.shape
     rows, nr = _rows(rows, n)
     s = np.empty(nr); a = np.empty(nr); b = np.empty(nr)
+    nb = np.empty(nr, dtype=np.int32) if want_nb else None
     rc = _load().orc_exact(_p(X, _f64p), n, d, _p(labels, _i32p), k, _metric(metric),
-                           _p(rows, _i64p), nr, _p(s, _f64p), _p(a, _f64p), _p(b, _f64p))
+                           _p(rows, _i64p), nr, _p(s, _f64p), _p(a, _f64p), _p(b, _f64p),
+                           _p(nb, _i32p))
     if rc != 0:
         raise ValueError("invalid arguments")
-    return s, a, b
+    return (s, a, b, nb) if want_nb else (s, a, b)
 
 
 def poisson_draw(seed, stream, cid, prob):
@@ -228,8 +231,9 @@ def build_sample(labels, k, in_f, p):
     return offsets, idx[:size].copy(), ps[:size].copy()
 
 
-def estimate(X, labels, k, metric, offsets, idx, ps, rows=None, want_w=False):
-    """Algorithm 1, Phase 2: s_hat, a_hat, b_hat (and W_hat if want_w)."""
+def estimate(X, labels, k, metric, offsets, idx, ps, rows=None, want_w=False, want_nb=False):
+    """Algorithm 1, Phase 2: s_hat, a_hat, b_hat (then W_hat if want_w, then the
+    neighbouring cluster if want_nb)."""
     X = _f64(X)
     labels = np.ascontiguousarray(labels, dtype=np.int32)
     n, d = X.shape
@@ -239,13 +243,14 @@ def estimate(X, labels, k, metric, offsets, idx, ps, rows=None, want_w=False):
     rows, nr = _rows(rows, n)
     s = np.empty(nr); a = np.empty(nr); b = np.empty(nr)
     W = np.empty((nr, k)) if want_w else None
+    nb = np.empty(nr, dtype=np.int32) if want_nb else None
     rc = _load().orc_estimate(_p(X, _f64p), n, d, _p(labels, _i32p), k, _metric(metric),
                               _p(offsets, _i64p), _p(idx, _i64p), _p(ps, _f64p),
                               _p(rows, _i64p), nr, _p(s, _f64p), _p(a, _f64p), _p(b, _f64p),
-                              _p(W, _f64p))
+                              _p(W, _f64p), _p(nb, _i32p))
     if rc != 0:
         raise ValueError("invalid arguments")
-    return (s, a, b, W) if want_w else (s, a, b)
+    return (s, a, b) + ((W,) if want_w else ()) + ((nb,) if want_nb else ())
 
 
 def cohsep(W, labels, k):

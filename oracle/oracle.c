@@ -153,28 +153,28 @@ int orc_cluster_sizes(const int32_t *labels, int64_t n, int k, int64_t *sizes)
 }
 
 /* s(e) from the k cluster weights W_j(e) of an element in cluster c (Eq. 1-2
- * with Eq. 4): a = W_c/(|C|-1), b = min_{j != c} W_j/|Cj|; singleton -> 0. */
+ * with Eq. 4): a = W_c/(|C|-1), b = min_{j != c} W_j/|Cj|; singleton -> 0.
+ * nb: the neighbouring cluster, the j != c attaining b (Example 1 names it
+ * for e14), the lowest such j among equal ratios. */
 static void orc_silhouette_from_weights(const double *W, const int64_t *sizes, int k, int c,
-                                        double *s, double *a, double *b)
+                                        double *s, double *a, double *b, int *nb)
 {
-    if (sizes[c] == 1) {
-        *s = 0.0; *a = 0.0;
-        double bmin = INFINITY;
-        for (int j = 0; j < k; ++j)
-            if (j != c && W[j] / (double)sizes[j] < bmin) bmin = W[j] / (double)sizes[j];
-        *b = bmin;
-        return;
-    }
-    double av = W[c] / (double)(sizes[c] - 1);
     double bv = INFINITY;
+    int arg = -1;
     for (int j = 0; j < k; ++j) {
         if (j == c) continue;
         double v = W[j] / (double)sizes[j];
-        if (v < bv) bv = v;
+        if (v < bv) { bv = v; arg = j; }
     }
+    *b = bv;
+    *nb = arg;
+    if (sizes[c] == 1) {
+        *s = 0.0; *a = 0.0;
+        return;
+    }
+    double av = W[c] / (double)(sizes[c] - 1);
     double m = av > bv ? av : bv;
     *a = av;
-    *b = bv;
     *s = (m > 0.0) ? (bv - av) / m : 0.0;
 }
 
@@ -183,7 +183,7 @@ static void orc_silhouette_from_weights(const double *W, const int64_t *sizes, i
 /* Exact silhouette (Eq. 1-2) of the listed rows (rows == NULL: all n).
  * W_j(e) = sum over every e' with label j of d(e, e'), e' ascending. */
 int orc_exact(const double *X, int64_t n, int d, const int32_t *labels, int k, int metric,
-              const int64_t *rows, int64_t nrows, double *s, double *a, double *b)
+              const int64_t *rows, int64_t nrows, double *s, double *a, double *b, int32_t *nb)
 {
     int64_t *sizes = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
     if (orc_cluster_sizes(labels, n, k, sizes) != 0 || d < 1) { free(sizes); return -1; }
@@ -200,10 +200,12 @@ int orc_exact(const double *X, int64_t n, int d, const int32_t *labels, int k, i
             for (int64_t f = 0; f < n; ++f)
                 W[labels[f]] = W[labels[f]] + orc_dist(metric, X + e * d, X + f * d, d);
             double sv, av, bv;
-            orc_silhouette_from_weights(W, sizes, k, labels[e], &sv, &av, &bv);
+            int nv;
+            orc_silhouette_from_weights(W, sizes, k, labels[e], &sv, &av, &bv, &nv);
             s[r] = sv;
             if (a) a[r] = av;
             if (b) b[r] = bv;
+            if (nb) nb[r] = nv;
         }
         free(W);
     }
@@ -330,11 +332,12 @@ int64_t orc_build_sample(const int32_t *labels, int64_t n, int k, const uint8_t 
 
 /* Algorithm 1, Phase 2 for the listed rows (rows == NULL: all n):
  * W_hat_j(e) = sum_{e' in F_j} d(e, e') / p_{e'}, then a_hat, b_hat, s_hat.
- * w_hat (nullable) receives the nrows x k estimated weights. */
+ * w_hat (nullable) receives the nrows x k estimated weights, nb (nullable) the
+ * neighbouring cluster of each row. */
 int orc_estimate(const double *X, int64_t n, int d, const int32_t *labels, int k, int metric,
                  const int64_t *offsets, const int64_t *idx, const double *ps,
                  const int64_t *rows, int64_t nrows, double *s, double *a, double *b,
-                 double *w_hat)
+                 double *w_hat, int32_t *nb)
 {
     int64_t *sizes = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
     if (orc_cluster_sizes(labels, n, k, sizes) != 0 || d < 1) { free(sizes); return -1; }
@@ -355,10 +358,12 @@ int orc_estimate(const double *X, int64_t n, int d, const int32_t *labels, int k
                 if (w_hat) w_hat[r * k + j] = acc;
             }
             double sv, av, bv;
-            orc_silhouette_from_weights(W, sizes, k, labels[e], &sv, &av, &bv);
+            int nv;
+            orc_silhouette_from_weights(W, sizes, k, labels[e], &sv, &av, &bv, &nv);
             s[r] = sv;
             if (a) a[r] = av;
             if (b) b[r] = bv;
+            if (nb) nb[r] = nv;
         }
         free(W);
     }

@@ -93,14 +93,18 @@ void ensure_pool_retains(int device);
 // division per cluster: a candidate (acc, size) replaces the best (bacc, bsz)
 // when acc * bsz < bacc * size (sizes are positive; each product is rounded
 // once), and the minimum itself is formed once, bacc / bsz.  Ties keep the
-// lower cluster index.  FP64 division is many times the cost of a multiply.
+// lower cluster index (clusters are offered in increasing order), which is
+// kept as the neighbouring cluster.  FP64 division is many times the cost of
+// a multiply.
 struct RatioMin {
     double acc, size;
-    __device__ __forceinline__ RatioMin() : acc(INFINITY), size(1.0) {}
-    __device__ __forceinline__ void add(double a, double sz) {
+    int arg;
+    __device__ __forceinline__ RatioMin() : acc(INFINITY), size(1.0), arg(-1) {}
+    __device__ __forceinline__ void add(double a, double sz, int j) {
         if (a * size < acc * sz) {
             acc = a;
             size = sz;
+            arg = j;
         }
     }
     __device__ __forceinline__ double value() const { return acc / size; }

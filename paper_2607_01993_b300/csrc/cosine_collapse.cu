@@ -131,7 +131,8 @@ k_collapse_rows(const T *__restrict__ X, int d, int64_t ld, int64_t n,
                 const double *__restrict__ Sw,
                 const double *__restrict__ Zw, const double *__restrict__ Rw,
                 const int64_t *__restrict__ rows, int64_t nrows, float *__restrict__ s_out,
-                float *__restrict__ a_out, float *__restrict__ b_out) {
+                float *__restrict__ a_out, float *__restrict__ b_out,
+                int32_t *__restrict__ nb_out) {
     constexpr int CH = (D <= 32) ? 64 : 16;
     __shared__ __align__(16) float sh_hi[CH * D];
     __shared__ __align__(16) float sh_lo[CH * D];
@@ -165,6 +166,7 @@ k_collapse_rows(const T *__restrict__ X, int d, int64_t ld, int64_t n,
     // every term below is non-negative and carries a few FP32 roundings, so
     // W_hat_j and its ratio to |C_j| stay FP32; a_hat, b_hat, s_hat are FP64
     float wown = 0.f, bmin = INFINITY;
+    int barg = -1;                          // neighbouring cluster (lowest j on ties)
     for (int j0 = 0; j0 < k; j0 += CH) {
         const int nb = min(CH, k - j0);
         __syncthreads();
@@ -198,7 +200,10 @@ k_collapse_rows(const T *__restrict__ X, int d, int64_t ld, int64_t n,
             const float dist = (acc0.x + acc0.y) + (acc1.x + acc1.y);
             const float w = zero ? sh_all[q] : fmaf(sh_s[q], dist, sh_c[q]);
             if (j0 + q == own) wown = w;
-            else bmin = fminf(bmin, w * sh_inv[q]);
+            else if (w * sh_inv[q] < bmin) {
+                bmin = w * sh_inv[q];
+                barg = j0 + q;
+            }
         }
     }
     if (rr >= nrows) return;
@@ -217,20 +222,21 @@ k_collapse_rows(const T *__restrict__ X, int d, int64_t ld, int64_t n,
     s_out[rr] = sv;
     if (a_out) a_out[rr] = av;
     if (b_out) b_out[rr] = bv;
+    if (nb_out) nb_out[rr] = (own < 0) ? -1 : barg;
 }
 
 template <class T>
 void launch_rows(int D, cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
                  const int32_t *labels, int k, const int64_t *sizes, const float *nmu_hi,
                  const float *nmu_lo, const double *Sw, const double *Zw, const double *Rw, const int64_t *rows,
-                 int64_t nrows, float *s, float *a, float *b) {
+                 int64_t nrows, float *s, float *a, float *b, int32_t *nb) {
     const int grid = (int)((nrows + kRowThreads - 1) / kRowThreads);
     switch (D) {
-        case 8: k_collapse_rows<T, 8><<<grid, kRowThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, nmu_hi, nmu_lo, Sw, Zw, Rw, rows, nrows, s, a, b); break;
-        case 16: k_collapse_rows<T, 16><<<grid, kRowThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, nmu_hi, nmu_lo, Sw, Zw, Rw, rows, nrows, s, a, b); break;
-        case 32: k_collapse_rows<T, 32><<<grid, kRowThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, nmu_hi, nmu_lo, Sw, Zw, Rw, rows, nrows, s, a, b); break;
-        case 64: k_collapse_rows<T, 64><<<grid, kRowThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, nmu_hi, nmu_lo, Sw, Zw, Rw, rows, nrows, s, a, b); break;
-        default: k_collapse_rows<T, 128><<<grid, kRowThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, nmu_hi, nmu_lo, Sw, Zw, Rw, rows, nrows, s, a, b); break;
+        case 8: k_collapse_rows<T, 8><<<grid, kRowThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, nmu_hi, nmu_lo, Sw, Zw, Rw, rows, nrows, s, a, b, nb); break;
+        case 16: k_collapse_rows<T, 16><<<grid, kRowThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, nmu_hi, nmu_lo, Sw, Zw, Rw, rows, nrows, s, a, b, nb); break;
+        case 32: k_collapse_rows<T, 32><<<grid, kRowThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, nmu_hi, nmu_lo, Sw, Zw, Rw, rows, nrows, s, a, b, nb); break;
+        case 64: k_collapse_rows<T, 64><<<grid, kRowThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, nmu_hi, nmu_lo, Sw, Zw, Rw, rows, nrows, s, a, b, nb); break;
+        default: k_collapse_rows<T, 128><<<grid, kRowThreads, 0, stream>>>(X, d, ld, n, labels, k, sizes, nmu_hi, nmu_lo, Sw, Zw, Rw, rows, nrows, s, a, b, nb); break;
     }
     count_launches(1);
 }
@@ -243,7 +249,7 @@ using namespace silh;
 extern "C" silh_status silh_estimate_cosine_collapsed(
         const void *X, silh_dtype dtype, int64_t n, int32_t d, int64_t ld, const int32_t *labels,
         int32_t k, const silh_sample *S, const int64_t *rows, int64_t nrows, float *s_hat,
-        float *a_hat, float *b_hat, void *stream_) {
+        float *a_hat, float *b_hat, int32_t *nb, void *stream_) {
     cudaStream_t stream = (cudaStream_t)stream_;
     silh_status st = SILH_OK;
     Scratch sc(stream);
@@ -265,6 +271,7 @@ extern "C" silh_status silh_estimate_cosine_collapsed(
     SILH_DEVPTR(s_hat, "s_hat");
     SILH_DEVPTR_OPT(a_hat, "a_hat");
     SILH_DEVPTR_OPT(b_hat, "b_hat");
+    SILH_DEVPTR_OPT(nb, "neighbour");
     SILH_DEVPTR_OPT(rows, "rows");
     if (rows == nullptr) nrows = n;
     SILH_REQ(nrows >= 0, "nrows < 0");
@@ -289,11 +296,11 @@ extern "C" silh_status silh_estimate_cosine_collapsed(
     if (nrows > 0) {
         if (dtype == SILH_F32)
             launch_rows<float>(D, stream, (const float *)X, d, ld, n, labels, k, S->sizes, nmu_hi, nmu_lo,
-                               Sw, Zw, Rw, rows, nrows, s_hat, a_hat, b_hat);
+                               Sw, Zw, Rw, rows, nrows, s_hat, a_hat, b_hat, nb);
         else
             launch_rows<__nv_bfloat16>(D, stream, (const __nv_bfloat16 *)X, d, ld, n, labels, k,
                                        S->sizes, nmu_hi, nmu_lo, Sw, Zw, Rw, rows, nrows, s_hat,
-                                       a_hat, b_hat);
+                                       a_hat, b_hat, nb);
         SILH_CK(cudaGetLastError());
     }
 done:

@@ -301,7 +301,7 @@ __device__ __forceinline__ void sweep_rows(
         const float *__restrict__ wY, const float *__restrict__ zY,
         const unsigned *__restrict__ crange, const int64_t *__restrict__ rows, int64_t nrows,
         float *__restrict__ s_out,
-        float *__restrict__ a_out, float *__restrict__ b_out,
+        float *__restrict__ a_out, float *__restrict__ b_out, int32_t *__restrict__ nb_out,
         double *__restrict__ wown_out = nullptr, double *__restrict__ wsep_out = nullptr) {
     __shared__ __align__(16) float sh_y[BN * D];
     __shared__ __align__(16) float sh_ya[METRIC == SILH_CANBERRA ? BN * D : 4];
@@ -432,7 +432,7 @@ __device__ __forceinline__ void sweep_rows(
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             if (j == own[r]) wown[r] = accd[r];
-            else bmin[r].add(accd[r], csz);
+            else bmin[r].add(accd[r], csz, j);
             if (j > own[r]) wsep[r] += accd[r];
         }
     }
@@ -454,6 +454,7 @@ __device__ __forceinline__ void sweep_rows(
         if (s_out) s_out[rr] = sv;
         if (a_out) a_out[rr] = av;
         if (b_out) b_out[rr] = bv;
+        if (nb_out) nb_out[rr] = (own[r] < 0) ? -1 : bmin[r].arg;
         if (wown_out) wown_out[rr] = (own[r] >= 0) ? wown[r] : 0.0;
         if (wsep_out) wsep_out[rr] = (own[r] >= 0) ? wsep[r] : 0.0;
     }
@@ -470,7 +471,7 @@ k_sweep_cohsep(const T *__restrict__ X, int d, int64_t ld, int64_t n,
                double *__restrict__ wsep) {
     sweep_rows<T, METRIC, D, RPT, BN>((int64_t)blockIdx.x * kThreads * RPT, X, d, ld, n, labels, k,
                                       sizes, offsets, Y, wY, zY, crange, nullptr, n, nullptr,
-                                      nullptr, nullptr, wown, wsep);
+                                      nullptr, nullptr, nullptr, wown, wsep);
 }
 
 // Coh = (1/2) sum wown / sum_j C(|Cj|,2), Sep = sum wsep / sum_{j1<j2} |Cj1||Cj2|
@@ -518,11 +519,12 @@ k_sweep(const T *__restrict__ X, int d, int64_t ld, int64_t n, const int32_t *__
         int k, const int64_t *__restrict__ sizes, const int64_t *__restrict__ offsets,
         const float *__restrict__ Y, const float *__restrict__ wY, const float *__restrict__ zY,
         const unsigned *__restrict__ crange, const int64_t *__restrict__ rows, int64_t nrows,
-        float *__restrict__ s_out, float *__restrict__ a_out, float *__restrict__ b_out) {
+        float *__restrict__ s_out, float *__restrict__ a_out, float *__restrict__ b_out,
+        int32_t *__restrict__ nb_out) {
     if (METRIC == SILH_CANBERRA && canb_tiny_data(crange, canb_scale(crange)) != TINY) return;
     sweep_rows<T, METRIC, D, RPT, BN, TINY>((int64_t)blockIdx.x * kThreads * RPT, X, d, ld, n, labels, k,
                                       sizes, offsets, Y, wY, zY, crange, rows, nrows, s_out, a_out,
-                                      b_out);
+                                      b_out, nb_out);
 }
 
 template <class T, int METRIC>
@@ -595,7 +597,7 @@ k_sweep_batched(const __grid_constant__ BatchParams bp, const T *__restrict__ X,
         sweep_rows<T, METRIC, D, RPT, BN>(rt * kThreads * RPT, X, d, ld, n, it.labels, it.k,
                                           it.sizes, it.offsets, Y + it.col_base * D,
                                           wY + it.col_base, zY + it.col_base, crange, nullptr, n,
-                                          it.s_out, nullptr, nullptr);
+                                          it.s_out, nullptr, nullptr, nullptr);
     }
 }
 
@@ -712,16 +714,17 @@ template <class T, int METRIC, int D>
 void launch_sweep(cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
                   const int32_t *labels, int k, const int64_t *sizes, const int64_t *offsets,
                   const float *Y, const float *wY, const float *zY, const unsigned *crange,
-                  const int64_t *rows, int64_t nrows, float *s, float *a, float *b) {
+                  const int64_t *rows, int64_t nrows, float *s, float *a, float *b,
+                  int32_t *nb) {
     constexpr int RPT = (D <= 32) ? 2 : 1;
     constexpr int BN = (D <= 32) ? 64 : 32;
     int grid = (int)((nrows + kThreads * RPT - 1) / (kThreads * RPT));
     k_sweep<T, METRIC, D, RPT, BN, false><<<grid, kThreads, 0, stream>>>(
-        X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, rows, nrows, s, a, b);
+        X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, rows, nrows, s, a, b, nb);
     count_launches(1);
     if (METRIC == SILH_CANBERRA) {
         k_sweep<T, METRIC, D, RPT, BN, METRIC == SILH_CANBERRA><<<grid, kThreads, 0, stream>>>(
-            X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, rows, nrows, s, a, b);
+            X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, rows, nrows, s, a, b, nb);
         count_launches(1);
     }
 }
@@ -730,11 +733,12 @@ template <class T, int METRIC>
 void launch_sweep_d(int D, cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
                     const int32_t *labels, int k, const int64_t *sizes, const int64_t *offsets,
                     const float *Y, const float *wY, const float *zY, const unsigned *crange,
-                    const int64_t *rows, int64_t nrows, float *s, float *a, float *b) {
+                    const int64_t *rows, int64_t nrows, float *s, float *a, float *b,
+                    int32_t *nb) {
 #define SILH_SWEEP_D(DD)                                                                      \
     case DD:                                                                                  \
         launch_sweep<T, METRIC, DD>(stream, X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, \
-                                    crange, rows, nrows, s, a, b);                          \
+                                    crange, rows, nrows, s, a, b, nb);                      \
         break;
     switch (D) {
         SILH_SWEEP_D(8)
@@ -752,23 +756,23 @@ void launch_sweep_m(int metric, int D, cudaStream_t stream, const T *X, int d, i
                     int64_t n, const int32_t *labels, int k, const int64_t *sizes,
                     const int64_t *offsets, const float *Y, const float *wY, const float *zY,
                     const unsigned *crange, const int64_t *rows, int64_t nrows, float *s, float *a,
-                    float *b) {
+                    float *b, int32_t *nb) {
     switch (metric) {
         case SILH_EUCLIDEAN:
             launch_sweep_d<T, SILH_EUCLIDEAN>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
-                                              Y, wY, zY, crange, rows, nrows, s, a, b);
+                                              Y, wY, zY, crange, rows, nrows, s, a, b, nb);
             break;
         case SILH_COSINE:
             launch_sweep_d<T, SILH_COSINE>(D, stream, X, d, ld, n, labels, k, sizes, offsets, Y,
-                                           wY, zY, crange, rows, nrows, s, a, b);
+                                           wY, zY, crange, rows, nrows, s, a, b, nb);
             break;
         case SILH_MANHATTAN:
             launch_sweep_d<T, SILH_MANHATTAN>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
-                                              Y, wY, zY, crange, rows, nrows, s, a, b);
+                                              Y, wY, zY, crange, rows, nrows, s, a, b, nb);
             break;
         default:
             launch_sweep_d<T, SILH_CANBERRA>(D, stream, X, d, ld, n, labels, k, sizes, offsets,
-                                             Y, wY, zY, crange, rows, nrows, s, a, b);
+                                             Y, wY, zY, crange, rows, nrows, s, a, b, nb);
             break;
     }
 }
@@ -968,14 +972,15 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
 __global__ void k_exact_finalize(const double *__restrict__ W, const int32_t *__restrict__ lab_s,
                                  const int32_t *__restrict__ order, const int64_t *__restrict__ sizes,
                                  int64_t n, int k, float *__restrict__ s_out,
-                                 float *__restrict__ a_out, float *__restrict__ b_out) {
+                                 float *__restrict__ a_out, float *__restrict__ b_out,
+                                 int32_t *__restrict__ nb_out) {
     const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= n) return;
     const int own = lab_s[pos];
     const double *w = W + pos * k;
     RatioMin bm;
     for (int j = 0; j < k; ++j)
-        if (j != own) bm.add(w[j], (double)sizes[j]);
+        if (j != own) bm.add(w[j], (double)sizes[j], j);
     const double bmin = bm.value();
     const int64_t nc = sizes[own];
     const double a = (nc > 1) ? w[own] / (double)(nc - 1) : 0.0;
@@ -984,6 +989,7 @@ __global__ void k_exact_finalize(const double *__restrict__ W, const int32_t *__
     s_out[o] = (float)((nc > 1 && mx > 0.0) ? (bmin - a) / mx : 0.0);
     if (a_out) a_out[o] = (float)a;
     if (b_out) b_out[o] = (float)bmin;
+    if (nb_out) nb_out[o] = bm.arg;
 }
 
 __global__ void k_sorted_labels(const int32_t *__restrict__ labels, const int32_t *__restrict__ order,
@@ -1099,18 +1105,18 @@ silh_status phase2_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
                          const int64_t *sizes, const int64_t *offsets, const float *Y,
                          const float *wY, const float *zY, const unsigned *crange, int64_t m, int D,
                          const int64_t *rows, int64_t nrows, float *s, float *a, float *b,
-                         cudaStream_t stream) {
+                         int32_t *nb, cudaStream_t stream) {
     silh_status st = SILH_OK;
     (void)prec;
     (void)m;
     if (nrows > 0) {
         if (dtype == SILH_F32)
             launch_sweep_m<float>(metric, D, stream, (const float *)X, d, ld, n, labels, k, sizes,
-                                  offsets, Y, wY, zY, crange, rows, nrows, s, a, b);
+                                  offsets, Y, wY, zY, crange, rows, nrows, s, a, b, nb);
         else
             launch_sweep_m<__nv_bfloat16>(metric, D, stream, (const __nv_bfloat16 *)X, d, ld, n,
                                           labels, k, sizes, offsets, Y, wY, zY, crange, rows, nrows,
-                                          s, a, b);
+                                          s, a, b, nb);
     }
     SILH_CK(cudaGetLastError());
 done:
@@ -1143,7 +1149,7 @@ static silh_status estimate_impl(const void *X, silh_dtype dtype, int64_t n, int
                                  const int32_t *labels, int32_t k, silh_metric metric,
                                  silh_prec prec, const silh_sample *S, const int64_t *d_m,
                                  const int64_t *rows, int64_t nrows, float *s_hat, float *a_hat,
-                                 float *b_hat, cudaStream_t stream) {
+                                 float *b_hat, int32_t *nb, cudaStream_t stream) {
     silh_status st = check_data_args(X, dtype, n, d, ld, labels, k, metric, prec);
     if (st != SILH_OK) return st;
     int dev = 0;
@@ -1160,6 +1166,7 @@ static silh_status estimate_impl(const void *X, silh_dtype dtype, int64_t n, int
     SILH_DEVPTR(s_hat, "s_hat");
     SILH_DEVPTR_OPT(a_hat, "a_hat");
     SILH_DEVPTR_OPT(b_hat, "b_hat");
+    SILH_DEVPTR_OPT(nb, "neighbour");
     SILH_DEVPTR_OPT(rows, "rows");
     SILH_DEVPTR_OPT(d_m, "d_size");
     if (rows == nullptr) nrows = n;
@@ -1169,7 +1176,7 @@ static silh_status estimate_impl(const void *X, silh_dtype dtype, int64_t n, int
     if (m > 0 && nrows > 0 && tc_eligible(metric, prec, d)) {
         // a cluster holds at most all m sampled columns
         st = tc_sweep(X, dtype, n, d, ld, labels, k, metric, prec, S->sizes, S->offsets, S->idx,
-                      S->p, m, m, rows, nrows, s_hat, a_hat, b_hat, sc, stream, d_m);
+                      S->p, m, m, rows, nrows, s_hat, a_hat, b_hat, nb, sc, stream, d_m);
         goto done;
     }
     SILH_CK(sc.alloc(&Y, (size_t)m * D));
@@ -1184,7 +1191,7 @@ static silh_status estimate_impl(const void *X, silh_dtype dtype, int64_t n, int
                         d_m);
     if (st != SILH_OK) goto done;
     st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, S->sizes, S->offsets, Y, wY, zY,
-                      crange, m, D, rows, nrows, s_hat, a_hat, b_hat, stream);
+                      crange, m, D, rows, nrows, s_hat, a_hat, b_hat, nb, stream);
 done:
     return st;
 }
@@ -1193,9 +1200,9 @@ extern "C" silh_status silh_estimate(const void *X, silh_dtype dtype, int64_t n,
                                      int64_t ld, const int32_t *labels, int32_t k,
                                      silh_metric metric, silh_prec prec, const silh_sample *S,
                                      const int64_t *rows, int64_t nrows, float *s_hat,
-                                     float *a_hat, float *b_hat, void *stream_) {
+                                     float *a_hat, float *b_hat, int32_t *nb, void *stream_) {
     return estimate_impl(X, dtype, n, d, ld, labels, k, metric, prec, S, nullptr, rows, nrows,
-                         s_hat, a_hat, b_hat, (cudaStream_t)stream_);
+                         s_hat, a_hat, b_hat, nb, (cudaStream_t)stream_);
 }
 
 extern "C" silh_status silh_estimate_async(const void *X, silh_dtype dtype, int64_t n, int32_t d,
@@ -1203,16 +1210,17 @@ extern "C" silh_status silh_estimate_async(const void *X, silh_dtype dtype, int6
                                            silh_metric metric, silh_prec prec,
                                            const silh_sample *S, const int64_t *d_size,
                                            const int64_t *rows, int64_t nrows, float *s_hat,
-                                           float *a_hat, float *b_hat, void *stream_) {
+                                           float *a_hat, float *b_hat, int32_t *nb,
+                                           void *stream_) {
     if (d_size == nullptr) return fail(SILH_EINVAL, "d_size is null");
     return estimate_impl(X, dtype, n, d, ld, labels, k, metric, prec, S, d_size, rows, nrows,
-                         s_hat, a_hat, b_hat, (cudaStream_t)stream_);
+                         s_hat, a_hat, b_hat, nb, (cudaStream_t)stream_);
 }
 
 extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, int32_t d,
                                   int64_t ld, const int32_t *labels, int32_t k, silh_metric metric,
                                   silh_prec prec, const int64_t *rows, int64_t nrows, float *s,
-                                  float *a, float *b, void *stream_) {
+                                  float *a, float *b, int32_t *nb, void *stream_) {
     cudaStream_t stream = (cudaStream_t)stream_;
     silh_status st = check_data_args(X, dtype, n, d, ld, labels, k, metric, prec);
     if (st != SILH_OK) return st;
@@ -1231,6 +1239,7 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
     SILH_DEVPTR(s, "s");
     SILH_DEVPTR_OPT(a, "a");
     SILH_DEVPTR_OPT(b, "b");
+    SILH_DEVPTR_OPT(nb, "neighbour");
     SILH_DEVPTR_OPT(rows, "rows");
     if (rows == nullptr) nrows = n;
     SILH_REQ(nrows >= 0, "nrows < 0");
@@ -1253,10 +1262,10 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
             (double)(n + 31.0 * k) * (double)k * 8.0 <= 4294967296.0) {
             // all points: each pair once, row and column sums into an FP64 matrix
             st = tc_exact_sym(X, dtype, n, d, ld, k, metric, prec, sizes, coff, order, h_sizes, s,
-                              a, b, sc, stream);
+                              a, b, nb, sc, stream);
         } else {
             st = tc_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, order, nullptr,
-                          n, maxc, rows, nrows, s, a, b, sc, stream);
+                          n, maxc, rows, nrows, s, a, b, nb, sc, stream);
         }
         goto done;
     }
@@ -1279,13 +1288,13 @@ extern "C" silh_status silh_exact(const void *X, silh_dtype dtype, int64_t n, in
             default: launch_exact_sym_d<SILH_CANBERRA>(D, stream, Y, zY, lab_s, n, k, crange, tiny, W); break;
         }
         k_exact_finalize<<<ceil_div_i(n, 256), 256, 0, stream>>>(W, lab_s, order, sizes, n, k, s, a,
-                                                                 b);
+                                                                 b, nb);
         count_launches(1);
         SILH_CK(cudaGetLastError());
         goto done;
     }
     st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, prec, sizes, coff, Y, wY, zY, crange, n,
-                      D, rows, nrows, s, a, b, stream);
+                      D, rows, nrows, s, a, b, nb, stream);
 done:
     return st;
 }

@@ -68,7 +68,7 @@ extern "C" silh_status silh_estimate_noalloc(const void *X, silh_dtype dtype, in
                                              silh_metric metric, silh_prec prec,
                                              const silh_sample *S, const int64_t *rows,
                                              int64_t nrows, float *s_hat, float *a_hat,
-                                             float *b_hat, void *stream_) {
+                                             float *b_hat, int32_t *nb, void *stream_) {
     cudaStream_t stream = (cudaStream_t)stream_;
     silh_status st = SILH_OK;
     int D = 0;
@@ -93,6 +93,7 @@ extern "C" silh_status silh_estimate_noalloc(const void *X, silh_dtype dtype, in
     SILH_DEVPTR(s_hat, "s_hat");
     SILH_DEVPTR_OPT(a_hat, "a_hat");
     SILH_DEVPTR_OPT(b_hat, "b_hat");
+    SILH_DEVPTR_OPT(nb, "neighbour");
     SILH_DEVPTR_OPT(rows, "rows");
     D = padded_dim(d);
     if (m > kNoAllocMaxColumns || m * D > kNoAllocMaxFloats) {
@@ -117,7 +118,7 @@ extern "C" silh_status silh_estimate_noalloc(const void *X, silh_dtype dtype, in
     st = gather_columns(X, dtype, d, ld, S->idx, S->p, m, D, metric, crange, Y, wY, zY, stream);
     if (st != SILH_OK) goto done;
     st = phase2_sweep(X, dtype, n, d, ld, labels, k, metric, SILH_PREC_FP32, S->sizes, S->offsets,
-                      Y, wY, zY, crange, m, D, rows, nrows, s_hat, a_hat, b_hat, stream);
+                      Y, wY, zY, crange, m, D, rows, nrows, s_hat, a_hat, b_hat, nb, stream);
 done:
     return st;
 }

@@ -48,7 +48,7 @@ silh_status phase2_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
                          const int64_t *sizes, const int64_t *offsets, const float *Y,
                          const float *wY, const float *zY, const unsigned *crange, int64_t m, int D,
                          const int64_t *rows, int64_t nrows, float *s, float *a, float *b,
-                         cudaStream_t stream);
+                         int32_t *nb, cudaStream_t stream);
 
 // Padded row width of the column operand for a given d.
 int padded_dim(int d);
@@ -59,7 +59,7 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
                      const int32_t *labels, int32_t k, int metric, int prec, const int64_t *sizes,
                      const int64_t *offsets, const int32_t *col_idx, const double *col_p, int64_t m,
                      int64_t max_cluster_cols, const int64_t *rows, int64_t nrows, float *s,
-                     float *a, float *b, Scratch &sc, cudaStream_t stream,
+                     float *a, float *b, int32_t *nb, Scratch &sc, cudaStream_t stream,
                      const int64_t *d_m = nullptr);
 // Phase 2 of many clusterings of X (all rows each) on the tensor cores: per
 // clustering the operands of tc_sweep, then one persistent sweep over every
@@ -79,7 +79,7 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
                          int32_t k, int metric, int prec, const int64_t *sizes,
                          const int64_t *coff, const int32_t *order,
                          const std::vector<int64_t> &h_sizes, float *s, float *a, float *b,
-                         Scratch &sc, cudaStream_t stream);
+                         int32_t *nb, Scratch &sc, cudaStream_t stream);
 // 1 if a bounded wait in the tensor-core sweep gave up since the last call
 // (and clears it), 0 if not, -1 on a CUDA error.  Synchronous.
 int tc_take_error();

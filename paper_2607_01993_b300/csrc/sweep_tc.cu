@@ -270,8 +270,10 @@ struct TcBatchArg<true> {
 __device__ __forceinline__ int64_t bt_total_work(const TcBatchArg<false> &) { return 0; }
 __device__ __forceinline__ int64_t bt_total_work(const TcBatchArg<true> &b) { return b.total_work; }
 
+// NB: the instantiation that also writes the neighbouring cluster (its
+// running argmin is a register the others do without).
 template <int METRIC, int KD, bool SPLIT, bool BF, bool SYM = false, bool WIDE = false,
-          bool BATCH = false>
+          bool BATCH = false, bool NB = false>
 __global__ void __launch_bounds__(TcCfg<KD, SPLIT, BF, WIDE>::THREADS, 1)
 k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CUtensorMap m_alo,
            const __grid_constant__ CUtensorMap m_bhi, const __grid_constant__ CUtensorMap m_blo,
@@ -284,7 +286,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
            const int64_t *__restrict__ poff,
            const int64_t *__restrict__ sizes, int k, float tau, int dq,
            const double *__restrict__ w_own, float *__restrict__ s_out,
-           float *__restrict__ a_out_v, float *__restrict__ b_out_v, double *__restrict__ W,
+           float *__restrict__ a_out_v, float *__restrict__ b_out_v,
+           int32_t *__restrict__ nb_out_v, double *__restrict__ W,
            const int4 *__restrict__ sym_work, int64_t n_sym_work,
            const __grid_constant__ TcBatchArg<BATCH> bt) {
     static_assert(!(BATCH && SYM), "the symmetric exact sweep is not batched");
@@ -659,7 +662,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         if (SYM) {
                             if (accd != 0.0 && rw != 0.f) atomicAdd(&W[pos * k + j], accd);
                         } else if (j != own) {
-                            bmin.add(accd, (double)v.sizes[j]);
+                            bmin.add(accd, (double)v.sizes[j], j);
                         }
                         accd = 0.0;
                         ++j;
@@ -916,7 +919,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 while (j < vk) {
                     accd += (double)accf;
                     accf = 0.f;
-                    if (j != own) bmin.add(accd, (double)v.sizes[j]);
+                    if (j != own) bmin.add(accd, (double)v.sizes[j], j);
                     accd = 0.0;
                     ++j;
                 }
@@ -938,6 +941,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     v.s_out[o] = sv;
                     if (a_out_v) a_out_v[o] = av;
                     if (b_out_v) b_out_v[o] = bv;
+                    if (NB) nb_out_v[o] = (own < 0 || own >= vk) ? -1 : bmin.arg;
                 }
             }
         }
@@ -1534,7 +1538,7 @@ __global__ void k_tc_sym_finalize(const double *__restrict__ W,
                                   const int32_t *__restrict__ plab, const int64_t *__restrict__ outi,
                                   const int64_t *__restrict__ sizes, int64_t mp_max, int k,
                                   float *__restrict__ s_out, float *__restrict__ a_out,
-                                  float *__restrict__ b_out) {
+                                  float *__restrict__ b_out, int32_t *__restrict__ nb_out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= mp_max) return;
     const int64_t o = outi[i];
@@ -1543,7 +1547,7 @@ __global__ void k_tc_sym_finalize(const double *__restrict__ W,
     const double *w = W + i * k;
     RatioMin bm;
     for (int j = 0; j < k; ++j)
-        if (j != own) bm.add(w[j], (double)sizes[j]);
+        if (j != own) bm.add(w[j], (double)sizes[j], j);
     const double bmin = bm.value();
     const int64_t nc = sizes[own];
     const double a = (nc > 1) ? w[own] / (double)(nc - 1) : 0.0;    // own-cluster sum
@@ -1551,6 +1555,7 @@ __global__ void k_tc_sym_finalize(const double *__restrict__ W,
     s_out[o] = (float)((nc > 1 && mx > 0.0) ? (bmin - a) / mx : 0.0);
     if (a_out) a_out[o] = (float)a;
     if (b_out) b_out[o] = (float)bmin;
+    if (nb_out) nb_out[o] = bm.arg;
 }
 
 // ------------------------------------------------------------- host side
@@ -1620,7 +1625,7 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
                       const float *y_wn4,
                       const int64_t *poff, const int64_t *sizes, int k, float tau, int dq,
                       int64_t max_cluster_cols, double *w_own, float *s, float *a, float *b,
-                      double *W = nullptr, const OwnItem *own_items = nullptr,
+                      int32_t *nb, double *W = nullptr, const OwnItem *own_items = nullptr,
                       int64_t n_own_items = 0, const int4 *sym_work = nullptr,
                       int64_t n_sym_work = 0) {
     constexpr bool WIDE = wide_tiles(KD, BF);
@@ -1637,7 +1642,8 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
                                                     y_wn, poff, k, max_cluster_cols, w_own);
         if (e0 != cudaSuccess) return e0;
     }
-    auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF, SYM, WIDE>;
+    auto kern = (!SYM && nb != nullptr) ? k_sweep_tc<METRIC, KD, SPLIT, BF, SYM, WIDE, false, true>
+                                        : k_sweep_tc<METRIC, KD, SPLIT, BF, SYM, WIDE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     const int64_t groups = SYM ? n_sym_work
@@ -1647,7 +1653,7 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
     kern<<<grid, C::THREADS, C::SMEM, stream>>>(ahi, alo, bhi, blo, a_hi, a_lo, a_il, a_norm,
                                                 a_lab, a_out, nrows, y_full, y_il, y_wn,
                                                 reinterpret_cast<const float4 *>(y_wn4), poff,
-                                                sizes, k, tau, dq, w_own, s, a, b, W, sym_work,
+                                                sizes, k, tau, dq, w_own, s, a, b, nb, W, sym_work,
                                                 n_sym_work, TcBatchArg<false>{});
     count_launches(1);
     return cudaGetLastError();
@@ -1675,7 +1681,7 @@ cudaError_t launch_tc_batched(int nsm, cudaStream_t stream, const CUtensorMap &a
                                                 a_lab, a_out, 0, y_full, y_il, y_wn,
                                                 reinterpret_cast<const float4 *>(y_wn4), poff, nullptr,
                                                 0, tau, dq, w_own, nullptr, nullptr, nullptr,
-                                                nullptr, nullptr, 0, bt);
+                                                nullptr, nullptr, nullptr, 0, bt);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1788,7 +1794,8 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
                      const int32_t *labels, int32_t k, int metric, int prec, const int64_t *sizes,
                      const int64_t *offsets, const int32_t *col_idx, const double *col_p, int64_t m,
                      int64_t max_cluster_cols, const int64_t *rows, int64_t nrows, float *s,
-                     float *a, float *b, Scratch &sc, cudaStream_t stream, const int64_t *d_m) {
+                     float *a, float *b, int32_t *nb, Scratch &sc, cudaStream_t stream,
+                     const int64_t *d_m) {
     silh_status st = SILH_OK;
     const int KD = d <= 32 ? 32 : 64;
     const bool split = prec == SILH_PREC_3XTF32 || prec == SILH_PREC_BF16X3;
@@ -1837,7 +1844,7 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
         SILH_CK((launch_tc<MET, KDV, SP, BFV>(                                                  \
             nsm, stream, m_ahi, m_alo, m_bhi, m_blo, BFV ? o.rfull : (const float *)o.rhi,     \
             BFV ? nullptr : (const float *)o.rlo, o.ril, o.rn, o.lab, o.outi, nrows, o.yf,      \
-            o.yil, o.ywn, o.ywn4, o.poff, sizes, k, tau, (d + 3) / 4, max_cluster_cols, w_own, s, a, b))); \
+            o.yil, o.ywn, o.ywn4, o.poff, sizes, k, tau, (d + 3) / 4, max_cluster_cols, w_own, s, a, b, nb))); \
     }
 #define SILH_TC_CASES(MET, KDV)             \
     SILH_TC_CASE(MET, KDV, true, false)     \
@@ -2025,7 +2032,7 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
                          int32_t k, int metric, int prec, const int64_t *sizes,
                          const int64_t *coff, const int32_t *order,
                          const std::vector<int64_t> &h_sizes, float *s, float *a, float *b,
-                         Scratch &sc, cudaStream_t stream) {
+                         int32_t *nb, Scratch &sc, cudaStream_t stream) {
     silh_status st = SILH_OK;
     const int KD = d <= 32 ? 32 : 64;
     const bool split = prec == SILH_PREC_3XTF32 || prec == SILH_PREC_BF16X3;
@@ -2146,7 +2153,7 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
     if (metric == MET && KD == KDV && split == SP && bf == BFV) {                              \
         SILH_CK((launch_tc<MET, KDV, SP, BFV, true>(                                            \
             nsm, stream, m_ahi, m_alo, m_bhi, m_blo, yf, nullptr, yil, rn, plab, outi, mp_max, yf, \
-            yil, ywn, ywn4, poff, sizes, k, tau, (d + 3) / 4, 0, nullptr, nullptr, nullptr, nullptr, W, \
+            yil, ywn, ywn4, poff, sizes, k, tau, (d + 3) / 4, 0, nullptr, nullptr, nullptr, nullptr, nullptr, W, \
             own_items, (int64_t)h_items.size(), sym_work, (int64_t)h_work.size())));            \
     }
 #define SILH_TC_SYM_CASES(MET, KDV)             \
@@ -2161,7 +2168,7 @@ silh_status tc_exact_sym(const void *X, silh_dtype dtype, int64_t n, int32_t d, 
 #undef SILH_TC_SYM_CASES
 #undef SILH_TC_SYM_CASE
     k_tc_sym_finalize<<<ceil_div_i(mp_max, 256), 256, 0, stream>>>(W, plab, outi, sizes,
-                                                                   mp_max, k, s, a, b);
+                                                                   mp_max, k, s, a, b, nb);
     count_launches(1);
     SILH_CK(cudaGetLastError());
 done:

@@ -67,7 +67,8 @@ def load(path: str = LIB_PATH):
                                     ctypes.POINTER(SilhSample), vp]
     lib.silh_sample_pps.restype = ctypes.c_int
     lib.silh_estimate.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32, ctypes.c_int,
-                                  ctypes.c_int, ctypes.POINTER(SilhSample), vp, i64, vp, vp, vp, vp]
+                                  ctypes.c_int, ctypes.POINTER(SilhSample), vp, i64, vp, vp, vp, vp,
+                                  vp]
     lib.silh_estimate.restype = ctypes.c_int
     lib.silh_sample_pps_async.argtypes = list(lib.silh_sample_pps.argtypes[:-1]) + [vp, vp, vp]
     lib.silh_sample_pps_async.restype = ctypes.c_int
@@ -77,7 +78,7 @@ def load(path: str = LIB_PATH):
     lib.silh_estimate_noalloc.argtypes = list(lib.silh_estimate.argtypes)
     lib.silh_estimate_noalloc.restype = ctypes.c_int
     lib.silh_exact.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32, ctypes.c_int,
-                               ctypes.c_int, vp, i64, vp, vp, vp, vp]
+                               ctypes.c_int, vp, i64, vp, vp, vp, vp, vp]
     lib.silh_exact.restype = ctypes.c_int
     lib.silh_global.argtypes = [vp, i64, vp, vp]
     lib.silh_global.restype = ctypes.c_int
@@ -93,7 +94,7 @@ def load(path: str = LIB_PATH):
     lib.silh_estimate_batched.restype = ctypes.c_int
     lib.silh_estimate_cosine_collapsed.argtypes = [vp, ctypes.c_int, i64, i32, i64, vp, i32,
                                                    ctypes.POINTER(SilhSample), vp, i64, vp, vp,
-                                                   vp, vp]
+                                                   vp, vp, vp]
     lib.silh_estimate_cosine_collapsed.restype = ctypes.c_int
     lib.silh_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
     lib.silh_pipe_rates.restype = ctypes.c_int
@@ -236,8 +237,21 @@ def silh_sample_pps_async(X, labels, k, metric="euclidean", t=64.0, m0=None, del
     return smp, d_size, d_status
 
 
+def _outputs(nrows, device, want_ab, want_nb):
+    a = torch.empty(nrows, dtype=torch.float32, device=device) if want_ab else None
+    b = torch.empty(nrows, dtype=torch.float32, device=device) if want_ab else None
+    nb = torch.empty(nrows, dtype=torch.int32, device=device) if want_nb else None
+    return a, b, nb
+
+
+def _ret(s, a, b, nb, want_ab, want_nb):
+    """s; (s, a, b) with want_ab; (s, nb) with want_nb; (s, a, b, nb) with both."""
+    out = (s,) + ((a, b) if want_ab else ()) + ((nb,) if want_nb else ())
+    return out if len(out) > 1 else s
+
+
 def silh_estimate_async(X, labels, k, sample: Sample, d_size, metric="euclidean", prec="fp32",
-                        rows=None, want_ab=False, out=None, stream=None):
+                        rows=None, want_ab=False, out=None, stream=None, want_nb=False):
     """Phase 2 for a sample whose size is on the device (d_size, int64 CUDA)."""
     lib = load()
     dt, n, d, ld = _data(X)
@@ -245,39 +259,38 @@ def silh_estimate_async(X, labels, k, sample: Sample, d_size, metric="euclidean"
     rows, nr = _rows(rows)
     nrows = n if rows is None else nr
     s = _out(out, nrows, X.device)
-    a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
-    b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    a, b, nb = _outputs(nrows, X.device, want_ab, want_nb)
     if _empty_rows(rows, nr):
-        return (s, a, b) if want_ab else s
+        return _ret(s, a, b, nb, want_ab, want_nb)
     st = sample.as_struct()
     _check(lib.silh_estimate_async(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric],
                                    PRECS[prec], ctypes.byref(st), _ptr(d_size), _ptr(rows), nr,
-                                   _ptr(s), _ptr(a), _ptr(b), _stream(stream)))
-    return (s, a, b) if want_ab else s
+                                   _ptr(s), _ptr(a), _ptr(b), _ptr(nb), _stream(stream)))
+    return _ret(s, a, b, nb, want_ab, want_nb)
 
 
 def silh_estimate(X, labels, k, sample: Sample, metric="euclidean", prec="fp32", rows=None,
-                  want_ab=False, out=None, stream=None):
-    """Algorithm 1, Phase 2: s_hat (and a_hat, b_hat) for all rows or a row list."""
+                  want_ab=False, out=None, stream=None, want_nb=False):
+    """Algorithm 1, Phase 2: s_hat (and a_hat, b_hat; the neighbouring cluster
+    with want_nb) for all rows or a row list."""
     lib = load()
     dt, n, d, ld = _data(X)
     labels = _labels(labels)
     rows, nr = _rows(rows)
     nrows = n if rows is None else nr
     s = _out(out, nrows, X.device)
-    a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
-    b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    a, b, nb = _outputs(nrows, X.device, want_ab, want_nb)
     if _empty_rows(rows, nr):
-        return (s, a, b) if want_ab else s
+        return _ret(s, a, b, nb, want_ab, want_nb)
     st = sample.as_struct()
     _check(lib.silh_estimate(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric],
                              PRECS[prec], ctypes.byref(st), _ptr(rows), nr, _ptr(s), _ptr(a),
-                             _ptr(b), _stream(stream)))
-    return (s, a, b) if want_ab else s
+                             _ptr(b), _ptr(nb), _stream(stream)))
+    return _ret(s, a, b, nb, want_ab, want_nb)
 
 
 def silh_estimate_noalloc(X, labels, k, sample: Sample, metric="euclidean", prec="fp32",
-                          rows=None, want_ab=False, out=None, stream=None):
+                          rows=None, want_ab=False, out=None, stream=None, want_nb=False):
     """silh_estimate through the no-allocation entry point (fixed device scratch).
 
     For callers that cannot allocate device memory during the call; the output
@@ -289,19 +302,18 @@ def silh_estimate_noalloc(X, labels, k, sample: Sample, metric="euclidean", prec
     rows, nr = _rows(rows)
     nrows = n if rows is None else nr
     s = _out(out, nrows, X.device)
-    a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
-    b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    a, b, nb = _outputs(nrows, X.device, want_ab, want_nb)
     if _empty_rows(rows, nr):
-        return (s, a, b) if want_ab else s
+        return _ret(s, a, b, nb, want_ab, want_nb)
     st = sample.as_struct()
     _check(lib.silh_estimate_noalloc(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric],
                                      PRECS[prec], ctypes.byref(st), _ptr(rows), nr, _ptr(s),
-                                     _ptr(a), _ptr(b), _stream(stream)))
-    return (s, a, b) if want_ab else s
+                                     _ptr(a), _ptr(b), _ptr(nb), _stream(stream)))
+    return _ret(s, a, b, nb, want_ab, want_nb)
 
 
 def silh_estimate_cosine_collapsed(X, labels, k, sample: Sample, rows=None, want_ab=False,
-                                   out=None, stream=None):
+                                   out=None, stream=None, want_nb=False):
     """Cosine Phase 2 in O(n k d) (parallel-axis collapse of the weighted sums)."""
     lib = load()
     dt, n, d, ld = _data(X)
@@ -309,15 +321,14 @@ def silh_estimate_cosine_collapsed(X, labels, k, sample: Sample, rows=None, want
     rows, nr = _rows(rows)
     nrows = n if rows is None else nr
     s = _out(out, nrows, X.device)
-    a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
-    b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    a, b, nb = _outputs(nrows, X.device, want_ab, want_nb)
     if _empty_rows(rows, nr):
-        return (s, a, b) if want_ab else s
+        return _ret(s, a, b, nb, want_ab, want_nb)
     st = sample.as_struct()
     _check(lib.silh_estimate_cosine_collapsed(_ptr(X), dt, n, d, ld, _ptr(labels), k,
                                               ctypes.byref(st), _ptr(rows), nr, _ptr(s), _ptr(a),
-                                              _ptr(b), _stream(stream)))
-    return (s, a, b) if want_ab else s
+                                              _ptr(b), _ptr(nb), _stream(stream)))
+    return _ret(s, a, b, nb, want_ab, want_nb)
 
 
 def pipe_rates(stream=None):
@@ -362,7 +373,7 @@ def silh_estimate_batched(X, items, metric="euclidean", variant=-1, outs=None, s
 
 
 def silh_exact(X, labels, k, metric="euclidean", prec="fp32", rows=None, want_ab=False,
-               stream=None):
+               stream=None, want_nb=False):
     """Exact silhouette (Eq. 1-2) of all rows or a row list."""
     lib = load()
     dt, n, d, ld = _data(X)
@@ -370,13 +381,12 @@ def silh_exact(X, labels, k, metric="euclidean", prec="fp32", rows=None, want_ab
     rows, nr = _rows(rows)
     nrows = n if rows is None else nr
     s = torch.empty(nrows, dtype=torch.float32, device=X.device)
-    a = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
-    b = torch.empty(nrows, dtype=torch.float32, device=X.device) if want_ab else None
+    a, b, nb = _outputs(nrows, X.device, want_ab, want_nb)
     if _empty_rows(rows, nr):
-        return (s, a, b) if want_ab else s
+        return _ret(s, a, b, nb, want_ab, want_nb)
     _check(lib.silh_exact(_ptr(X), dt, n, d, ld, _ptr(labels), k, METRICS[metric], PRECS[prec],
-                          _ptr(rows), nr, _ptr(s), _ptr(a), _ptr(b), _stream(stream)))
-    return (s, a, b) if want_ab else s
+                          _ptr(rows), nr, _ptr(s), _ptr(a), _ptr(b), _ptr(nb), _stream(stream)))
+    return _ret(s, a, b, nb, want_ab, want_nb)
 
 
 def silh_cohsep(X, labels, k, sample: Sample, metric="euclidean", stream=None):

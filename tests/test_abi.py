@@ -60,11 +60,11 @@ def test_argument_validation_without_device(lib):
     assert rc == -1
     assert b"null" in lib.silh_last_error()
     rc = lib.silh_estimate(None, 0, 10, 2, 2, None, 2, 0, 0, None, None, 0, None, None, None,
-                           None)
+                           None, None)
     assert rc == -1
     # k = 1 is not a clustering for the silhouette (b undefined)
     rc = lib.silh_exact(ctypes.c_void_p(16), 0, 10, 2, 2, ctypes.c_void_p(16), 1, 0, 0, None, 0,
-                        None, None, None, None)
+                        None, None, None, None, None)
     assert rc == -1
     rc = lib.silh_global(None, 10, None, None)
     assert rc == -1

@@ -135,7 +135,7 @@ def test_scratch_exhaustion_is_enomem_and_the_context_survives():
     s = torch.empty(n, dtype=torch.float32, device="cuda")
     launches = silh.kernel_launches()
     rc = lib.silh_estimate(Xt.data_ptr(), 0, n, d, d, lt.data_ptr(), 4, 2, 0, ctypes.byref(huge),
-                           None, 0, s.data_ptr(), None, None, None)
+                           None, 0, s.data_ptr(), None, None, None, None)
     assert rc == -2, (rc, lib.silh_last_error())
     assert silh.kernel_launches() == launches
     s2 = silh.silh_estimate(Xt, lt, 4, gs, "manhattan")

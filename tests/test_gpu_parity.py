@@ -486,13 +486,13 @@ def test_pageable_host_buffers_are_rejected_before_any_launch():
     launches = silh.kernel_launches()
     cases = [
         lib.silh_estimate(Xh.ctypes.data, 0, n, d, d, lt.data_ptr(), k, 0, 0, ctypes.byref(st),
-                          None, 0, s.data_ptr(), None, None, None),
+                          None, 0, s.data_ptr(), None, None, None, None),
         lib.silh_estimate(Xt.data_ptr(), 0, n, d, d, lh.ctypes.data, k, 0, 0, ctypes.byref(st),
-                          None, 0, s.data_ptr(), None, None, None),
+                          None, 0, s.data_ptr(), None, None, None, None),
         lib.silh_estimate(Xt.data_ptr(), 0, n, d, d, lt.data_ptr(), k, 0, 0, ctypes.byref(st),
-                          None, 0, sh.ctypes.data, None, None, None),
+                          None, 0, sh.ctypes.data, None, None, None, None),
         lib.silh_exact(Xh.ctypes.data, 0, n, d, d, lt.data_ptr(), k, 0, 0, None, 0,
-                       s.data_ptr(), None, None, None),
+                       s.data_ptr(), None, None, None, None),
         lib.silh_global(sh.ctypes.data, n, g.data_ptr(), None),
         lib.silh_global(s.data_ptr(), n, sh.ctypes.data, None),
     ]

@@ -444,3 +444,72 @@ def test_cohesion_separation_error_bounded_by_weight_error():
         ch, sh = oracle.cohsep(Wh, lab, k)
         assert abs(ch - coh) <= eps * coh * (1 + 1e-12)
         assert abs(sh - sep) <= eps * sep * (1 + 1e-12)
+
+
+def _neighbour_brute(X, lab, k, metric):
+    """b(e) and its cluster written out from Eq. 2 with plain loops: the mean
+    distance to every other cluster, the smallest one, the lowest cluster
+    index among equal means."""
+    n = X.shape[0]
+    nb = np.empty(n, dtype=np.int64)
+    bv = np.empty(n)
+    for e in range(n):
+        best, arg = np.inf, -1
+        for j in range(k):
+            if j == lab[e]:
+                continue
+            members = [f for f in range(n) if lab[f] == j]
+            m = sum(oracle.dist(metric, X[e], X[f]) for f in members) / len(members)
+            if m < best:
+                best, arg = m, j
+        nb[e], bv[e] = arg, best
+    return nb, bv
+
+
+def test_figure1_neighbour_of_e14_gives_the_printed_value():
+    # With the printed values' reading of e14 (-2.5, -3), b(e14) is its distance
+    # to the singleton C4 = {e15}, 0.5, which with a(e14) gives the printed
+    # s(e14) = -0.89 (Example 1 names C3, the reading of the drawn coordinate)
+    X, lab, printed, _ = _figure1()
+    s, a, b, nb = oracle.exact(X, lab, 4, "euclidean", want_nb=True)
+    assert nb[13] == 3 and b[13] == 0.5
+    assert round((b[13] - a[13]) / a[13], 2) == printed[13]
+    want, bw = _neighbour_brute(X, lab, 4, "euclidean")
+    np.testing.assert_array_equal(nb, want)
+    np.testing.assert_allclose(b, bw, rtol=1e-14)
+
+
+@pytest.mark.parametrize("metric", ["euclidean", "cosine", "manhattan", "canberra"])
+def test_exact_neighbour_matches_brute_force(metric):
+    X, lab = _blobs(60, 3, 4, seed=11, sigma=4.0, shift=(metric == "canberra"))
+    s, a, b, nb = oracle.exact(X, lab, 4, metric, want_nb=True)
+    want, bw = _neighbour_brute(X, lab, 4, metric)
+    np.testing.assert_array_equal(nb, want)
+    np.testing.assert_allclose(b, bw, rtol=1e-12)
+    assert (nb != lab).all()
+
+
+def test_neighbour_ties_take_the_lowest_cluster():
+    # clusters 1 and 2 are mirror images about the y axis, so every point of
+    # cluster 0 (on the axis) is at exactly equal mean distance from them
+    X = np.array([[0.0, 0.0], [0.0, 1.0], [0.0, -1.5],
+                  [4.0, 0.0], [5.0, 1.0], [6.0, -2.0],
+                  [-4.0, 0.0], [-5.0, 1.0], [-6.0, -2.0]])
+    lab = np.array([0, 0, 0, 1, 1, 1, 2, 2, 2], dtype=np.int32)
+    for metric in ("euclidean", "manhattan"):
+        _, _, b, nb = oracle.exact(X, lab, 3, metric, want_nb=True)
+        assert (nb[:3] == 1).all()
+        lab2 = np.array([0, 0, 0, 2, 2, 2, 1, 1, 1], dtype=np.int32)   # swap the names
+        _, _, b2, nb2 = oracle.exact(X, lab2, 3, metric, want_nb=True)
+        assert (nb2[:3] == 1).all() and np.array_equal(b[:3], b2[:3])
+
+
+def test_estimate_neighbour_with_every_p_one_is_exact():
+    # t >= max |Cj|: every p = 1, F_j = C_j, and Eq. 8 is Eq. 1-2
+    X, lab = _blobs(80, 4, 5, seed=12, sigma=3.0)
+    smp = oracle.sample_pps(X, lab, 5, "euclidean", t=1000.0, seed=1)
+    assert (smp.p == 1.0).all()
+    _, _, _, nb_e = oracle.estimate(X, lab, 5, "euclidean", smp.offsets, smp.idx, smp.ps,
+                                    want_nb=True)
+    _, _, _, nb_x = oracle.exact(X, lab, 5, "euclidean", want_nb=True)
+    np.testing.assert_array_equal(nb_e, nb_x)
