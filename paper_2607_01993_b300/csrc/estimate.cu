@@ -780,14 +780,20 @@ void launch_sweep_m(int metric, int D, cudaStream_t stream, const T *X, int d, i
 
 // ----------------------------------------------------- exact, symmetric
 
+// Column tiles one block of the symmetric exact sweep takes in a row (the row
+// tile's registers and running sums carry over from one to the next).
+constexpr int64_t kSymSeg = 4;
+
 // Exact silhouette over all n rows: d(x, y) = d(y, x), so each pair of
 // cluster-sorted position tiles (I <= J) is evaluated once.  A CTA owns the
-// T = 128 RPT positions of tile I as rows and streams tile J as columns:
-// every distance is added to its row's sum for the column's cluster
-// (registers, flushed at cluster changes) and, for I < J, to its column's sum
-// for the row's cluster (reduced over the CTA's rows with warp shuffles and
-// shared memory).  Both land in the n x k FP64 weight matrix W with atomic
-// adds (so results are reproducible to rounding order, not bitwise).
+// T = 128 RPT positions of tile I as rows and streams a segment of up to
+// kSymSeg tiles J >= I as columns: every distance is added to its row's sum
+// for the column's cluster (registers, flushed at cluster changes) and, for
+// I < J, to its column's sum for the row's cluster (reduced over the CTA's rows
+// with warp shuffles and shared memory).  Both land in the n x k FP64 weight
+// matrix W with atomic adds (so results are reproducible to rounding order,
+// not bitwise).
+
 template <int METRIC, int D, int RPT, bool TINY>
 __global__ void __launch_bounds__(kThreads)
 k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
@@ -802,17 +808,24 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
     __shared__ int sh_lab[BN];
     __shared__ float sh_col[NW][BN];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // upper-triangular tile pair (I, J) from the linear block index
+    // Row tile I and a segment of up to kSymSeg of its column tiles J >= I from
+    // the linear block index: row tile i has ceil((ntiles - i) / kSymSeg)
+    // segments, so the blocks before row tile I number F(ntiles) - F(ntiles - I)
+    // with F(x) = sum_{m <= x} ceil(m / kSymSeg).
     const int64_t b = blockIdx.x;
-    int64_t lo = 0, hi = ntiles - 1;   // largest I with start(I) <= b
+    auto segs_upto = [](int64_t x) -> int64_t {
+        const int64_t q = x / kSymSeg, r = x % kSymSeg;
+        return kSymSeg * q * (q + 1) / 2 + r * (q + 1);
+    };
+    const int64_t ftot = segs_upto(ntiles);
+    int64_t lo = 0, hi = ntiles - 1;   // largest I with F(ntiles) - F(ntiles - I) <= b
     while (lo < hi) {
         const int64_t mid = (lo + hi + 1) >> 1;
-        const int64_t st = mid * ntiles - mid * (mid - 1) / 2;
-        if (st <= b) lo = mid; else hi = mid - 1;
+        if (ftot - segs_upto(ntiles - mid) <= b) lo = mid; else hi = mid - 1;
     }
     const int64_t I = lo;
-    const int64_t J = I + (b - (I * ntiles - I * (I - 1) / 2));
-    const bool diag = (I == J);
+    const int64_t J_begin = I + (b - (ftot - segs_upto(ntiles - I))) * kSymSeg;
+    const int64_t J_end = min(J_begin + kSymSeg, ntiles);
     constexpr int NA = RowAbs<METRIC, D, RPT>::NA;
     float2 x[RPT][D / 2];
     float2 ax[RPT][NA];
@@ -846,11 +859,13 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
     if (tiny_data) any_slow = __syncthreads_or(any_slow);
     const int64_t rlast = min(I * T + T, n) - 1;
     const int cI0 = lab_s[I * T], cI1 = lab_s[rlast];
-    const int64_t c_begin = J * T, c_end = min(J * T + T, n);
     int cur = -1;                      // column cluster of the running row sums
     float accr[RPT];
 #pragma unroll
     for (int r = 0; r < RPT; ++r) accr[r] = 0.f;
+    for (int64_t J = J_begin; J < J_end; ++J) {
+    const bool diag = (I == J);
+    const int64_t c_begin = J * T, c_end = min(J * T + T, n);
     for (int64_t cb = c_begin; cb < c_end; cb += BN) {
         const int nb = (int)min((int64_t)BN, c_end - cb);
         __syncthreads();
@@ -960,6 +975,7 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
             }
         }
     }
+    }
     if (cur >= 0) {
 #pragma unroll
         for (int r = 0; r < RPT; ++r)
@@ -1004,7 +1020,8 @@ void launch_exact_sym(cudaStream_t stream, const float *Y, const float *zY, cons
     constexpr int RPT = (D <= 32) ? 2 : 1;
     constexpr int T = kThreads * RPT;
     const int64_t nt = (n + T - 1) / T;
-    const int64_t nblk = nt * (nt + 1) / 2;
+    const int64_t q = nt / kSymSeg, r = nt % kSymSeg;
+    const int64_t nblk = kSymSeg * q * (q + 1) / 2 + r * (q + 1);   // row-tile segments
     if (METRIC == SILH_CANBERRA && tiny)
         k_exact_sym<METRIC, D, RPT, METRIC == SILH_CANBERRA><<<(unsigned)nblk, kThreads, 0, stream>>>(
             Y, zY, lab_s, n, k, nt, crange, W);
