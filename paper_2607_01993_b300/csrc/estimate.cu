@@ -717,7 +717,7 @@ void launch_sweep(cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
                   const int64_t *rows, int64_t nrows, float *s, float *a, float *b,
                   int32_t *nb) {
     constexpr int RPT = (D <= 32) ? 2 : 1;
-    constexpr int BN = (D <= 32) ? 64 : 32;
+    constexpr int BN = (D <= 32) ? 128 : 32;
     int grid = (int)((nrows + kThreads * RPT - 1) / (kThreads * RPT));
     k_sweep<T, METRIC, D, RPT, BN, false><<<grid, kThreads, 0, stream>>>(
         X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, rows, nrows, s, a, b, nb);
