@@ -241,10 +241,13 @@ typedef struct silh_batch_item {
  * persistent launch (the work items are (clustering, row tile) pairs, taken
  * round-robin by CTAs sized to fill the GPU), all rows of every item.
  * prec SILH_PREC_FP32 (or a tensor-core mode the metric or d rules out): CUDA
- * cores, the arithmetic and results of silh_estimate with SILH_PREC_FP32 on
- * each item; variant selects the tile shape (rows per thread x columns per
- * stage: 0 = 1x32, 1 = 1x64, 2 = 2x32, 3 = 2x64; -1 = default) -- the choice
- * an autotuner makes by timing.  prec TF32 / 3XTF32 / BF16 / BF16X3 with the
+ * cores, the arithmetic of silh_estimate with SILH_PREC_FP32 on each item;
+ * variant selects the tile shape (rows per thread x columns per stage: 0 =
+ * 1x32, 1 = 1x64, 2 = 2x32, 3 = 2x128 (2x64 for d > 32, 2x32 for d > 64);
+ * -1 = default, the single sweep's shape, whose results equal silh_estimate's
+ * bit for bit; the other shapes group each cluster's FP32 partial sums
+ * differently, so their last bits can differ) -- the choice an autotuner
+ * makes by timing.  prec TF32 / 3XTF32 / BF16 / BF16X3 with the
  * Euclidean or cosine distance and d <= 64: tensor cores; each item first gets
  * the operands of the single-clustering tensor-core sweep (rows sorted by its
  * clusters, its padded sample columns, its own-cluster sums), then one

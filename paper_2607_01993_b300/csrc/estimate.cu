@@ -670,13 +670,14 @@ template <class T, int METRIC, int D>
 cudaError_t launch_batched(int variant, const BatchParams &bp, cudaStream_t stream, const T *X,
                            int d, int64_t ld, int64_t n, const float *Y, const float *wY,
                            const float *zY, const unsigned *crange, unsigned long long *nw) {
-    if (variant < 0) variant = (D <= 32) ? 3 : 0;     // as the single sweep: (2, 64) / (1, 32)
+    // default: as the single sweep, (2, 128) for rows of up to 32 elements, else (1, 32)
+    if (variant < 0) variant = (D <= 32) ? 3 : 0;
     switch (variant) {
         case 0: return launch_batched_v<T, METRIC, D, 1, 32>(bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
         case 1: return launch_batched_v<T, METRIC, D, 1, 64>(bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
         case 2: return launch_batched_v<T, METRIC, D, 2, 32>(bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
-        default: return launch_batched_v<T, METRIC, D, 2, (D >= 128 ? 32 : 64)>(bp, stream, X, d, ld,
-                                                                               n, Y, wY, zY, crange, nw);
+        default: return launch_batched_v<T, METRIC, D, 2, (D <= 32 ? 128 : D >= 128 ? 32 : 64)>(
+            bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
     }
 }
 

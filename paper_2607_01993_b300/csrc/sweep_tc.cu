@@ -1012,18 +1012,19 @@ k_own_direct(const float *__restrict__ a_hi, const float *__restrict__ a_lo,
         pos[r] = base + threadIdx.x + r * 128;
         const bool valid = pos[r] < nrows;
         own[r] = valid ? a_lab[pos[r]] : -1;
+        // the row as float4 loads (hi + lo for TF32 operands)
 #pragma unroll
-        for (int c = 0; c < KD; c += 2) {
-            float v0 = 0.f, v1 = 0.f;
+        for (int q = 0; q < KD / 4; ++q) {
+            float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
             if (valid) {
-                v0 = a_hi[pos[r] * KD + c];
-                v1 = a_hi[pos[r] * KD + c + 1];
+                h = reinterpret_cast<const float4 *>(a_hi + pos[r] * KD)[q];
                 if (!BF) {
-                    v0 += a_lo[pos[r] * KD + c];
-                    v1 += a_lo[pos[r] * KD + c + 1];
+                    const float4 l = reinterpret_cast<const float4 *>(a_lo + pos[r] * KD)[q];
+                    h = make_float4(h.x + l.x, h.y + l.y, h.z + l.z, h.w + l.w);
                 }
             }
-            x[r][c / 2] = make_float2(v0, v1);
+            x[r][2 * q] = make_float2(h.x, h.y);
+            x[r][2 * q + 1] = make_float2(h.z, h.w);
         }
         zx[r] = (METRIC == SILH_COSINE && valid && a_norm[pos[r]] == 0.f) ? 0.5f : 0.f;
     }
@@ -1126,9 +1127,12 @@ k_own_sym(const float *__restrict__ yf, const float2 *__restrict__ ywn,
         zx[r] = (METRIC == SILH_COSINE && valid && wn.y == 0.f) ? 0.5f : 0.f;
         accr[r] = 0.f;
 #pragma unroll
-        for (int c = 0; c < KD / 2; ++c)
-            x[r][c] = valid ? make_float2(yf[pos[r] * KD + 2 * c], yf[pos[r] * KD + 2 * c + 1])
-                            : make_float2(0.f, 0.f);
+        for (int q = 0; q < KD / 4; ++q) {
+            const float4 h = valid ? reinterpret_cast<const float4 *>(yf + pos[r] * KD)[q]
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[r][2 * q] = make_float2(h.x, h.y);
+            x[r][2 * q + 1] = make_float2(h.z, h.w);
+        }
     }
     const int64_t cs_ = base + (int64_t)it.J * T, ce = min(cs_ + T, end);
     for (int64_t cb = cs_; cb < ce; cb += BN) {
