@@ -849,11 +849,20 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
         lp[r] = v ? lab_s[p] : -1;
         zx[r] = (METRIC == SILH_COSINE && v) ? zY[p] : 0.f;
         if (tiny_data && v && zY[p] != 0.f) any_slow = 1;    // a tiny row
+        // float4 loads of the padded row; Canberra's slot order (c0, c2, c1, c3)
+        // pairs the loaded lanes (x, z) and (y, w)
 #pragma unroll
-        for (int c = 0; c < D / 2; ++c)
-            x[r][c] = v ? make_float2(Y[p * D + canb_slot<METRIC>(2 * c)] * cscale,
-                                      Y[p * D + canb_slot<METRIC>(2 * c + 1)] * cscale)
-                        : make_float2(0.f, 0.f);
+        for (int q = 0; q < D / 4; ++q) {
+            const float4 u = v ? reinterpret_cast<const float4 *>(Y + p * D)[q]
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (METRIC == SILH_CANBERRA) {
+                x[r][2 * q] = make_float2(u.x * cscale, u.z * cscale);
+                x[r][2 * q + 1] = make_float2(u.y * cscale, u.w * cscale);
+            } else {
+                x[r][2 * q] = make_float2(u.x, u.y);
+                x[r][2 * q + 1] = make_float2(u.z, u.w);
+            }
+        }
 #pragma unroll
         for (int c = 0; c < NA; ++c) ax[r][c] = make_float2(fabsf(x[r][c].x), fabsf(x[r][c].y));
     }
