@@ -801,7 +801,9 @@ k_exact_sym(const float *__restrict__ Y, const float *__restrict__ zY,
             const int32_t *__restrict__ lab_s, int64_t n, int k, int64_t ntiles,
             const unsigned *__restrict__ crange, double *__restrict__ W) {
     constexpr int T = kThreads * RPT;
-    constexpr int BN = (D >= 128) ? 32 : 64;   // static shared memory stays under 48 KB
+    // columns per stage (static shared memory under 48 KB; Canberra measured
+    // faster with 64 at D = 32, the others with 128)
+    constexpr int BN = (D <= 32 && METRIC != SILH_CANBERRA) ? 128 : (D >= 128) ? 32 : 64;
     constexpr int NW = kThreads / 32;
     __shared__ __align__(16) float sh_y[BN * D];
     __shared__ __align__(16) float sh_ya[METRIC == SILH_CANBERRA ? BN * D : 4];
