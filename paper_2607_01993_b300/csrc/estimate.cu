@@ -670,8 +670,9 @@ template <class T, int METRIC, int D>
 cudaError_t launch_batched(int variant, const BatchParams &bp, cudaStream_t stream, const T *X,
                            int d, int64_t ld, int64_t n, const float *Y, const float *wY,
                            const float *zY, const unsigned *crange, unsigned long long *nw) {
-    // default: as the single sweep, (2, 128) for rows of up to 32 elements, else (1, 32)
-    if (variant < 0) variant = (D <= 32) ? 3 : 0;
+    // default: as the single sweep, (2, 128) for rows of up to 32 elements, else
+    // (1, 64), or (1, 32) for Canberra rows of 128
+    if (variant < 0) variant = (D <= 32) ? 3 : (D == 64 || METRIC != SILH_CANBERRA) ? 1 : 0;
     switch (variant) {
         case 0: return launch_batched_v<T, METRIC, D, 1, 32>(bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
         case 1: return launch_batched_v<T, METRIC, D, 1, 64>(bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
@@ -718,7 +719,7 @@ void launch_sweep(cudaStream_t stream, const T *X, int d, int64_t ld, int64_t n,
                   const int64_t *rows, int64_t nrows, float *s, float *a, float *b,
                   int32_t *nb) {
     constexpr int RPT = (D <= 32) ? 2 : 1;
-    constexpr int BN = (D <= 32) ? 128 : 32;
+    constexpr int BN = (D <= 32) ? 128 : (D == 64 || METRIC != SILH_CANBERRA) ? 64 : 32;
     int grid = (int)((nrows + kThreads * RPT - 1) / (kThreads * RPT));
     k_sweep<T, METRIC, D, RPT, BN, false><<<grid, kThreads, 0, stream>>>(
         X, d, ld, n, labels, k, sizes, offsets, Y, wY, zY, crange, rows, nrows, s, a, b, nb);

@@ -227,3 +227,23 @@ def test_batched_tensor_cores_graph_capture_and_replay(batch):
         torch.cuda.synchronize()
         for a, b in zip(outs, ref):
             assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("d", [40, 100])
+@pytest.mark.parametrize("metric", ["euclidean", "canberra"])
+def test_batched_equals_single_wide_rows(d, metric):
+    # rows padded to 64 and 128 elements: the default tile shape is the single
+    # sweep's (64 columns per stage; 32 for Canberra at 128), so the results
+    # are equal bit for bit
+    X, _, _ = synth.gaussian_mixture(5000, d, 6, seed=d, sigma=1.5)
+    if metric == "canberra":
+        X = synth.abs_shift(X)
+    Xt = torch.from_numpy(X).cuda()
+    items, ks = [], [3, 7]
+    for c, k in enumerate(ks):
+        lt = torch.from_numpy(synth.nearest_centre_labels(X, k, seed=c)).cuda()
+        items.append((lt, silh.silh_sample_pps(Xt, lt, k, metric, t=64.0, seed=c,
+                                               clustering_id=c)))
+    outs = silh.silh_estimate_batched(Xt, items, metric)
+    for (lt, smp), k, out in zip(items, ks, outs):
+        assert torch.equal(out, silh.silh_estimate(Xt, lt, k, smp, metric, prec="fp32"))
