@@ -675,7 +675,9 @@ cudaError_t launch_batched(int variant, const BatchParams &bp, cudaStream_t stre
     if (variant < 0) variant = (D <= 32) ? 3 : (D == 64 || METRIC != SILH_CANBERRA) ? 1 : 0;
     switch (variant) {
         case 0: return launch_batched_v<T, METRIC, D, 1, 32>(bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
-        case 1: return launch_batched_v<T, METRIC, D, 1, 64>(bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
+        case 1:   // Canberra rows of 128 keep 32 columns (two staged copies in 48 KB)
+            return launch_batched_v<T, METRIC, D, 1, (D >= 128 && METRIC == SILH_CANBERRA) ? 32 : 64>(
+                bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
         case 2: return launch_batched_v<T, METRIC, D, 2, 32>(bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);
         default: return launch_batched_v<T, METRIC, D, 2, (D <= 32 ? 128 : D >= 128 ? 32 : 64)>(
             bp, stream, X, d, ld, n, Y, wY, zY, crange, nw);

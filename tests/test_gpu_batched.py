@@ -247,3 +247,8 @@ def test_batched_equals_single_wide_rows(d, metric):
     outs = silh.silh_estimate_batched(Xt, items, metric)
     for (lt, smp), k, out in zip(items, ks, outs):
         assert torch.equal(out, silh.silh_estimate(Xt, lt, k, smp, metric, prec="fp32"))
+    # every tile shape launches at these widths and agrees to rounding
+    for v in range(silh.BATCH_VARIANTS):
+        got = silh.silh_estimate_batched(Xt, items, metric, variant=v)
+        for a, b in zip(got, outs):
+            assert (a - b).abs().max().item() <= 1e-6
