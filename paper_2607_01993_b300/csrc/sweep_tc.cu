@@ -250,6 +250,43 @@ struct TcItem {
     int32_t k;
     int32_t pad_;
 };
+// Close pairs of 64-element rows, deferred from the sweep's epilogue: a lane
+// whose chunk holds close pairs records them (the row, the chunk's first
+// operand column, the mask of close columns) instead of evaluating them, and
+// the cluster they belong to is "dirty" for that row: at its end the partial
+// W_hat_j (without those pairs) is recorded too (mask 0), in a slot reserved
+// with the cluster's first record.  Each row's records are chained (prev), in
+// the order the sweep met them.  A row with any dirty cluster leaves its
+// running minimum over the clean clusters in a row record instead of its
+// outputs.  k_defer_fix then evaluates every recorded chunk's close pairs
+// directly in FP32, and k_defer_final walks each dirty row's chain in a fixed
+// order, completes its dirty clusters, merges them into the minimum and writes
+// the outputs -- so results are deterministic and a batched item equals its
+// single call.  Lanes beyond the record capacity evaluate their pairs in the
+// epilogue as before.
+struct TcDeferEntry {
+    int32_t row;       // operand row
+    int32_t col;       // first operand column of the chunk
+    uint32_t mask;     // close columns of the chunk; 0: the end of a dirty cluster
+    int32_t prev;      // the row's previous record, -1 for its first
+    int32_t j;         // the cluster
+    int32_t pad_;
+    double val;        // chunk: sum of w d over its close pairs; end: partial W_hat_j
+};
+struct TcDeferRow {
+    double bacc, bsize;    // minimum over the clean clusters of W_hat_j / |Cj| (as RatioMin)
+    int32_t barg, head;    // its cluster; the row's last record
+    int32_t row, item;     // operand row; clustering (batched) or 0
+    int64_t out;           // output index
+};
+struct TcDefer {
+    TcDeferEntry *ent;          // nullptr: no deferral (the epilogue evaluates close pairs)
+    TcDeferRow *rec;
+    unsigned long long *ctr;    // [0] records reserved, [1] dirty rows
+    int64_t ent_cap, rec_cap;
+    int64_t nrows_ops, ncols_ops;   // rows and columns of the operands (bounds of the records)
+};
+
 constexpr int kMaxTcBatch = 256;
 // Column tiles of (w, |y|^2) the producer may stage ahead of the epilogue.
 constexpr int kWnRing = 8;
@@ -288,12 +325,13 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
            const double *__restrict__ w_own, float *__restrict__ s_out,
            float *__restrict__ a_out_v, float *__restrict__ b_out_v,
            int32_t *__restrict__ nb_out_v, double *__restrict__ W,
-           const int4 *__restrict__ sym_work, int64_t n_sym_work,
+           const int4 *__restrict__ sym_work, int64_t n_sym_work, const TcDefer df,
            const __grid_constant__ TcBatchArg<BATCH> bt) {
     static_assert(!(BATCH && SYM), "the symmetric exact sweep is not batched");
     using C = TcCfg<KD, SPLIT, BF, WIDE>;
     constexpr int TN = C::TN;
     constexpr bool kColRedo = tc_col_redo(KD);
+    constexpr bool kDefer = !SYM && !kColRedo;    // 64-element rows may defer close pairs
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_full[C::STAGES], bar_empty[C::STAGES];
     __shared__ uint64_t bar_afull, bar_aempty, bar_accf[C::SLOTS][C::NACC], bar_acce[C::SLOTS][C::NACC];
@@ -326,7 +364,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
         int64_t rg, arow, ccol, nrows, mp, nct, ct_b, ct_e;
         const int64_t *poff, *sizes;
         float *s_out;
-        int k;
+        int k, item;
     };
     auto view_of = [&](int64_t w) -> View {
         View v;
@@ -346,6 +384,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             v.sizes = it.sizes;
             v.s_out = it.s_out;
             v.k = it.k;
+            v.item = lo;
         } else {
             v.rg = w;
             v.arow = 0;
@@ -355,6 +394,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             v.sizes = sizes;
             v.s_out = s_out;
             v.k = k;
+            v.item = 0;
         }
         v.mp = v.poff[v.k];
         v.nct = (v.mp + TN - 1) / TN;
@@ -631,6 +671,8 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             int64_t pbnd = (j < vk) ? vpoff[j + 1] : LLONG_MAX;
             double accd = 0.0;
             RatioMin bmin;
+            int32_t dlast = -1, dmark = -1;           // deferral: last record; dirty cluster's end slot
+            bool ddirty = false;                      // the row has a dirty cluster
             float accf = 0.f;                         // current cluster, this tile
             bool dead = false;
             for (int64_t ct = ct0; ct < ct_end; ++ct) {
@@ -662,7 +704,13 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                         if (SYM) {
                             if (accd != 0.0 && rw != 0.f) atomicAdd(&W[pos * k + j], accd);
                         } else if (j != own) {
-                            bmin.add(accd, (double)v.sizes[j], j);
+                            if (kDefer && dmark >= 0) {   // a dirty cluster ends: its partial sum
+                                df.ent[dmark] = TcDeferEntry{(int32_t)apos, 0, 0u, dlast, j, 0, accd};
+                                dlast = dmark;
+                                dmark = -1;
+                            } else {
+                                bmin.add(accd, (double)v.sizes[j], j);
+                            }
                         }
                         accd = 0.0;
                         ++j;
@@ -784,6 +832,40 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                             }
                         }
                         if (mine || !valid) fm = 0u;     // own-cluster sums come from w_own
+                        if (kDefer && df.ent != nullptr) {
+                            // record the close pairs instead (a cluster's first record also
+                            // reserves its end slot); slots are taken for the warp at once
+                            const uint32_t need = (fm != 0u) ? (dmark >= 0 ? 1u : 2u) : 0u;
+                            uint32_t incl = need;
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (lane >= o) incl += t;
+                            }
+                            const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+                            if (tot != 0u) {
+                                unsigned long long b0 = 0ull;
+                                if (lane == 0) b0 = atomicAdd(&df.ctr[0], (unsigned long long)tot);
+                                b0 = __shfl_sync(0xffffffffu, b0, 0);
+                                const unsigned long long my = b0 + incl - need;
+                                const unsigned long long cap = (unsigned long long)df.ent_cap;
+                                if (need != 0u && my + need <= cap) {
+                                    df.ent[my] = TcDeferEntry{(int32_t)apos, (int32_t)(v.ccol + c0), fm,
+                                                              dlast, j, 0, 0.0};
+                                    dlast = (int32_t)my;
+                                    if (dmark < 0) {
+                                        dmark = (int32_t)(my + 1);
+                                        ddirty = true;
+                                    }
+                                    fm = 0u;                // done here; k_defer_fix evaluates them
+                                } else {
+                                    // past the capacity: this lane evaluates its pairs below;
+                                    // slots of its reservation that lie inside are left empty
+                                    for (unsigned long long q = my; q < my + need && q < cap; ++q)
+                                        df.ent[q].mask = 0u, df.ent[q].row = -1;
+                                }
+                            }
+                        }
                         constexpr bool kFullRows = BF;
                         // Dense chunks (many close pairs per marked column): each lane
                         // evaluates its own marked pairs column by column, the lanes in
@@ -919,12 +1001,26 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 while (j < vk) {
                     accd += (double)accf;
                     accf = 0.f;
-                    if (j != own) bmin.add(accd, (double)v.sizes[j], j);
+                    if (j != own) {
+                        if (kDefer && dmark >= 0) {
+                            df.ent[dmark] = TcDeferEntry{(int32_t)apos, 0, 0u, dlast, j, 0, accd};
+                            dlast = dmark;
+                            dmark = -1;
+                        } else {
+                            bmin.add(accd, (double)v.sizes[j], j);
+                        }
+                    }
                     accd = 0.0;
                     ++j;
                 }
                 const double wown = (valid && own >= 0) ? w_own[apos] : 0.0;
-                if (valid) {
+                if (kDefer && valid && ddirty) {
+                    // outputs come from k_defer_final, which completes the dirty clusters
+                    const unsigned long long ri = atomicAdd(&df.ctr[1], 1ull);
+                    if (ri < (unsigned long long)df.rec_cap)
+                        df.rec[ri] = TcDeferRow{bmin.acc, bmin.size, bmin.arg, dlast, (int32_t)apos,
+                                                v.item, a_out[apos]};
+                } else if (valid) {
                     const int64_t o = a_out[apos];
                     float sv, av, bv;
                     if (own < 0 || own >= vk) {
@@ -970,6 +1066,115 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     if (warp == 1) {
         __syncwarp();
         tmem_dealloc(tmem, C::TMEM_COLS);
+    }
+}
+
+// Deferred close pairs, step 1: every recorded chunk's close pairs evaluated
+// directly in FP32 from the coordinates (a warp per record, two coordinates
+// per lane, a shuffle sum per pair, the pairs in column order); the sum of
+// w d goes to the record.  Rows: a_hi (+ a_lo for TF32 operands: x = hi + lo
+// exactly); columns: y_full, weights from y_wn.  Records outside the operands
+// (left empty by a reservation past the capacity) are skipped.
+template <int METRIC, int KD, bool BF>
+__global__ void __launch_bounds__(256)
+k_defer_fix(const TcDefer df, const float *__restrict__ a_hi, const float *__restrict__ a_lo,
+            int64_t nrows_ops, const float *__restrict__ y_full,
+            const float2 *__restrict__ y_wn, int64_t ncols_ops) {
+    static_assert(KD == 64, "deferral is for 64-element rows");
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t count = min((int64_t)df.ctr[0], df.ent_cap);
+    for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < count;
+         e += nw) {
+        const uint32_t mask = df.ent[e].mask;
+        const int64_t row = df.ent[e].row, col = df.ent[e].col;
+        if (mask == 0u || row < 0 || row >= nrows_ops || col < 0 || col + 32 > ncols_ops) continue;
+        const float2 h = reinterpret_cast<const float2 *>(a_hi + row * KD)[lane];
+        float2 x = h;
+        if (!BF) {
+            const float2 l = reinterpret_cast<const float2 *>(a_lo + row * KD)[lane];
+            x = make_float2(h.x + l.x, h.y + l.y);
+        }
+        float acc = 0.f;
+        uint32_t m = mask;
+        while (m != 0u) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1u;
+            const float2 y = reinterpret_cast<const float2 *>(y_full + (col + i) * KD)[lane];
+            const float t0 = x.x - y.x, t1 = x.y - y.y;
+            float ss = fmaf(t0, t0, t1 * t1);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            const float dist = (METRIC == SILH_EUCLIDEAN) ? sqrtf(ss) : 0.5f * ss;
+            acc = fmaf(y_wn[col + i].x, dist, acc);
+        }
+        if (lane == 0) df.ent[e].val = (double)acc;
+    }
+}
+
+// Deferred close pairs, step 2: per dirty row, its records walked from the
+// last one back (a fixed order): each dirty cluster's partial W_hat_j plus its
+// chunks' sums, merged into the row's minimum over the clean clusters (lower
+// cluster index on equal ratios), then s_hat, a_hat, b_hat and the neighbour
+// as the sweep writes them.
+template <bool BATCH>
+__global__ void __launch_bounds__(256)
+k_defer_final(const TcDefer df, const int32_t *__restrict__ a_lab, const double *__restrict__ w_own,
+              const int64_t *__restrict__ sizes, int k, float *__restrict__ s_out,
+              float *__restrict__ a_out_v, float *__restrict__ b_out_v, int32_t *__restrict__ nb_out_v,
+              const __grid_constant__ TcBatchArg<BATCH> bt) {
+    const int64_t count = min((int64_t)df.ctr[1], df.rec_cap);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < count;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const TcDeferRow R = df.rec[r];
+        const int64_t *sz = sizes;
+        float *so = s_out;
+        int kk = k;
+        if constexpr (BATCH) {
+            sz = bt.items[R.item].sizes;
+            so = bt.items[R.item].s_out;
+            kk = bt.items[R.item].k;
+        }
+        double acc = R.bacc, bsz = R.bsize;
+        int arg = R.barg;
+        auto merge = [&](int j, double w) {
+            const double sj = (double)sz[j];
+            const double lhs = w * bsz, rhs = acc * sj;
+            if (lhs < rhs || (lhs == rhs && j < arg)) {
+                acc = w;
+                bsz = sj;
+                arg = j;
+            }
+        };
+        int cj = -1;
+        double csum = 0.0;
+        for (int32_t e = R.head; e >= 0; e = df.ent[e].prev) {
+            if (df.ent[e].mask == 0u) {           // the end of a dirty cluster
+                if (cj >= 0) merge(cj, csum);
+                cj = df.ent[e].j;
+                csum = df.ent[e].val;
+            } else {
+                csum += df.ent[e].val;
+            }
+        }
+        if (cj >= 0) merge(cj, csum);
+        const int own = a_lab[R.row];
+        float sv, av, bv;
+        if (own < 0 || own >= kk) {
+            sv = av = bv = NAN;
+        } else {
+            const int64_t nc = sz[own];
+            const double a = (nc > 1) ? w_own[R.row] / (double)(nc - 1) : 0.0;
+            const double b = acc / bsz;
+            const double mx = fmax(a, b);
+            sv = (float)((nc > 1 && mx > 0.0) ? (b - a) / mx : 0.0);
+            av = (float)a;
+            bv = (float)b;
+        }
+        so[R.out] = sv;
+        if (a_out_v) a_out_v[R.out] = av;
+        if (b_out_v) b_out_v[R.out] = bv;
+        if (nb_out_v) nb_out_v[R.out] = (own < 0 || own >= kk) ? -1 : arg;
     }
 }
 
@@ -1631,7 +1836,7 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
                       int64_t max_cluster_cols, double *w_own, float *s, float *a, float *b,
                       int32_t *nb, double *W = nullptr, const OwnItem *own_items = nullptr,
                       int64_t n_own_items = 0, const int4 *sym_work = nullptr,
-                      int64_t n_sym_work = 0) {
+                      int64_t n_sym_work = 0, const TcDefer df = TcDefer{}) {
     constexpr bool WIDE = wide_tiles(KD, BF);
     using C = TcCfg<KD, SPLIT, BF, WIDE>;
     if (SYM) {
@@ -1658,8 +1863,17 @@ cudaError_t launch_tc(int nsm, cudaStream_t stream, const CUtensorMap &ahi, cons
                                                 a_lab, a_out, nrows, y_full, y_il, y_wn,
                                                 reinterpret_cast<const float4 *>(y_wn4), poff,
                                                 sizes, k, tau, dq, w_own, s, a, b, nb, W, sym_work,
-                                                n_sym_work, TcBatchArg<false>{});
+                                                n_sym_work, df, TcBatchArg<false>{});
     count_launches(1);
+    if constexpr (KD == 64 && !SYM) {
+        if (df.ent != nullptr) {      // the close pairs the sweep recorded, then the dirty rows
+            k_defer_fix<METRIC, KD, BF><<<nsm * 8, 256, 0, stream>>>(df, a_hi, a_lo, df.nrows_ops,
+                                                                      y_full, y_wn, df.ncols_ops);
+            k_defer_final<false><<<nsm * 4, 256, 0, stream>>>(df, a_lab, w_own, sizes, k, s, a, b,
+                                                              nb, TcBatchArg<false>{});
+            count_launches(2);
+        }
+    }
     return cudaGetLastError();
 }
 
@@ -1675,7 +1889,7 @@ cudaError_t launch_tc_batched(int nsm, cudaStream_t stream, const CUtensorMap &a
                               const float *y_full, const float *y_il, const float2 *y_wn,
                               const float *y_wn4, const int64_t *poff,
                               float tau, int dq, const double *w_own,
-                              const TcBatchArg<true> &bt) {
+                              const TcBatchArg<true> &bt, const TcDefer df) {
     using C = TcCfg<KD, SPLIT, BF, WIDE>;
     auto kern = k_sweep_tc<METRIC, KD, SPLIT, BF, false, WIDE, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
@@ -1685,8 +1899,17 @@ cudaError_t launch_tc_batched(int nsm, cudaStream_t stream, const CUtensorMap &a
                                                 a_lab, a_out, 0, y_full, y_il, y_wn,
                                                 reinterpret_cast<const float4 *>(y_wn4), poff, nullptr,
                                                 0, tau, dq, w_own, nullptr, nullptr, nullptr,
-                                                nullptr, nullptr, nullptr, 0, bt);
+                                                nullptr, nullptr, nullptr, 0, df, bt);
     count_launches(1);
+    if constexpr (KD == 64) {
+        if (df.ent != nullptr) {
+            k_defer_fix<METRIC, KD, BF><<<nsm * 8, 256, 0, stream>>>(df, a_hi, a_lo, df.nrows_ops,
+                                                                      y_full, y_wn, df.ncols_ops);
+            k_defer_final<true><<<nsm * 4, 256, 0, stream>>>(df, a_lab, w_own, nullptr, 0, nullptr,
+                                                             nullptr, nullptr, nullptr, bt);
+            count_launches(2);
+        }
+    }
     return cudaGetLastError();
 }
 
@@ -1811,6 +2034,7 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     int dev = 0, nsm = 0;
     double *w_own = nullptr;
     TcOps o = {};
+    TcDefer df = {};
     CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
     const float tau = 0.25f;
 
@@ -1831,6 +2055,16 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
     // the sweep stages whole 128-column tiles of (w, |y|^2): zeros past mp_max
     SILH_CK(sc.alloc(&o.ywn4, (size_t)2 * wn_cols));
     SILH_CK(cudaMemsetAsync(o.ywn4, 0, sizeof(float) * 2 * (size_t)wn_cols, stream));
+    if (KD == 64) {        // records of deferred close pairs (a few per row covers the typical case)
+        df.ent_cap = std::min<int64_t>(4 * nrows + (int64_t(1) << 20), int64_t(1) << 27);
+        df.rec_cap = nrows;
+        df.nrows_ops = nrows;
+        df.ncols_ops = mp_max;
+        SILH_CK(sc.alloc(&df.ent, (size_t)df.ent_cap));
+        SILH_CK(sc.alloc(&df.rec, (size_t)nrows));
+        SILH_CK(sc.alloc(&df.ctr, 2));
+        SILH_CK(cudaMemsetAsync(df.ctr, 0, 2 * sizeof(unsigned long long), stream));
+    }
     st = tc_prepare(X, dtype, n, d, ld, labels, k, metric, KD, bf, offsets, col_idx, col_p, m,
                     rows, nrows, nrows, mp_max, o, stream, d_m);
     if (st != SILH_OK) goto done;
@@ -1848,7 +2082,8 @@ silh_status tc_sweep(const void *X, silh_dtype dtype, int64_t n, int32_t d, int6
         SILH_CK((launch_tc<MET, KDV, SP, BFV>(                                                  \
             nsm, stream, m_ahi, m_alo, m_bhi, m_blo, BFV ? o.rfull : (const float *)o.rhi,     \
             BFV ? nullptr : (const float *)o.rlo, o.ril, o.rn, o.lab, o.outi, nrows, o.yf,      \
-            o.yil, o.ywn, o.ywn4, o.poff, sizes, k, tau, (d + 3) / 4, max_cluster_cols, w_own, s, a, b, nb))); \
+            o.yil, o.ywn, o.ywn4, o.poff, sizes, k, tau, (d + 3) / 4, max_cluster_cols, w_own, s, a, b, nb, \
+            nullptr, nullptr, 0, nullptr, 0, df)));                                             \
     }
 #define SILH_TC_CASES(MET, KDV)             \
     SILH_TC_CASE(MET, KDV, true, false)     \
@@ -1891,8 +2126,10 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
         const silh_sample *S = items[i].sample;
         return (S->size + 31 * (int64_t)S->k + 127) / 128 * 128;
     };
+    // per row also the records of deferred close pairs (64-element rows)
+    const size_t defer_row_bytes = (KD == 64) ? 4 * sizeof(TcDeferEntry) + sizeof(TcDeferRow) : 0;
     auto bytes_of = [&](int32_t i) -> size_t {
-        return (size_t)rows_pad * row_bytes + (size_t)cols_of(i) * col_bytes +
+        return (size_t)rows_pad * (row_bytes + defer_row_bytes) + (size_t)cols_of(i) * col_bytes +
                8 * (size_t)(items[i].sample->k + 1);
     };
     SILH_CK(cudaGetDevice(&dev));
@@ -1915,6 +2152,7 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
         const int64_t rows_total = rows_pad * nb;
         Scratch gs(stream);                       // this group's operands
         TcOps g = {};
+        TcDefer df = {};
         double *w_own = nullptr;
         CUtensorMap m_ahi, m_alo, m_bhi, m_blo;
         TcBatchArg<true> bt;
@@ -1936,6 +2174,16 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
         SILH_CK(gs.alloc(&g.ylo, (size_t)cols_total * KE * ebytes));
         SILH_CK(gs.alloc(&g.ywn, (size_t)cols_total));
         SILH_CK(gs.alloc(&g.ywn4, (size_t)2 * cols_total));   // whole tiles, all written
+        if (KD == 64) {    // deferred close pairs of every clustering of the group
+            df.ent_cap = std::min<int64_t>(4 * rows_total + (int64_t(1) << 20), int64_t(1) << 27);
+            df.rec_cap = rows_total;
+            df.nrows_ops = rows_total;
+            df.ncols_ops = cols_total;
+            SILH_CK(gs.alloc(&df.ent, (size_t)df.ent_cap));
+            SILH_CK(gs.alloc(&df.rec, (size_t)rows_total));
+            SILH_CK(gs.alloc(&df.ctr, 2));
+            SILH_CK(cudaMemsetAsync(df.ctr, 0, 2 * sizeof(unsigned long long), stream));
+        }
         {
             int64_t ccol = 0, pbase = 0;
             for (int c = 0; c < nb; ++c) {
@@ -2000,7 +2248,7 @@ silh_status tc_sweep_batched(const void *X, silh_dtype dtype, int64_t n, int32_t
                 nsm, stream, m_ahi, m_alo, m_bhi, m_blo,                                        \
                 BFV ? g.rfull : (const float *)g.rhi, BFV ? nullptr : (const float *)g.rlo,     \
                 g.ril, g.rn, g.lab, g.outi, g.yf, g.yil, g.ywn, g.ywn4, g.poff, tau, (d + 3) / 4, w_own, \
-                bt)));                                                                          \
+                bt, df)));                                                                      \
         }
 #define SILH_TC_BCASE(MET, KDV, SP, BFV) SILH_TC_BCASE_W(MET, KDV, SP, BFV, wide_tiles(KDV, BFV))
 #define SILH_TC_BCASES(MET, KDV)             \
