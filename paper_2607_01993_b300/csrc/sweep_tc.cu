@@ -1070,18 +1070,20 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
 }
 
 // Deferred close pairs, step 1: every recorded chunk's close pairs evaluated
-// directly in FP32 from the coordinates (a warp per record, two coordinates
-// per lane, a shuffle sum per pair, the pairs in column order); the sum of
-// w d goes to the record.  Rows: a_hi (+ a_lo for TF32 operands: x = hi + lo
-// exactly); columns: y_full, weights from y_wn.  Records outside the operands
-// (left empty by a reservation past the capacity) are skipped.
+// directly in FP32 from the coordinates, a warp per record and two pairs at a
+// time (each half-warp one pair, four coordinates per lane, a four-step
+// shuffle sum), the terms added in column order; the sum of w d goes to the
+// record.  Rows: a_hi (+ a_lo for TF32 operands: x = hi + lo exactly);
+// columns: y_full, weights from y_wn.  Records outside the operands (left
+// empty by a reservation past the capacity) are skipped.
 template <int METRIC, int KD, bool BF>
 __global__ void __launch_bounds__(256)
 k_defer_fix(const TcDefer df, const float *__restrict__ a_hi, const float *__restrict__ a_lo,
             int64_t nrows_ops, const float *__restrict__ y_full,
             const float2 *__restrict__ y_wn, int64_t ncols_ops) {
-    static_assert(KD == 64, "deferral is for 64-element rows");
-    const int lane = threadIdx.x & 31;
+    static_assert(KD == 64, "deferral is for 64-element rows (16 lanes x 4 coordinates)");
+    const int lane = threadIdx.x & 31, h = lane & 15;
+    const bool upper = lane >= 16;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t count = min((int64_t)df.ctr[0], df.ent_cap);
     for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < count;
@@ -1089,24 +1091,29 @@ k_defer_fix(const TcDefer df, const float *__restrict__ a_hi, const float *__res
         const uint32_t mask = df.ent[e].mask;
         const int64_t row = df.ent[e].row, col = df.ent[e].col;
         if (mask == 0u || row < 0 || row >= nrows_ops || col < 0 || col + 32 > ncols_ops) continue;
-        const float2 h = reinterpret_cast<const float2 *>(a_hi + row * KD)[lane];
-        float2 x = h;
+        float4 x = reinterpret_cast<const float4 *>(a_hi + row * KD)[h];
         if (!BF) {
-            const float2 l = reinterpret_cast<const float2 *>(a_lo + row * KD)[lane];
-            x = make_float2(h.x + l.x, h.y + l.y);
+            const float4 l = reinterpret_cast<const float4 *>(a_lo + row * KD)[h];
+            x = make_float4(x.x + l.x, x.y + l.y, x.z + l.z, x.w + l.w);
         }
         float acc = 0.f;
         uint32_t m = mask;
         while (m != 0u) {
-            const int i = __ffs(m) - 1;
+            const int ia = __ffs(m) - 1;          // this round's pairs: the next two columns
             m &= m - 1u;
-            const float2 y = reinterpret_cast<const float2 *>(y_full + (col + i) * KD)[lane];
-            const float t0 = x.x - y.x, t1 = x.y - y.y;
-            float ss = fmaf(t0, t0, t1 * t1);
+            const int ib = (m != 0u) ? __ffs(m) - 1 : -1;
+            if (m != 0u) m &= m - 1u;
+            const int i = upper ? (ib < 0 ? ia : ib) : ia;
+            const float4 y = reinterpret_cast<const float4 *>(y_full + (col + i) * KD)[h];
+            const float t0 = x.x - y.x, t1 = x.y - y.y, t2 = x.z - y.z, t3 = x.w - y.w;
+            float ss = fmaf(t0, t0, t1 * t1) + fmaf(t2, t2, t3 * t3);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            for (int o = 8; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
             const float dist = (METRIC == SILH_EUCLIDEAN) ? sqrtf(ss) : 0.5f * ss;
-            acc = fmaf(y_wn[col + i].x, dist, acc);
+            const float term = y_wn[col + i].x * dist;
+            const float tb = __shfl_sync(0xffffffffu, term, 16);   // the upper half's pair
+            acc += term;                                            // column order: a, then b
+            if (ib >= 0) acc += tb;
         }
         if (lane == 0) df.ent[e].val = (double)acc;
     }
