@@ -537,7 +537,6 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 if (w == -2) break;
                 if (w < 0) continue;
                 const View v = view_of(w);
-                const int64_t rg = v.rg;
                 if (!mbar_wait(&bar_afull, (uint32_t)(idx & 1), kWaitNs)) {
                     abort_flag = 1;
                     break;
@@ -616,7 +615,6 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
         const int g = (warp - 2) >> 2;          // row-tile slot of this group
         const int q = warp & 3;                 // TMEM lane quarter of this warp
         const int r_local = 32 * q + lane;
-        const int et = threadIdx.x - 64 - 128 * g;
         const uint32_t tlane = (uint32_t)(32 * q) << 16;
         uint32_t acc = 0, acc_phase = 0;
         uint64_t wt = 0;                         // column tiles consumed from the ring so far
@@ -626,7 +624,6 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
             if (w < 0) continue;
             const View v = view_of(w);
             const int64_t rg = v.rg;
-            const int64_t mp = v.mp;
             const int64_t ct_end = v.ct_e;
             const int64_t *vpoff = v.poff;
             const int vk = v.k;
