@@ -1567,57 +1567,89 @@ __device__ __forceinline__ void store_split(float v, int64_t row, int c, int KD,
 // 32-element rows reads it), squared norm (Euclidean) or unit scaling
 // (cosine), label, output index.
 // Positions nrows .. nrows_pad - 1 get zero hi/lo rows (the tail of a row
-// group that the tile loads read).
+// group that the tile loads read).  A warp per position, grid-stride with two
+// positions in flight per warp (each position's loads -- its permutation
+// entry, then its row and label -- depend on one another, so the second
+// position's chain overlaps the first's); lane c holds elements c, c + 32, ...
 template <class T, bool BF>
-__global__ void k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int64_t n,
-                                 const int32_t *__restrict__ labels, const int64_t *__restrict__ rows,
-                                 const int64_t *__restrict__ perm, int64_t nrows, int64_t nrows_pad,
-                                 int KD, int k, int metric, const float *__restrict__ mu,
-                                 void *__restrict__ hi, void *__restrict__ lo,
-                                 float *__restrict__ full, float *__restrict__ il,
-                                 float *__restrict__ nrm, int32_t *__restrict__ lab,
-                                 int64_t *__restrict__ outi) {
-    const int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+__global__ void __launch_bounds__(256)
+k_gather_rows_tc(const T *__restrict__ X, int d, int64_t ld, int64_t n,
+                 const int32_t *__restrict__ labels, const int64_t *__restrict__ rows,
+                 const int64_t *__restrict__ perm, int64_t nrows, int64_t nrows_pad,
+                 int KD, int k, int metric, const float *__restrict__ mu,
+                 void *__restrict__ hi, void *__restrict__ lo,
+                 float *__restrict__ full, float *__restrict__ il,
+                 float *__restrict__ nrm, int32_t *__restrict__ lab,
+                 int64_t *__restrict__ outi) {
+    constexpr int U = 2;                      // positions in flight per warp
+    constexpr int NE = 4;                     // elements per lane (rows of up to 128)
     const int lane = threadIdx.x & 31;
-    if (p >= nrows_pad) return;
-    if (p >= nrows) {
-        for (int c = lane; c < (BF ? 64 : KD); c += 32) {
-            store_split<BF>(0.f, p, c, KD, hi, lo);
-            if (il != nullptr && c < KD) il[il_index(p, c, KD)] = 0.f;
+    const int KE = BF ? 64 : KD;              // elements stored per row
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t p0 = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; p0 < nrows_pad;
+         p0 += U * wstride) {
+        int64_t r[U], e[U];
+        bool ok[U];
+        float v[U][NE];
+        int32_t l[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t p = p0 + u * wstride;
+            r[u] = (p < nrows) ? perm[p] : -1;
         }
-        return;
-    }
-    const int64_t r = perm[p];
-    const int64_t e = rows ? rows[r] : r;
-    const bool ok = e >= 0 && e < n;
-    const T *x = X + (ok ? e : 0) * ld;
-    // norms in FP32 (pairwise over the lanes): they enter the epilogue in FP32
-    float s = 0.f;
-    if (metric == SILH_COSINE) {
-        for (int c = lane; c < d; c += 32) {
-            const float v = ok ? to_f32<T>(x[c]) : 0.f;
-            s = fmaf(v, v, s);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            e[u] = (r[u] >= 0) ? (rows ? rows[r[u]] : r[u]) : -1;
+            ok[u] = e[u] >= 0 && e[u] < n;
+            const T *x = X + (ok[u] ? e[u] : 0) * ld;
+#pragma unroll
+            for (int i = 0; i < NE; ++i) {
+                const int c = lane + 32 * i;
+                v[u][i] = (ok[u] && c < d) ? to_f32<T>(x[c]) : 0.f;
+            }
+            l[u] = ok[u] ? labels[e[u]] : -1;
         }
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    }
-    const float scale = (metric == SILH_COSINE) ? (s > 0.f ? rsqrtf(s) : 0.f) : 1.f;
-    float ss = 0.f;
-    const int KE = BF ? 64 : KD;
-    for (int c = lane; c < KE; c += 32) {
-        float v = (ok && c < d) ? to_f32<T>(x[c]) * scale : 0.f;
-        if (mu != nullptr && c < d) v = v - mu[c];
-        store_split<BF>(v, p, c, KD, hi, lo);
-        if (BF && c < KD) full[p * KD + c] = v;
-        if (il != nullptr && c < KD) il[il_index(p, c, KD)] = v;
-        ss = fmaf(v, v, ss);
-    }
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) {
-        // Euclidean: squared norm of the (centred) row; cosine: 1, or 0 for a zero row
-        nrm[p] = (metric == SILH_COSINE) ? (s > 0.f ? 1.f : 0.f) : ss;
-        const int32_t l = ok ? labels[e] : -1;
-        lab[p] = (l >= 0 && l < k) ? l : -1;
-        outi[p] = r;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t p = p0 + u * wstride;
+            if (p >= nrows_pad) continue;         // uniform over the warp
+            if (p >= nrows) {
+                for (int c = lane; c < (BF ? 64 : KD); c += 32) {
+                    store_split<BF>(0.f, p, c, KD, hi, lo);
+                    if (il != nullptr && c < KD) il[il_index(p, c, KD)] = 0.f;
+                }
+                continue;
+            }
+            // norms in FP32 (pairwise over the lanes): they enter the epilogue in FP32
+            float s = 0.f;
+            if (metric == SILH_COSINE) {
+#pragma unroll
+                for (int i = 0; i < NE; ++i)
+                    if (lane + 32 * i < d) s = fmaf(v[u][i], v[u][i], s);
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            }
+            const float scale = (metric == SILH_COSINE) ? (s > 0.f ? rsqrtf(s) : 0.f) : 1.f;
+            float ss = 0.f;
+#pragma unroll
+            for (int i = 0; i < NE; ++i) {
+                const int c = lane + 32 * i;
+                if (c < KE) {
+                    float w = (c < d) ? v[u][i] * scale : 0.f;
+                    if (mu != nullptr && c < d) w = w - mu[c];
+                    store_split<BF>(w, p, c, KD, hi, lo);
+                    if (BF && c < KD) full[p * KD + c] = w;
+                    if (il != nullptr && c < KD) il[il_index(p, c, KD)] = w;
+                    ss = fmaf(w, w, ss);
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            if (lane == 0) {
+                // Euclidean: squared norm of the (centred) row; cosine: 1, or 0 for a zero row
+                nrm[p] = (metric == SILH_COSINE) ? (s > 0.f ? 1.f : 0.f) : ss;
+                lab[p] = (l[u] >= 0 && l[u] < k) ? l[u] : -1;
+                outi[p] = r[u];
+            }
+        }
     }
 }
 
@@ -1945,6 +1977,7 @@ silh_status tc_prepare(const void *X, silh_dtype dtype, int64_t n, int32_t d, in
                        const int64_t *d_m = nullptr) {
     silh_status st = SILH_OK;
     Scratch sc(stream);                          // temporaries, released on return
+    int gdev = 0, gsm = 0, gather_blocks = 1;
     const int tile = (k <= 512) ? 1024 : 8192;
     const int ntiles = (int)std::max<int64_t>(1, (nrows + tile - 1) / tile);
     const size_t hsmem = sizeof(int32_t) * (size_t)(k + 1);
@@ -1993,8 +2026,13 @@ silh_status tc_prepare(const void *X, silh_dtype dtype, int64_t n, int32_t d, in
     if (o.yil != nullptr && mp_pad % 32 != 0)      // and so are columns past mp_pad
         SILH_CK(cudaMemsetAsync(o.yil + (mp_pad / 32) * 32 * KD, 0, sizeof(float) * 32 * KD,
                                 stream));
+    // row gather: grid-stride, eight CTAs of eight warps per SM at most
+    SILH_CK(cudaGetDevice(&gdev));
+    SILH_CK(cudaDeviceGetAttribute(&gsm, cudaDevAttrMultiProcessorCount, gdev));
+    gather_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((nrows_pad + 15) / 16,
+                                                                (int64_t)gsm * 8));
 #define SILH_TC_GATHER(T, BFV)                                                                  \
-    k_gather_rows_tc<T, BFV><<<ceil_div_i(nrows_pad, 8), 256, 0, stream>>>(                    \
+    k_gather_rows_tc<T, BFV><<<gather_blocks, 256, 0, stream>>>(                               \
         (const T *)X, d, ld, n, labels, rows, perm, nrows, nrows_pad, KD, k, metric, mu, o.rhi, \
         o.rlo, o.rfull, o.ril, o.rn, o.lab, o.outi);                                            \
     k_gather_cols_tc<T, BFV><<<ceil_div_i(mp_pad, 8), 256, 0, stream>>>(                       \
