@@ -161,6 +161,30 @@ def test_exact_matches_oracle(case, metric):
     assert abs(g - oracle.mean(s_o)) <= S_TOL / 10
 
 
+@pytest.mark.parametrize("d", [27, 32])
+@pytest.mark.parametrize("metric", ["manhattan", "canberra"])
+def test_exact_32_element_rows_match_oracle(metric, d):
+    """Exact silhouette (Eq. 1-2) of 32-element rows on CUDA cores, whose
+    symmetric kernel takes blocks of columns inside one cluster without
+    per-column checks: cluster ends inside column blocks, row tiles that span
+    clusters, a 4-point cluster, a ragged last tile, several column tiles per
+    block; all rows element by element, and a row list."""
+    sizes = [1201, 777, 513, 389, 250, 203, 4]
+    X, lab, _ = synth.gaussian_mixture(sum(sizes), d, len(sizes), seed=31, sizes=sizes,
+                                       sigma_range=(0.5, 3.0))
+    if metric == "canberra":
+        X = synth.abs_shift(X)
+    k = len(sizes)
+    Xt, lt = _to_dev(X, lab)
+    Xh = _host_values(Xt)
+    s, a, b = silh.silh_exact(Xt, lt, k, metric, want_ab=True)
+    s_o, a_o, b_o = oracle.exact(Xh, lab, k, metric)
+    _assert_close(s, s_o, a, a_o, b, b_o)
+    rows = np.array([3336, 0, 1700, 2999, 5, 1201])
+    sr = silh.silh_exact(Xt, lt, k, metric, rows=torch.from_numpy(rows).cuda())
+    _assert_close(sr, s_o[rows])
+
+
 def test_bf16_storage_matches_oracle_on_rounded_values():
     X, lab, k, kw = _case("multitile")
     Xt, lt = _to_dev(X, lab, torch.bfloat16)
