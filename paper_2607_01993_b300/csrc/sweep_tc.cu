@@ -332,6 +332,11 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
     constexpr int TN = C::TN;
     constexpr bool kColRedo = tc_col_redo(KD);
     constexpr bool kDefer = !SYM && !kColRedo;    // 64-element rows may defer close pairs
+    // 32-element rows: the accumulator is released after the tile's last
+    // tensor-memory load, before that chunk's arithmetic (64-element rows
+    // re-read a flagged chunk from tensor memory; keeping the last chunk's
+    // products in registers for that instead measured slower)
+    constexpr bool kEarlyRelease = kColRedo;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_full[C::STAGES], bar_empty[C::STAGES];
     __shared__ uint64_t bar_afull, bar_aempty, bar_accf[C::SLOTS][C::NACC], bar_acce[C::SLOTS][C::NACC];
@@ -734,6 +739,14 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                     if (ch + 1 < TN / 32) {
                         __syncwarp();
                         tmem_ld16_issue(tcol + (ch + 1) * 32, ra);
+                    } else if (kEarlyRelease) {
+                        // the tile's last read of tensor memory (the close-pair
+                        // recompute of 32-element rows reads coordinates only): the
+                        // accumulator goes back to the MMA issuer now, so the next
+                        // tile's MMAs overlap this chunk's arithmetic
+                        fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&bar_acce[g][acc]);
                     }
                     if (!skip) {
                         if (SYM) cs1 = half_chunk_sym<METRIC>(rb, wn4 + 8, xn, tau, rw, lane, part, flag, col1);
@@ -980,7 +993,7 @@ k_sweep_tc(const __grid_constant__ CUtensorMap m_ahi, const __grid_constant__ CU
                 fence_before_sync();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(&bar_acce[g][acc]);
+                    if (!kEarlyRelease) mbar_arrive(&bar_acce[g][acc]);
                     mbar_arrive(&bar_wne[ws]);
                 }
                 acc = (acc + 1 == (uint32_t)C::NACC) ? 0u : acc + 1;
