@@ -4,8 +4,10 @@ oracle evaluates it at any magnitude.  The GPU must agree with the oracle on
 the same data scaled by 1e-20 ... 1e18 (Phase 1 sample, Phase 2 estimate,
 exact silhouette, batched and no-alloc calls, cohesion/separation), and on
 data whose coordinates span more than FP32's pairwise range (tiny nonzero
-coordinates, denormals, zeros beside magnitudes near 1e25).  Tolerances are
-those of the other parity tests (1e-5 on s, 1e-5 relative on a, b).
+coordinates, denormals, zeros beside magnitudes near 1e25), and on data of
+either sign, all negative, with exact zeros, with magnitudes 2^35 apart, and at
+row lengths with and without padding.  Tolerances are those of the other
+parity tests (1e-5 on s, 1e-5 relative on a, b).
 """
 import numpy as np
 import pytest
@@ -48,8 +50,50 @@ def _wide_range():
     return X.astype(np.float32), lab, k
 
 
+def _mixed_sign():
+    """Coordinates of both signs (no |x| + 1 shift)."""
+    X, lab, _ = synth.gaussian_mixture(5003, 13, 6, seed=3,
+                                       sizes=[2500, 1200, 700, 550, 30, 23])
+    return X.astype(np.float32), lab, 6
+
+
+def _negative():
+    """Every coordinate negative."""
+    X, lab, k = _ragged(seed=21)
+    return (-X).astype(np.float32), lab, k
+
+
+def _with_zeros():
+    """Positive data with exact zeros in one coordinate (0/0 terms are 0)."""
+    X, lab, k = _ragged(seed=22)
+    X = X.copy()
+    X[np.random.default_rng(6).choice(X.shape[0], 400, replace=False), 2] = 0.0
+    return X, lab, k
+
+
+def _spread():
+    """Positive data with a few coordinates ~1e-9 against a largest ~20
+    (2^-35 of the scale: not tiny, far below the bulk)."""
+    X, lab, k = _ragged(seed=23)
+    X = X.copy()
+    X[np.random.default_rng(7).choice(X.shape[0], 100, replace=False), 4] = 1e-9
+    return X, lab, k
+
+
+def _positive(d):
+    """Positive data at d = 32 (no padding) and d = 5 (three padding slots of
+    eight)."""
+    def make():
+        X, lab, _ = synth.gaussian_mixture(5003, d, 5, seed=d, sizes=[2000, 1500, 800, 680, 23],
+                                           sigma=2.0)
+        return synth.abs_shift(X), lab, 5
+    return make
+
+
 def _cases():
-    return [("scale%g" % s, lambda s=s: _scaled(s)) for s in SCALES] + [("wide", _wide_range)]
+    return ([("scale%g" % s, lambda s=s: _scaled(s)) for s in SCALES] + [("wide", _wide_range)]
+            + [("mixed_sign", _mixed_sign), ("negative", _negative), ("zeros", _with_zeros),
+               ("spread", _spread), ("positive_d32", _positive(32)), ("positive_d5", _positive(5))])
 
 
 @pytest.mark.parametrize("name,make", _cases(), ids=[c[0] for c in _cases()])
