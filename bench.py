@@ -733,8 +733,9 @@ def run_serving(args, emit=True):
     against one request at a time with the plain synchronising calls, both in
     FP32 on CUDA cores.  Reports the capacity of each (back to back on the
     load-test requests), p50/p99 latency of each at ~80% of the plain path's
-    capacity under the same Poisson arrivals, and the specified 2000 req/s
-    stream (with queue growth)."""
+    capacity under the same Poisson arrivals (also with the small requests'
+    chains on high-priority streams), and the specified 2000 req/s stream
+    (with queue growth)."""
     import torch
     from paper_2607_01993_b300 import serve, silh
     torch.cuda.set_device(0)
@@ -760,13 +761,14 @@ def run_serving(args, emit=True):
         d = {"requests": count, "offered_req_s": rate, "slots": slots,
              "achieved_req_s": round(count / (t1 - t0), 2),
              "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+             "p90_ms": round(float(np.percentile(lat_ms, 90)), 3),
              "p99_ms": round(float(np.percentile(lat_ms, 99)), 3)}
         d.update(extra)
         return d
 
-    def served(reqs, rate, slots, cosine="per_pair"):
-        due = arrivals(len(reqs), rate)
-        srv = serve.SilhServer(datasets, slots=slots, cosine=cosine)
+    def served(reqs, rate, slots, cosine="per_pair", priority=None, due=None):
+        due = arrivals(len(reqs), rate) if due is None else due
+        srv = serve.SilhServer(datasets, slots=slots, cosine=cosine, priority=priority)
         t0 = time.perf_counter()
         futs, max_q = [], 0
         for r, a in zip(reqs, due):
@@ -783,10 +785,10 @@ def run_serving(args, emit=True):
                        {"max_queue": max_q, "peak_running": srv.peak_running,
                         "redone_capacity": srv.redone}), res
 
-    def one_at_a_time(reqs, rate, prec):
+    def one_at_a_time(reqs, rate, prec, due=None):
         """Requests in arrival order, each with the plain synchronising calls
         once the previous one has finished (a queue of one server)."""
-        due = arrivals(len(reqs), rate)
+        due = arrivals(len(reqs), rate) if due is None else due
         t0 = time.perf_counter()
         lat, res = [], []
         for r, a in zip(reqs, due):
@@ -813,21 +815,25 @@ def run_serving(args, emit=True):
     sat_cc, _ = served(load, 0, 8, cosine="collapsed")
     capacity = plain_cap["achieved_req_s"]
     rate = 0.8 * capacity
-    at80_served, res_b = served(load, rate, 8)
-    at80_plain, _ = one_at_a_time(load, rate, "fp32")
+    due80 = arrivals(len(load), rate)                           # the same arrivals for all three
+    at80_served, res_b = served(load, rate, 8, due=due80)
+    at80_plain, _ = one_at_a_time(load, rate, "fp32", due=due80)
+    at80_small, res_p = served(load, rate, 8, priority="small", due=due80)
     spec_reqs = make_requests(args.serve_spec, 30_000)
     specified, _ = served(spec_reqs, 2000.0, 8)
     # the server's results equal the same requests run alone, bit for bit
     same = all(a.s_global == b.s_global and a.sample_size == b.sample_size
                for a, b in zip(res_b, res_alone)) and \
-        all(a.s_global == b.s_global for a, b in zip(res_sat, res_alone))
+        all(a.s_global == b.s_global for a, b in zip(res_sat, res_alone)) and \
+        all(a.s_global == b.s_global for a, b in zip(res_p, res_alone))
     out = {"capacity_req_s": {"server_8_slots": sat["achieved_req_s"],
                               "one_at_a_time_plain_fp32": plain_cap["achieved_req_s"]},
            "capacity_vs_plain_fp32": round(sat["achieved_req_s"] / capacity, 3),
            "capacity_server_collapsed_cosine_req_s": sat_cc["achieved_req_s"],
            "capacity_collapsed_cosine_vs_plain_fp32": round(sat_cc["achieved_req_s"] / capacity, 3),
            "at_80pct_of_plain_capacity": {"offered_req_s": round(rate, 2),
-                                          "server": at80_served, "plain_fp32": at80_plain},
+                                          "server": at80_served, "plain_fp32": at80_plain,
+                                          "server_small_requests_first": at80_small},
            "specified_stream_2000_req_s": specified,
            "results_identical_served_vs_alone": same,
            "precision": "FP32 on CUDA cores for every request, server and baselines (on these "

@@ -97,18 +97,37 @@ class _Flight:
         self.event = None
         self.s = self.smp = self.d_size = self.d_status = self.g = None
         self.host = None
+        self.stream = None
+
+
+def request_work(n: int, d: int, k: int, t: float) -> float:
+    """Phase-2 work of a request in coordinate terms: n rows against its
+    expected sample of min(n, k t) columns, d coordinates each."""
+    return float(n) * min(float(n), k * t) * d
 
 
 class SilhServer:
     """cosine="collapsed" runs cosine requests' Phase 2 in the O(n k d) form of
     silh_estimate_cosine_collapsed (the same estimate up to rounding; |ds| within
-    the FP32 bound of the oracle) instead of the per-pair sweep."""
+    the FP32 bound of the oracle) instead of the per-pair sweep.
+
+    priority="large" launches requests whose request_work is at least big_work
+    on high-priority streams (the GPU's block scheduler then starts their
+    thread blocks before those of other requests, so the longest requests,
+    which set the latency tail, are slowed least by the others);
+    priority="small" does the opposite; None (the default) gives every stream
+    the same priority.  Results do not depend on the choice."""
 
     def __init__(self, datasets, slots: int = 4, hbm_budget_bytes: int | None = None,
-                 cosine: str = "per_pair"):
+                 cosine: str = "per_pair", priority: str | None = None,
+                 big_work: float = 2e11):
         if cosine not in ("per_pair", "collapsed"):
             raise ValueError("cosine must be 'per_pair' or 'collapsed'")
+        if priority not in (None, "large", "small"):
+            raise ValueError("priority must be None, 'large' or 'small'")
         self.cosine = cosine
+        self.priority = priority
+        self.big_work = float(big_work)
         self.datasets = datasets                                   # list of 2-D CUDA tensors
         self.device = datasets[0].device
         self.slots = max(1, int(slots))
@@ -125,6 +144,8 @@ class SilhServer:
         self._stop = False
         self.completed = []                                        # (request, result)
         self._streams = [torch.cuda.Stream(self.device) for _ in range(self.slots)]
+        self._streams_hi = ([torch.cuda.Stream(self.device, priority=-1)
+                             for _ in range(self.slots)] if priority else None)
         # pinned (global mean, |S|, status) per slot, written by the chain's last copies
         self._host = [torch.zeros(3, dtype=torch.float64).pin_memory() for _ in range(self.slots)]
         self._free_slots = list(range(self.slots))
@@ -178,12 +199,21 @@ class SilhServer:
                 return _Flight(req, fut, need, self._free_slots.pop())
         return None
 
+    def _stream_for(self, fl: _Flight):
+        """The slot's stream, or its high-priority twin (see priority)."""
+        if self.priority is None:
+            return self._streams[fl.slot]
+        n, d = self.datasets[fl.req.dataset].shape
+        big = request_work(n, d, fl.req.k, fl.req.t) >= self.big_work
+        hi = big if self.priority == "large" else not big
+        return self._streams_hi[fl.slot] if hi else self._streams[fl.slot]
+
     def _launch(self, fl: _Flight):
         """Enqueue the request's whole chain on its slot stream (no host waits)."""
         req = fl.req
         X = self.datasets[req.dataset]
         n, d = X.shape
-        stream = self._streams[fl.slot]
+        stream = fl.stream = self._stream_for(fl)
         prec = resolve_prec(req.prec, req.metric, d)
         with torch.cuda.stream(stream):
             cap = sample_capacity(n, req.k, req.t)
@@ -212,7 +242,7 @@ class SilhServer:
         """The synchronising path, for a request whose capacity overflowed."""
         req = fl.req
         X = self.datasets[req.dataset]
-        stream = self._streams[fl.slot]
+        stream = fl.stream
         prec = resolve_prec(req.prec, req.metric, X.shape[1])
         with torch.cuda.stream(stream):
             smp = silh.silh_sample_pps(X, req.labels, req.k, req.metric, t=req.t, seed=req.seed,

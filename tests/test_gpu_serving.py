@@ -3,8 +3,9 @@
 Requests over three device-resident datasets (FP32 and BF16, d in {8, 16, 64}),
 mixed metrics and k, run (a) one at a time and (b) concurrently on four slots
 with overlapping kernels; every global estimate and every per-point s_hat must
-be bit-identical.  Admission by HBM footprint must cap concurrency, and one
-request is checked against the oracle.
+be bit-identical, also with high-priority streams for the small or the large
+requests.  Admission by HBM footprint must cap concurrency, and one request is
+checked against the oracle.
 """
 import numpy as np
 import pytest
@@ -54,6 +55,21 @@ def test_same_result_alone_and_in_the_mix(setup):
         assert a.sample_size == b.sample_size
         assert torch.equal(a.s_hat, b.s_hat)
     silh.silh_stream_status()
+
+
+@pytest.mark.parametrize("priority", ["small", "large"])
+def test_stream_priorities_leave_results_unchanged(setup, priority):
+    # a mid-range threshold puts some requests on each kind of stream
+    host, dev, reqs = setup
+    alone = serve.run_one_at_a_time(dev, _requests(reqs))
+    works = sorted(serve.request_work(dev[r["dataset"]].shape[0], dev[r["dataset"]].shape[1],
+                                      r["k"], r["t"]) for r in reqs)
+    with serve.SilhServer(dev, slots=4, hbm_budget_bytes=1 << 40, priority=priority,
+                          big_work=works[len(works) // 2]) as srv:
+        mixed = [f.result(timeout=300) for f in [srv.submit(r) for r in _requests(reqs)]]
+    for a, b in zip(alone, mixed):
+        assert a.s_global == b.s_global and a.sample_size == b.sample_size
+        assert torch.equal(a.s_hat, b.s_hat)
 
 
 def test_admission_by_footprint_caps_concurrency(setup):
