@@ -539,7 +539,11 @@ def run_batching(args, emit=True):
 
     separate()
     ms_separate = timed(separate, max(1, args.steps // 2))
-    same = all(torch.equal(a, b) for a, b in zip(outs, sep_outs)) if variant == -1 else None
+    # the default tile shape (2 rows per thread, 128 columns per stage for rows of
+    # up to 32 elements, else 1 x 64 for Euclidean) is the single sweep's: equal bit for bit
+    default_variant = 3 if X.shape[1] <= 32 else 1
+    same = (all(torch.equal(a, b) for a, b in zip(outs, sep_outs))
+            if variant in (-1, default_variant) else None)
     maxdiff = max((a - b).abs().max().item() for a, b in zip(outs, sep_outs))
     del g
 
