@@ -138,3 +138,41 @@ def test_batching_workload_sampled_parity():
                                     rows=rows)
         _assert_close(out[rows_t], s_o)
         _assert_close(out_tc[rows_t], s_o)
+
+
+def test_serving_workload_largest_requests_sampled_parity():
+    """The serving workload's 64 resident datasets; requests on its largest
+    ones (n 0.74M-1.6M, d 64 and 128, FP32 and BF16 storage), one per metric,
+    with k up to 100 nearest-centre clusters and t = 64, served concurrently by
+    the continuous-batching server (FP32, the asynchronous chain).  Each
+    request's sample set must equal the oracle's (up to the tie band), and its
+    per-point s_hat must match the oracle's estimate on 100 seeded rows."""
+    from paper_2607_01993_b300 import serve
+    datasets, spec = synth.serving(seed=4)
+    cases = [(9, "canberra", 64), (0, "euclidean", 100), (47, "cosine", 37), (49, "manhattan", 80)]
+    reqs = []
+    for i, (ds, metric, k) in enumerate(cases):
+        lab = synth.nearest_centre_labels_device(datasets[ds].float(), k, seed=500 + i)
+        reqs.append(serve.Request(dataset=ds, labels=lab, k=k, metric=metric, t=64.0,
+                                  seed=900 + i, clustering_id=i, want_s=True))
+    torch.cuda.synchronize()
+    with serve.SilhServer(datasets, slots=4) as srv:
+        res = [f.result(timeout=600) for f in [srv.submit(r) for r in reqs]]
+    for i, ((ds, metric, k), req, r) in enumerate(zip(cases, reqs, res)):
+        X = datasets[ds]
+        n = X.shape[0]
+        Xh = X.float().cpu().numpy().astype(np.float64)     # BF16 values exactly
+        lab = req.labels.cpu().numpy()
+        os_ = oracle.sample_pps(Xh, lab, k, metric, t=64.0, seed=900 + i, cid=i)
+        gs = silh.silh_sample_pps(X, req.labels, k, metric, t=64.0, seed=900 + i,
+                                  clustering_id=i)
+        assert assert_same_sample(gs, os_, k, 900 + i, i, metric, lab) <= 2
+        assert r.sample_size == gs.size
+        rows = synth.seeded_rows(n, 100, seed=31 + i)
+        s_o, _, _ = oracle.estimate(Xh, lab, k, metric, gs.offsets.cpu().numpy(),
+                                    gs.idx[: gs.size].cpu().numpy().astype(np.int64),
+                                    gs.p[: gs.size].cpu().numpy(), rows=rows)
+        _assert_close(r.s_hat[torch.from_numpy(rows).cuda()], s_o)
+        s_h = r.s_hat.cpu().numpy().astype(np.float64)
+        assert abs(r.s_global - s_h.mean()) <= 1e-9
+        assert spec[ds][0] == n
