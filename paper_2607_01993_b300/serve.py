@@ -112,11 +112,11 @@ class SilhServer:
     the FP32 bound of the oracle) instead of the per-pair sweep.
 
     priority="large" launches requests whose request_work is at least big_work
-    on high-priority streams (the GPU's block scheduler then starts their
-    thread blocks before those of other requests, so the longest requests,
-    which set the latency tail, are slowed least by the others);
-    priority="small" does the opposite; None (the default) gives every stream
-    the same priority.  Results do not depend on the choice."""
+    on high-priority streams (the GPU's block scheduler starts the pending
+    thread blocks of higher-priority streams first); priority="small" puts the
+    other requests there instead, which shortens the small requests' latency
+    and lengthens the largest ones'; None (the default) gives every stream the
+    same priority.  Results do not depend on the choice."""
 
     def __init__(self, datasets, slots: int = 4, hbm_budget_bytes: int | None = None,
                  cosine: str = "per_pair", priority: str | None = None,
